@@ -1,0 +1,371 @@
+"""Seeded synthetic inputs for the radiation integral: trajectories and grids.
+
+This module creates inputs only. It holds none of the radiation arithmetic
+(no phase, no integrand, no spectrum), so the FP64 oracle and the CUDA path can
+both consume its output without sharing any of the method's code.
+
+Trajectory record layout (one per time sample, float64, 10 fields, 80 bytes):
+    t, x, y, dz, vx, vy, dvz, ax, ay, az
+in the small-angle variables of Sec. II (c = 1, lengths and times in metres):
+dz = z - beta0 t, dvz = v_z - beta0 with beta0 := 1 - 1/(2 gamma^2), and
+(ax, ay, az) = d(beta)/dt. Particles are concatenated; particle p owns records
+offsets[p] .. offsets[p+1]-1.
+
+Physical constants (CODATA 2018) used to express workloads in eV and metres.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import math
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+HBARC_EV_M = 1.973269804e-7        # hbar*c in eV*m
+ME_EV = 0.51099895000e6            # electron rest energy, eV
+NREC = 10
+FIELDS = ("t", "x", "y", "dz", "vx", "vy", "dvz", "ax", "ay", "az")
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "_trajgen.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the C generator in place (gcc, OpenMP, no FMA contraction)."""
+    src = os.path.join(_HERE, "trajgen.c")
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
+        tmp = _SO + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp",
+                               "-ffp-contract=off", "-fno-fast-math", src, "-o", tmp, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            d, i64, u64, i32 = ctypes.c_double, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int
+            P = ctypes.c_void_p
+            lib.tg_channeling.argtypes = [d, d, i32, d, d, d, d, d, d, i32, d, u64, i64, P, P, P, P]
+            lib.tg_channeling.restype = i32
+            lib.tg_channeling_given.argtypes = [P, d, i32, d, d, d, d, d, i32, d, u64, i64, P, P, P, P]
+            lib.tg_channeling_given.restype = i32
+            lib.tg_lognormal_lengths.argtypes = [u64, i64, d, d, i64, i64, P]
+            lib.tg_lognormal_lengths.restype = i32
+            lib.tg_philox4x32_10.argtypes = [P, P, P]
+            lib.tg_philox4x32_10.restype = None
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    """Raw Philox4x32-10 block (exposed so tests can check the published vectors)."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    _load().tg_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+# --------------------------------------------------------------------------- #
+# Containers
+# --------------------------------------------------------------------------- #
+@dataclasses.dataclass
+class Trajectories:
+    """Concatenated trajectories plus per-particle scalars (all float64/int64)."""
+    samples: np.ndarray       # [n_total, 10]
+    offsets: np.ndarray       # [n_particles + 1] int64
+    gamma: np.ndarray         # [n_particles]
+    energy_eV: np.ndarray     # [n_particles]
+    weight: np.ndarray        # [n_particles]
+
+    @property
+    def n_particles(self) -> int:
+        return int(self.offsets.shape[0] - 1)
+
+    @property
+    def n_total(self) -> int:
+        return int(self.samples.shape[0])
+
+    def lengths(self) -> np.ndarray:
+        return np.diff(self.offsets)
+
+    def subset(self, idx) -> "Trajectories":
+        idx = np.asarray(idx, dtype=np.int64)
+        parts = [self.samples[self.offsets[p]:self.offsets[p + 1]] for p in idx]
+        lens = np.array([len(x) for x in parts], dtype=np.int64)
+        off = np.zeros(len(idx) + 1, dtype=np.int64)
+        off[1:] = np.cumsum(lens)
+        smp = np.ascontiguousarray(np.concatenate(parts, axis=0)) if parts else np.zeros((0, NREC))
+        return Trajectories(smp, off, self.gamma[idx].copy(), self.energy_eV[idx].copy(),
+                            self.weight[idx].copy())
+
+
+@dataclasses.dataclass
+class Grid:
+    """Photon-energy grid and direction grid (cell-centred, dOmega = dtheta_x dtheta_y)."""
+    hbar_omega_eV: np.ndarray  # [n_omega]
+    theta_x: np.ndarray        # [n_angles]
+    theta_y: np.ndarray        # [n_angles]
+    d_omega: np.ndarray        # [n_angles]
+    nx: int = 0
+    ny: int = 0
+
+    @property
+    def n_omega(self) -> int:
+        return int(self.hbar_omega_eV.shape[0])
+
+    @property
+    def n_angles(self) -> int:
+        return int(self.theta_x.shape[0])
+
+
+def single(samples: np.ndarray, gamma: float, mass_eV: float = ME_EV, weight: float = 1.0) -> Trajectories:
+    samples = np.ascontiguousarray(samples, dtype=np.float64)
+    return Trajectories(samples, np.array([0, samples.shape[0]], dtype=np.int64),
+                        np.array([gamma]), np.array([gamma * mass_eV]), np.array([weight]))
+
+
+def concat(trajs) -> Trajectories:
+    trajs = list(trajs)
+    lens = np.concatenate([t.lengths() for t in trajs]) if trajs else np.zeros(0, np.int64)
+    off = np.zeros(len(lens) + 1, dtype=np.int64)
+    off[1:] = np.cumsum(lens)
+    return Trajectories(np.ascontiguousarray(np.concatenate([t.samples for t in trajs], axis=0)),
+                        off, np.concatenate([t.gamma for t in trajs]),
+                        np.concatenate([t.energy_eV for t in trajs]),
+                        np.concatenate([t.weight for t in trajs]))
+
+
+# --------------------------------------------------------------------------- #
+# Grids
+# --------------------------------------------------------------------------- #
+def angle_grid(nx: int, ny: int, half_x: float, half_y: float | None = None,
+               center_x: float = 0.0, center_y: float = 0.0) -> tuple:
+    """Cell-centred rectangular grid; index j = iy*nx + ix (x fastest)."""
+    half_y = half_x if half_y is None else half_y
+    dx, dy = 2.0 * half_x / nx, 2.0 * half_y / ny
+    tx = center_x - half_x + (np.arange(nx) + 0.5) * dx
+    ty = center_y - half_y + (np.arange(ny) + 0.5) * dy
+    TX, TY = np.meshgrid(tx, ty, indexing="xy")
+    return (np.ascontiguousarray(TX.ravel()), np.ascontiguousarray(TY.ravel()),
+            np.full(nx * ny, dx * dy))
+
+
+def omega_linear(n: int, hw_max: float) -> np.ndarray:
+    """hbar*omega_i = (i+1)/n * hw_max, i = 0..n-1 (excludes 0)."""
+    return (np.arange(1, n + 1, dtype=np.float64) / n) * hw_max
+
+
+def omega_log(n: int, lo: float, hi: float) -> np.ndarray:
+    return lo * (hi / lo) ** (np.arange(n, dtype=np.float64) / max(n - 1, 1))
+
+
+def make_grid(hw: np.ndarray, nx: int, ny: int, half_x: float, half_y: float | None = None,
+              **kw) -> Grid:
+    tx, ty, dom = angle_grid(nx, ny, half_x, half_y, **kw)
+    return Grid(np.ascontiguousarray(hw, dtype=np.float64), tx, ty, dom, nx, ny)
+
+
+def radial_bins(theta_x: np.ndarray, theta_y: np.ndarray, n_bins: int, theta_max: float) -> np.ndarray:
+    """bin_of_angle[j] in [0, n_bins) by polar angle, or -1 beyond theta_max."""
+    th = np.hypot(theta_x, theta_y)
+    b = np.floor(th / theta_max * n_bins).astype(np.int64)
+    b[(b >= n_bins) | (th >= theta_max)] = -1
+    return b.astype(np.int32)
+
+
+# --------------------------------------------------------------------------- #
+# Analytic trajectories
+# --------------------------------------------------------------------------- #
+def weak_undulator(gamma=1000.0, a=0.5e-10, lam=10e-6, n_periods=5, n_samples=4096,
+                   mass_eV=ME_EV) -> Trajectories:
+    """Planar harmonic motion x = a sin(k t), uniform samples over n_periods.
+
+    Longitudinal variables to leading order: dvz = -vx^2/2, az = -vx*ax,
+    dz = -(a k)^2/4 (t + sin(2kt)/(2k)).
+    """
+    k = 2.0 * math.pi / lam
+    t = np.linspace(0.0, n_periods * lam, n_samples)
+    s = np.zeros((n_samples, NREC))
+    s[:, 0] = t
+    s[:, 1] = a * np.sin(k * t)
+    s[:, 4] = a * k * np.cos(k * t)
+    s[:, 7] = -a * k * k * np.sin(k * t)
+    s[:, 6] = -0.5 * s[:, 4] ** 2
+    s[:, 9] = -s[:, 4] * s[:, 7]
+    s[:, 3] = -0.25 * (a * k) ** 2 * (t + np.sin(2.0 * k * t) / (2.0 * k))
+    return single(s, gamma, mass_eV)
+
+
+def undulator_first_harmonic_eV(gamma, a, lam, theta=0.0):
+    k = 2.0 * math.pi / lam
+    K = gamma * a * k
+    return 2.0 * gamma ** 2 * HBARC_EV_M * k / (1.0 + 0.5 * K * K + (gamma * theta) ** 2)
+
+
+def circular_arc(gamma, rho, half_angle, n_samples, mass_eV=ME_EV) -> Trajectories:
+    """Exact circular motion in the x-z plane, velocity angle alpha(t) = beta t / rho,
+    t in [-T, T] with beta T / rho = half_angle; the tangent at t = 0 is the z axis."""
+    beta = math.sqrt(1.0 - 1.0 / gamma ** 2)
+    beta0 = 1.0 - 1.0 / (2.0 * gamma ** 2)
+    # beta - beta0 = (beta^2 - beta0^2)/(beta + beta0) = -1/(4 gamma^4)/(beta + beta0)
+    bmb0 = -1.0 / (4.0 * gamma ** 4) / (beta + beta0)
+    T = half_angle * rho / beta
+    t = np.linspace(-T, T, n_samples)
+    al = beta * t / rho
+    s = np.zeros((n_samples, NREC))
+    s[:, 0] = t
+    s[:, 1] = 2.0 * rho * np.sin(0.5 * al) ** 2
+    s[:, 4] = beta * np.sin(al)
+    # dvz = beta cos(al) - beta0, written without cancellation
+    s[:, 6] = bmb0 - 2.0 * beta * np.sin(0.5 * al) ** 2
+    # dz = rho sin(al) - beta0 t = beta t (sin(al)/al - 1) + (beta - beta0) t
+    with np.errstate(invalid="ignore", divide="ignore"):
+        sinc_m1 = np.where(np.abs(al) > 1e-4, np.sin(al) / al - 1.0,
+                           -al ** 2 / 6.0 + al ** 4 / 120.0)
+    s[:, 3] = beta * t * sinc_m1 + bmb0 * t
+    s[:, 7] = beta ** 2 / rho * np.cos(al)
+    s[:, 9] = -beta ** 2 / rho * np.sin(al)
+    return single(s, gamma, mass_eV)
+
+
+def straight_line(gamma=1000.0, theta_x=1e-4, theta_y=-2e-4, length=1e-5, n_samples=1024,
+                  mass_eV=ME_EV) -> Trajectories:
+    """Uniform motion (zero acceleration) in a tilted direction."""
+    beta0 = 1.0 - 1.0 / (2.0 * gamma ** 2)
+    vp2 = theta_x ** 2 + theta_y ** 2
+    vz = math.sqrt(1.0 - 1.0 / gamma ** 2 - vp2)
+    dvz = -(vp2 + 1.0 / (4.0 * gamma ** 4)) / (vz + beta0)
+    t = np.linspace(0.0, length, n_samples)
+    s = np.zeros((n_samples, NREC))
+    s[:, 0] = t
+    s[:, 1] = theta_x * t
+    s[:, 2] = theta_y * t
+    s[:, 3] = dvz * t
+    s[:, 4] = theta_x
+    s[:, 5] = theta_y
+    s[:, 6] = dvz
+    return single(s, gamma, mass_eV)
+
+
+# --------------------------------------------------------------------------- #
+# Channeling ensembles (C generator)
+# --------------------------------------------------------------------------- #
+SI110_DP = 1.92e-10        # Si (110) interplanar distance, m
+SI_X0 = 0.0937             # Si radiation length, m
+EPS_S_EV = 10.6e6          # MS energy constant of Sec. III
+RHO_THERMAL = 0.075e-10    # thermal vibration amplitude used for n(r), m (not given in the paper)
+
+
+def channeling(n_particles: int, E_eV: float, charge: int, lengths, dt: float, seed: int,
+               U0_eV: float = 20.0, d_p: float = SI110_DP, sigma_theta_frac: float = 0.3,
+               ms: bool = True, mass_eV: float = ME_EV, return_entry: bool = False):
+    """Planar-channeling ensemble in a harmonic well (positrons charge=+1, electrons -1)."""
+    lens = np.broadcast_to(np.asarray(lengths, dtype=np.int64), (n_particles,)).copy()
+    off = np.zeros(n_particles + 1, dtype=np.int64)
+    off[1:] = np.cumsum(lens)
+    out = np.empty((int(off[-1]), NREC), dtype=np.float64)
+    theta_L = math.sqrt(2.0 * U0_eV / E_eV)
+    ex0 = np.empty(n_particles)
+    eth = np.empty(n_particles)
+    rc = _load().tg_channeling(E_eV, mass_eV, int(charge), U0_eV, d_p, sigma_theta_frac * theta_L,
+                               EPS_S_EV, SI_X0, RHO_THERMAL, int(bool(ms)), dt, int(seed),
+                               n_particles, _ptr(off), _ptr(out), _ptr(ex0), _ptr(eth))
+    if rc != 0:
+        raise RuntimeError("tg_channeling failed")
+    g = E_eV / mass_eV
+    tr = Trajectories(out, off, np.full(n_particles, g), np.full(n_particles, E_eV),
+                      np.full(n_particles, 1.0 / max(n_particles, 1)))
+    if return_entry:
+        return tr, ex0, eth
+    return tr
+
+
+def channeling_given(x0, thx0, gammas, n_samples: int, dt: float, charge: int = 1,
+                     U0_eV: float = 20.0, d_p: float = SI110_DP, ms: bool = False, seed: int = 0,
+                     mass_eV: float = ME_EV) -> Trajectories:
+    """Trajectories for given entry conditions (absolute x0, angle) and Lorentz factors."""
+    x0 = np.ascontiguousarray(x0, dtype=np.float64)
+    thx0 = np.ascontiguousarray(thx0, dtype=np.float64)
+    E = np.ascontiguousarray(np.asarray(gammas, dtype=np.float64) * mass_eV)
+    n = x0.shape[0]
+    off = np.arange(n + 1, dtype=np.int64) * int(n_samples)
+    out = np.empty((n * int(n_samples), NREC), dtype=np.float64)
+    rc = _load().tg_channeling_given(_ptr(E), mass_eV, int(charge), U0_eV, d_p, EPS_S_EV, SI_X0,
+                                     RHO_THERMAL, int(bool(ms)), dt, int(seed), n, _ptr(off),
+                                     _ptr(x0), _ptr(thx0), _ptr(out))
+    if rc != 0:
+        raise RuntimeError("tg_channeling_given failed")
+    return Trajectories(out, off, E / mass_eV, E, np.full(n, 1.0 / max(n, 1)))
+
+
+def lognormal_lengths(n: int, seed: int, median: float = 20000.0, sigma: float = math.log(10) / 3,
+                      lo: int = 2000, hi: int = 200000) -> np.ndarray:
+    out = np.empty(n, dtype=np.int64)
+    _load().tg_lognormal_lengths(int(seed), n, median, sigma, lo, hi, _ptr(out))
+    return out
+
+
+def planar_undulator(gamma: float, K: float, lam_u: float, n_periods: int, samples_per_period: int,
+                     mass_eV: float = ME_EV) -> Trajectories:
+    """Planar undulator of deflection parameter K (field B0 sin(2 pi z / lam_u) along y).
+
+    vx = (K/gamma) cos(k t), x = K/(gamma k) sin(k t), k = 2 pi / lam_u, t over whole periods;
+    longitudinal variables to leading order in vx: dvz = -vx^2/2, az = -vx ax,
+    dz = -(K/gamma)^2/4 (t + sin(2kt)/(2k)).
+    """
+    k = 2.0 * math.pi / lam_u
+    n = n_periods * samples_per_period + 1
+    t = np.linspace(0.0, n_periods * lam_u, n)
+    amp = K / gamma
+    s = np.zeros((n, NREC))
+    s[:, 0] = t
+    s[:, 1] = amp / k * np.sin(k * t)
+    s[:, 4] = amp * np.cos(k * t)
+    s[:, 7] = -amp * k * np.sin(k * t)
+    s[:, 6] = -0.5 * s[:, 4] ** 2
+    s[:, 9] = -s[:, 4] * s[:, 7]
+    s[:, 3] = -0.25 * amp ** 2 * (t + np.sin(2.0 * k * t) / (2.0 * k))
+    return single(s, gamma, mass_eV)
+
+
+def undulator_K(B0_T: float, lam_u: float) -> float:
+    """K = e B0 lam_u / (2 pi m c) = B0 * lam_u * c / (2 pi * m c^2 / e)."""
+    c = 299792458.0
+    return B0_T * lam_u * c / (2.0 * math.pi * ME_EV)
+
+
+def elliptical_undulator(gamma=2000.0, a=0.4e-10, b=0.25e-10, phase=0.7, lam=10e-6, n_periods=3,
+                         n_samples=3073, mass_eV=ME_EV) -> Trajectories:
+    """x = a sin(kt), y = b sin(kt + phase): motion in both transverse planes.
+
+    dvz = -(vx^2 + vy^2)/2, az = -(vx ax + vy ay), dz the exact integral of dvz from t = 0.
+    """
+    k = 2.0 * math.pi / lam
+    t = np.linspace(0.0, n_periods * lam, n_samples)
+    s = np.zeros((n_samples, NREC))
+    s[:, 0] = t
+    s[:, 1] = a * np.sin(k * t)
+    s[:, 2] = b * np.sin(k * t + phase)
+    s[:, 4] = a * k * np.cos(k * t)
+    s[:, 5] = b * k * np.cos(k * t + phase)
+    s[:, 7] = -a * k * k * np.sin(k * t)
+    s[:, 8] = -b * k * k * np.sin(k * t + phase)
+    s[:, 6] = -0.5 * (s[:, 4] ** 2 + s[:, 5] ** 2)
+    s[:, 9] = -(s[:, 4] * s[:, 7] + s[:, 5] * s[:, 8])
+    s[:, 3] = (-0.25 * (a * k) ** 2 * (t + np.sin(2.0 * k * t) / (2.0 * k))
+               - 0.25 * (b * k) ** 2 * (t + (np.sin(2.0 * (k * t + phase)) - np.sin(2.0 * phase))
+                                        / (2.0 * k)))
+    return single(s, gamma, mass_eV)

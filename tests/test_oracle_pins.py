@@ -1,0 +1,420 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test ties the oracle to something other than itself: closed forms (dipole
+undulator, Jackson's synchrotron spectrum, the on-axis Bessel series of a strong
+undulator), identities (Parseval in retarded time, integration by parts of the
+acceleration form, the Larmor energy), brute force of the unexpanded
+Lienard-Wiechert integrand in 50-digit arithmetic, quadrature order, symmetry
+and additivity. test_planted_mistakes_are_caught plants single mistakes in the
+oracle and checks that a pin fails for each one.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy.special import jv, kv
+
+import oracle as O
+from paper_1910_10391_gb300 import inputs as I
+
+PREF = O.ALPHA / (4.0 * math.pi ** 2)
+
+# configuration of the analytic single-trajectory workload (weak planar undulator)
+G1, A1, LAM1 = 1000.0, 0.5e-10, 10e-6
+K1 = 2.0 * math.pi / LAM1
+
+
+@pytest.fixture(scope="module")
+def weak():
+    tr = I.weak_undulator(G1, A1, LAM1, 5, 4096)
+    hw1 = I.undulator_first_harmonic_eV(G1, A1, LAM1)
+    grid = I.make_grid(I.omega_linear(128, 1.2 * hw1), 16, 16, 2.0 / G1)
+    return tr, grid, hw1
+
+
+@pytest.fixture(scope="module")
+def weak_cube(weak):
+    tr, grid, _ = weak
+    return O.spectrum_cube(tr, grid, O.CLASSICAL)
+
+
+def dipole_closed_form(grid, n_periods=5):
+    """|I|^2 of the weak undulator to leading order in K (constant g, linear phase)."""
+    K = G1 * A1 * K1
+    w = grid.hbar_omega_eV / I.HBARC_EV_M
+    T = n_periods * LAM1
+    nx, ny = grid.theta_x, grid.theta_y
+    th2 = nx ** 2 + ny ** 2
+    eps = (1 + 0.5 * K * K + G1 * G1 * th2) / (2 * G1 * G1)
+    gg = 1.0 / eps ** 2
+    ak2 = A1 * K1 * K1
+    bx = (ny ** 2 - nx ** 2) / 2 + 1 / (2 * G1 * G1) + (A1 * K1) ** 2 / 4
+    cx = bx * ak2 * gg
+    cy = -nx * ny * ak2 * gg
+    cz = -(1 / (2 * G1 * G1) - th2 / 2 + (A1 * K1) ** 2 / 4) * nx * ak2 * gg
+    om = w[:, None] * eps[None, :]
+    # int_0^T sin(kt) e^{i Om t} dt = k (e^{i Om T} - 1)/(Om^2 - k^2) for whole periods
+    #   = i k T e^{i d T/2} sinc(d T/2) / (Om + k),  d = Om - k  (no 0/0 at resonance)
+    d = om - K1
+    F = 1j * K1 * T * np.exp(0.5j * d * T) * np.sinc(d * T / (2 * np.pi)) / (om + K1)
+    return (cx ** 2 + cy ** 2 + cz ** 2)[None, :] * np.abs(F) ** 2
+
+
+# --------------------------------------------------------------------------- #
+def test_straight_line_is_exactly_zero():
+    tr = I.straight_line()
+    grid = I.make_grid(I.omega_log(7, 1e2, 1e5), 5, 4, 3e-3)
+    for mode in (O.CLASSICAL, O.SPIN0, O.SPIN_HALF):
+        cube = O.spectrum_cube(tr, grid, mode)
+        assert np.all(cube == 0.0)
+
+
+def test_weak_undulator_dipole_amplitudes(weak, weak_cube):
+    tr, grid, _ = weak
+    S = PREF * dipole_closed_form(grid)
+    err = np.abs(weak_cube - S) / S.max(axis=0, keepdims=True)
+    gth = G1 * np.hypot(grid.theta_x, grid.theta_y)
+    assert err[:, gth <= 0.5].max() < 0.01
+    assert err.max() < 0.05
+    # within half maximum of each line the error relative to the local value stays small too; the
+    # neglected O(K^2, (2 K gamma theta)^2) ~ 1e-3 terms shift the line by ~1e-3 and the flank
+    # has d ln S / d ln w ~ 10, hence 2 %
+    pk = S >= 0.5 * S.max(axis=0, keepdims=True)
+    assert (np.abs(weak_cube - S) / S)[pk & (gth <= 0.5)[None, :]].max() < 0.02
+
+
+def test_weak_undulator_harmonic_positions(weak):
+    """Line centres follow w1 = 2 gamma^2 k / (1 + K^2/2 + gamma^2 theta^2)."""
+    tr, _, hw1 = weak
+    K = G1 * A1 * K1
+    for gtx, gty in [(0.0, 0.0), (0.5, 0.0), (0.3, 0.9), (1.2, -0.4)]:
+        th = math.hypot(gtx, gty) / G1
+        hwt = I.undulator_first_harmonic_eV(G1, A1, LAM1, th)
+        hw = hwt * np.linspace(0.9, 1.1, 801)
+        grid = I.Grid(hw, np.array([gtx / G1]), np.array([gty / G1]), np.array([1.0]))
+        s = O.spectrum_cube(tr, grid, O.CLASSICAL)[:, 0]
+        sd = dipole_closed_form(grid)[:, 0]
+        i, j = int(np.argmax(s)), int(np.argmax(sd))
+        # second-order terms the dipole form drops ((2 K gamma theta)^2 ~ 6e-4 at gamma theta = 0.5)
+        # move the centre of a line of relative width 1/N = 0.2 by ~1e-3
+        assert abs(hw[i] / hw[j] - 1.0) < 2.5e-3
+        # the closed form's maximum sits at w1 (1 - 3/(2 pi^2 N^2)) for N periods (sinc^2 times
+        # the 1/(Om + k)^2 envelope); check it against the harmonic formula
+        assert abs(hw[j] / (hwt * (1 - 3 / (2 * math.pi ** 2 * 25))) - 1.0) < 1e-3
+    assert K == pytest.approx(0.0314, rel=1e-2)
+
+
+def test_parseval_in_retarded_time(weak):
+    """int_0^inf |I(w)|^2 dw = pi int |f|^2 / (1 - n.beta) dt (Fourier transform in t - n.r)."""
+    tr, _, hw1 = weak
+    s = tr.samples
+    vx, vy, dvz, ax, ay, az = (s[:, c] for c in range(4, 10))
+    for tx, ty in [(0.0, 0.0), (0.7 / G1, 0.3 / G1), (1.5 / G1, -1.0 / G1)]:
+        hw = I.omega_log(3000, 1e-3 * hw1, 60 * hw1)
+        grid = I.Grid(hw, np.array([tx]), np.array([ty]), np.array([1.0]))
+        spec = O.spectrum_cube(tr, grid, O.CLASSICAL)[:, 0] / PREF
+        lhs = np.trapezoid(spec, hw / I.HBARC_EV_M)
+        # f from the vector identity f = (n - beta)(n.beta_dot) - beta_dot (1 - n.beta), over D^2
+        D = 1 / (2 * G1 * G1) + (tx * tx + ty * ty) / 2 - dvz - tx * vx - ty * vy
+        m = az + tx * ax + ty * ay
+        fx = ((tx - vx) * m - ax * D) / D ** 2
+        fy = ((ty - vy) * m - ay * D) / D ** 2
+        fz = ((1 / (2 * G1 * G1) - (tx * tx + ty * ty) / 2 - dvz) * m - az * D) / D ** 2
+        rhs = math.pi * np.trapezoid((fx ** 2 + fy ** 2 + fz ** 2) / D, s[:, 0])
+        assert abs(lhs / rhs - 1.0) < 1e-4
+
+
+def test_larmor_energy():
+    """int dhw int dOmega d2I/dhw dOmega = (2/3) e^2 gamma^6 int [bdot^2 - (b x bdot)^2] dt."""
+    g = G1
+    tr = I.weak_undulator(g, A1, LAM1, 2, 513)
+    hw1 = I.undulator_first_harmonic_eV(g, A1, LAM1)
+    hw = I.omega_log(200, 5e-3 * hw1, 20 * hw1)
+    grid = I.make_grid(hw, 48, 48, 6.0 / g)
+    cube = O.spectrum_cube(tr, grid, O.CLASSICAL)
+    spec, _ = O.reduce(cube, grid.d_omega)
+    e_spec = np.trapezoid(spec, hw)
+    s = tr.samples
+    beta = np.stack([s[:, 4], s[:, 5], (1 - 1 / (2 * g * g)) + s[:, 6]], 1)
+    bd = s[:, 7:10]
+    cr = np.cross(beta, bd)
+    e_larmor = (2 / 3) * O.ALPHA * I.HBARC_EV_M * g ** 6 * np.trapezoid(
+        (bd ** 2).sum(1) - (cr ** 2).sum(1), s[:, 0])
+    assert abs(e_spec / e_larmor - 1.0) < 0.02
+
+
+def test_jackson_synchrotron():
+    """Jackson, Classical Electrodynamics 3rd ed. Eq. 14.79 for a circular arc of +-20/gamma."""
+    gam, rho = 2e4, 1.0
+    tr = I.circular_arc(gam, rho, 20.0 / gam, 100000)
+    wc = 1.5 * gam ** 3 / rho
+    xs = np.array([0.1, 0.3, 1.0, 3.0])
+    ths = np.array([0.0, 0.5, 1.0]) / gam
+    hw = xs * wc * I.HBARC_EV_M
+    grid = I.Grid(hw, np.zeros(3), ths, np.ones(3))
+    s = O.spectrum_cube(tr, grid, O.CLASSICAL) / PREF
+    w = hw / I.HBARC_EV_M
+    a2 = 1 / gam ** 2 + ths ** 2
+    xi = (w[:, None] * rho / 3) * a2[None, :] ** 1.5
+    sj = (4 / 3) * (w[:, None] * rho) ** 2 * a2[None, :] ** 2 * (
+        kv(2 / 3, xi) ** 2 + (ths ** 2 / a2)[None, :] * kv(1 / 3, xi) ** 2)
+    assert np.abs(s / sj - 1.0).max() < 0.01
+
+
+def _by_parts(s, g, ws, tx, ty):
+    """Velocity-form amplitudes: f = d/dt[(n - beta)/D], j = d/dt[1/D], A' = D, so
+    I = [(n-beta)/D e^{iwA}] - i w int (n-beta) e^{iwA} dt,  J = [e^{iwA}/D] - i w int e^{iwA} dt."""
+    c = 1 / (2 * g * g) + (tx * tx + ty * ty) / 2
+    A = c * s[:, 0] - s[:, 3] - tx * s[:, 1] - ty * s[:, 2]
+    D = c - s[:, 6] - tx * s[:, 4] - ty * s[:, 5]
+    e = np.exp(1j * ws * A)
+    nb = np.stack([tx - s[:, 4], ty - s[:, 5], 1 / (2 * g * g) - (tx * tx + ty * ty) / 2 - s[:, 6]], 1)
+    Iv = (nb[-1] * e[-1] / D[-1] - nb[0] * e[0] / D[0]) - 1j * ws * np.trapezoid(
+        nb * e[:, None], s[:, 0], axis=0)
+    Jv = (e[-1] / D[-1] - e[0] / D[0]) - 1j * ws * np.trapezoid(e, s[:, 0])
+    return Iv, Jv
+
+
+def _by_parts_errors():
+    tr = I.elliptical_undulator()
+    s, g = tr.samples, float(tr.gamma[0])
+    hw1 = I.undulator_first_harmonic_eV(g, 0.4e-10, 10e-6)
+    worst = 0.0
+    for tx, ty, fr in [(0.3 / g, 0.2 / g, 1.0), (1.2 / g, -0.5 / g, 0.37), (-0.8 / g, 1.1 / g, 2.2),
+                       (0.0, 0.0, 0.8)]:
+        ws = fr * hw1 / I.HBARC_EV_M
+        a = O.amplitudes(s, g, ws, tx, ty)
+        Io = np.array([a[0] + 1j * a[1], a[2] + 1j * a[3], a[4] + 1j * a[5]])
+        Jo = a[6] + 1j * a[7]
+        Iv, Jv = _by_parts(s, g, ws, tx, ty)
+        worst = max(worst, np.abs(Io - Iv).max() / a[8], abs(Jo - Jv) / a[9])
+    return worst
+
+
+def test_integration_by_parts_I_and_J():
+    assert _by_parts_errors() < 1e-3
+
+
+def _bruteforce_errors():
+    """Unexpanded Eqs. 1-2 (full 3-vectors, n_z = sqrt(1 - theta^2)) in 50-digit arithmetic."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    tr = I.elliptical_undulator(n_periods=1, n_samples=129)
+    s, g = tr.samples, float(tr.gamma[0])
+    hw1 = I.undulator_first_harmonic_eV(g, 0.4e-10, 10e-6)
+    b0 = mp.mpf(1) - mp.mpf(1) / (2 * mp.mpf(g) ** 2)
+    L = s.shape[0]
+    worst_comp, worst_sq = 0.0, 0.0
+    for tx, ty, fr in [(0.3 / g, 0.2 / g, 1.0), (1.2 / g, -0.5 / g, 0.37), (1.9 / g, 1.9 / g, 2.0)]:
+        ws = fr * hw1 / I.HBARC_EV_M
+        n = [mp.mpf(tx), mp.mpf(ty), mp.sqrt(1 - mp.mpf(tx) ** 2 - mp.mpf(ty) ** 2)]
+        acc = [mp.mpc(0)] * 3
+        tt = [mp.mpf(float(v)) for v in s[:, 0]]
+        for k in range(L):
+            t, x, y, dz, vx, vy, dvz, ax, ay, az = [mp.mpf(float(v)) for v in s[k]]
+            r = [x, y, b0 * t + dz]
+            be = [vx, vy, b0 + dvz]
+            bd = [ax, ay, az]
+            nmb = [n[i] - be[i] for i in range(3)]
+            c1 = [nmb[1] * bd[2] - nmb[2] * bd[1], nmb[2] * bd[0] - nmb[0] * bd[2],
+                  nmb[0] * bd[1] - nmb[1] * bd[0]]
+            c2 = [n[1] * c1[2] - n[2] * c1[1], n[2] * c1[0] - n[0] * c1[2], n[0] * c1[1] - n[1] * c1[0]]
+            den = (1 - sum(be[i] * n[i] for i in range(3))) ** 2
+            ph = mp.mpf(ws) * (t - sum(n[i] * r[i] for i in range(3)))
+            if k == 0:
+                w = (tt[1] - tt[0]) / 2
+            elif k == L - 1:
+                w = (tt[L - 1] - tt[L - 2]) / 2
+            else:
+                w = (tt[k + 1] - tt[k - 1]) / 2
+            e = mp.expj(ph)
+            for i in range(3):
+                acc[i] += w * c2[i] / den * e
+        a = O.amplitudes(s, g, ws, tx, ty)
+        Io = np.array([a[0] + 1j * a[1], a[2] + 1j * a[3], a[4] + 1j * a[5]])
+        Iex = np.array([complex(v) for v in acc])
+        worst_comp = max(worst_comp, np.abs(Iex - Io).max() / a[8])
+        worst_sq = max(worst_sq, abs((np.abs(Iex) ** 2).sum() / (np.abs(Io) ** 2).sum() - 1))
+    return worst_comp, worst_sq
+
+
+def test_expansion_against_unexpanded_bruteforce():
+    comp, sq = _bruteforce_errors()
+    assert comp < 1e-5
+    assert sq < 1e-4
+
+
+def test_trapezoid_is_second_order():
+    hw1 = I.undulator_first_harmonic_eV(G1, A1, LAM1)
+    grid = I.Grid(np.array([0.9 * hw1, 2.5 * hw1]), np.array([0.3 / G1, 1.0 / G1]),
+                  np.array([0.1 / G1, 0.4 / G1]), np.ones(2))
+    vals = [O.spectrum_cube(I.weak_undulator(G1, A1, LAM1, 2, L), grid, O.CLASSICAL).ravel()
+            for L in (257, 513, 1025)]
+    ratio = (vals[0] - vals[1]) / (vals[1] - vals[2])
+    assert np.all((ratio > 3.5) & (ratio < 4.5))
+
+
+def test_spin0_is_lindhard_substitution():
+    """dI_q/dhw(w) = (w/w*) dI_c/dhw(w*), per direction, w* = w/(1 - hw/E)."""
+    tr = I.elliptical_undulator(gamma=300.0)
+    E = float(tr.energy_eV[0])
+    hw = np.array([0.05, 0.2, 0.45, 0.8]) * E * 0.05
+    u = hw / E
+    grid_q = I.make_grid(hw, 3, 3, 2.0 / 300.0)
+    grid_c = I.make_grid(hw / (1.0 - u), 3, 3, 2.0 / 300.0)
+    sq = O.spectrum_cube(tr, grid_q, O.SPIN0)
+    sc = O.spectrum_cube(tr, grid_c, O.CLASSICAL)
+    # w* reached two ways (hw/hbar_c/(1-u) vs (hw/(1-u))/hbar_c) differs by an ulp; with phases
+    # ~4e4 rad that moves low-valued bins by ~1e-9 relative. A wrong coefficient or a missing
+    # substitution would be O(u) ~ 1e-2.
+    np.testing.assert_allclose(sq, (1.0 - u)[:, None] * sc, rtol=1e-8, atol=0)
+
+
+def test_spin_half_reduces_to_classical():
+    """BCK: coefficient of |I|^2 is 1 - u + u^2/2, J enters at O(u^2): slope -1 as u -> 0."""
+    base = I.elliptical_undulator(gamma=2000.0)
+    g = 2000.0
+    hw1 = I.undulator_first_harmonic_eV(g, 0.4e-10, 10e-6)
+    hw = np.array([0.7, 1.0, 1.6]) * hw1
+    grid = I.make_grid(hw, 3, 3, 1.5 / g)
+    for u_target in (1e-9, 1e-4, 1e-3):
+        E = hw1 / u_target
+        tr = I.Trajectories(base.samples, base.offsets, base.gamma, np.array([E]), base.weight)
+        u = hw / E
+        s_half = O.spectrum_cube(tr, grid, O.SPIN_HALF)
+        gs = I.Grid(hw / (1.0 - u), grid.theta_x, grid.theta_y, grid.d_omega)
+        s_cl = O.spectrum_cube(tr, gs, O.CLASSICAL)
+        slope = (s_half / s_cl - 1.0) / u[:, None]
+        assert np.all(np.abs(slope + 1.0) < 0.02)
+
+
+def test_spin_half_J_term():
+    """S_1/2 - (1 + (1-u)^2)/2 S_cl(w*) = u^2/(2 gamma^2) |J(w*)|^2 with J the by-parts-pinned amplitude."""
+    tr = I.elliptical_undulator(gamma=500.0)
+    g = 500.0
+    E = float(tr.energy_eV[0])
+    hw = np.array([0.1, 0.3]) * E
+    grid = I.Grid(hw, np.array([0.4 / g, -1.0 / g]), np.array([0.2 / g, 0.5 / g]), np.ones(2))
+    s_half = O.spectrum_cube(tr, grid, O.SPIN_HALF)
+    u = hw / E
+    ws = hw / I.HBARC_EV_M / (1 - u)
+    for i in range(2):
+        for j in range(2):
+            a = O.amplitudes(tr.samples, g, ws[i], grid.theta_x[j], grid.theta_y[j])
+            I2 = (a[:6] ** 2).sum()
+            J2 = a[6] ** 2 + a[7] ** 2
+            cI = 0.5 * (1 + (1 - u[i]) ** 2)
+            assert s_half[i, j] / PREF - cI * I2 == pytest.approx(u[i] ** 2 / (2 * g * g) * J2, rel=1e-6)
+            assert J2 > 0
+
+
+def test_planar_motion_symmetry(weak):
+    tr, _, hw1 = weak
+    hw = np.array([0.3, 0.9, 1.1]) * hw1
+    tx = np.array([0.2, -0.7, 1.3]) / G1
+    ty = np.array([0.5, 0.9, -1.1]) / G1
+    g1 = I.Grid(hw, tx, ty, np.ones(3))
+    g2 = I.Grid(hw, tx, -ty, np.ones(3))
+    for mode in (O.CLASSICAL, O.SPIN_HALF):
+        tr2 = I.Trajectories(tr.samples, tr.offsets, tr.gamma, np.array([3e6]), tr.weight)
+        np.testing.assert_allclose(O.spectrum_cube(tr2, g1, mode), O.spectrum_cube(tr2, g2, mode),
+                                   rtol=1e-12)
+
+
+def test_ensemble_additivity_and_permutation():
+    trs = [I.elliptical_undulator(gamma=g, a=a, n_samples=n) for g, a, n in
+           [(1500.0, 0.3e-10, 1025), (2000.0, 0.4e-10, 2049), (2500.0, 0.2e-10, 1537)]]
+    ens = I.concat(trs)
+    ens.weight = np.array([0.2, 0.5, 0.3])
+    grid = I.make_grid(I.omega_log(5, 1e4, 2e6), 3, 3, 1e-3)
+    for mode in (O.CLASSICAL, O.SPIN0, O.SPIN_HALF):
+        tot = O.spectrum_cube(ens, grid, mode)
+        parts = sum(w * O.spectrum_cube(t, grid, mode) for w, t in zip(ens.weight, trs))
+        np.testing.assert_allclose(tot, parts, rtol=1e-12)
+        perm = ens.subset([2, 0, 1])
+        np.testing.assert_allclose(O.spectrum_cube(perm, grid, mode), tot, rtol=1e-12)
+
+
+def _read_golden(name):
+    vals = {}
+    with open(__file__.replace("test_oracle_pins.py", f"golden/{name}")) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                k, v = line.split()[:2]
+                vals[k] = float(v)
+    return vals
+
+
+def test_strong_undulator_golden_peak():
+    """Paper's integral test (Sec. IV): 2 GeV e-, 53 mm, 20 periods, 1 T; peak at 380 eV.
+
+    The 380 eV line is the 7th on-axis harmonic; its height follows the textbook odd-harmonic
+    formula d2I/dhw dOmega = alpha N^2 gamma^2 F_n(K),
+    F_n = n^2 K^2/(1+K^2/2)^2 [J_{(n-1)/2}(xi) - J_{(n+1)/2}(xi)]^2, xi = n K^2/(4 (1+K^2/2)).
+    """
+    gd = _read_golden("strong_undulator.txt")
+    g = gd["energy_eV"] / I.ME_EV
+    K = I.undulator_K(gd["B0_T"], gd["lambda_u_m"])
+    N = int(gd["n_periods"])
+    tr = I.planar_undulator(g, K, gd["lambda_u_m"], N, 2048)
+    k = 2 * math.pi / gd["lambda_u_m"]
+    hw1 = 2 * g * g * I.HBARC_EV_M * k / (1 + K * K / 2)
+    n = 7
+    assert abs(n * hw1 / gd["peak_eV"] - 1) < 0.005
+    hw = n * hw1 * np.linspace(0.99, 1.01, 201)
+    grid = I.Grid(hw, np.zeros(1), np.zeros(1), np.ones(1))
+    s = O.spectrum_cube(tr, grid, O.CLASSICAL)[:, 0]
+    i = int(np.argmax(s))
+    assert abs(hw[i] / (n * hw1) - 1) < 1e-3
+    xi = n * K * K / (4 * (1 + K * K / 2))
+    Fn = n * n * K * K / (1 + K * K / 2) ** 2 * (jv((n - 1) // 2, xi) - jv((n + 1) // 2, xi)) ** 2
+    peak = O.ALPHA * N * N * g * g * Fn
+    s_center = O.spectrum_cube(tr, I.Grid(np.array([n * hw1]), np.zeros(1), np.zeros(1), np.ones(1)),
+                               O.CLASSICAL)[0, 0]
+    assert abs(s_center / peak - 1) < 0.02
+    # even harmonics vanish on axis for a planar undulator
+    s_even = O.spectrum_cube(tr, I.Grid(np.array([6 * hw1]), np.zeros(1), np.zeros(1), np.ones(1)),
+                             O.CLASSICAL)[0, 0]
+    assert s_even < 1e-3 * peak
+
+
+def test_reduce_partitions():
+    rng = np.random.default_rng(3)
+    cube = rng.random((5, 36))
+    tx, ty, dom = I.angle_grid(6, 6, 2e-3)
+    boa = I.radial_bins(tx, ty, 3, 2e-3)
+    spec, bins = O.reduce(cube, dom, boa, 3)
+    inside = boa >= 0
+    np.testing.assert_allclose(bins.sum(1), (cube[:, inside] * dom[inside]).sum(1), rtol=1e-14)
+    c2 = np.full((2, 36), 3.0)
+    spec2, _ = O.reduce(c2, dom)
+    np.testing.assert_allclose(spec2, 3.0 * (4e-3) ** 2, rtol=1e-14)
+
+
+def test_invalid_inputs_rejected():
+    tr = I.weak_undulator(n_samples=64)
+    grid = I.make_grid(np.array([1e3]), 2, 2, 1e-3)
+    bad = I.Trajectories(tr.samples[:1], np.array([0, 1]), tr.gamma, tr.energy_eV, tr.weight)
+    with pytest.raises(ValueError):
+        O.spectrum_cube(bad, grid, O.CLASSICAL)
+    g2 = I.make_grid(np.array([2.0 * tr.energy_eV[0]]), 2, 2, 1e-3)
+    O.spectrum_cube(tr, g2, O.CLASSICAL)     # classical accepts any hw > 0
+    with pytest.raises(ValueError):
+        O.spectrum_cube(tr, g2, O.SPIN_HALF)  # quantum modes need hw < E
+    with pytest.raises(ValueError):
+        O.spectrum_cube(tr, grid, 7)
+
+
+@pytest.mark.parametrize("plant", [1, 2, 3, 4])
+def test_planted_mistakes_are_caught(plant):
+    """Each planted mistake (dropped bracket in f_x, sign in J, dropped f_z, sign of ny*y) must
+    make at least one pin fail."""
+    O.set_plant(plant)
+    try:
+        caught = _by_parts_errors() > 1e-3
+        comp, sq = _bruteforce_errors()
+        caught = caught or comp > 1e-5 or sq > 1e-4
+    finally:
+        O.set_plant(0)
+    assert caught
