@@ -1,0 +1,418 @@
+#!/usr/bin/env python
+"""Benchmark of the radiation-integral hot path on GB300.
+
+Workload (the plain-FP64 ensemble configuration): 1024 positrons, E = 10 GeV, harmonic planar
+well (U0 = 20 eV, d_p = 1.92 A), seeded RK4 trajectories with scattering kicks, 20,000 samples
+each (100 um); 512 log-spaced photon energies in [1e-4 E, 0.5 E] x 64 x 64 directions; classical
+and Baier-Katkov spin-1/2 models. A step is one pass of the whole path (device checks, the
+integral kernel, the particle/angle combine and the angle integral) over a batch of particles
+in both models. `value` is the chosen form (mixed precision: FP64 phase base and particle sums,
+FP32 sincos and amplitudes) in integrand terms/s; the plain FP64 kernel is timed on the same
+inputs and reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "integrand terms/s (ω·n·t) & spectra/s: plain FP64 vs chosen form at stated err"
+N_PART, N_SAMP, N_OMEGA, N_SIDE = 1024, 20000, 512, 64
+WORKLOAD = ("positron ensemble: 1024 e+ at 10 GeV, harmonic planar well (U0 = 20 eV, d_p = 1.92 A), "
+            "RK4 + scattering kicks, 20000 samples over 100 um; 512 log hw in [1e-4 E, 0.5 E] x 64x64 "
+            "directions within +-(theta_L + 3/gamma); classical + spin-1/2")
+SM_COUNT, SM_MAX_MHZ = 152, 2070.0
+SFU_PER_SM_CLK = 16          # special-function unit ops per SM per clock (4 per SM sub-partition)
+FMA_PER_SM_CLK = 128         # FP32 FMA lanes per SM
+FP64_PER_SM_CLK = 2          # FP64 FMA per SM per clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=32, help="particles per step (mixed form)")
+    ap.add_argument("--fp64-batch", type=int, default=1, help="particles per plain-FP64 step")
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------- clocks
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        load = [x for x in sm if x > 0.5 * max(sm)]
+        return {"sm_mhz": statistics.median(load or sm), "sm_max_mhz": float(rows[0][2]),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit()),
+                "samples": len(rows), "reasons": reasons}
+
+
+# --------------------------------------------------------------------------- helpers
+def workload_inputs():
+    from paper_1910_10391_gb300 import inputs as I
+    return I.workload_positron_ensemble(N_PART, N_SAMP, seed=2, n_omega=N_OMEGA, n_side=N_SIDE)
+
+
+def terms_of(n_particles, grid):
+    return n_particles * N_SAMP * grid.n_omega * grid.n_angles
+
+
+def cpu_sample_bins(grid, n_dirs, seed=11):
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    dirs = rng.choice(grid.n_angles, size=n_dirs, replace=False)
+    bi = np.repeat(np.arange(grid.n_omega), n_dirs)
+    bj = np.tile(dirs, grid.n_omega)
+    return bi, bj
+
+
+def run_oracle_sample(tr, grid, n_dirs, modes):
+    """Oracle (FP64 CPU, all host cores) on particle 0 at every hw x n_dirs directions."""
+    import oracle as O
+    bi, bj = cpu_sample_bins(grid, n_dirs)
+    one = tr.subset([0])
+    one.weight[:] = 1.0
+    vals = {}
+    t0 = time.perf_counter()
+    for m in modes:
+        vals[m] = O.spectrum_bins(one, grid, {0: O.CLASSICAL, 2: O.SPIN_HALF}[m], bi, bj)
+    dt = time.perf_counter() - t0
+    terms = len(modes) * len(bi) * N_SAMP
+    return vals, bi, bj, terms, dt, O.max_threads()
+
+
+# --------------------------------------------------------------------------- reference arm
+def reference_arm(args, rank):
+    if rank != 0:
+        return
+    tr, grid = workload_inputs()
+    n_dirs = 64
+    for _ in range(args.warmup):
+        run_oracle_sample(tr, grid, n_dirs, (0, 2))
+    t_all = 0.0
+    terms_all = 0
+    cores = 1
+    for _ in range(args.steps):
+        _, _, _, terms, dt, cores = run_oracle_sample(tr, grid, n_dirs, (0, 2))
+        t_all += dt
+        terms_all += terms
+    v = terms_all / t_all
+    sample = (f"particle 0 of the workload (20000 samples) x all 512 hw x {n_dirs} seeded directions, "
+              "classical + spin-1/2, per step")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "terms/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": v, "unit": "terms/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "terms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+# --------------------------------------------------------------------------- our arm
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return reference_arm(args, rank)
+
+    import numpy as np
+    import torch
+    import paper_1910_10391_gb300 as rad
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    rad.load()
+
+    tr, grid = workload_inputs()
+    B = args.batch
+    n_batches = N_PART // B
+    # whole ensemble resident in HBM (1.64 GB); each step takes a contiguous batch of particles
+    d_samples = torch.from_numpy(tr.samples).to(dev)
+    d_gamma = torch.from_numpy(tr.gamma).to(dev)
+    d_energy = torch.from_numpy(tr.energy_eV).to(dev)
+    d_weight = torch.from_numpy(tr.weight).to(dev)
+    d_hw = torch.from_numpy(grid.hbar_omega_eV).to(dev)
+    d_tx = torch.from_numpy(grid.theta_x).to(dev)
+    d_ty = torch.from_numpy(grid.theta_y).to(dev)
+    d_dom = torch.from_numpy(grid.d_omega).to(dev)
+    no, na = grid.n_omega, grid.n_angles
+
+    def batch_args(b, nb):
+        p0 = b * nb
+        offs = torch.arange(nb + 1, dtype=torch.int64, device=dev) * N_SAMP
+        return (d_samples[p0 * N_SAMP:(p0 + nb) * N_SAMP].contiguous(), offs, d_gamma[p0:p0 + nb],
+                d_energy[p0:p0 + nb], d_weight[p0:p0 + nb], d_hw, d_tx, d_ty, d_dom)
+
+    modes = (rad.RAD_CLASSICAL, rad.RAD_SPIN_HALF)
+    cube = {m: torch.empty(no * na, dtype=torch.float64, device=dev) for m in modes}
+    spec = {m: torch.zeros(no, dtype=torch.float64, device=dev) for m in modes}
+
+    def make_plans(prec, nb):
+        return {m: rad.Plan(nb * N_SAMP, nb, no, na, m, prec, 3, 0) for m in modes}
+
+    plans = make_plans(rad.RAD_MIXED, B)
+    tuned = {}
+    if not args.no_autotune:
+        # tune the launch shape on a 2-particle slice of the same grids, then apply it
+        sub = batch_args(0, 2)
+        for m in modes:
+            tp = rad.Plan(2 * N_SAMP, 2, no, na, m, rad.RAD_MIXED, 3, 0)
+            tmp_c = torch.empty(no * na, dtype=torch.float64, device=dev)
+            tmp_s = torch.empty(no, dtype=torch.float64, device=dev)
+            tp.autotune(*sub, tmp_c, tmp_s, None, None, budget_ms=60000)
+            d = dict(kv.split("=") for kv in tp.describe().split())
+            tuned[m] = (int(d["R"]), int(d["NW"]), int(d["T"]))
+            tp.close()
+            plans[m].set_shape(*tuned[m], 1)
+    for m in modes:
+        plans[m].set_timing(True)
+
+    l2_flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(s, ps, nb, kernel_ms=None):
+        b = (s * world + rank) % (N_PART // nb)
+        a = batch_args(b, nb)
+        l2_flush.zero_()
+        for m in modes:
+            rc = ps[m].execute(*a, cube[m], spec[m], None, None, accumulate=0)
+            if rc:
+                raise rad.RadError(rc, "rad_plan_execute")
+            if kernel_ms is not None:
+                kernel_ms.append((m, ps[m].last_kernel_ms()))
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(ps, nb, K, W, collect=None):
+        for s in range(W):
+            step(s, ps, nb)
+        barrier()
+        t0 = time.perf_counter()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for s in range(K):
+            step(W + s, ps, nb, collect)
+        e1.record()
+        barrier()
+        wall = time.perf_counter() - t0
+        ms = e0.elapsed_time(e1)
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        if dist is not None:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item()), wall
+
+    # ---- chosen form (mixed precision) ----
+    clocks = Clocks(local)
+    kms = []
+    for s in range(args.warmup):
+        step(s, plans, B)
+    clocks.start()
+    ms_total, wall = timed(plans, B, args.steps, 0, kms)
+    clk = clocks.stop()
+    ms_step = ms_total / args.steps
+    terms_step = len(modes) * terms_of(B, grid)
+    value = world * terms_step / (ms_step * 1e-3)
+    spectra_s = world * len(modes) * B / (ms_step * 1e-3)
+    mixed_desc = {m: plans[m].describe() for m in modes}
+    launches_per_step = sum(plans[m].kernel_launches() for m in modes)
+    ens = spec[modes[0]].clone()
+    if dist is not None:
+        dist.all_reduce(ens)  # ensemble sum of the last step's spectra across ranks
+
+    # ---- plain FP64 on the same inputs ----
+    fp = make_plans(rad.RAD_FP64, args.fp64_batch)
+    for m in modes:
+        fp[m].set_timing(True)
+    fkms = []
+    fms, _ = timed(fp, args.fp64_batch, args.fp64_steps, 1, fkms)
+    fms_step = fms / args.fp64_steps
+    f_terms = len(modes) * terms_of(args.fp64_batch, grid)
+    fp64_value = world * f_terms / (fms_step * 1e-3)
+
+    # ---- end to end through the host-buffer entry point (pinned memory, copies timed) ----
+    nb_e = B
+    p0 = (rank * nb_e) % N_PART
+    h_samples = torch.from_numpy(tr.samples[p0 * N_SAMP:(p0 + nb_e) * N_SAMP]).pin_memory()
+    h_offs = torch.arange(nb_e + 1, dtype=torch.int64).pin_memory()
+    h_offs.mul_(N_SAMP)
+    h_g = torch.from_numpy(tr.gamma[p0:p0 + nb_e].copy()).pin_memory()
+    h_e = torch.from_numpy(tr.energy_eV[p0:p0 + nb_e].copy()).pin_memory()
+    h_w = torch.from_numpy(tr.weight[p0:p0 + nb_e].copy()).pin_memory()
+    h_grid = [torch.from_numpy(x.copy()).pin_memory() for x in
+              (grid.hbar_omega_eV, grid.theta_x, grid.theta_y, grid.d_omega)]
+    h_cube = torch.empty(no * na, dtype=torch.float64).pin_memory()
+    h_spec = torch.empty(no, dtype=torch.float64).pin_memory()
+    h_in = [h_samples, h_offs, h_g, h_e, h_w] + h_grid
+    h2d = len(modes) * sum(t.numel() * t.element_size() for t in h_in)
+    d2h = len(modes) * (h_cube.numel() + h_spec.numel()) * 8
+
+    def e2e_step():
+        for m in modes:
+            rc = rad.rad_spectrum_host(*h_in, m, rad.RAD_MIXED, h_cube, h_spec)
+            if rc:
+                raise rad.RadError(rc, "rad_spectrum_host")
+
+    e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        e2e_step()
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    e2e_value = world * terms_step / float(tt.item())
+
+    status = rad.rad_device_status(1)
+    if status != rad.RAD_OK:
+        raise rad.RadError(status, "device status")
+
+    # ---- roofline of the dominant kernel (mixed integral kernel) ----
+    mk = [ms for (_, ms) in kms]
+    kernel_ms_avg = sum(mk) / len(mk)
+    terms_launch = terms_of(B, grid)
+    sfu_ops = 2.0 * terms_launch / (kernel_ms_avg * 1e-3)     # one sin and one cos per term
+    sfu_peak = SM_COUNT * SFU_PER_SM_CLK * SM_MAX_MHZ * 1e6
+    roofline = {"bound": "alu", "pipe": "sfu", "kernel": "k_mixed", "achieved": sfu_ops / 1e12,
+                "peak": sfu_peak / 1e12, "unit": "Tops/s", "frac": sfu_ops / sfu_peak,
+                "traffic": None, "terms_per_launch": terms_launch, "kernel_ms_avg": kernel_ms_avg,
+                "peak_source": "152 SMs x 16 SFU/clk x 2070 MHz (unit counts and max clock)"}
+    fk = [ms for (_, ms) in fkms]
+    f_terms_launch = terms_of(args.fp64_batch, grid)
+    fp64_kernel_ms = sum(fk) / len(fk)
+    fp64_roof = {"kernel": "k_fp64", "kernel_ms_avg": fp64_kernel_ms,
+                 "terms_per_s": f_terms_launch / (fp64_kernel_ms * 1e-3),
+                 "fp64_ops_per_term": 20,
+                 "frac_fp64_pipe": 20 * f_terms_launch / (fp64_kernel_ms * 1e-3) /
+                 (SM_COUNT * FP64_PER_SM_CLK * SM_MAX_MHZ * 1e6)}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "particles_per_step": B, "samples_per_particle": N_SAMP,
+                   "n_omega": no, "n_angles": na, "modes": ["classical", "spin_half"], "precision": "mixed",
+                   "parallelism": f"replicas x{world} (disjoint particle batches)",
+                   "l2": "256 MB buffer written between steps (flush)", "shape": mixed_desc},
+        "spectra_per_s": spectra_s,
+        "plain_fp64": {"value": fp64_value, "unit": "terms/s", "particles_per_step": args.fp64_batch,
+                       "ms_per_step": fms_step, "spectra_per_s": world * len(modes) * args.fp64_batch /
+                       (fms_step * 1e-3), "shape": {m: fp[m].describe() for m in modes}, "kernel": fp64_roof},
+        "mixed_over_fp64": value / fp64_value,
+        "roofline": roofline,
+        "e2e": {"value": e2e_value, "unit": "terms/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "entry": "rad_spectrum_host (pinned host buffers, copies inside the timed region)"},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+        "wall_s_timed": wall,
+    }
+
+    # ---- CPU baseline: the oracle on a bounded sample, and the GPU error on that sample ----
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n_dirs = 128
+        vals, bi, bj, terms, dt, cores = run_oracle_sample(tr, grid, n_dirs, modes)
+        one = batch_args(0, 1)
+        errs = {}
+        for prec, name in ((rad.RAD_MIXED, "mixed"), (rad.RAD_FP64, "fp64")):
+            for m in modes:
+                p1 = rad.Plan(N_SAMP, 1, no, na, m, prec, 1, 0)
+                c1 = torch.empty(no * na, dtype=torch.float64, device=dev)
+                w1 = torch.ones(1, dtype=torch.float64, device=dev)
+                a = list(one)
+                a[4] = w1
+                rc = p1.execute(*a, c1, None, None, None)
+                assert rc == 0
+                g = c1.view(no, na).cpu().numpy()[bi, bj]
+                r = vals[m]
+                peak = np.abs(r).max()
+                if prec == rad.RAD_MIXED:
+                    sel = r >= 1e-3 * peak
+                    rel = np.abs(g[sel] - r[sel]) / r[sel]
+                    errs[f"{name}_{'classical' if m == 0 else 'spin_half'}"] = {
+                        "max_rel_on_bins_ge_1e-3_peak": float(rel.max()),
+                        "median_rel": float(np.median(rel)), "bins": int(sel.sum())}
+                else:
+                    rel = np.abs(g - r) / np.maximum(np.abs(r), 1e-6 * peak)
+                    errs[f"{name}_{'classical' if m == 0 else 'spin_half'}"] = {
+                        "max_rel_floor_1e-6_peak": float(rel.max()), "bins": int(r.size)}
+                p1.close()
+        line["cpu_baseline"] = {
+            "value": terms / dt, "unit": "terms/s", "cores": cores, "kind": "oracle",
+            "sample": f"particle 0 (20000 samples) x 512 hw x {n_dirs} seeded directions x 2 models "
+                      f"= {terms:.3e} terms in {dt:.1f} s"}
+        line["err_vs_oracle"] = errs
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

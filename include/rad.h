@@ -1,0 +1,231 @@
+/*
+ * rad.h -- C ABI of the GB300 (sm_103a) radiation-integral library.
+ *
+ * The library evaluates the Lienard-Wiechert radiation integral of
+ * C. F. Nielsen, "GPU Accelerated Simulation of Channeling Radiation of
+ * Relativistic Particles" (arXiv:1910.10391), Sec. II:
+ *
+ *   d2I/(dw dOmega) = e^2/(4 pi^2) | int f(t, n) exp(i w (t - n.x(t))) dt |^2      (Eq. 1, 2)
+ *
+ * in the paper's small-angle expanded form (f_x, f_y, f_z, g and the phase of
+ * Sec. II), for many trajectories at once, on a grid of photon energies hw_i and
+ * emission directions n_j = (theta_x, theta_y), in three models:
+ *   RAD_CLASSICAL  Eq. 1 as is;
+ *   RAD_SPIN0      Lindhard substitution w -> w* = w/(1 - hw/E), intensity scaled by
+ *                  w/w* (Sec. II, Eq. Lindhard_substi), applied per direction;
+ *   RAD_SPIN_HALF  Belkacem-Cue-Kimball / Baier-Katkov semiclassical formula
+ *                  (Sec. II, Eqs. cue, Iterm, J): (E*^2+E^2)/(2E^2) |I|^2 +
+ *                  hw^2/(2 E^2 gamma^2) |J|^2 with I, J at w*, E* = E - hw.
+ *
+ * Conventions (all entry points):
+ *   - c = 1; times and lengths in metres; photon energies in eV; w = hw/(hbar c).
+ *   - Trajectory record: 10 float64 per time sample, in this order
+ *       t, x, y, dz, vx, vy, dvz, ax, ay, az
+ *     with dz = z - beta0 t, dvz = v_z - beta0, beta0 := 1 - 1/(2 gamma^2), and
+ *     (ax, ay, az) = d(beta)/dt. Particle p owns records offsets[p] .. offsets[p+1]-1
+ *     of one contiguous array; each particle needs at least 2 samples.
+ *     Sections of a trajectory with different energies (Sec. II, energy loss) are
+ *     passed as separate particles with their own gamma and energy.
+ *   - Time integral: trapezoid weights (t_{k+1} - t_{k-1})/2, one-sided at the ends.
+ *   - Output: d2I/(d(hw) dOmega), dimensionless, = alpha/(4 pi^2) * sum_p weight_p S_p,
+ *     cube layout out_cube[i * n_angles + j] (i: photon energy, j: direction).
+ *     out_spectrum[i] = sum_j cube[i][j] * d_omega[j]   (dI/d(hw), angle integral of Sec. IV)
+ *     out_bins[i * n_bins + b] = sum over j with bin_of_angle[j] == b of cube[i][j] d_omega[j]
+ *     (bin_of_angle[j] < 0 or >= n_bins excludes direction j).
+ *   - Pointers named "device" must be device memory of the current CUDA device
+ *     (cudaMalloc/torch); the caller owns them. samples must be 16-byte aligned.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t passed as void*; NULL is the
+ *     legacy default stream). Host-side argument checks run before anything is
+ *     enqueued: on failure nothing is enqueued and the error code is returned.
+ *     Checks that need device data (finite values, offsets, gamma > 1, hw > 0,
+ *     hw < E in quantum modes) run in a small kernel on the same stream; a failure
+ *     skips the computation and is recorded in the per-device status word read by
+ *     rad_device_status(). Outputs of a call whose device checks failed are left
+ *     unchanged.
+ *   - Each device-side wait in the kernels has an iteration limit; if it runs out
+ *     the kernel records RAD_ETIMEOUT in the status word and returns.
+ *   - There is no CPU fallback: without a usable sm_103a device every compute entry
+ *     point returns RAD_ECUDA.
+ */
+#ifndef RAD_H
+#define RAD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define RAD_OK 0
+#define RAD_EINVAL 1       /* bad argument (null pointer, negative size, bad enum, ...)   */
+#define RAD_ENOMEM 2       /* device allocation failed                                    */
+#define RAD_ECUDA 3        /* a CUDA call failed; rad_status_string(RAD_ECUDA) has detail  */
+#define RAD_ETIMEOUT 4     /* a bounded device-side wait ran out                          */
+#define RAD_EUNSUPPORTED 5 /* valid request this build cannot serve (e.g. no sm_103a GPU) */
+#define RAD_EDATA 6        /* device-side data check failed (see rad.h conventions)       */
+
+/* ---- enums ---- */
+#define RAD_CLASSICAL 0
+#define RAD_SPIN0 1
+#define RAD_SPIN_HALF 2
+
+#define RAD_FP64 0  /* every operation in FP64 (the paper's precision, Sec. IV)          */
+#define RAD_MIXED 1 /* FP64 phase base and particle sums; FP32 sincos, f and tile sums   */
+
+#define RAD_NREC 10 /* float64 fields per trajectory record */
+
+/*
+ * rad_spectrum -- one call of the hot path (Sec. II integral, Sec. IV grid of
+ * N_x x N_y x N_omega integrals per trajectory, angle sum and particle average).
+ *
+ *   samples          device, [n_samples_total][10] float64 records (layout above)
+ *   offsets          device, [n_particles + 1] int64, offsets[0] = 0,
+ *                    offsets[n_particles] = n_samples_total, nondecreasing with
+ *                    offsets[p+1] - offsets[p] >= 2
+ *   gamma            device, [n_particles] Lorentz factor (> 1) of each particle/section
+ *   energy_eV        device, [n_particles] particle energy E (used by quantum modes)
+ *   weight           device, [n_particles] ensemble weight, or NULL for all 1
+ *   hbar_omega_eV    device, [n_omega] photon energies (> 0; < E in quantum modes)
+ *   theta_x, theta_y device, [n_angles] transverse components of n (radians)
+ *   d_omega          device, [n_angles] solid angle of each direction cell; may be NULL
+ *                    when neither out_spectrum nor out_bins is requested
+ *   mode             RAD_CLASSICAL | RAD_SPIN0 | RAD_SPIN_HALF
+ *   precision        RAD_FP64 | RAD_MIXED
+ *   out_cube         device, [n_omega * n_angles] or NULL
+ *   out_spectrum     device, [n_omega] or NULL
+ *   bin_of_angle     device, [n_angles] int32 or NULL (required when out_bins != NULL)
+ *   n_bins           number of radial/angular bins (>= 1 when out_bins != NULL)
+ *   out_bins         device, [n_omega * n_bins] or NULL
+ *   accumulate       0: outputs are overwritten; 1: results are added to them
+ *   stream           cudaStream_t as void*
+ * Returns RAD_OK when the work was enqueued. n_particles, n_omega or n_angles equal
+ * to 0 is valid: outputs are zeroed (accumulate = 0) or left as they are.
+ * Scratch memory is allocated by the library on first use of a shape and reused
+ * (see rad_release). Thread-safe; concurrent calls on different streams are allowed.
+ */
+int rad_spectrum(const double *samples, int64_t n_samples_total, const int64_t *offsets,
+                 int64_t n_particles, const double *gamma, const double *energy_eV,
+                 const double *weight, const double *hbar_omega_eV, int64_t n_omega,
+                 const double *theta_x, const double *theta_y, const double *d_omega,
+                 int64_t n_angles, int mode, int precision, double *out_cube,
+                 double *out_spectrum, const int32_t *bin_of_angle, int32_t n_bins,
+                 double *out_bins, int accumulate, void *stream);
+
+/*
+ * rad_spectrum_host -- rad_spectrum on HOST arrays (same arguments, all pointers
+ * host memory; pinned memory gives the fastest copies). Copies the inputs to the
+ * device, computes, copies the requested outputs back and returns when they are
+ * complete. Uses library-owned device buffers, grown as needed and reused.
+ * Device-side data check failures are returned as RAD_EDATA.
+ */
+int rad_spectrum_host(const double *samples, int64_t n_samples_total, const int64_t *offsets,
+                      int64_t n_particles, const double *gamma, const double *energy_eV,
+                      const double *weight, const double *hbar_omega_eV, int64_t n_omega,
+                      const double *theta_x, const double *theta_y, const double *d_omega,
+                      int64_t n_angles, int mode, int precision, double *out_cube,
+                      double *out_spectrum, const int32_t *bin_of_angle, int32_t n_bins,
+                      double *out_bins, int accumulate, void *stream);
+
+/* ---- plans: bind a shape once, then execute, autotune or capture into a CUDA graph ---- */
+typedef struct rad_plan_s *rad_plan;
+
+/*
+ * rad_plan_create -- validates the shape and allocates the scratch it needs.
+ *   n_samples_total, n_particles, n_omega, n_angles, mode, precision: as rad_spectrum;
+ *   want: bit mask of outputs (1 cube, 2 spectrum, 4 bins); n_bins for bins.
+ * On success *plan receives a handle owned by the caller (rad_plan_destroy).
+ * Allocation happens here, so a plan can be executed inside CUDA stream capture.
+ */
+int rad_plan_create(int64_t n_samples_total, int64_t n_particles, int64_t n_omega,
+                    int64_t n_angles, int mode, int precision, int want, int32_t n_bins,
+                    rad_plan *plan);
+
+/* rad_plan_execute -- same pointer arguments as rad_spectrum, for the plan's shape. */
+int rad_plan_execute(rad_plan plan, const double *samples, const int64_t *offsets,
+                     const double *gamma, const double *energy_eV, const double *weight,
+                     const double *hbar_omega_eV, const double *theta_x, const double *theta_y,
+                     const double *d_omega, double *out_cube, double *out_spectrum,
+                     const int32_t *bin_of_angle, double *out_bins, int accumulate, void *stream);
+
+/*
+ * rad_plan_autotune -- times the plan's candidate launch shapes (frequencies per
+ * thread, warps per block, time-tile length, work split) on the given inputs for at
+ * most about budget_ms milliseconds, keeps the fastest in the plan and in the
+ * library's tuning cache (used by rad_spectrum for the same shape). Synchronous.
+ * Writes to the outputs (they hold a valid result of the chosen shape on return).
+ */
+int rad_plan_autotune(rad_plan plan, const double *samples, const int64_t *offsets,
+                      const double *gamma, const double *energy_eV, const double *weight,
+                      const double *hbar_omega_eV, const double *theta_x, const double *theta_y,
+                      const double *d_omega, double *out_cube, double *out_spectrum,
+                      const int32_t *bin_of_angle, double *out_bins, int budget_ms, void *stream);
+
+/*
+ * rad_plan_set_shape -- selects the plan's launch shape explicitly:
+ *   R           photon energies per thread (FP64: 1, 2, 4; mixed: 1, 2, 4)
+ *   NW          warps per block = directions per tile (4 or 8)
+ *   T           time-tile length (FP64: 64; mixed: 64 or 128)
+ *   chunk_mult  >= 1, multiplies the default number of work items (finer split)
+ * Returns RAD_EINVAL for a shape this build does not provide (the plan is unchanged).
+ * May reallocate scratch (waits for the device); not allowed during stream capture.
+ */
+int rad_plan_set_shape(rad_plan plan, int R, int NW, int T, int chunk_mult);
+
+/*
+ * rad_plan_describe -- writes a short text description of the plan's chosen launch
+ * shape into buf (at most len bytes, NUL-terminated). Returns RAD_OK.
+ */
+int rad_plan_describe(rad_plan plan, char *buf, int len);
+
+/*
+ * rad_plan_set_timing -- enable != 0 makes every later rad_plan_execute of this plan
+ * record CUDA events on its stream just before and after the main integral kernel;
+ * rad_plan_last_kernel_ms waits for the last recorded pair and returns the main
+ * kernel's duration in milliseconds in *ms. Do not enable timing on a plan that is
+ * captured into a graph.
+ */
+int rad_plan_set_timing(rad_plan plan, int enable);
+int rad_plan_last_kernel_ms(rad_plan plan, double *ms);
+
+/* rad_plan_kernel_launches -- number of kernel launches one execute enqueues. */
+int rad_plan_kernel_launches(rad_plan plan);
+
+/* rad_plan_destroy -- frees the plan's scratch (waits for the device first). */
+int rad_plan_destroy(rad_plan plan);
+
+/*
+ * CUDA graphs: rad_graph_create captures one rad_plan_execute with the given pointers
+ * on `stream` into an executable graph; rad_graph_launch replays it on any stream.
+ * The pointers are baked into the graph. The plan must outlive the graph.
+ */
+typedef struct rad_graph_s *rad_graph;
+int rad_graph_create(rad_plan plan, const double *samples, const int64_t *offsets,
+                     const double *gamma, const double *energy_eV, const double *weight,
+                     const double *hbar_omega_eV, const double *theta_x, const double *theta_y,
+                     const double *d_omega, double *out_cube, double *out_spectrum,
+                     const int32_t *bin_of_angle, double *out_bins, int accumulate, void *stream,
+                     rad_graph *graph);
+int rad_graph_launch(rad_graph graph, void *stream);
+int rad_graph_destroy(rad_graph graph);
+
+/*
+ * rad_device_status -- waits for the current device to finish, returns the first
+ * device-side error recorded since the last reset (RAD_OK, RAD_EDATA or RAD_ETIMEOUT)
+ * and clears it when reset != 0.
+ */
+int rad_device_status(int reset);
+
+/* rad_status_string -- static description of a status code (RAD_ECUDA: last CUDA error). */
+const char *rad_status_string(int status);
+
+/* rad_version -- library version string. */
+const char *rad_version(void);
+
+/* rad_release -- frees library-owned buffers and the tuning cache (after a device sync). */
+void rad_release(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RAD_H */

@@ -1,0 +1,13 @@
+"""GB300-native (sm_103a) library for the radiation integral of arXiv:1910.10391.
+
+The compute path is the CUDA library ``librad.so`` (C ABI in include/rad.h),
+reached through the thin ctypes binding in ``_binding``; ``inputs`` creates
+seeded synthetic trajectories and grids. Importing this package does not load
+CUDA; the first call of an ``rad_*`` function loads (and if needed builds) the
+library, and raises if it cannot.
+"""
+from ._binding import (  # noqa: F401
+    MODES, PRECISIONS, RAD_CLASSICAL, RAD_ECUDA, RAD_EDATA, RAD_EINVAL, RAD_ENOMEM, RAD_ETIMEOUT,
+    RAD_EUNSUPPORTED, RAD_FP64, RAD_MIXED, RAD_NREC, RAD_OK, RAD_SPIN0, RAD_SPIN_HALF, DeviceInputs, Graph,
+    Plan, RadError, header_symbols, load, rad_device_status, rad_release, rad_spectrum, rad_spectrum_host,
+    rad_status_string, rad_version, spectrum)

@@ -1,0 +1,346 @@
+"""ctypes binding of librad.so (include/rad.h). Argument marshalling only.
+
+The functions named ``rad_*`` mirror the C entry points one to one and take torch
+tensors (device tensors for the device entry points, host arrays for
+``rad_spectrum_host``). Sizes are taken from the tensors' shapes. Every step of the
+computation runs in the CUDA library; if it cannot be built or loaded, ``load()``
+raises and nothing falls back to the CPU.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librad.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "rad.h")
+
+RAD_OK, RAD_EINVAL, RAD_ENOMEM, RAD_ECUDA, RAD_ETIMEOUT, RAD_EUNSUPPORTED, RAD_EDATA = range(7)
+RAD_CLASSICAL, RAD_SPIN0, RAD_SPIN_HALF = 0, 1, 2
+RAD_FP64, RAD_MIXED = 0, 1
+RAD_NREC = 10
+MODES = {"classical": RAD_CLASSICAL, "spin0": RAD_SPIN0, "spin_half": RAD_SPIN_HALF}
+PRECISIONS = {"fp64": RAD_FP64, "mixed": RAD_MIXED}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class RadError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = "?"
+        try:
+            msg = load().rad_status_string(status).decode()
+        except Exception:  # pragma: no cover
+            pass
+        super().__init__(f"{where}: status {status} ({msg})")
+
+
+def header_symbols() -> list:
+    """Names of the functions declared in include/rad.h."""
+    with open(HEADER) as f:
+        txt = f.read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(rad_[a-z0-9_]+)\s*\(", txt)))
+
+
+def load(build_if_missing: bool = True):
+    """Load librad.so (building it in place with nvcc when missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        from . import build as _build
+        if build_if_missing and _build.needs_build():
+            _build.build()
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"CUDA library not built: {LIB_PATH} (run paper_1910_10391_gb300.build)")
+        lib = ctypes.CDLL(LIB_PATH)
+        P, i64, i32, c_int = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int
+        spec_args = [P, i64, P, i64, P, P, P, P, i64, P, P, P, i64, c_int, c_int, P, P, P, i32, P, c_int, P]
+        lib.rad_spectrum.argtypes = spec_args
+        lib.rad_spectrum.restype = c_int
+        lib.rad_spectrum_host.argtypes = spec_args
+        lib.rad_spectrum_host.restype = c_int
+        lib.rad_plan_create.argtypes = [i64, i64, i64, i64, c_int, c_int, c_int, i32, ctypes.POINTER(P)]
+        lib.rad_plan_create.restype = c_int
+        exec_args = [P, P, P, P, P, P, P, P, P, P, P, P, P, P, c_int, P]
+        lib.rad_plan_execute.argtypes = exec_args
+        lib.rad_plan_execute.restype = c_int
+        lib.rad_plan_autotune.argtypes = exec_args[:14] + [c_int, P]
+        lib.rad_plan_autotune.restype = c_int
+        lib.rad_plan_set_shape.argtypes = [P, c_int, c_int, c_int, c_int]
+        lib.rad_plan_set_shape.restype = c_int
+        lib.rad_plan_describe.argtypes = [P, ctypes.c_char_p, c_int]
+        lib.rad_plan_describe.restype = c_int
+        lib.rad_plan_set_timing.argtypes = [P, c_int]
+        lib.rad_plan_set_timing.restype = c_int
+        lib.rad_plan_last_kernel_ms.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
+        lib.rad_plan_last_kernel_ms.restype = c_int
+        lib.rad_plan_kernel_launches.argtypes = [P]
+        lib.rad_plan_kernel_launches.restype = c_int
+        lib.rad_plan_destroy.argtypes = [P]
+        lib.rad_plan_destroy.restype = c_int
+        lib.rad_graph_create.argtypes = exec_args + [ctypes.POINTER(P)]
+        lib.rad_graph_create.restype = c_int
+        lib.rad_graph_launch.argtypes = [P, P]
+        lib.rad_graph_launch.restype = c_int
+        lib.rad_graph_destroy.argtypes = [P]
+        lib.rad_graph_destroy.restype = c_int
+        lib.rad_device_status.argtypes = [c_int]
+        lib.rad_device_status.restype = c_int
+        lib.rad_status_string.argtypes = [c_int]
+        lib.rad_status_string.restype = ctypes.c_char_p
+        lib.rad_version.argtypes = []
+        lib.rad_version.restype = ctypes.c_char_p
+        lib.rad_release.argtypes = []
+        lib.rad_release.restype = None
+        _lib = lib
+        return lib
+
+
+# --------------------------------------------------------------------------- #
+# marshalling helpers
+# --------------------------------------------------------------------------- #
+def _dev_ptr(t, dtype=None, name="tensor"):
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name}: expected a torch tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name}: must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name}: expected {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host_ptr(a, dtype=None, name="array"):
+    if a is None:
+        return None
+    import torch
+    if isinstance(a, torch.Tensor):
+        if a.is_cuda:
+            raise ValueError(f"{name}: must be a host tensor")
+        if dtype is not None and a.dtype != dtype:
+            raise TypeError(f"{name}: expected {dtype}, got {a.dtype}")
+        if not a.is_contiguous():
+            raise ValueError(f"{name}: must be contiguous")
+        return ctypes.c_void_p(a.data_ptr())
+    import numpy as np
+    if not (isinstance(a, np.ndarray) and a.flags["C_CONTIGUOUS"]):
+        raise TypeError(f"{name}: expected a contiguous numpy array or host tensor")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _numel(t):
+    return 0 if t is None else int(t.numel())
+
+
+# --------------------------------------------------------------------------- #
+# entry points
+# --------------------------------------------------------------------------- #
+def rad_spectrum(samples, offsets, gamma, energy_eV, weight, hbar_omega_eV, theta_x, theta_y, d_omega,
+                 mode, precision, out_cube=None, out_spectrum=None, bin_of_angle=None, n_bins=0,
+                 out_bins=None, accumulate=0, stream=None) -> int:
+    import torch
+    lib = load()
+    f64, i64 = torch.float64, torch.int64
+    return lib.rad_spectrum(
+        _dev_ptr(samples, f64, "samples"), _numel(samples) // RAD_NREC, _dev_ptr(offsets, i64, "offsets"),
+        _numel(offsets) - 1, _dev_ptr(gamma, f64, "gamma"), _dev_ptr(energy_eV, f64, "energy_eV"),
+        _dev_ptr(weight, f64, "weight"), _dev_ptr(hbar_omega_eV, f64, "hbar_omega_eV"),
+        _numel(hbar_omega_eV), _dev_ptr(theta_x, f64, "theta_x"), _dev_ptr(theta_y, f64, "theta_y"),
+        _dev_ptr(d_omega, f64, "d_omega"), _numel(theta_x), int(mode), int(precision),
+        _dev_ptr(out_cube, f64, "out_cube"), _dev_ptr(out_spectrum, f64, "out_spectrum"),
+        _dev_ptr(bin_of_angle, torch.int32, "bin_of_angle"), int(n_bins), _dev_ptr(out_bins, f64, "out_bins"),
+        int(accumulate), _stream(stream))
+
+
+def rad_spectrum_host(samples, offsets, gamma, energy_eV, weight, hbar_omega_eV, theta_x, theta_y, d_omega,
+                      mode, precision, out_cube=None, out_spectrum=None, bin_of_angle=None, n_bins=0,
+                      out_bins=None, accumulate=0, stream=None) -> int:
+    import torch
+    lib = load()
+    f64, i64 = torch.float64, torch.int64
+    n = lambda a: 0 if a is None else int(a.numel() if isinstance(a, torch.Tensor) else a.size)
+    return lib.rad_spectrum_host(
+        _host_ptr(samples, f64, "samples"), n(samples) // RAD_NREC, _host_ptr(offsets, i64, "offsets"),
+        n(offsets) - 1, _host_ptr(gamma, f64, "gamma"), _host_ptr(energy_eV, f64, "energy_eV"),
+        _host_ptr(weight, f64, "weight"), _host_ptr(hbar_omega_eV, f64, "hbar_omega_eV"), n(hbar_omega_eV),
+        _host_ptr(theta_x, f64, "theta_x"), _host_ptr(theta_y, f64, "theta_y"), _host_ptr(d_omega, f64, "d_omega"),
+        n(theta_x), int(mode), int(precision), _host_ptr(out_cube, f64, "out_cube"),
+        _host_ptr(out_spectrum, f64, "out_spectrum"), _host_ptr(bin_of_angle, torch.int32, "bin_of_angle"),
+        int(n_bins), _host_ptr(out_bins, f64, "out_bins"), int(accumulate), _stream(stream))
+
+
+def rad_device_status(reset: int = 1) -> int:
+    return load().rad_device_status(int(reset))
+
+
+def rad_status_string(status: int) -> str:
+    return load().rad_status_string(int(status)).decode()
+
+
+def rad_version() -> str:
+    return load().rad_version().decode()
+
+
+def rad_release() -> None:
+    load().rad_release()
+
+
+class Plan:
+    """rad_plan_* bound to one shape; execute / autotune / set_shape / graph."""
+
+    def __init__(self, n_samples_total, n_particles, n_omega, n_angles, mode, precision, want=1, n_bins=0):
+        lib = load()
+        h = ctypes.c_void_p()
+        rc = lib.rad_plan_create(int(n_samples_total), int(n_particles), int(n_omega), int(n_angles),
+                                 int(mode), int(precision), int(want), int(n_bins), ctypes.byref(h))
+        if rc:
+            raise RadError(rc, "rad_plan_create")
+        self._h = h
+        self.n_bins = n_bins
+
+    def _args(self, samples, offsets, gamma, energy_eV, weight, hw, tx, ty, d_omega, out_cube, out_spectrum,
+              bin_of_angle, out_bins):
+        import torch
+        f64 = torch.float64
+        return [self._h, _dev_ptr(samples, f64, "samples"), _dev_ptr(offsets, torch.int64, "offsets"),
+                _dev_ptr(gamma, f64, "gamma"), _dev_ptr(energy_eV, f64, "energy_eV"),
+                _dev_ptr(weight, f64, "weight"), _dev_ptr(hw, f64, "hw"), _dev_ptr(tx, f64, "theta_x"),
+                _dev_ptr(ty, f64, "theta_y"), _dev_ptr(d_omega, f64, "d_omega"),
+                _dev_ptr(out_cube, f64, "out_cube"), _dev_ptr(out_spectrum, f64, "out_spectrum"),
+                _dev_ptr(bin_of_angle, torch.int32, "bin_of_angle"), _dev_ptr(out_bins, f64, "out_bins")]
+
+    def execute(self, *args, accumulate=0, stream=None) -> int:
+        return load().rad_plan_execute(*self._args(*args), int(accumulate), _stream(stream))
+
+    def autotune(self, *args, budget_ms=2000, stream=None) -> int:
+        return load().rad_plan_autotune(*self._args(*args), int(budget_ms), _stream(stream))
+
+    def set_shape(self, R, NW, T, chunk_mult=1) -> int:
+        return load().rad_plan_set_shape(self._h, int(R), int(NW), int(T), int(chunk_mult))
+
+    def describe(self) -> str:
+        buf = ctypes.create_string_buffer(512)
+        load().rad_plan_describe(self._h, buf, 512)
+        return buf.value.decode()
+
+    def set_timing(self, enable=True) -> int:
+        return load().rad_plan_set_timing(self._h, int(bool(enable)))
+
+    def last_kernel_ms(self) -> float:
+        v = ctypes.c_double()
+        rc = load().rad_plan_last_kernel_ms(self._h, ctypes.byref(v))
+        if rc:
+            raise RadError(rc, "rad_plan_last_kernel_ms")
+        return v.value
+
+    def kernel_launches(self) -> int:
+        return load().rad_plan_kernel_launches(self._h)
+
+    def graph(self, *args, accumulate=0, stream=None) -> "Graph":
+        g = ctypes.c_void_p()
+        rc = load().rad_graph_create(*self._args(*args), int(accumulate), _stream(stream), ctypes.byref(g))
+        if rc:
+            raise RadError(rc, "rad_graph_create")
+        return Graph(g, self)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().rad_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Graph:
+    def __init__(self, h, plan):
+        self._h = h
+        self._plan = plan  # keeps the plan alive
+
+    def launch(self, stream=None) -> int:
+        return load().rad_graph_launch(self._h, _stream(stream))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().rad_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# --------------------------------------------------------------------------- #
+# convenience layer over the same entry points
+# --------------------------------------------------------------------------- #
+class DeviceInputs:
+    """Trajectories and grid as device tensors (from the inputs module's containers)."""
+
+    def __init__(self, traj, grid, device="cuda", bin_of_angle=None, n_bins=0):
+        import torch
+        dev = torch.device(device)
+        t = lambda a, dt=torch.float64: torch.as_tensor(a, dtype=dt).contiguous().to(dev)
+        self.samples = t(traj.samples)
+        self.offsets = t(traj.offsets, torch.int64)
+        self.gamma = t(traj.gamma)
+        self.energy = t(traj.energy_eV)
+        self.weight = None if traj.weight is None else t(traj.weight)
+        self.hw = t(grid.hbar_omega_eV)
+        self.tx = t(grid.theta_x)
+        self.ty = t(grid.theta_y)
+        self.dom = t(grid.d_omega)
+        self.boa = None if bin_of_angle is None else t(bin_of_angle, torch.int32)
+        self.n_bins = int(n_bins)
+        self.n_omega = int(self.hw.numel())
+        self.n_angles = int(self.tx.numel())
+        self.n_particles = int(self.offsets.numel() - 1)
+        self.n_samples = int(self.samples.numel() // RAD_NREC)
+
+    def args(self):
+        return (self.samples, self.offsets, self.gamma, self.energy, self.weight, self.hw, self.tx, self.ty,
+                self.dom)
+
+
+def spectrum(inp: DeviceInputs, mode, precision, cube=True, spec=False, bins=False, stream=None):
+    """Allocate outputs and run rad_spectrum; returns dict of device tensors (raises RadError)."""
+    import torch
+    dev = inp.samples.device if inp.samples.numel() else inp.hw.device
+    out = {}
+    oc = torch.empty(inp.n_omega * inp.n_angles, dtype=torch.float64, device=dev) if cube else None
+    os_ = torch.empty(inp.n_omega, dtype=torch.float64, device=dev) if spec else None
+    ob = torch.empty(inp.n_omega * max(inp.n_bins, 1), dtype=torch.float64, device=dev) if bins else None
+    rc = rad_spectrum(*inp.args(), MODES.get(mode, mode), PRECISIONS.get(precision, precision), oc, os_,
+                      inp.boa if bins else None, inp.n_bins if bins else 0, ob, 0, stream)
+    if rc:
+        raise RadError(rc, "rad_spectrum")
+    if cube:
+        out["cube"] = oc.view(inp.n_omega, inp.n_angles)
+    if spec:
+        out["spectrum"] = os_
+    if bins:
+        out["bins"] = ob.view(inp.n_omega, inp.n_bins)
+    return out

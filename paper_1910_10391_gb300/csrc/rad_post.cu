@@ -1,0 +1,289 @@
+// Device-side input checks, the deterministic combine of per-item partials into the
+// d2I/(d hw dOmega) cube (particle sum of Sec. IV), and the angle integral and radial
+// binning of the cube (spectrum dI/d hw of Sec. IV). Fixed summation orders: results are
+// bitwise reproducible run to run.
+#include <math.h>
+
+#include <mutex>
+#include <vector>
+
+#include "rad_internal.cuh"
+
+namespace rad {
+namespace {
+
+__device__ __forceinline__ bool finite_d(double v) { return isfinite(v); }
+
+// One grid-stride pass over every device input; any violation sets RAD_EDATA.
+__global__ void k_validate(const Params P, const double *d_omega, int need_domega,
+                           double max_hw_unused) {
+  (void)max_hw_unused;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  const int64_t t0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  bool bad = false;
+  // particles
+  for (int64_t p = t0; p < P.n_particles; p += stride) {
+    const int64_t a = P.offsets[p], b = P.offsets[p + 1];
+    if (b - a < 2 || a < 0 || b > P.n_samples_total) bad = true;
+    const double g = P.gamma[p], E = P.energy[p];
+    if (!(finite_d(g) && g > 1.0)) bad = true;
+    if (!(finite_d(E) && E > 0.0)) bad = true;
+    if (P.weight && !finite_d(P.weight[p])) bad = true;
+  }
+  if (t0 == 0 && P.n_particles >= 0) {
+    if (P.offsets[0] != 0 || P.offsets[P.n_particles] != P.n_samples_total) bad = true;
+  }
+  // photon energies (and hw < E for every particle in the quantum modes)
+  for (int64_t i = t0; i < P.n_omega; i += stride) {
+    const double h = P.hw[i];
+    if (!(finite_d(h) && h > 0.0)) bad = true;
+  }
+  if (P.mode != RAD_CLASSICAL) {
+    const int64_t npairs = P.n_omega * P.n_particles;
+    for (int64_t e = t0; e < npairs; e += stride) {
+      const int64_t i = e % P.n_omega, p = e / P.n_omega;
+      if (!(P.hw[i] < P.energy[p])) bad = true;
+    }
+  }
+  // directions
+  for (int64_t j = t0; j < P.n_angles; j += stride) {
+    if (!finite_d(P.theta_x[j]) || !finite_d(P.theta_y[j])) bad = true;
+    if (need_domega && !finite_d(d_omega[j])) bad = true;
+  }
+  // trajectory records
+  const int64_t nv = P.n_samples_total * kRec;
+  for (int64_t e = t0; e < nv; e += stride)
+    if (!finite_d(P.samples[e])) bad = true;
+  if (bad) set_status(P.status, RAD_EDATA);
+}
+
+// Combine partials into the cube, tile-transposed: part layout [chunk][..][j][i] (i fastest),
+// cube layout [i][j] (j fastest). Block = 32 x 8 threads over a 32 x 32 tile.
+template <bool AMP, int NC>
+__global__ void k_finalize(const Params P, double *cube_new, double *out_cube, int accumulate,
+                           int *dev_status) {
+  __shared__ double tile[32][33];
+  const int st = *reinterpret_cast<volatile int *>(P.status);
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0 && st != 0)
+    atomicCAS(dev_status, 0, st);
+  if (st != 0) return;  // leave the outputs untouched
+  const int64_t i0 = static_cast<int64_t>(blockIdx.x) * 32;  // energy tile
+  const int64_t j0 = static_cast<int64_t>(blockIdx.y) * 32;  // direction tile
+  const double pref = kAlpha / (4.0 * kPi * kPi);
+  // read phase: thread (x, y) reads i = i0 + x, j = j0 + y + 8k
+  for (int kk = 0; kk < 32; kk += 8) {
+    const int64_t i = i0 + threadIdx.x, j = j0 + threadIdx.y + kk;
+    double v = 0.0;
+    if (i < P.n_omega && j < P.n_angles) {
+      if (!AMP) {
+        for (int64_t c = 0; c < P.n_chunks; ++c) v += P.part[(c * P.n_angles + j) * P.n_omega + i];
+      } else {
+        const double h = P.hw[i];
+        for (int64_t p = 0; p < P.n_particles; ++p) {
+          double a[NC];
+#pragma unroll
+          for (int c = 0; c < NC; ++c) a[c] = 0.0;
+          for (int q = 0; q < P.n_q; ++q) {
+            const int64_t ch = p * P.n_q + q;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) a[c] += P.part[((ch * NC + c) * P.n_angles + j) * P.n_omega + i];
+          }
+          double I2 = 0.0;
+#pragma unroll
+          for (int c = 0; c < 6; ++c) I2 = fma(a[c], a[c], I2);
+          double S;
+          if (P.mode == RAD_CLASSICAL) {
+            S = I2;
+          } else {
+            const double u = h / P.energy[p];
+            if (P.mode == RAD_SPIN0) {
+              S = (1.0 - u) * I2;
+            } else {
+              const double g = P.gamma[p];
+              const double J2 = (NC == 8) ? a[NC - 2] * a[NC - 2] + a[NC - 1] * a[NC - 1] : 0.0;
+              S = 0.5 * (1.0 + (1.0 - u) * (1.0 - u)) * I2 + (u * u) / (2.0 * g * g) * J2;
+            }
+          }
+          v = fma(P.weight ? P.weight[p] : 1.0, S, v);
+        }
+      }
+    }
+    tile[threadIdx.y + kk][threadIdx.x] = pref * v;
+  }
+  __syncthreads();
+  // write phase: thread (x, y) writes j = j0 + x, i = i0 + y + 8k
+  for (int kk = 0; kk < 32; kk += 8) {
+    const int64_t j = j0 + threadIdx.x, i = i0 + threadIdx.y + kk;
+    if (i < P.n_omega && j < P.n_angles) {
+      const double v = tile[threadIdx.x][threadIdx.y + kk];
+      const int64_t e = i * P.n_angles + j;
+      cube_new[e] = v;
+      if (out_cube) out_cube[e] = accumulate ? out_cube[e] + v : v;
+    }
+  }
+}
+
+// One block per photon energy: spectrum and radial bins with fixed-order tree sums.
+__global__ void k_reduce(const Params P, const double *cube_new, const double *d_omega,
+                         double *out_spectrum, const int32_t *bin_of_angle, int n_bins,
+                         double *out_bins, int accumulate) {
+  if (*reinterpret_cast<volatile int *>(P.status) != 0) return;
+  __shared__ double red[256];
+  const int64_t i = blockIdx.x;
+  const double *row = cube_new + i * P.n_angles;
+  auto block_sum = [&](double v) -> double {
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+      if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+      __syncthreads();
+    }
+    const double r = red[0];
+    __syncthreads();
+    return r;
+  };
+  if (out_spectrum) {
+    double v = 0.0;
+    for (int64_t j = threadIdx.x; j < P.n_angles; j += 256) v += row[j] * d_omega[j];
+    const double tot = block_sum(v);
+    if (threadIdx.x == 0) out_spectrum[i] = accumulate ? out_spectrum[i] + tot : tot;
+  }
+  if (out_bins) {
+    for (int b = 0; b < n_bins; ++b) {
+      double v = 0.0;
+      for (int64_t j = threadIdx.x; j < P.n_angles; j += 256)
+        if (bin_of_angle[j] == b) v += row[j] * d_omega[j];
+      const double tot = block_sum(v);
+      if (threadIdx.x == 0) {
+        const int64_t e = i * n_bins + b;
+        out_bins[e] = accumulate ? out_bins[e] + tot : tot;
+      }
+    }
+  }
+}
+
+std::mutex g_mu;
+struct DevRes {
+  double2 *table = nullptr;
+  int *status = nullptr;
+};
+std::vector<DevRes> g_dev;
+
+void fill_table_host(std::vector<double2> &t) {
+  // (cos, sin)(2 pi j / N): first quadrant from long double libm, others by exact symmetry
+  t.resize(kTabN);
+  const int Q = kTabN / 4;
+  const long double pi_l = 3.141592653589793238462643383279502884L;
+  for (int m = 0; m < Q; ++m) {
+    const long double th = 2.0L * pi_l * static_cast<long double>(m) / static_cast<long double>(kTabN);
+    const double c = static_cast<double>(cosl(th)), s = static_cast<double>(sinl(th));
+    t[m] = make_double2(c, s);
+    t[m + Q] = make_double2(-s, c);
+    t[m + 2 * Q] = make_double2(-c, -s);
+    t[m + 3 * Q] = make_double2(s, -c);
+  }
+}
+
+DevRes *dev_res(cudaError_t *err) {
+  int dev = 0;
+  *err = cudaGetDevice(&dev);
+  if (*err != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (static_cast<int>(g_dev.size()) <= dev) g_dev.resize(dev + 1);
+  DevRes &r = g_dev[dev];
+  if (!r.table) {
+    std::vector<double2> h;
+    fill_table_host(h);
+    double2 *d = nullptr;
+    *err = cudaMalloc(&d, sizeof(double2) * kTabN);
+    if (*err != cudaSuccess) return nullptr;
+    *err = cudaMemcpy(d, h.data(), sizeof(double2) * kTabN, cudaMemcpyHostToDevice);
+    if (*err != cudaSuccess) {
+      cudaFree(d);
+      return nullptr;
+    }
+    int *s = nullptr;
+    *err = cudaMalloc(&s, sizeof(int));
+    if (*err != cudaSuccess) {
+      cudaFree(d);
+      return nullptr;
+    }
+    *err = cudaMemset(s, 0, sizeof(int));
+    if (*err != cudaSuccess) {
+      cudaFree(d);
+      cudaFree(s);
+      return nullptr;
+    }
+    r.table = d;
+    r.status = s;
+  }
+  *err = cudaSuccess;
+  return &r;
+}
+
+}  // namespace
+
+const double2 *device_table(cudaError_t *err) {
+  DevRes *r = dev_res(err);
+  return r ? r->table : nullptr;
+}
+
+int *device_status_word(cudaError_t *err) {
+  DevRes *r = dev_res(err);
+  return r ? r->status : nullptr;
+}
+
+cudaError_t launch_validate(const Params &P, const double *d_omega, bool need_domega,
+                            const int32_t *bin_of_angle, cudaStream_t st) {
+  (void)bin_of_angle;
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t work = P.n_samples_total * kRec + P.n_particles + P.n_angles + P.n_omega * (1 + P.n_particles);
+  int64_t blocks = (work + 255) / 256;
+  const int64_t cap = static_cast<int64_t>(sms > 0 ? sms : 1) * 8;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  k_validate<<<static_cast<int>(blocks), 256, 0, st>>>(P, d_omega, need_domega ? 1 : 0, 0.0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const Params &P, double *cube_new, double *out_cube, int accumulate,
+                            cudaStream_t st) {
+  cudaError_t e;
+  int *ds = device_status_word(&e);
+  if (!ds) return e;
+  dim3 blk(32, 8);
+  dim3 grd(static_cast<unsigned>((P.n_omega + 31) / 32), static_cast<unsigned>((P.n_angles + 31) / 32));
+  if (grd.x == 0 || grd.y == 0) return cudaSuccess;
+  if (!P.amp_mode)
+    k_finalize<false, 6><<<grd, blk, 0, st>>>(P, cube_new, out_cube, accumulate, ds);
+  else if (P.mode == RAD_SPIN_HALF)
+    k_finalize<true, 8><<<grd, blk, 0, st>>>(P, cube_new, out_cube, accumulate, ds);
+  else
+    k_finalize<true, 6><<<grd, blk, 0, st>>>(P, cube_new, out_cube, accumulate, ds);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const Params &P, const double *cube_new, const double *d_omega,
+                          double *out_spectrum, const int32_t *bin_of_angle, int n_bins,
+                          double *out_bins, int accumulate, cudaStream_t st) {
+  if (P.n_omega == 0 || (!out_spectrum && !out_bins)) return cudaSuccess;
+  k_reduce<<<static_cast<unsigned>(P.n_omega), 256, 0, st>>>(P, cube_new, d_omega, out_spectrum,
+                                                           bin_of_angle, n_bins, out_bins, accumulate);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zero_outputs(const Params &P, double *out_cube, double *out_spectrum, int n_bins,
+                                double *out_bins, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  if (out_cube && P.n_omega * P.n_angles > 0)
+    e = cudaMemsetAsync(out_cube, 0, sizeof(double) * P.n_omega * P.n_angles, st);
+  if (e == cudaSuccess && out_spectrum && P.n_omega > 0)
+    e = cudaMemsetAsync(out_spectrum, 0, sizeof(double) * P.n_omega, st);
+  if (e == cudaSuccess && out_bins && P.n_omega * n_bins > 0)
+    e = cudaMemsetAsync(out_bins, 0, sizeof(double) * P.n_omega * n_bins, st);
+  return e;
+}
+
+}  // namespace rad

@@ -369,3 +369,52 @@ def elliptical_undulator(gamma=2000.0, a=0.4e-10, b=0.25e-10, phase=0.7, lam=10e
                - 0.25 * (b * k) ** 2 * (t + (np.sin(2.0 * (k * t + phase)) - np.sin(2.0 * phase))
                                         / (2.0 * k)))
     return single(s, gamma, mass_eV)
+
+
+# --------------------------------------------------------------------------- #
+# Named workloads (synthetic stand-ins with the paper's scales: GeV e+-, Si(110)
+# d_p = 1.92 A, ~0.1 mm crystals; the crystal potential is a harmonic well)
+# --------------------------------------------------------------------------- #
+def workload_undulator_4096():
+    """Analytic e+ trajectory, gamma = 1000, x = a sin(2 pi t / lambda), a = 0.5 A, lambda = 10 um,
+    4096 uniform samples over 5 periods; 128 linear hw up to 1.2 x first-harmonic edge; 16 x 16
+    cell-centred directions within +-2/gamma."""
+    g, a, lam = 1000.0, 0.5e-10, 10e-6
+    tr = weak_undulator(g, a, lam, 5, 4096)
+    hw1 = undulator_first_harmonic_eV(g, a, lam)
+    grid = make_grid(omega_linear(128, 1.2 * hw1), 16, 16, 2.0 / g)
+    return tr, grid
+
+
+def _ensemble_grid(E_eV, U0_eV, n_omega, n_side, mass_eV=ME_EV):
+    g = E_eV / mass_eV
+    thL = math.sqrt(2.0 * U0_eV / E_eV)
+    half = thL + 3.0 / g
+    return make_grid(omega_log(n_omega, 1e-4 * E_eV, 0.5 * E_eV), n_side, n_side, half)
+
+
+def workload_positron_ensemble(n_particles=1024, n_samples=20000, seed=2, n_omega=512, n_side=64,
+                               particles=None):
+    """e+ 10 GeV in a harmonic planar well (U0 = 20 eV, d_p = 1.92 A), x0 ~ U[0, d_p),
+    theta_x0 ~ N(0, (0.3 theta_L)^2), RK4 dt = 5 nm with scattering kicks; 512 log-spaced hw in
+    [1e-4 E, 0.5 E]; 64 x 64 directions within +-(theta_L + 3/gamma).
+    `particles` selects a subset (indices) after generation with the full-ensemble seed."""
+    E = 10e9
+    tr = channeling(n_particles, E, +1, n_samples, 5e-9, seed)
+    if particles is not None:
+        tr = tr.subset(particles)
+        tr.weight = np.full(tr.n_particles, 1.0 / n_particles)
+    return tr, _ensemble_grid(E, 20.0, n_omega, n_side)
+
+
+def workload_electron_batch(n_particles=4096, seed=4, n_omega=1024, n_side=32, median=20000.0,
+                            lo=2000, hi=200000, particles=None):
+    """e- 20 GeV, same well centred on the planes, lognormal lengths clip(exp(N(ln median,
+    ln(10)/3)), lo, hi); 1024 log-spaced hw in [1e-4 E, 0.5 E]; 32 x 32 directions."""
+    E = 20e9
+    L = lognormal_lengths(n_particles, seed, median=median, lo=lo, hi=hi)
+    tr = channeling(n_particles, E, -1, L, 5e-9, seed)
+    if particles is not None:
+        tr = tr.subset(particles)
+        tr.weight = np.full(tr.n_particles, 1.0 / n_particles)
+    return tr, _ensemble_grid(E, 20.0, n_omega, n_side)

@@ -1,0 +1,73 @@
+"""Shared helpers of the GPU parity tests: run the CUDA path through the C ABI and compare
+with the FP64 oracle under the tolerances stated in the tests."""
+import numpy as np
+
+import oracle as O
+import paper_1910_10391_gb300 as rad
+
+MODE_ORC = {rad.RAD_CLASSICAL: O.CLASSICAL, rad.RAD_SPIN0: O.SPIN0, rad.RAD_SPIN_HALF: O.SPIN_HALF}
+
+
+def gpu_cube(tr, grid, mode, precision, shape=None, outputs=("cube",), bin_of_angle=None, n_bins=0,
+             plan=False):
+    """Cube (and optional spectrum/bins) from the CUDA library, as numpy arrays."""
+    import torch
+    inp = rad.DeviceInputs(tr, grid, bin_of_angle=bin_of_angle, n_bins=n_bins)
+    want = ("cube" in outputs) * 1 + ("spectrum" in outputs) * 2 + ("bins" in outputs) * 4
+    oc = torch.full((inp.n_omega * inp.n_angles,), np.nan, dtype=torch.float64, device="cuda")
+    os_ = torch.full((inp.n_omega,), np.nan, dtype=torch.float64, device="cuda")
+    ob = torch.full((inp.n_omega * max(n_bins, 1),), np.nan, dtype=torch.float64, device="cuda")
+    oc_, os2, ob_ = (oc if want & 1 else None), (os_ if want & 2 else None), (ob if want & 4 else None)
+    if shape is None and not plan:
+        rc = rad.rad_spectrum(*inp.args(), mode, precision, oc_, os2, inp.boa if want & 4 else None,
+                              n_bins if want & 4 else 0, ob_, 0)
+        assert rc == rad.RAD_OK, rad.rad_status_string(rc)
+    else:
+        p = rad.Plan(inp.n_samples, inp.n_particles, inp.n_omega, inp.n_angles, mode, precision, want,
+                     n_bins if want & 4 else 0)
+        if shape is not None:
+            assert p.set_shape(*shape) == rad.RAD_OK, shape
+        rc = p.execute(*inp.args(), oc_, os2, inp.boa if want & 4 else None, ob_)
+        assert rc == rad.RAD_OK, rad.rad_status_string(rc)
+        torch.cuda.synchronize()
+        p.close()
+    torch.cuda.synchronize()
+    st = rad.rad_device_status(1)
+    assert st == rad.RAD_OK, rad.rad_status_string(st)
+    res = {}
+    if want & 1:
+        res["cube"] = oc.view(inp.n_omega, inp.n_angles).cpu().numpy()
+    if want & 2:
+        res["spectrum"] = os_.cpu().numpy()
+    if want & 4:
+        res["bins"] = ob.view(inp.n_omega, n_bins).cpu().numpy()
+    return res
+
+
+def assert_fp64_close(got, ref, rel=1e-9, floor=1e-6):
+    """|got - ref| <= rel * max(|ref|, floor * peak) per element (peak = max |ref|)."""
+    got, ref = np.asarray(got), np.asarray(ref)
+    peak = np.abs(ref).max()
+    bound = rel * np.maximum(np.abs(ref), floor * peak)
+    err = np.abs(got - ref)
+    bad = err > bound
+    if bad.any():
+        i = np.unravel_index(np.argmax(err / np.maximum(bound, 1e-300)), ref.shape)
+        raise AssertionError(f"{bad.sum()} / {bad.size} elements outside tolerance; worst at {i}: "
+                             f"got {got[i]!r} ref {ref[i]!r} (peak {peak:.3e})")
+    return float((err / np.maximum(np.abs(ref), floor * peak)).max()) if peak > 0 else 0.0
+
+
+def assert_mixed_close(got, ref, rel=1e-4, level=1e-3):
+    """Relative error <= rel on elements with ref >= level * peak; returns error statistics."""
+    got, ref = np.asarray(got), np.asarray(ref)
+    peak = np.abs(ref).max()
+    sel = np.abs(ref) >= level * peak
+    r = np.abs(got[sel] - ref[sel]) / np.abs(ref[sel])
+    stats = {"n": int(sel.sum()), "max": float(r.max()) if r.size else 0.0,
+             "p99": float(np.quantile(r, 0.99)) if r.size else 0.0,
+             "median": float(np.median(r)) if r.size else 0.0}
+    assert stats["max"] <= rel, stats
+    # everywhere else the absolute error stays below rel * level * peak
+    assert np.all(np.abs(got - ref)[~sel] <= rel * level * peak * 10), "small bins off"
+    return stats
