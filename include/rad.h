@@ -165,7 +165,7 @@ int rad_plan_autotune(rad_plan plan, const double *samples, const int64_t *offse
  * rad_plan_set_shape -- selects the plan's launch shape explicitly:
  *   R           photon energies per thread (FP64: 1, 2, 4; mixed: 1, 2, 4)
  *   NW          warps per block = directions per tile (4 or 8)
- *   T           time-tile length (FP64: 64; mixed: 64 or 128)
+ *   T           time-tile length (FP64: 64; mixed: 64, 128 or 256)
  *   chunk_mult  >= 1, multiplies the default number of work items (finer split)
  * Returns RAD_EINVAL for a shape this build does not provide (the plan is unchanged).
  * May reallocate scratch (waits for the device); not allowed during stream capture.

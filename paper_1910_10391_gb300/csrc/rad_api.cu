@@ -426,7 +426,7 @@ int rad_plan_autotune(rad_plan plan, const double *samples, const int64_t *offse
   std::vector<Choice> cands;
   const int Rs[] = {1, 2, 4};
   const int NWs[] = {4, 8};
-  const int Ts[] = {64, 128};
+  const int Ts[] = {64, 128, 256};
   const int mults[] = {1, 2, 4};
   for (int R : Rs)
     for (int NW : NWs)

@@ -2,17 +2,19 @@
 //
 // Precision split (the method is unchanged: the same trapezoid sum of Eq. 1 in the
 // expanded variables of Sec. II):
-//   - FP64: the phase at the first sample of each time tile, Phi0 = w* A_{k0}(n), and its
-//     reduction mod 2 pi; the per-sample longitudinal term q = -(dvz + v_perp^2/2) and the
-//     tile-relative differences of t, dz, x, y; the particle sum of |amplitude|^2.
-//   - FP32: the phase offset within the tile, x_k = (w*/2pi) (A_k - A_{k0}) in turns,
-//     reduced exactly to [-1/2, 1/2] (magic-number rounding: y + 1.5*2^23 - 1.5*2^23),
-//     sin/cos of 2 pi x on the SFU, f(t, n) and j(t, n) (Sec. II, with
+//   - FP64: the phase A at the middle sample of each time tile and the per-sample inputs
+//     (the longitudinal term q = -(dvz + v_perp^2/2), tile-relative differences of t, dz,
+//     x, y); the particle sum of |amplitude|^2.
+//   - double-float FP32 (T. J. Dekker, "A floating-point technique for extending the
+//     available precision", Numer. Math. 18 (1971)): the tile's base phase (w*/2pi) A_ref in
+//     turns and its exact reduction to [-1/2, 1/2] (magic-number rounding).
+//   - FP32: the phase offset within the tile, x_k = w* (A_k - A_ref), sin/cos of x_k on
+//     the SFU, f(t, n) and j(t, n) (Sec. II, with
 //     1 - n.beta = 1/(2 gamma^2) + |n_perp - v_perp|^2/2 + q, algebraically equal to the
 //     paper's g base and free of cancellation), tile sums of f e^{i phi}.
 //   - Tile sums are rotated by e^{i Phi0} and added to Kahan-compensated FP32 running sums
 //     (W. Kahan, "Further remarks on reducing truncation errors", CACM 8 (1965)).
-// Per term: 2 SFU ops (sin, cos), about 13 (classical/spin-0) or 15 (spin-1/2) FMA-pipe ops.
+// Per term: 2 SFU ops (sin, cos) and 8 (classical/spin-0) or 10 (spin-1/2) FMA-pipe ops.
 #include "rad_internal.cuh"
 
 namespace rad {
@@ -21,9 +23,6 @@ namespace {
 constexpr float kMagicF = 12582912.0f;  // 1.5 * 2^23
 constexpr float kTwoPiF = 6.28318530717958647692f;
 constexpr double kInvTwoPi = 0.159154943091895335768883763372514362;
-constexpr double kTwoPiHi = 6.283185307179586232;          // 2 * nearest double to pi
-constexpr double kTwoPiLo = 2.4492935982947063545e-16;      // 2 pi - kTwoPiHi
-constexpr double kMagicD = 6755399441055744.0;              // 1.5 * 2^52
 
 template <int MODE, int R, int NW, int T>
 struct MixLayout {
@@ -31,8 +30,8 @@ struct MixLayout {
   static constexpr int NS = 10;  // per-sample FP32 arrays: dt ddz dx dy vx vy axw ayw azw s0
   static constexpr int kStage = 0;
   static constexpr int kSamp = kStage + 2 * kStageDoubles * 8;
-  static constexpr int kRef = kSamp + NS * T * 4;          // 4 doubles: t, dz, x, y at k0
-  static constexpr int kNk = kRef + 32;                     // per warp: float4 [T] (+ float j[T])
+  static constexpr int kRef = kSamp + NS * T * 4;          // per warp: FP64 phase at the reference sample
+  static constexpr int kNk = kRef + 16 * NW;                // per warp: float4 [T] (+ float j[T])
   static constexpr int kNkWarp = T * 16 + ((MODE == RAD_SPIN_HALF) ? T * 4 : 0);
   static constexpr int kBar = kNk + NW * kNkWarp;
   static constexpr int kMisc = kBar + 16;
@@ -122,7 +121,8 @@ __global__ void __launch_bounds__(NW * 32) k_mixed(const Params P) {
       if (tid == 0) issue_tile<T>(P, cur, stage_base + s * L::kStageDoubles, &bar[s]);
       int64_t cur_p = -1;
       double ws[R];              // w* (1/m), FP64
-      float wt_hi[R], wt_lo[R];  // w*/(2 pi) split into two floats
+      float ws_f[R];             // w* in FP32 (radians per metre)
+      float wt_hi[R], wt_lo[R];  // w*/(2 pi) split into two floats (turns per metre)
       double inv2g2 = 0.0, cn = 0.0, wp = 1.0, gam = 2.0, En = 1.0;
       float cn_hi = 0.f, cn_lo = 0.f;
       for (;;) {
@@ -143,6 +143,7 @@ __global__ void __launch_bounds__(NW * 32) k_mixed(const Params P) {
           for (int r = 0; r < R; ++r) {
             const double w = hwv[r] / kHbarC;
             ws[r] = (MODE == RAD_CLASSICAL) ? w : w / (1.0 - hwv[r] / En);
+            ws_f[r] = static_cast<float>(ws[r]);
             const double wtd = ws[r] * kInvTwoPi;
             wt_hi[r] = static_cast<float>(wtd);
             wt_lo[r] = static_cast<float>(wtd - static_cast<double>(wt_hi[r]));
@@ -163,8 +164,10 @@ __global__ void __launch_bounds__(NW * 32) k_mixed(const Params P) {
         const double *st = stage_base + s * L::kStageDoubles;
         const int n = static_cast<int>((cur.ke - cur.k0) < T ? (cur.ke - cur.k0) : T);
 
-        // per-sample preparation (direction independent), FP64 -> FP32
-        const double *r0 = st + kRec;  // record of sample k0
+        // per-sample preparation (direction independent), FP64 -> FP32; offsets are taken
+        // from the tile's middle sample so that in-tile phases stay small
+        const int km = (n - 1) >> 1;
+        const double *r0 = st + (km + 1) * kRec;
         for (int k = tid; k < n; k += NW * 32) {
           const double *rc = st + (k + 1) * kRec;
           const int64_t K = cur.k0 + k;
@@ -183,11 +186,13 @@ __global__ void __launch_bounds__(NW * 32) k_mixed(const Params P) {
           sAz[k] = static_cast<float>(rc[F_AZ] * w);
           sS0[k] = static_cast<float>(inv2g2 - (rc[F_DVZ] + 0.5 * (vx * vx + vy * vy)));
         }
-        if (tid == 0) {
-          sRef[0] = r0[F_T];
-          sRef[1] = r0[F_DZ];
-          sRef[2] = r0[F_X];
-          sRef[3] = r0[F_Y];
+        if (tid < NW) {  // FP64 phase A at the reference sample, one per warp's direction
+          const int64_t jd = static_cast<int64_t>(nt) * NW + tid;
+          const double ux = jd < P.n_angles ? P.theta_x[jd] : 0.0;
+          const double uy = jd < P.n_angles ? P.theta_y[jd] : 0.0;
+          const double c_u = inv2g2 + (ux * ux + uy * uy) * 0.5;
+          const double A0 = ((c_u * r0[F_T] - r0[F_DZ]) - ux * r0[F_X]) - uy * r0[F_Y];
+          sRef[2 * tid] = A0;
         }
         __syncthreads();
 
@@ -210,17 +215,27 @@ __global__ void __launch_bounds__(NW * 32) k_mixed(const Params P) {
         }
         __syncwarp();
 
-        // base phase of the tile, FP64, reduced to (-pi, pi]
-        const double A0 = ((cn * sRef[0] - sRef[1]) - nx * sRef[2]) - ny * sRef[3];
+        // base phase of the tile: (w*/2pi) A0 in double-float FP32 (Dekker products with
+        // fmaf), reduced to [-1/2, 1/2] turns; FP64 for phases beyond 2^21 turns
+        const double A0 = sRef[2 * warp];
+        const float a0h = static_cast<float>(A0);
+        const float a0l = static_cast<float>(A0 - static_cast<double>(a0h));
         float c0[R], s0[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-          const double ph = ws[r] * A0;
-          const double y = fma(ph, kInvTwoPi, kMagicD);
-          const double jd = y - kMagicD;
-          double rr = fma(-jd, kTwoPiHi, ph);
-          rr = fma(-jd, kTwoPiLo, rr);
-          __sincosf(static_cast<float>(rr), &s0[r], &c0[r]);
+          const float p = wt_hi[r] * a0h;
+          float e = fmaf(wt_hi[r], a0h, -p);
+          e = fmaf(wt_hi[r], a0l, e);
+          e = fmaf(wt_lo[r], a0h, e);
+          float rr;
+          if (fabsf(p) < 2097152.0f) {
+            const float nr = __fsub_rn(__fadd_rn(p, kMagicF), kMagicF);
+            rr = __fadd_rn(__fsub_rn(p, nr), e);
+          } else {
+            const double ph = ws[r] * A0 * kInvTwoPi;
+            rr = static_cast<float>(ph - rint(ph));
+          }
+          __sincosf(rr * kTwoPiF, &s0[r], &c0[r]);
         }
 
         float tpart[R][NC];
@@ -228,18 +243,20 @@ __global__ void __launch_bounds__(NW * 32) k_mixed(const Params P) {
         for (int r = 0; r < R; ++r)
 #pragma unroll
           for (int c = 0; c < NC; ++c) tpart[r][c] = 0.f;
-#pragma unroll 2
+        // per term: phase offset x = w* (A_k - A_ref) in radians (the reference is the tile's
+        // middle sample, so |x| stays below ~1e3 rad), SFU sin/cos with the unit's own
+        // periodic argument handling (absolute error ~2e-7 |x|, random per term; bounded by
+        // tests/test_sfu.py), and the amplitude FMAs
+#pragma unroll 4
         for (int k = 0; k < n; ++k) {
           const float4 F = myF[k];
           float jj = 0.f;
           if (MODE == RAD_SPIN_HALF) jj = myJ[k];
 #pragma unroll
           for (int r = 0; r < R; ++r) {
-            const float x = fmaf(wt_hi[r], F.x, wt_lo[r] * F.x);   // turns
-            const float nr = __fsub_rn(__fadd_rn(x, kMagicF), kMagicF);
-            const float xr = __fsub_rn(x, nr);                      // exact, in [-1/2, 1/2]
+            const float x = ws_f[r] * F.x;
             float sn, cs;
-            __sincosf(xr * kTwoPiF, &sn, &cs);
+            __sincosf(x, &sn, &cs);
             tpart[r][0] = fmaf(F.y, cs, tpart[r][0]);
             tpart[r][1] = fmaf(F.y, sn, tpart[r][1]);
             tpart[r][2] = fmaf(F.z, cs, tpart[r][2]);
@@ -342,6 +359,8 @@ cudaError_t dispatch_mode(const Params &P, LaunchShape *sh, cudaStream_t st, int
   RAD_MIX_CASE(4, 4, 64)
   RAD_MIX_CASE(4, 8, 64)
   RAD_MIX_CASE(4, 8, 128)
+  RAD_MIX_CASE(2, 4, 256)
+  RAD_MIX_CASE(2, 8, 256)
 #undef RAD_MIX_CASE
   return cudaErrorInvalidValue;
 }
@@ -360,6 +379,7 @@ cudaError_t dispatch(const Params &P, LaunchShape *sh, cudaStream_t st, int *occ
 bool shape_supported_mixed(int R, int NW, int T) {
   if (T == 64) return (R == 1 && NW == 8) || ((R == 2 || R == 4) && (NW == 4 || NW == 8));
   if (T == 128) return (R == 2 || R == 4) && NW == 8;
+  if (T == 256) return R == 2 && (NW == 4 || NW == 8);
   return false;
 }
 

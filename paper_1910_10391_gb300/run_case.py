@@ -1,0 +1,80 @@
+"""Run one radiation-integral case on the GPU and print its timing (profiling and checks).
+
+  python -m paper_1910_10391_gb300.run_case --workload ensemble --particles 128 --samples 20000 \
+      --n-omega 64 --n-side 16 --mode classical --precision mixed --repeat 2
+
+Workloads: `ensemble` (10 GeV e+ planar channeling, fixed length), `batch` (20 GeV e-,
+lognormal lengths), `undulator` (the analytic 4096-sample trajectory and its grid).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="ensemble", choices=["ensemble", "batch", "undulator"])
+    ap.add_argument("--particles", type=int, default=16)
+    ap.add_argument("--samples", type=int, default=20000)
+    ap.add_argument("--n-omega", type=int, default=512)
+    ap.add_argument("--n-side", type=int, default=64)
+    ap.add_argument("--mode", default="classical", choices=["classical", "spin0", "spin_half"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--shape", default="", help="R,NW,T,chunk_mult")
+    ap.add_argument("--repeat", type=int, default=2)
+    ap.add_argument("--graph", action="store_true", help="replay a captured CUDA graph")
+    a = ap.parse_args(argv)
+
+    import torch
+
+    import paper_1910_10391_gb300 as rad
+    from paper_1910_10391_gb300 import inputs as I
+
+    if a.workload == "ensemble":
+        tr = I.channeling(a.particles, 10e9, +1, a.samples, 5e-9, seed=2)
+        grid = I._ensemble_grid(10e9, 20.0, a.n_omega, a.n_side)
+    elif a.workload == "batch":
+        L = I.lognormal_lengths(a.particles, seed=4)
+        tr = I.channeling(a.particles, 20e9, -1, L, 5e-9, seed=4)
+        grid = I._ensemble_grid(20e9, 20.0, a.n_omega, a.n_side)
+    else:
+        tr, grid = I.workload_undulator_4096()
+    inp = rad.DeviceInputs(tr, grid)
+    mode, prec = rad.MODES[a.mode], rad.PRECISIONS[a.precision]
+    plan = rad.Plan(inp.n_samples, inp.n_particles, inp.n_omega, inp.n_angles, mode, prec, 1, 0)
+    if a.shape:
+        rc = plan.set_shape(*[int(x) for x in a.shape.split(",")])
+        if rc:
+            raise rad.RadError(rc, "set_shape")
+    out = torch.empty(inp.n_omega * inp.n_angles, dtype=torch.float64, device="cuda")
+    s = torch.cuda.Stream()
+    times = []
+    with torch.cuda.stream(s):
+        g = plan.graph(*inp.args(), out, None, None, None, stream=s) if a.graph else None
+        for _ in range(a.repeat):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            rc = g.launch(s) if g else plan.execute(*inp.args(), out, None, None, None, stream=s)
+            if rc:
+                raise rad.RadError(rc, "execute")
+            e1.record(s)
+            s.synchronize()
+            times.append(e0.elapsed_time(e1))
+    st = rad.rad_device_status(1)
+    if st:
+        raise rad.RadError(st, "device status")
+    terms = int(tr.lengths().sum()) * inp.n_omega * inp.n_angles
+    best = min(times)
+    print(json.dumps({"case": vars(a), "shape": plan.describe(), "terms": terms, "ms": times,
+                      "terms_per_s": terms / (best * 1e-3), "checksum": float(out.sum().item())}))
+    if g:
+        g.close()
+    plan.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -115,7 +115,8 @@ def test_mixed_ensemble(ensemble_small, mode):
 
 
 @pytest.mark.parametrize("shape", [(1, 8, 64, 1), (2, 4, 64, 2), (2, 8, 64, 1), (2, 8, 128, 1),
-                                   (4, 4, 64, 4), (4, 8, 64, 1), (4, 8, 128, 2)])
+                                   (4, 4, 64, 4), (4, 8, 64, 1), (4, 8, 128, 2), (2, 4, 256, 1),
+                                   (2, 8, 256, 3)])
 def test_mixed_every_shape(ragged_batch, shape):
     tr, grid = ragged_batch
     ref = oracle_cube(tr, grid, rad.RAD_SPIN_HALF)
