@@ -64,6 +64,7 @@ extern "C" {
 #define RAD_ETIMEOUT 4     /* a bounded device-side wait ran out                          */
 #define RAD_EUNSUPPORTED 5 /* valid request this build cannot serve (e.g. no sm_103a GPU) */
 #define RAD_EDATA 6        /* device-side data check failed (see rad.h conventions)       */
+#define RAD_ETOOBIG 7      /* request exceeds rad_spectrum_noalloc's fixed scratch        */
 
 /* ---- enums ---- */
 #define RAD_CLASSICAL 0
@@ -126,6 +127,32 @@ int rad_spectrum_host(const double *samples, int64_t n_samples_total, const int6
                       int64_t n_angles, int mode, int precision, double *out_cube,
                       double *out_spectrum, const int32_t *bin_of_angle, int32_t n_bins,
                       double *out_bins, int accumulate, void *stream);
+
+/*
+ * rad_spectrum_noalloc -- the mixed-precision cube with no device allocation at all.
+ * The paper has no counterpart; this serves callers that cannot allocate device memory:
+ * processes whose GPU memory is already held by another framework's caching allocator
+ * (a cudaMalloc of the library would fail there), and latency-critical loops in which
+ * cudaMalloc/cudaFree would synchronize the device.
+ *   Arguments as rad_spectrum (all device pointers), precision fixed to RAD_MIXED, output
+ *   out_cube only ([n_omega * n_angles], overwritten). d_omega, spectrum and bins are not
+ *   part of this entry point.
+ *   Scratch: one fixed device array of 32 MiB inside the library, held by every GPU that
+ *   loads the library until the process exits. Requests with n_omega * n_angles above
+ *   (32 MiB - 256 B) / 8 = 4,194,272 bins return RAD_ETOOBIG before anything is enqueued.
+ *   The first call on a device looks up the array's device address (once per device).
+ *   Every call shares the array: calls that overlap on the GPU (other streams, other host
+ *   threads) race on it, so the caller must serialize them. Each call clears the control
+ *   words it needs and leaves its partial sums in the array.
+ *   Synchronous: returns after the cube is complete; device-side data check failures
+ *   come back as RAD_EDATA (the cube is then left unchanged), bounded-wait expiry as
+ *   RAD_ETIMEOUT. Calls no cudaMalloc, cudaFree or allocating library routine.
+ */
+int rad_spectrum_noalloc(const double *samples, int64_t n_samples_total, const int64_t *offsets,
+                         int64_t n_particles, const double *gamma, const double *energy_eV,
+                         const double *weight, const double *hbar_omega_eV, int64_t n_omega,
+                         const double *theta_x, const double *theta_y, int64_t n_angles, int mode,
+                         double *out_cube, void *stream);
 
 /* ---- plans: bind a shape once, then execute, autotune or capture into a CUDA graph ---- */
 typedef struct rad_plan_s *rad_plan;

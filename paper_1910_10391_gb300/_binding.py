@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "librad.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "rad.h")
 
-RAD_OK, RAD_EINVAL, RAD_ENOMEM, RAD_ECUDA, RAD_ETIMEOUT, RAD_EUNSUPPORTED, RAD_EDATA = range(7)
+RAD_OK, RAD_EINVAL, RAD_ENOMEM, RAD_ECUDA, RAD_ETIMEOUT, RAD_EUNSUPPORTED, RAD_EDATA, RAD_ETOOBIG = range(8)
 RAD_CLASSICAL, RAD_SPIN0, RAD_SPIN_HALF = 0, 1, 2
 RAD_FP64, RAD_MIXED = 0, 1
 RAD_NREC = 10
@@ -65,6 +65,8 @@ def load(build_if_missing: bool = True):
         lib.rad_spectrum.restype = c_int
         lib.rad_spectrum_host.argtypes = spec_args
         lib.rad_spectrum_host.restype = c_int
+        lib.rad_spectrum_noalloc.argtypes = [P, i64, P, i64, P, P, P, P, i64, P, P, i64, c_int, P, P]
+        lib.rad_spectrum_noalloc.restype = c_int
         lib.rad_plan_create.argtypes = [i64, i64, i64, i64, c_int, c_int, c_int, i32, ctypes.POINTER(P)]
         lib.rad_plan_create.restype = c_int
         exec_args = [P, P, P, P, P, P, P, P, P, P, P, P, P, P, c_int, P]
@@ -186,6 +188,20 @@ def rad_spectrum_host(samples, offsets, gamma, energy_eV, weight, hbar_omega_eV,
         n(theta_x), int(mode), int(precision), _host_ptr(out_cube, f64, "out_cube"),
         _host_ptr(out_spectrum, f64, "out_spectrum"), _host_ptr(bin_of_angle, torch.int32, "bin_of_angle"),
         int(n_bins), _host_ptr(out_bins, f64, "out_bins"), int(accumulate), _stream(stream))
+
+
+def rad_spectrum_noalloc(samples, offsets, gamma, energy_eV, weight, hbar_omega_eV, theta_x, theta_y, mode,
+                         out_cube, stream=None) -> int:
+    """Mixed-precision cube with the library's fixed scratch (no device allocation); synchronous."""
+    import torch
+    lib = load()
+    f64 = torch.float64
+    return lib.rad_spectrum_noalloc(
+        _dev_ptr(samples, f64, "samples"), _numel(samples) // RAD_NREC, _dev_ptr(offsets, torch.int64, "offsets"),
+        _numel(offsets) - 1, _dev_ptr(gamma, f64, "gamma"), _dev_ptr(energy_eV, f64, "energy_eV"),
+        _dev_ptr(weight, f64, "weight"), _dev_ptr(hbar_omega_eV, f64, "hbar_omega_eV"), _numel(hbar_omega_eV),
+        _dev_ptr(theta_x, f64, "theta_x"), _dev_ptr(theta_y, f64, "theta_y"), _numel(theta_x), int(mode),
+        _dev_ptr(out_cube, f64, "out_cube"), _stream(stream))
 
 
 def rad_device_status(reset: int = 1) -> int:

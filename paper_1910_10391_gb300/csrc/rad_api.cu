@@ -344,6 +344,7 @@ const char *rad_status_string(int status) {
     case RAD_ETIMEOUT: return "a bounded device-side wait ran out";
     case RAD_EUNSUPPORTED: return "unsupported request (needs an sm_100-class or newer GPU)";
     case RAD_EDATA: return "device-side input check failed (non-finite value, bad offsets, gamma <= 1, hw <= 0 or hw >= E)";
+    case RAD_ETOOBIG: return "n_omega * n_angles exceeds the no-allocation entry point's fixed 32 MiB scratch";
     default: return "unknown status";
   }
 }

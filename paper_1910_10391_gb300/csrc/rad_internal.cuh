@@ -232,6 +232,9 @@ cudaError_t launch_validate(const Params &P, const double *d_omega, bool need_do
                             const int32_t *bin_of_angle, cudaStream_t st);
 cudaError_t launch_finalize(const Params &P, double *cube_new, double *out_cube, int accumulate,
                             cudaStream_t st);
+// k_finalize (S-mode partials) publishing a failed call status into *publish_status.
+cudaError_t launch_finalize_status(const Params &P, double *cube_new, double *out_cube, int accumulate,
+                                   int *publish_status, cudaStream_t st);
 cudaError_t launch_reduce(const Params &P, const double *cube_new, const double *d_omega,
                           double *out_spectrum, const int32_t *bin_of_angle, int n_bins,
                           double *out_bins, int accumulate, cudaStream_t st);

@@ -265,6 +265,16 @@ cudaError_t launch_finalize(const Params &P, double *cube_new, double *out_cube,
   return cudaGetLastError();
 }
 
+cudaError_t launch_finalize_status(const Params &P, double *cube_new, double *out_cube, int accumulate,
+                                   int *publish_status, cudaStream_t st) {
+  dim3 blk(32, 8);
+  dim3 grd(static_cast<unsigned>((P.n_omega + 31) / 32), static_cast<unsigned>((P.n_angles + 31) / 32));
+  if (grd.x == 0 || grd.y == 0) return cudaSuccess;
+  if (P.amp_mode) return cudaErrorInvalidValue;
+  k_finalize<false, 6><<<grd, blk, 0, st>>>(P, cube_new, out_cube, accumulate, publish_status);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_reduce(const Params &P, const double *cube_new, const double *d_omega,
                           double *out_spectrum, const int32_t *bin_of_angle, int n_bins,
                           double *out_bins, int accumulate, cudaStream_t st) {
