@@ -154,13 +154,32 @@ int rad_spectrum_noalloc(const double *samples, int64_t n_samples_total, const i
                          const double *theta_x, const double *theta_y, int64_t n_angles, int mode,
                          double *out_cube, void *stream);
 
+/*
+ * rad_spectrum_particles -- the same integral without the particle sum: one spectrum per
+ * particle (Sec. IV's angle integral per trajectory), e.g. to build per-particle training sets.
+ *   out_spectrum [n_particles][n_omega] (or NULL), out_bins [n_particles][n_omega][n_bins]
+ *   (or NULL, n_bins <= 16): alpha/(4 pi^2) weight_p sum_j S_p(i, j) d_omega[j] (per bin).
+ *   d_omega is required. Other arguments, checks and asynchrony as rad_spectrum; results
+ *   overwrite the outputs. Scratch grows with n_particles * n_omega * n_angles doubles.
+ */
+int rad_spectrum_particles(const double *samples, int64_t n_samples_total, const int64_t *offsets,
+                           int64_t n_particles, const double *gamma, const double *energy_eV,
+                           const double *weight, const double *hbar_omega_eV, int64_t n_omega,
+                           const double *theta_x, const double *theta_y, const double *d_omega,
+                           int64_t n_angles, int mode, int precision, double *out_spectrum,
+                           const int32_t *bin_of_angle, int32_t n_bins, double *out_bins, void *stream);
+
+#define RAD_PER_PARTICLE 8 /* rad_plan_create `want` bit: per-particle spectrum/bins (no cube) */
+
 /* ---- plans: bind a shape once, then execute, autotune or capture into a CUDA graph ---- */
 typedef struct rad_plan_s *rad_plan;
 
 /*
  * rad_plan_create -- validates the shape and allocates the scratch it needs.
  *   n_samples_total, n_particles, n_omega, n_angles, mode, precision: as rad_spectrum;
- *   want: bit mask of outputs (1 cube, 2 spectrum, 4 bins); n_bins for bins.
+ *   want: bit mask of outputs (1 cube, 2 spectrum, 4 bins); n_bins for bins; with
+ *   RAD_PER_PARTICLE (8) the spectrum and bins are per particle and the cube is not available
+ *   (rad_plan_execute then writes [n_particles][...] outputs as rad_spectrum_particles does).
  * On success *plan receives a handle owned by the caller (rad_plan_destroy).
  * Allocation happens here, so a plan can be executed inside CUDA stream capture.
  */
@@ -200,6 +219,15 @@ int rad_plan_autotune(rad_plan plan, const double *samples, const int64_t *offse
 int rad_plan_set_shape(rad_plan plan, int R, int NW, int T, int chunk_mult);
 
 /*
+ * rad_plan_set_prepass -- mixed precision only: enable != 0 selects the kernel fed by a
+ * per-sample pre-pass (FP64 preparation once per sample, 48 bytes of scratch per sample),
+ * 0 the kernel that prepares each time tile itself (no per-sample scratch). The current
+ * (R, NW, T) must exist for the chosen kernel, else RAD_EINVAL (plan unchanged). When
+ * rad_plan_set_shape asks for a shape only the other kernel provides, it switches kernels.
+ */
+int rad_plan_set_prepass(rad_plan plan, int enable);
+
+/*
  * rad_plan_describe -- writes a short text description of the plan's chosen launch
  * shape into buf (at most len bytes, NUL-terminated). Returns RAD_OK.
  */
@@ -207,7 +235,8 @@ int rad_plan_describe(rad_plan plan, char *buf, int len);
 
 /*
  * rad_plan_set_timing -- enable != 0 makes every later rad_plan_execute of this plan
- * record CUDA events on its stream just before and after the main integral kernel;
+ * record CUDA events on its stream just before and after the main integral kernel (after
+ * the mixed kernel's per-sample pre-pass, which is not included);
  * rad_plan_last_kernel_ms waits for the last recorded pair and returns the main
  * kernel's duration in milliseconds in *ms. Do not enable timing on a plan that is
  * captured into a graph.
@@ -235,6 +264,59 @@ int rad_graph_create(rad_plan plan, const double *samples, const int64_t *offset
                      rad_graph *graph);
 int rad_graph_launch(rad_graph graph, void *stream);
 int rad_graph_destroy(rad_graph graph);
+
+/* ---- surrogate MLP (learned per-particle spectra; not part of the paper) ----
+ *
+ * A fully connected network x (n_in) -> depth x [Linear(width) -> GELU] -> Linear(n_out),
+ * trained on spectra computed by rad_spectrum. The first layer is FP32; the others use BF16
+ * weights and activations with FP32 accumulation on the tensor cores. FP32 master weights,
+ * AdamW updates, mean-squared-error loss. All float pointers below are DEVICE pointers unless
+ * named host_*; calls are asynchronous on `stream` except create/destroy/get/set.
+ */
+typedef struct rad_mlp_s *rad_mlp;
+
+/* rad_mlp_create -- allocates a network for batches of up to max_batch rows (width and n_out
+ * even); weights uniform in +-1/sqrt(fan_in) from `seed`, biases 0. */
+int rad_mlp_create(int n_in, int width, int depth, int n_out, int64_t max_batch, uint64_t seed,
+                   rad_mlp *out);
+int rad_mlp_destroy(rad_mlp mlp);
+int64_t rad_mlp_num_params(rad_mlp mlp);
+
+/* rad_mlp_forward -- y [batch][n_out] = network(x [batch][n_in]); any batch size. */
+int rad_mlp_forward(rad_mlp mlp, const float *x, int64_t batch, float *y, void *stream);
+
+/* rad_mlp_backward -- forward pass, loss = mean((y - target)^2) written to *loss (device, may be
+ * NULL) and the gradient of the loss w.r.t. every parameter kept in the network (batch <= max_batch). */
+int rad_mlp_backward(rad_mlp mlp, const float *x, const float *target, int64_t batch, float *loss,
+                     void *stream);
+
+/* rad_mlp_adamw -- one AdamW update of all parameters from the stored gradients. */
+int rad_mlp_adamw(rad_mlp mlp, float lr, float beta1, float beta2, float eps, float weight_decay,
+                  void *stream);
+
+/* rad_mlp_train_step -- rad_mlp_backward then rad_mlp_adamw (beta 0.9/0.999, eps 1e-8). */
+int rad_mlp_train_step(rad_mlp mlp, const float *x, const float *target, int64_t batch, float lr,
+                       float weight_decay, float *loss, void *stream);
+
+/* rad_mlp_get -- copies parameters (what 0), gradients (1) or Adam moments (2, 3) to host_out
+ * [rad_mlp_num_params]. Layout per layer l = 0..depth: W_l [out][in] row-major, then b_l [out]. */
+int rad_mlp_get(rad_mlp mlp, int what, float *host_out);
+/* rad_mlp_set_params -- loads parameters (same layout) from host memory (checkpoint restore). */
+int rad_mlp_set_params(rad_mlp mlp, const float *host_in);
+
+/* rad_mlp_ensemble_estimate -- preds [n_models][batch][n_out] of log10 spectra -> mean
+ * [batch][n_out] and err[batch] = ln(10) sqrt(mean over outputs of the models' variance), the
+ * relative spectrum error implied by the ensemble spread (the surrogate's error estimate). */
+int rad_mlp_ensemble_estimate(const float *preds, int n_models, int64_t batch, int n_out, float *mean,
+                              float *err, void *stream);
+
+/* rad_log_targets -- out[i] = log10(max(values[i], floor_value)) (FP64 in, FP32 out). */
+int rad_log_targets(const double *values, int64_t n, double floor_value, float *out, void *stream);
+/* rad_column_stats -- per-column mean and standard deviation of y [rows][cols]. */
+int rad_column_stats(const float *y, int64_t rows, int cols, float *mean, float *stdv, void *stream);
+/* rad_standardize -- y = (y - mean) / std per column, or the inverse when inverse != 0. */
+int rad_standardize(float *y, int64_t rows, int cols, const float *mean, const float *stdv, int inverse,
+                    void *stream);
 
 /*
  * rad_device_status -- waits for the current device to finish, returns the first

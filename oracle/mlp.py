@@ -1,0 +1,69 @@
+"""FP64 numpy reference of the surrogate MLP -- test infrastructure only.
+
+Same network as the CUDA surrogate: x -> depth x [Linear -> GELU] -> Linear, GELU in its
+exact form 0.5 z (1 + erf(z / sqrt 2)), loss = mean((y - t)^2). Parameters use the CUDA
+library's flat layout: for each layer l = 0..depth, W_l [out][in] row-major then b_l [out].
+Gradients come from the chain rule written out layer by layer (plain backpropagation).
+Pinned in tests by central finite differences of the loss (tests/test_mlp_reference.py).
+"""
+from __future__ import annotations
+
+import numpy as np
+from scipy.special import erf
+
+
+def layout(n_in, width, depth, n_out):
+    """[(w_off, b_off, n_out_l, n_in_l)] per layer and the total parameter count."""
+    out, off = [], 0
+    for l in range(depth + 1):
+        fi = n_in if l == 0 else width
+        fo = n_out if l == depth else width
+        out.append((off, off + fi * fo, fo, fi))
+        off += fi * fo + fo
+    return out, off
+
+
+def unpack(params, n_in, width, depth, n_out):
+    lay, _ = layout(n_in, width, depth, n_out)
+    p = np.asarray(params, dtype=np.float64)
+    return [(p[wo:wo + fo * fi].reshape(fo, fi), p[bo:bo + fo]) for (wo, bo, fo, fi) in lay]
+
+
+def gelu(z):
+    return 0.5 * z * (1.0 + erf(z / np.sqrt(2.0)))
+
+
+def gelu_grad(z):
+    return 0.5 * (1.0 + erf(z / np.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / np.sqrt(2.0 * np.pi)
+
+
+def forward(params, x, n_in, width, depth, n_out, keep=False):
+    layers = unpack(params, n_in, width, depth, n_out)
+    h = np.asarray(x, dtype=np.float64)
+    zs, hs = [], [h]
+    for (W, b) in layers[:-1]:
+        z = h @ W.T + b
+        h = gelu(z)
+        zs.append(z)
+        hs.append(h)
+    W, b = layers[-1]
+    y = h @ W.T + b
+    return (y, zs, hs) if keep else y
+
+
+def loss_and_grad(params, x, t, n_in, width, depth, n_out):
+    """(loss, flat gradient) of mean((y - t)^2) over all batch x output elements."""
+    layers = unpack(params, n_in, width, depth, n_out)
+    y, zs, hs = forward(params, x, n_in, width, depth, n_out, keep=True)
+    t = np.asarray(t, dtype=np.float64)
+    n = y.size
+    loss = float(np.sum((y - t) ** 2) / n)
+    d = 2.0 * (y - t) / n
+    grads = [None] * len(layers)
+    for l in range(len(layers) - 1, -1, -1):
+        W, _ = layers[l]
+        grads[l] = (d.T @ hs[l], d.sum(axis=0))
+        if l > 0:
+            d = (d @ W) * gelu_grad(zs[l - 1])
+    flat = np.concatenate([np.concatenate([gW.ravel(), gb]) for (gW, gb) in grads])
+    return loss, flat

@@ -9,5 +9,6 @@ library, and raises if it cannot.
 from ._binding import (  # noqa: F401
     MODES, PRECISIONS, RAD_CLASSICAL, RAD_ECUDA, RAD_EDATA, RAD_EINVAL, RAD_ENOMEM, RAD_ETIMEOUT,
     RAD_ETOOBIG, RAD_EUNSUPPORTED, RAD_FP64, RAD_MIXED, RAD_NREC, RAD_OK, RAD_SPIN0, RAD_SPIN_HALF, DeviceInputs, Graph,
-    Plan, RadError, header_symbols, load, rad_device_status, rad_release, rad_spectrum, rad_spectrum_host, rad_spectrum_noalloc,
-    rad_status_string, rad_version, spectrum)
+    MLP, Plan, RadError, header_symbols, load, rad_column_stats, rad_device_status, rad_log_targets,
+    rad_mlp_ensemble_estimate, rad_release, rad_spectrum, rad_spectrum_host, rad_spectrum_noalloc,
+    rad_spectrum_particles, rad_standardize, rad_status_string, rad_version, spectrum)

@@ -67,6 +67,36 @@ def load(build_if_missing: bool = True):
         lib.rad_spectrum_host.restype = c_int
         lib.rad_spectrum_noalloc.argtypes = [P, i64, P, i64, P, P, P, P, i64, P, P, i64, c_int, P, P]
         lib.rad_spectrum_noalloc.restype = c_int
+        lib.rad_spectrum_particles.argtypes = [P, i64, P, i64, P, P, P, P, i64, P, P, P, i64, c_int, c_int, P, P,
+                                               i32, P, P]
+        lib.rad_spectrum_particles.restype = c_int
+        u64, f32 = ctypes.c_uint64, ctypes.c_float
+        lib.rad_mlp_create.argtypes = [c_int, c_int, c_int, c_int, i64, u64, ctypes.POINTER(P)]
+        lib.rad_mlp_create.restype = c_int
+        lib.rad_mlp_destroy.argtypes = [P]
+        lib.rad_mlp_destroy.restype = c_int
+        lib.rad_mlp_num_params.argtypes = [P]
+        lib.rad_mlp_num_params.restype = i64
+        lib.rad_mlp_forward.argtypes = [P, P, i64, P, P]
+        lib.rad_mlp_forward.restype = c_int
+        lib.rad_mlp_backward.argtypes = [P, P, P, i64, P, P]
+        lib.rad_mlp_backward.restype = c_int
+        lib.rad_mlp_adamw.argtypes = [P, f32, f32, f32, f32, f32, P]
+        lib.rad_mlp_adamw.restype = c_int
+        lib.rad_mlp_train_step.argtypes = [P, P, P, i64, f32, f32, P, P]
+        lib.rad_mlp_train_step.restype = c_int
+        lib.rad_mlp_get.argtypes = [P, c_int, P]
+        lib.rad_mlp_get.restype = c_int
+        lib.rad_mlp_set_params.argtypes = [P, P]
+        lib.rad_mlp_set_params.restype = c_int
+        lib.rad_mlp_ensemble_estimate.argtypes = [P, c_int, i64, c_int, P, P, P]
+        lib.rad_mlp_ensemble_estimate.restype = c_int
+        lib.rad_log_targets.argtypes = [P, i64, ctypes.c_double, P, P]
+        lib.rad_log_targets.restype = c_int
+        lib.rad_column_stats.argtypes = [P, i64, c_int, P, P, P]
+        lib.rad_column_stats.restype = c_int
+        lib.rad_standardize.argtypes = [P, i64, c_int, P, P, c_int, P]
+        lib.rad_standardize.restype = c_int
         lib.rad_plan_create.argtypes = [i64, i64, i64, i64, c_int, c_int, c_int, i32, ctypes.POINTER(P)]
         lib.rad_plan_create.restype = c_int
         exec_args = [P, P, P, P, P, P, P, P, P, P, P, P, P, P, c_int, P]
@@ -76,6 +106,8 @@ def load(build_if_missing: bool = True):
         lib.rad_plan_autotune.restype = c_int
         lib.rad_plan_set_shape.argtypes = [P, c_int, c_int, c_int, c_int]
         lib.rad_plan_set_shape.restype = c_int
+        lib.rad_plan_set_prepass.argtypes = [P, c_int]
+        lib.rad_plan_set_prepass.restype = c_int
         lib.rad_plan_describe.argtypes = [P, ctypes.c_char_p, c_int]
         lib.rad_plan_describe.restype = c_int
         lib.rad_plan_set_timing.argtypes = [P, c_int]
@@ -204,6 +236,131 @@ def rad_spectrum_noalloc(samples, offsets, gamma, energy_eV, weight, hbar_omega_
         _dev_ptr(out_cube, f64, "out_cube"), _stream(stream))
 
 
+def rad_spectrum_particles(samples, offsets, gamma, energy_eV, weight, hbar_omega_eV, theta_x, theta_y, d_omega,
+                           mode, precision, out_spectrum=None, bin_of_angle=None, n_bins=0, out_bins=None,
+                           stream=None) -> int:
+    import torch
+    lib = load()
+    f64 = torch.float64
+    return lib.rad_spectrum_particles(
+        _dev_ptr(samples, f64, "samples"), _numel(samples) // RAD_NREC, _dev_ptr(offsets, torch.int64, "offsets"),
+        _numel(offsets) - 1, _dev_ptr(gamma, f64, "gamma"), _dev_ptr(energy_eV, f64, "energy_eV"),
+        _dev_ptr(weight, f64, "weight"), _dev_ptr(hbar_omega_eV, f64, "hbar_omega_eV"), _numel(hbar_omega_eV),
+        _dev_ptr(theta_x, f64, "theta_x"), _dev_ptr(theta_y, f64, "theta_y"), _dev_ptr(d_omega, f64, "d_omega"),
+        _numel(theta_x), int(mode), int(precision), _dev_ptr(out_spectrum, f64, "out_spectrum"),
+        _dev_ptr(bin_of_angle, torch.int32, "bin_of_angle"), int(n_bins), _dev_ptr(out_bins, f64, "out_bins"),
+        _stream(stream))
+
+
+class MLP:
+    """rad_mlp_* handle: x (n_in) -> depth x [Linear(width) -> GELU] -> Linear(n_out)."""
+
+    def __init__(self, n_in=3, width=256, depth=3, n_out=2048, max_batch=1024, seed=0):
+        h = ctypes.c_void_p()
+        rc = load().rad_mlp_create(int(n_in), int(width), int(depth), int(n_out), int(max_batch), int(seed),
+                                   ctypes.byref(h))
+        if rc:
+            raise RadError(rc, "rad_mlp_create")
+        self._h, self.n_in, self.width, self.depth, self.n_out, self.max_batch = h, n_in, width, depth, n_out, max_batch
+
+    @property
+    def num_params(self) -> int:
+        return int(load().rad_mlp_num_params(self._h))
+
+    def forward(self, x, y=None, stream=None):
+        import torch
+        if y is None:
+            y = torch.empty((x.shape[0], self.n_out), dtype=torch.float32, device=x.device)
+        rc = load().rad_mlp_forward(self._h, _dev_ptr(x, torch.float32, "x"), int(x.shape[0]),
+                                    _dev_ptr(y, torch.float32, "y"), _stream(stream))
+        if rc:
+            raise RadError(rc, "rad_mlp_forward")
+        return y
+
+    def backward(self, x, t, loss=None, stream=None):
+        import torch
+        rc = load().rad_mlp_backward(self._h, _dev_ptr(x, torch.float32, "x"), _dev_ptr(t, torch.float32, "t"),
+                                     int(x.shape[0]), _dev_ptr(loss, torch.float32, "loss"), _stream(stream))
+        if rc:
+            raise RadError(rc, "rad_mlp_backward")
+
+    def adamw(self, lr, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0, stream=None):
+        rc = load().rad_mlp_adamw(self._h, float(lr), float(beta1), float(beta2), float(eps), float(weight_decay),
+                                  _stream(stream))
+        if rc:
+            raise RadError(rc, "rad_mlp_adamw")
+
+    def train_step(self, x, t, lr, weight_decay=0.0, loss=None, stream=None):
+        import torch
+        rc = load().rad_mlp_train_step(self._h, _dev_ptr(x, torch.float32, "x"), _dev_ptr(t, torch.float32, "t"),
+                                       int(x.shape[0]), float(lr), float(weight_decay),
+                                       _dev_ptr(loss, torch.float32, "loss"), _stream(stream))
+        if rc:
+            raise RadError(rc, "rad_mlp_train_step")
+
+    def get(self, what=0):
+        import numpy as np
+        out = np.empty(self.num_params, dtype=np.float32)
+        rc = load().rad_mlp_get(self._h, int(what), out.ctypes.data_as(ctypes.c_void_p))
+        if rc:
+            raise RadError(rc, "rad_mlp_get")
+        return out
+
+    def set_params(self, params):
+        import numpy as np
+        a = np.ascontiguousarray(params, dtype=np.float32)
+        rc = load().rad_mlp_set_params(self._h, a.ctypes.data_as(ctypes.c_void_p))
+        if rc:
+            raise RadError(rc, "rad_mlp_set_params")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().rad_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rad_mlp_ensemble_estimate(preds, mean, err, stream=None):
+    import torch
+    K, B, O = preds.shape
+    rc = load().rad_mlp_ensemble_estimate(_dev_ptr(preds, torch.float32, "preds"), int(K), int(B), int(O),
+                                          _dev_ptr(mean, torch.float32, "mean"), _dev_ptr(err, torch.float32, "err"),
+                                          _stream(stream))
+    if rc:
+        raise RadError(rc, "rad_mlp_ensemble_estimate")
+
+
+def rad_log_targets(values, floor_value, out, stream=None):
+    import torch
+    rc = load().rad_log_targets(_dev_ptr(values, torch.float64, "values"), int(values.numel()), float(floor_value),
+                                _dev_ptr(out, torch.float32, "out"), _stream(stream))
+    if rc:
+        raise RadError(rc, "rad_log_targets")
+
+
+def rad_column_stats(y, mean, stdv, stream=None):
+    import torch
+    rc = load().rad_column_stats(_dev_ptr(y, torch.float32, "y"), int(y.shape[0]), int(y.shape[1]),
+                                 _dev_ptr(mean, torch.float32, "mean"), _dev_ptr(stdv, torch.float32, "std"),
+                                 _stream(stream))
+    if rc:
+        raise RadError(rc, "rad_column_stats")
+
+
+def rad_standardize(y, mean, stdv, inverse=False, stream=None):
+    import torch
+    rc = load().rad_standardize(_dev_ptr(y, torch.float32, "y"), int(y.shape[0]), int(y.shape[1]),
+                                _dev_ptr(mean, torch.float32, "mean"), _dev_ptr(stdv, torch.float32, "std"),
+                                int(bool(inverse)), _stream(stream))
+    if rc:
+        raise RadError(rc, "rad_standardize")
+
+
 def rad_device_status(reset: int = 1) -> int:
     return load().rad_device_status(int(reset))
 
@@ -252,6 +409,9 @@ class Plan:
 
     def set_shape(self, R, NW, T, chunk_mult=1) -> int:
         return load().rad_plan_set_shape(self._h, int(R), int(NW), int(T), int(chunk_mult))
+
+    def set_prepass(self, enable=True) -> int:
+        return load().rad_plan_set_prepass(self._h, int(bool(enable)))
 
     def describe(self) -> str:
         buf = ctypes.create_string_buffer(512)

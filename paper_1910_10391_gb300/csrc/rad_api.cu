@@ -30,6 +30,7 @@ int cuda_fail(cudaError_t e) {
 struct Choice {
   int R, NW, T;
   int chunk_mult;  // multiplies the default number of work items
+  int pp;          // mixed precision: 1 = per-sample pre-pass kernel, 0 = in-kernel preparation
 };
 
 }  // namespace
@@ -47,7 +48,8 @@ struct rad_plan_s {
   double *part = nullptr;
   size_t part_cap = 0;  // doubles
   double *cube_new = nullptr;
-  int *ctrl = nullptr;  // [0] work counter, [1] call status
+  float *prep = nullptr;  // pre-pass records (mixed precision with pp = 1), 12 floats per sample
+  int *ctrl = nullptr;    // [0] work counter, [1] call status
   std::string desc;
   bool timing = false;
   bool timed_once = false;
@@ -72,20 +74,26 @@ ShapeKey key_of(int dev, int64_t ns, int64_t np, int64_t no, int64_t na, int mod
 }
 
 Choice default_choice(int precision) {
-  if (precision == RAD_FP64) return Choice{2, 8, 64, 1};
-  return Choice{2, 8, 128, 1};
+  if (precision == RAD_FP64) return Choice{2, 8, 64, 1, 0};
+  return Choice{2, 8, 256, 1, 1};
 }
 
 bool supported(int precision, const Choice &c) {
-  return precision == RAD_FP64 ? shape_supported_fp64(c.R, c.NW, c.T)
-                               : shape_supported_mixed(c.R, c.NW, c.T);
+  if (precision == RAD_FP64) return c.pp == 0 && shape_supported_fp64(c.R, c.NW, c.T);
+  return c.pp ? shape_supported_mixed_pp(c.R, c.NW, c.T) : shape_supported_mixed(c.R, c.NW, c.T);
+}
+
+bool same_choice(const Choice &a, const Choice &b) {
+  return a.R == b.R && a.NW == b.NW && a.T == b.T && a.chunk_mult == b.chunk_mult && a.pp == b.pp;
 }
 
 // Work decomposition for a choice; (re)allocates scratch when it grows.
 int configure(rad_plan p, const Choice &c) {
   if (!supported(p->precision, c)) return RAD_EINVAL;
   LaunchShape sh{c.R, c.NW, c.T, 0, 0};
-  const int occ = p->precision == RAD_FP64 ? occupancy_fp64(sh) : occupancy_mixed(sh);
+  const int occ = p->precision == RAD_FP64 ? occupancy_fp64(sh)
+                  : c.pp                   ? occupancy_mixed_pp(sh)
+                                           : occupancy_mixed(sh);
   if (occ <= 0) return RAD_EUNSUPPORTED;
   const int64_t resident = static_cast<int64_t>(p->sms) * occ;
   p->n_wt = static_cast<int>((p->n_omega + 32 * c.R - 1) / (32 * c.R));
@@ -95,7 +103,10 @@ int configure(rad_plan p, const Choice &c) {
   p->amp_mode = 0;
   p->n_q = 1;
   p->n_chunks = 1;
-  if (tiles > 0 && tiles < target) {
+  const bool per_particle = (p->want & RAD_PER_PARTICLE) != 0;
+  if (per_particle) {
+    p->n_chunks = std::max<int64_t>(p->n_particles, 1);  // one chunk per particle: partials are per particle
+  } else if (tiles > 0 && tiles < target) {
     const int64_t factor = (target + tiles - 1) / tiles;
     if (p->n_particles >= factor || p->n_particles >= 64) {
       p->n_chunks = std::min<int64_t>(factor, std::max<int64_t>(p->n_particles, 1));
@@ -112,6 +123,7 @@ int configure(rad_plan p, const Choice &c) {
   // keep the partials within 4 GiB
   const int64_t per_chunk = p->n_omega * p->n_angles * (p->amp_mode ? ncomp : 1);
   const int64_t cap_chunks = per_chunk > 0 ? std::max<int64_t>(1, (int64_t(1) << 29) / per_chunk) : 1;
+  if (per_particle && p->n_chunks > cap_chunks) return RAD_ENOMEM;
   if (p->n_chunks > cap_chunks) {
     if (p->amp_mode) {
       p->n_q = static_cast<int>(std::max<int64_t>(1, cap_chunks / std::max<int64_t>(p->n_particles, 1)));
@@ -134,12 +146,16 @@ int configure(rad_plan p, const Choice &c) {
     if (e != cudaSuccess) return cuda_fail(e);
     p->part_cap = need;
   }
+  if (c.pp && !p->prep && p->n_samples_total > 0) {
+    cudaError_t e = cudaMalloc(&p->prep, sizeof(float) * 12 * static_cast<size_t>(p->n_samples_total));
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
   char buf[256];
   std::snprintf(buf, sizeof buf,
-                "precision=%s mode=%d R=%d NW=%d T=%d grid=%d occ=%d items=%lld chunks=%lld amp=%d nq=%d",
+                "precision=%s mode=%d R=%d NW=%d T=%d grid=%d occ=%d items=%lld chunks=%lld amp=%d nq=%d pp=%d",
                 p->precision == RAD_FP64 ? "fp64" : "mixed", p->mode, c.R, c.NW, c.T, sh.grid, occ,
                 static_cast<long long>(p->n_items), static_cast<long long>(p->n_chunks), p->amp_mode,
-                p->n_q);
+                p->n_q, c.pp);
   p->desc = buf;
   return RAD_OK;
 }
@@ -149,8 +165,12 @@ int check_shape(int64_t ns, int64_t np, int64_t no, int64_t na, int mode, int pr
   if (ns < 0 || np < 0 || no < 0 || na < 0) return RAD_EINVAL;
   if (mode < RAD_CLASSICAL || mode > RAD_SPIN_HALF) return RAD_EINVAL;
   if (prec != RAD_FP64 && prec != RAD_MIXED) return RAD_EINVAL;
-  if (want < 0 || want > 7) return RAD_EINVAL;
+  if (want < 0 || want > 15) return RAD_EINVAL;
   if ((want & 4) && nb < 1) return RAD_EINVAL;
+  if (want & RAD_PER_PARTICLE) {
+    if ((want & 1) || !(want & 6)) return RAD_EINVAL;  // per particle: spectrum and/or bins, no cube
+    if ((want & 4) && nb > 16) return RAD_EINVAL;
+  }
   if (np > 0 && ns < 2 * np) return RAD_EINVAL;
   if (np == 0 && ns != 0) return RAD_EINVAL;
   if (no > (int64_t(1) << 31) || na > (int64_t(1) << 31)) return RAD_EINVAL;
@@ -197,6 +217,7 @@ int execute(rad_plan p, const double *samples, const int64_t *offsets, const dou
   if (out_bins && (!bin_of_angle || p->n_bins < 1)) return RAD_EINVAL;
   if ((out_cube && !(p->want & 1)) || (out_spectrum && !(p->want & 2)) || (out_bins && !(p->want & 4)))
     return RAD_EINVAL;
+  if ((p->want & RAD_PER_PARTICLE) && accumulate) return RAD_EINVAL;
   if (p->n_omega > 0 && p->n_angles > 0) {
     if (p->n_particles > 0 && (!samples || !offsets || !gamma || !energy)) return RAD_EINVAL;
     if (!offsets) return RAD_EINVAL;
@@ -209,6 +230,14 @@ int execute(rad_plan p, const double *samples, const int64_t *offsets, const dou
   if (e != cudaSuccess) return cuda_fail(e);
   if (dev != p->device) return RAD_EINVAL;
   if (p->n_omega == 0) return RAD_OK;
+  if (p->n_angles == 0 && (p->want & RAD_PER_PARTICLE)) {
+    cudaError_t e2 = cudaSuccess;
+    if (out_spectrum && p->n_particles > 0)
+      e2 = cudaMemsetAsync(out_spectrum, 0, sizeof(double) * p->n_particles * p->n_omega, st);
+    if (e2 == cudaSuccess && out_bins && p->n_particles > 0)
+      e2 = cudaMemsetAsync(out_bins, 0, sizeof(double) * p->n_particles * p->n_omega * p->n_bins, st);
+    return e2 == cudaSuccess ? RAD_OK : cuda_fail(e2);
+  }
   if (p->n_angles == 0) {
     // no directions: spectrum and bins are empty sums
     Params Z = make_params(p, samples, offsets, gamma, energy, weight, hw, tx, ty, nullptr);
@@ -226,16 +255,30 @@ int execute(rad_plan p, const double *samples, const int64_t *offsets, const dou
   e = launch_validate(P, d_omega, need_dom, bin_of_angle, st);
   if (e != cudaSuccess) return cuda_fail(e);
   LaunchShape sh = p->shape;
-  if (p->timing) {
+  if (p->precision == RAD_MIXED && p->choice.pp) {
+    e = launch_prep_samples(P, sh.T, p->prep, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  if (p->timing) {  // events bracket the integral kernel alone
     e = cudaEventRecord(p->ev0, st);
     if (e != cudaSuccess) return cuda_fail(e);
   }
-  e = (p->precision == RAD_FP64) ? launch_fp64(P, &sh, st) : launch_mixed(P, &sh, st);
+  if (p->precision == RAD_FP64) {
+    e = launch_fp64(P, &sh, st);
+  } else if (p->choice.pp) {
+    e = launch_mixed_pp(P, p->prep, &sh, st);
+  } else {
+    e = launch_mixed(P, &sh, st);
+  }
   if (e != cudaSuccess) return cuda_fail(e);
   if (p->timing) {
     e = cudaEventRecord(p->ev1, st);
     if (e != cudaSuccess) return cuda_fail(e);
     p->timed_once = true;
+  }
+  if (p->want & RAD_PER_PARTICLE) {
+    e = launch_reduce_particles(P, d_omega, out_spectrum, bin_of_angle, p->n_bins, out_bins, st);
+    return e == cudaSuccess ? RAD_OK : cuda_fail(e);
   }
   e = launch_finalize(P, p->cube_new, out_cube, accumulate, st);
   if (e != cudaSuccess) return cuda_fail(e);
@@ -302,6 +345,7 @@ int plan_create(int64_t ns, int64_t np, int64_t no, int64_t na, int mode, int pr
 void plan_free(rad_plan p) {
   if (!p) return;
   cudaDeviceSynchronize();
+  if (p->prep) cudaFree(p->prep);
   if (p->ev0) cudaEventDestroy(p->ev0);
   if (p->ev1) cudaEventDestroy(p->ev1);
   if (p->part) cudaFree(p->part);
@@ -365,9 +409,21 @@ int rad_plan_execute(rad_plan plan, const double *samples, const int64_t *offset
                  static_cast<cudaStream_t>(stream));
 }
 
+int rad_plan_set_prepass(rad_plan plan, int enable) {
+  if (!plan || plan->precision != RAD_MIXED) return RAD_EINVAL;
+  Choice c = plan->choice;
+  c.pp = enable ? 1 : 0;
+  if (!supported(plan->precision, c)) return RAD_EINVAL;
+  const Choice old = plan->choice;
+  int rc = configure(plan, c);
+  if (rc) configure(plan, old);
+  return rc;
+}
+
 int rad_plan_set_shape(rad_plan plan, int R, int NW, int T, int chunk_mult) {
   if (!plan || chunk_mult < 1) return RAD_EINVAL;
-  const Choice c{R, NW, T, chunk_mult};
+  Choice c{R, NW, T, chunk_mult, plan->choice.pp};
+  if (plan->precision == RAD_MIXED && !supported(plan->precision, c)) c.pp = 1 - c.pp;
   if (!supported(plan->precision, c)) return RAD_EINVAL;
   const Choice old = plan->choice;
   int rc = configure(plan, c);
@@ -407,7 +463,9 @@ int rad_plan_last_kernel_ms(rad_plan plan, double *ms) {
 int rad_plan_kernel_launches(rad_plan plan) {
   if (!plan) return 0;
   if (plan->n_omega == 0 || plan->n_angles == 0) return 0;
-  int n = 3;  // validate, main, finalize
+  const int pre = (plan->precision == RAD_MIXED && plan->choice.pp) ? 1 : 0;  // pre-pass
+  if (plan->want & RAD_PER_PARTICLE) return 3 + pre;  // validate, main, per-particle reduce
+  int n = 3 + pre;  // validate, main, finalize
   if (plan->want & 6) n += 1;
   return n;
 }
@@ -429,13 +487,14 @@ int rad_plan_autotune(rad_plan plan, const double *samples, const int64_t *offse
   const int NWs[] = {4, 8};
   const int Ts[] = {64, 128, 256};
   const int mults[] = {1, 2, 4};
-  for (int R : Rs)
-    for (int NW : NWs)
-      for (int T : Ts)
-        for (int m : mults) {
-          Choice c{R, NW, T, m};
-          if (supported(plan->precision, c)) cands.push_back(c);
-        }
+  for (int pp = 0; pp <= 1; ++pp)
+    for (int R : Rs)
+      for (int NW : NWs)
+        for (int T : Ts)
+          for (int m : mults) {
+            Choice c{R, NW, T, m, pp};
+            if (supported(plan->precision, c)) cands.push_back(c);
+          }
   const Choice start = plan->choice;
   Choice best = start;
   float best_ms = 1e30f;
@@ -517,9 +576,7 @@ int rad_spectrum(const double *samples, int64_t n_samples_total, const int64_t *
       have_tuned = true;
     }
   }
-  if (p && have_tuned &&
-      (tuned.R != p->choice.R || tuned.NW != p->choice.NW || tuned.T != p->choice.T ||
-       tuned.chunk_mult != p->choice.chunk_mult)) {
+  if (p && have_tuned && !same_choice(tuned, p->choice)) {
     // a newer autotuned shape: reconfigure (scratch growth frees with cudaFree, which waits
     // for the device, so work still using the old scratch has finished)
     rc = configure(p, tuned);
@@ -537,6 +594,41 @@ int rad_spectrum(const double *samples, int64_t n_samples_total, const int64_t *
   }
   return execute(p, samples, offsets, gamma, energy_eV, weight, hbar_omega_eV, theta_x, theta_y, d_omega,
                  out_cube, out_spectrum, bin_of_angle, out_bins, accumulate, static_cast<cudaStream_t>(stream));
+}
+
+int rad_spectrum_particles(const double *samples, int64_t n_samples_total, const int64_t *offsets,
+                           int64_t n_particles, const double *gamma, const double *energy_eV, const double *weight,
+                           const double *hbar_omega_eV, int64_t n_omega, const double *theta_x,
+                           const double *theta_y, const double *d_omega, int64_t n_angles, int mode, int precision,
+                           double *out_spectrum, const int32_t *bin_of_angle, int32_t n_bins, double *out_bins,
+                           void *stream) {
+  const int want = RAD_PER_PARTICLE | (out_spectrum ? 2 : 0) | (out_bins ? 4 : 0);
+  int rc = check_shape(n_samples_total, n_particles, n_omega, n_angles, mode, precision, want, n_bins);
+  if (rc) return rc;
+  if (n_angles > 0 && !d_omega) return RAD_EINVAL;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e);
+  const int32_t nb = (want & 4) ? n_bins : 0;
+  const ShapeKey k = key_of(dev, n_samples_total, n_particles, n_omega, n_angles, mode, precision, want, nb);
+  rad_plan p = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_plans.find({k, stream});
+    if (it != g_plans.end()) p = it->second;
+  }
+  if (!p) {
+    rc = plan_create(n_samples_total, n_particles, n_omega, n_angles, mode, precision, want, nb, &p);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto ins = g_plans.emplace(std::make_tuple(k, stream), p);
+    if (!ins.second) {
+      plan_free(p);
+      p = ins.first->second;
+    }
+  }
+  return execute(p, samples, offsets, gamma, energy_eV, weight, hbar_omega_eV, theta_x, theta_y, d_omega,
+                 nullptr, out_spectrum, bin_of_angle, out_bins, 0, static_cast<cudaStream_t>(stream));
 }
 
 int rad_spectrum_host(const double *samples, int64_t n_samples_total, const int64_t *offsets,

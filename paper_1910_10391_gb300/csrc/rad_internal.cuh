@@ -226,6 +226,11 @@ int occupancy_fp64(const LaunchShape &s);
 int occupancy_mixed(const LaunchShape &s);
 bool shape_supported_fp64(int R, int NW, int T);
 bool shape_supported_mixed(int R, int NW, int T);
+// mixed kernel fed by the per-sample pre-pass (rad_mixed_pp.cu); prep holds 12 floats per sample
+bool shape_supported_mixed_pp(int R, int NW, int T);
+int occupancy_mixed_pp(const LaunchShape &s);
+cudaError_t launch_prep_samples(const Params &P, int T, float *prep, cudaStream_t st);
+cudaError_t launch_mixed_pp(const Params &P, const float *prep, LaunchShape *shape, cudaStream_t st);
 
 // post-processing kernels (rad_post.cu)
 cudaError_t launch_validate(const Params &P, const double *d_omega, bool need_domega,
@@ -238,6 +243,10 @@ cudaError_t launch_finalize_status(const Params &P, double *cube_new, double *ou
 cudaError_t launch_reduce(const Params &P, const double *cube_new, const double *d_omega,
                           double *out_spectrum, const int32_t *bin_of_angle, int n_bins,
                           double *out_bins, int accumulate, cudaStream_t st);
+// Per-particle spectrum / radial bins from S-mode partials with one chunk per particle
+// (n_bins <= 16).
+cudaError_t launch_reduce_particles(const Params &P, const double *d_omega, double *out_spectrum,
+                                   const int32_t *bin_of_angle, int n_bins, double *out_bins, cudaStream_t st);
 cudaError_t launch_zero_outputs(const Params &P, double *out_cube, double *out_spectrum,
                                 int n_bins, double *out_bins, cudaStream_t st);
 const double2 *device_table(cudaError_t *err);  // per-device FP64 sincos table

@@ -1,0 +1,431 @@
+// Mixed-precision radiation-integral kernel fed by a per-sample pre-pass (sm_103a).
+//
+// Same method and precision split as k_mixed (rad_mixed.cu), reorganised so that the FP64
+// per-sample work runs once per call instead of once per work item:
+//   k_prep_samples  one pass over the trajectory records: for every sample, FP32 offsets of t,
+//                   dz, x, y from the middle sample of its time tile (the tiling is the main
+//                   kernel's), the transverse velocity, the trapezoid-weighted acceleration and
+//                   s0 = 1/(2 gamma^2) - (dvz + v_perp^2/2), written as 48-byte records.
+//   k_mixed_pp      stages those records with cp.async.bulk (48 B x T per tile, no halo),
+//                   each warp computes f, j and the in-tile phase for its own direction, releases
+//                   the stage through an mbarrier, and runs its term loop. There is no block-wide
+//                   barrier per tile: warps only meet when a new work item is fetched.
+#include "rad_internal.cuh"
+
+namespace rad {
+namespace {
+
+constexpr int kPP = 12;  // floats per prepared record (10 used + 2 pad: 48 B, 16-byte aligned)
+constexpr float kMagicF = 12582912.0f;
+constexpr float kTwoPiF = 6.28318530717958647692f;
+constexpr double kInvTwoPi = 0.159154943091895335768883763372514362;
+
+// Tile geometry shared by the pre-pass and the kernel: sample k of particle p (length L)
+// belongs to the tile starting at k0 with n samples; its reference is the tile's middle sample.
+__device__ __forceinline__ void tile_of(const Params &P, int64_t L, int64_t k, int T, int64_t &k0,
+                                        int64_t &km) {
+  int64_t kb = 0, ke = L;
+  if (P.amp_mode) {
+    int64_t q = (k * P.n_q) / L;
+    while (q + 1 < P.n_q && (L * (q + 1)) / P.n_q <= k) ++q;
+    while (q > 0 && (L * q) / P.n_q > k) --q;
+    kb = (L * q) / P.n_q;
+    ke = (L * (q + 1)) / P.n_q;
+  }
+  k0 = kb + ((k - kb) / T) * T;
+  const int64_t n = (ke - k0) < T ? (ke - k0) : T;
+  km = k0 + (n - 1) / 2;
+}
+
+__global__ void k_prep_samples(const Params P, int T, float *__restrict__ out) {
+  if (*reinterpret_cast<volatile int *>(P.status) != 0) return;  // device data check failed
+  const int64_t p = blockIdx.y;
+  const int64_t off = P.offsets[p];
+  const int64_t L = P.offsets[p + 1] - off;
+  const double g = P.gamma[p];
+  const double inv2g2 = 1.0 / (2.0 * g * g);
+  const double *S = P.samples + off * kRec;
+  for (int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; k < L;
+       k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    int64_t k0, km;
+    tile_of(P, L, k, T, k0, km);
+    const double *rc = S + k * kRec;
+    const double *r0 = S + km * kRec;
+    const double tm = (k == 0) ? rc[F_T] : S[(k - 1) * kRec + F_T];
+    const double tp = (k == L - 1) ? rc[F_T] : S[(k + 1) * kRec + F_T];
+    const double w = 0.5 * (tp - tm);
+    const double vx = rc[F_VX], vy = rc[F_VY];
+    float *o = out + (off + k) * kPP;
+    float4 a, b, c;
+    a.x = static_cast<float>(rc[F_T] - r0[F_T]);
+    a.y = static_cast<float>(rc[F_DZ] - r0[F_DZ]);
+    a.z = static_cast<float>(rc[F_X] - r0[F_X]);
+    a.w = static_cast<float>(rc[F_Y] - r0[F_Y]);
+    b.x = static_cast<float>(vx);
+    b.y = static_cast<float>(vy);
+    b.z = static_cast<float>(rc[F_AX] * w);
+    b.w = static_cast<float>(rc[F_AY] * w);
+    c.x = static_cast<float>(rc[F_AZ] * w);
+    c.y = static_cast<float>(inv2g2 - (rc[F_DVZ] + 0.5 * (vx * vx + vy * vy)));
+    c.z = 0.f;
+    c.w = 0.f;
+    reinterpret_cast<float4 *>(o)[0] = a;
+    reinterpret_cast<float4 *>(o)[1] = b;
+    reinterpret_cast<float4 *>(o)[2] = c;
+  }
+}
+
+template <int MODE, int R, int NW, int T>
+struct PPLayout {
+  static constexpr int kStageBytes = T * kPP * 4;
+  static constexpr int kStage = 0;
+  static constexpr int kNk = kStage + 2 * kStageBytes;
+  static constexpr int kNkWarp = T * 16 + ((MODE == RAD_SPIN_HALF) ? T * 4 : 0);
+  static constexpr int kBar = kNk + NW * kNkWarp;  // full[2], empty[2]
+  static constexpr int kMisc = kBar + 32;
+  static constexpr int kTotal = kMisc + 16;
+};
+
+__device__ __forceinline__ void kahan_add(float &s, float &c, float v) {
+  const float y = __fsub_rn(v, c);
+  const float t = __fadd_rn(s, y);
+  c = __fsub_rn(__fsub_rn(t, s), y);
+  s = t;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+template <int MODE, int R, int NW, int T>
+__global__ void __launch_bounds__(NW * 32, (R <= 2 && NW == 8) ? 2 : 1) k_mixed_pp(const Params P, const float *__restrict__ prep) {
+  using L = PPLayout<MODE, R, NW, T>;
+  constexpr int NC = (MODE == RAD_SPIN_HALF) ? 8 : 6;
+  extern __shared__ __align__(128) unsigned char sm[];
+  uint64_t *full = reinterpret_cast<uint64_t *>(sm + L::kBar);
+  uint64_t *empty = full + 2;
+  int *s_item = reinterpret_cast<int *>(sm + L::kMisc);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float4 *myF = reinterpret_cast<float4 *>(sm + L::kNk + warp * L::kNkWarp);
+  float *myJ = reinterpret_cast<float *>(sm + L::kNk + warp * L::kNkWarp + T * 16);
+
+  if (tid == 0) s_item[1] = *reinterpret_cast<volatile int *>(P.status);
+  __syncthreads();
+  if (s_item[1] != 0) return;
+  if (tid == 0) {
+    mbar_init(&full[0], 1);
+    mbar_init(&full[1], 1);
+    mbar_init(&empty[0], NW);
+    mbar_init(&empty[1], NW);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  uint32_t full_par[2] = {0u, 0u};   // consumers: next parity of full[s]
+  uint32_t uses[2] = {0u, 0u};       // producer (thread 0): copies issued into stage s so far
+  const int64_t per_chunk = static_cast<int64_t>(P.n_wt) * P.n_nt;
+  int s = 0;
+
+  // thread 0: wait until every warp released stage st's previous tile, then fill it
+  auto produce = [&](const TileCursor &c, int st) -> bool {
+    if (uses[st] > 0 && !mbar_wait_bounded(&empty[st], (uses[st] - 1) & 1u)) return false;
+    const int64_t n = (c.ke - c.k0) < T ? (c.ke - c.k0) : T;
+    const uint32_t bytes = static_cast<uint32_t>(n * kPP * 4);
+    const float *src = prep + (P.offsets[c.p] + c.k0) * kPP;
+    fence_proxy_async();
+    mbar_arrive_expect_tx(&full[st], bytes);
+    bulk_g2s(sm + L::kStage + st * L::kStageBytes, src, bytes, &full[st]);
+    uses[st] += 1;
+    return true;
+  };
+
+  for (;;) {
+    if (tid == 0) s_item[0] = atomicAdd(P.counter, 1);
+    __syncthreads();
+    const int64_t item = s_item[0];
+    __syncthreads();
+    if (item >= P.n_items) break;
+    const int64_t chunk = item / per_chunk;
+    const int64_t rem = item % per_chunk;
+    const int nt = static_cast<int>(rem / P.n_wt), wt = static_cast<int>(rem % P.n_wt);
+    const int64_t jdir = static_cast<int64_t>(nt) * NW + warp;
+    const bool jvalid = jdir < P.n_angles;
+    const double nx = jvalid ? P.theta_x[jdir] : 0.0;
+    const double ny = jvalid ? P.theta_y[jdir] : 0.0;
+    const double th2h = (nx * nx + ny * ny) * 0.5;
+    const float nxf = static_cast<float>(nx), nyf = static_cast<float>(ny);
+
+    int64_t iw[R];
+    double hwv[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      iw[r] = static_cast<int64_t>(wt) * 32 * R + r * 32 + lane;
+      hwv[r] = iw[r] < P.n_omega ? P.hw[iw[r]] : 1.0;
+    }
+    double S_acc[R];
+    float ks[R][NC], kc[R][NC];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      S_acc[r] = 0.0;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) ks[r][c] = kc[r][c] = 0.f;
+    }
+    int64_t p0, p1;
+    int q;
+    chunk_range(P, chunk, p0, p1, q);
+    TileCursor cur;
+    cur.p = p0;
+    cur.p_end = p1;
+    cursor_settle(P, cur, q);
+    bool failed = false;
+    if (cur.valid) {
+      if (tid == 0 && !produce(cur, s)) failed = true;
+      int64_t cur_p = -1;
+      double ws[R];
+      float ws_f[R], wt_hi[R], wt_lo[R];
+      double inv2g2 = 0.0, cn = 0.0, wp = 1.0, gam = 2.0, En = 1.0;
+      float cn_hi = 0.f, cn_lo = 0.f;
+      for (;;) {
+        TileCursor nxt = cur;
+        cursor_next<T>(P, nxt, q);
+        if (tid == 0 && nxt.valid && !failed && !produce(nxt, s ^ 1)) failed = true;
+        if (cur.p != cur_p) {
+          cur_p = cur.p;
+          gam = P.gamma[cur_p];
+          En = P.energy[cur_p];
+          wp = P.weight ? P.weight[cur_p] : 1.0;
+          inv2g2 = 1.0 / (2.0 * gam * gam);
+          cn = inv2g2 + th2h;
+          cn_hi = static_cast<float>(cn);
+          cn_lo = static_cast<float>(cn - static_cast<double>(cn_hi));
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const double w = hwv[r] / kHbarC;
+            ws[r] = (MODE == RAD_CLASSICAL) ? w : w / (1.0 - hwv[r] / En);
+            ws_f[r] = static_cast<float>(ws[r]);
+            const double wtd = ws[r] * kInvTwoPi;
+            wt_hi[r] = static_cast<float>(wtd);
+            wt_lo[r] = static_cast<float>(wtd - static_cast<double>(wt_hi[r]));
+#pragma unroll
+            for (int c = 0; c < NC; ++c) ks[r][c] = kc[r][c] = 0.f;
+          }
+        }
+        const bool ok = !failed && mbar_wait_bounded(&full[s], full_par[s]);
+        full_par[s] ^= 1u;
+        if (__any_sync(0xffffffffu, !ok)) {  // bounded wait ran out (or the producer gave up)
+          if (lane == 0) set_status(P.status, RAD_ETIMEOUT);
+          if (tid == 0) {
+            mbar_wait_bounded(&full[s], full_par[s] ^ 1u);
+            if (nxt.valid) mbar_wait_bounded(&full[s ^ 1], full_par[s ^ 1]);
+          }
+          return;
+        }
+        const float *st = reinterpret_cast<const float *>(sm + L::kStage + s * L::kStageBytes);
+        const int n = static_cast<int>((cur.ke - cur.k0) < T ? (cur.ke - cur.k0) : T);
+        const int km = (n - 1) >> 1;
+
+        // per (n, k): weighted f, j and the FP32 phase offset for this warp's direction
+        for (int k = lane; k < n; k += 32) {
+          const float4 ra = reinterpret_cast<const float4 *>(st + k * kPP)[0];
+          const float4 rb = reinterpret_cast<const float4 *>(st + k * kPP)[1];
+          const float2 rcz = reinterpret_cast<const float2 *>(st + k * kPP)[4];
+          const float a = nxf - rb.x, b = nyf - rb.y;
+          const float axw = rb.z, ayw = rb.w, azw = rcz.x;
+          const float m = fmaf(nyf, ayw, fmaf(nxf, axw, azw));
+          const float D = fmaf(0.5f, fmaf(a, a, b * b), rcz.y);
+          const float rD = __frcp_rn(D);
+          const float g = rD * rD;
+          const float cz = fmaf(-nyf, b, fmaf(-nxf, a, D));
+          float4 o;
+          o.x = fmaf(-nyf, ra.w, fmaf(-nxf, ra.z, fmaf(cn_hi, ra.x, fmaf(cn_lo, ra.x, -ra.y))));
+          o.y = fmaf(a, m, -axw * D) * g;
+          o.z = fmaf(b, m, -ayw * D) * g;
+          o.w = fmaf(cz, m, -azw * D) * g;
+          myF[k] = o;
+          if (MODE == RAD_SPIN_HALF) myJ[k] = m * g;
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);  // this warp is done with the stage
+
+        // base phase at the reference (middle) sample, FP64 by lane 0, as a double-float pair
+        float a0h = 0.f, a0l = 0.f;
+        if (lane == 0) {
+          const double *r0 = P.samples + (P.offsets[cur.p] + cur.k0 + km) * kRec;
+          const double A0 = ((cn * r0[F_T] - r0[F_DZ]) - nx * r0[F_X]) - ny * r0[F_Y];
+          a0h = static_cast<float>(A0);
+          a0l = static_cast<float>(A0 - static_cast<double>(a0h));
+        }
+        a0h = __shfl_sync(0xffffffffu, a0h, 0);
+        a0l = __shfl_sync(0xffffffffu, a0l, 0);
+        float c0[R], s0[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const float p = wt_hi[r] * a0h;
+          float e = fmaf(wt_hi[r], a0h, -p);
+          e = fmaf(wt_hi[r], a0l, e);
+          e = fmaf(wt_lo[r], a0h, e);
+          float rr;
+          if (fabsf(p) < 2097152.0f) {
+            const float nr = __fsub_rn(__fadd_rn(p, kMagicF), kMagicF);
+            rr = __fadd_rn(__fsub_rn(p, nr), e);
+          } else {
+            const double ph = ws[r] * (static_cast<double>(a0h) + static_cast<double>(a0l)) * kInvTwoPi;
+            rr = static_cast<float>(ph - rint(ph));
+          }
+          __sincosf(rr * kTwoPiF, &s0[r], &c0[r]);
+        }
+
+        float tpart[R][NC];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+          for (int c = 0; c < NC; ++c) tpart[r][c] = 0.f;
+#pragma unroll 4
+        for (int k = 0; k < n; ++k) {
+          const float4 F = myF[k];
+          float jj = 0.f;
+          if (MODE == RAD_SPIN_HALF) jj = myJ[k];
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const float x = ws_f[r] * F.x;
+            float sn, cs;
+            __sincosf(x, &sn, &cs);
+            tpart[r][0] = fmaf(F.y, cs, tpart[r][0]);
+            tpart[r][1] = fmaf(F.y, sn, tpart[r][1]);
+            tpart[r][2] = fmaf(F.z, cs, tpart[r][2]);
+            tpart[r][3] = fmaf(F.z, sn, tpart[r][3]);
+            tpart[r][4] = fmaf(F.w, cs, tpart[r][4]);
+            tpart[r][5] = fmaf(F.w, sn, tpart[r][5]);
+            if (MODE == RAD_SPIN_HALF) {
+              tpart[r][6] = fmaf(jj, cs, tpart[r][6]);
+              tpart[r][7] = fmaf(jj, sn, tpart[r][7]);
+            }
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+#pragma unroll
+          for (int c = 0; c < NC; c += 2) {
+            const float re = fmaf(c0[r], tpart[r][c], -s0[r] * tpart[r][c + 1]);
+            const float im = fmaf(s0[r], tpart[r][c], c0[r] * tpart[r][c + 1]);
+            kahan_add(ks[r][c], kc[r][c], re);
+            kahan_add(ks[r][c + 1], kc[r][c + 1], im);
+          }
+        }
+        const bool last_of_particle = !nxt.valid || nxt.p != cur.p;
+        if (last_of_particle && !P.amp_mode) {
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            double I2 = 0.0;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+              const double v = static_cast<double>(ks[r][c]) - static_cast<double>(kc[r][c]);
+              I2 = fma(v, v, I2);
+            }
+            double Sv;
+            if (MODE == RAD_CLASSICAL) {
+              Sv = I2;
+            } else {
+              const double u = hwv[r] / En;
+              if (MODE == RAD_SPIN0) {
+                Sv = (1.0 - u) * I2;
+              } else {
+                const double jr = static_cast<double>(ks[r][6]) - static_cast<double>(kc[r][6]);
+                const double ji = static_cast<double>(ks[r][7]) - static_cast<double>(kc[r][7]);
+                Sv = 0.5 * (1.0 + (1.0 - u) * (1.0 - u)) * I2 + (u * u) / (2.0 * gam * gam) * (jr * jr + ji * ji);
+              }
+            }
+            S_acc[r] = fma(wp, Sv, S_acc[r]);
+          }
+        }
+        s ^= 1;
+        if (!nxt.valid) break;
+        cur = nxt;
+      }
+    }
+    if (jvalid) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        if (iw[r] >= P.n_omega) continue;
+        if (!P.amp_mode) {
+          P.part[(chunk * P.n_angles + jdir) * P.n_omega + iw[r]] = S_acc[r];
+        } else {
+#pragma unroll
+          for (int c = 0; c < NC; ++c)
+            P.part[((chunk * NC + c) * P.n_angles + jdir) * P.n_omega + iw[r]] =
+                static_cast<double>(ks[r][c]) - static_cast<double>(kc[r][c]);
+        }
+      }
+    }
+  }
+  // drain: the last copies of every stage were consumed; nothing is in flight here
+}
+
+template <int MODE, int R, int NW, int T>
+cudaError_t launch_t(const Params &P, const float *prep, LaunchShape *shape, cudaStream_t st, int *occ) {
+  using L = PPLayout<MODE, R, NW, T>;
+  auto kern = k_mixed_pp<MODE, R, NW, T>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kTotal);
+  if (e != cudaSuccess) return e;
+  shape->smem = L::kTotal;
+  if (occ) {
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, NW * 32, L::kTotal);
+    *occ = (e == cudaSuccess) ? nb : 0;
+    return e;
+  }
+  if (shape->grid <= 0) return cudaErrorInvalidConfiguration;
+  kern<<<shape->grid, NW * 32, L::kTotal, st>>>(P, prep);
+  return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t dispatch_mode(const Params &P, const float *prep, LaunchShape *sh, cudaStream_t st, int *occ) {
+#define RAD_PP_CASE(RR, WW, TT) \
+  if (sh->R == RR && sh->NW == WW && sh->T == TT) return launch_t<MODE, RR, WW, TT>(P, prep, sh, st, occ);
+  RAD_PP_CASE(2, 8, 128)
+  RAD_PP_CASE(2, 8, 256)
+  RAD_PP_CASE(2, 4, 256)
+  RAD_PP_CASE(4, 8, 128)
+  RAD_PP_CASE(4, 8, 256)
+#undef RAD_PP_CASE
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t dispatch(const Params &P, const float *prep, LaunchShape *sh, cudaStream_t st, int *occ) {
+  switch (P.mode) {
+    case RAD_CLASSICAL: return dispatch_mode<RAD_CLASSICAL>(P, prep, sh, st, occ);
+    case RAD_SPIN0: return dispatch_mode<RAD_SPIN0>(P, prep, sh, st, occ);
+    case RAD_SPIN_HALF: return dispatch_mode<RAD_SPIN_HALF>(P, prep, sh, st, occ);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+bool shape_supported_mixed_pp(int R, int NW, int T) {
+  if (T == 128) return (R == 2 || R == 4) && NW == 8;
+  if (T == 256) return (R == 2 && (NW == 4 || NW == 8)) || (R == 4 && NW == 8);
+  return false;
+}
+
+cudaError_t launch_prep_samples(const Params &P, int T, float *prep, cudaStream_t st) {
+  if (P.n_particles == 0) return cudaSuccess;
+  dim3 grd(8, static_cast<unsigned>(P.n_particles));
+  k_prep_samples<<<grd, 256, 0, st>>>(P, T, prep);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mixed_pp(const Params &P, const float *prep, LaunchShape *shape, cudaStream_t st) {
+  return dispatch(P, prep, shape, st, nullptr);
+}
+
+int occupancy_mixed_pp(const LaunchShape &s) {
+  Params P{};
+  P.mode = RAD_SPIN_HALF;
+  LaunchShape sh = s;
+  int occ = 0;
+  if (dispatch(P, nullptr, &sh, nullptr, &occ) != cudaSuccess) return 0;
+  return occ;
+}
+
+}  // namespace rad

@@ -1,2 +1,551 @@
-// Surrogate MLP kernels (filled in by the surrogate component).
+// Surrogate MLP for per-particle spectra: training and inference kernels.
+//
+// Network: x (n_in, FP32) -> [Linear -> GELU] x depth (width) -> Linear -> y (n_out, FP32).
+// The first layer (n_in = 3 inputs) runs in FP32 so the entry conditions are not quantized;
+// every other layer is a BF16 x BF16 -> FP32 tensor-core GEMM (mma.sync m16n8k16) with the
+// bias, GELU (exact erf form) and their derivatives fused into the GEMM epilogues. FP32 master
+// weights are updated by AdamW (Loshchilov & Hutter, "Decoupled weight decay
+// regularization", ICLR 2019) and copied to BF16 for the GEMMs. Loss: mean squared error.
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include <cstdio>
+#include <random>
+#include <vector>
+
 #include "rad_internal.cuh"
+
+namespace rad {
+namespace {
+
+using bf16 = __nv_bfloat16;
+
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float z) {
+  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * __expf(-0.5f * z * z);
+}
+
+__device__ __forceinline__ uint32_t ld_u32(const bf16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// C[M x N] = sum_k A(m, k) B(k, n), BF16 inputs, FP32 accumulation, epilogue epi(m, n, value).
+//   A(m, k) = A_KM ? A[m * lda + k] : A[k * lda + m]
+//   B(k, n) = B_KN ? B[n * ldb + k] : B[k * ldb + n]
+// Block tile 64 x 64 x 32, 4 warps (2 x 2), warp tile 32 x 32 (2 x 4 mma tiles).
+template <bool A_KM, bool B_KN, class Epi>
+__global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const bf16 *__restrict__ A, int lda,
+                                              const bf16 *__restrict__ B, int ldb, Epi epi) {
+  __shared__ __align__(16) bf16 As[64][40];
+  __shared__ __align__(16) bf16 Bs[64][40];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+  float acc[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[i][j][c] = 0.f;
+  const bf16 zero = __float2bfloat16(0.f);
+  for (int k0 = 0; k0 < K; k0 += 32) {
+    for (int e = tid; e < 64 * 32; e += 128) {
+      int mm, kk;
+      if (A_KM) {
+        mm = e >> 5;
+        kk = e & 31;
+      } else {
+        kk = e >> 6;
+        mm = e & 63;
+      }
+      const int m = m0 + mm, k = k0 + kk;
+      As[mm][kk] = (m < M && k < K) ? (A_KM ? A[static_cast<int64_t>(m) * lda + k]
+                                            : A[static_cast<int64_t>(k) * lda + m])
+                                    : zero;
+      int nn, kb;
+      if (B_KN) {
+        nn = e >> 5;
+        kb = e & 31;
+      } else {
+        kb = e >> 6;
+        nn = e & 63;
+      }
+      const int n = n0 + nn, k2 = k0 + kb;
+      Bs[nn][kb] = (n < N && k2 < K) ? (B_KN ? B[static_cast<int64_t>(n) * ldb + k2]
+                                             : B[static_cast<int64_t>(k2) * ldb + n])
+                                     : zero;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ks = 0; ks < 32; ks += 16) {
+      const int c = ks + (lane & 3) * 2;
+      uint32_t a[2][4], b[4][2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int r = wm + i * 16 + (lane >> 2);
+        a[i][0] = ld_u32(&As[r][c]);
+        a[i][1] = ld_u32(&As[r + 8][c]);
+        a[i][2] = ld_u32(&As[r][c + 8]);
+        a[i][3] = ld_u32(&As[r + 8][c + 8]);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int nn = wn + j * 8 + (lane >> 2);
+        b[j][0] = ld_u32(&Bs[nn][c]);
+        b[j][1] = ld_u32(&Bs[nn][c + 8]);
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], a[i][0], a[i][1], a[i][2], a[i][3], b[j][0], b[j][1]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int m = m0 + wm + i * 16 + (lane >> 2) + ((c & 2) ? 8 : 0);
+        const int n = n0 + wn + j * 8 + (lane & 3) * 2 + (c & 1);
+        if (m < M && n < N) epi(m, n, acc[i][j][c]);
+      }
+}
+
+// ---- epilogues ----
+struct EpiHidden {  // Z = acc + b; H = bf16(gelu(Z)); Z kept for the backward pass (may be null)
+  const float *bias;
+  float *Z;
+  bf16 *H;
+  int ld;
+  __device__ void operator()(int m, int n, float v) const {
+    const float z = v + bias[n];
+    const int64_t e = static_cast<int64_t>(m) * ld + n;
+    if (Z) Z[e] = z;
+    H[e] = __float2bfloat16(gelu(z));
+  }
+};
+struct EpiOut {  // Y = acc + b (FP32)
+  const float *bias;
+  float *Y;
+  int ld;
+  __device__ void operator()(int m, int n, float v) const { Y[static_cast<int64_t>(m) * ld + n] = v + bias[n]; }
+};
+struct EpiGradAct {  // dZ = bf16(acc * gelu'(Z))
+  const float *Z;
+  bf16 *dZ;
+  int ld;
+  __device__ void operator()(int m, int n, float v) const {
+    const int64_t e = static_cast<int64_t>(m) * ld + n;
+    dZ[e] = __float2bfloat16(v * gelu_grad(Z[e]));
+  }
+};
+struct EpiStore {  // plain FP32 store
+  float *C;
+  int ld;
+  __device__ void operator()(int m, int n, float v) const { C[static_cast<int64_t>(m) * ld + n] = v; }
+};
+
+template <bool A_KM, bool B_KN, class Epi>
+cudaError_t gemm(int M, int N, int K, const bf16 *A, int lda, const bf16 *B, int ldb, Epi epi, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  dim3 grd((N + 63) / 64, (M + 63) / 64);
+  k_gemm<A_KM, B_KN, Epi><<<grd, 128, 0, st>>>(M, N, K, A, lda, B, ldb, epi);
+  return cudaGetLastError();
+}
+
+// First layer in FP32: Z1[b][n] = sum_k x[b][k] W1[n][k] + b1[n]; H1 = bf16(gelu(Z1)).
+__global__ void k_layer1(int64_t B, int n_in, int width, const float *__restrict__ x, const float *__restrict__ W,
+                         const float *__restrict__ bias, float *Z, bf16 *H) {
+  const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= B * width) return;
+  const int64_t b = e / width;
+  const int n = static_cast<int>(e % width);
+  float z = bias[n];
+  for (int k = 0; k < n_in; ++k) z = fmaf(x[b * n_in + k], W[n * n_in + k], z);
+  if (Z) Z[e] = z;
+  H[e] = __float2bfloat16(gelu(z));
+}
+
+// First-layer weight gradient in FP32: dW1[n][k] = sum_b dZ1[b][n] x[b][k] (one thread per (n, k)).
+__global__ void k_layer1_grad(int64_t B, int n_in, int width, const float *__restrict__ x,
+                              const bf16 *__restrict__ dZ, float *dW) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= width * n_in) return;
+  const int n = e / n_in, k = e % n_in;
+  float s = 0.f;
+  for (int64_t b = 0; b < B; ++b) s = fmaf(__bfloat162float(dZ[b * width + n]), x[b * n_in + k], s);
+  dW[e] = s;
+}
+
+// Column sums (bias gradients): db[n] = sum_b dZ[b][n].
+__global__ void k_colsum(int64_t rows, int cols, const bf16 *__restrict__ dZ, float *db) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= cols) return;
+  float s = 0.f;
+  for (int64_t b = 0; b < rows; ++b) s += __bfloat162float(dZ[b * cols + n]);
+  db[n] = s;
+}
+
+// Loss and output gradient: dY = bf16(2 (Y - T) / (B O)); per-block squared-error partials.
+__global__ void k_loss(int64_t n, float scale, const float *__restrict__ Y, const float *__restrict__ T, bf16 *dY,
+                       float *partial) {
+  __shared__ float red[256];
+  float s = 0.f;
+  for (int64_t e = static_cast<int64_t>(blockIdx.x) * 256 + threadIdx.x; e < n; e += static_cast<int64_t>(gridDim.x) * 256) {
+    const float d = Y[e] - T[e];
+    dY[e] = __float2bfloat16(2.f * d * scale);
+    s = fmaf(d, d, s);
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = 128; k > 0; k >>= 1) {
+    if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void k_loss_final(int nblocks, float scale, const float *partial, float *loss) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    float s = 0.f;
+    for (int i = 0; i < nblocks; ++i) s += partial[i];
+    *loss = s * scale;
+  }
+}
+
+__global__ void k_adamw(int64_t n, float lr, float b1, float b2, float eps, float wd, float bc1, float bc2,
+                        float *__restrict__ w, const float *__restrict__ g, float *__restrict__ m, float *__restrict__ v) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  const float mh = mi / bc1, vh = vi / bc2;
+  w[i] = w[i] - lr * (mh / (sqrtf(vh) + eps) + wd * w[i]);
+}
+
+__global__ void k_to_bf16(int64_t n, const float *__restrict__ a, bf16 *b) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = __float2bfloat16(a[i]);
+}
+
+// Ensemble estimate: preds [K][B][O] -> mean [B][O], err[b] = ln(10) * sqrt(mean_o var_k),
+// the relative error of the spectrum implied by the models' spread of log10 predictions.
+__global__ void k_ensemble(int K, int64_t B, int O, const float *__restrict__ preds, float *mean, float *err) {
+  __shared__ float red[256];
+  const int64_t b = blockIdx.x;
+  float acc = 0.f;
+  for (int o = threadIdx.x; o < O; o += 256) {
+    float s = 0.f, s2 = 0.f;
+    for (int k = 0; k < K; ++k) {
+      const float p = preds[(static_cast<int64_t>(k) * B + b) * O + o];
+      s += p;
+      s2 = fmaf(p, p, s2);
+    }
+    const float mu = s / K;
+    mean[b * O + o] = mu;
+    acc += fmaxf(s2 / K - mu * mu, 0.f) * (K > 1 ? static_cast<float>(K) / (K - 1) : 0.f);
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int k = 128; k > 0; k >>= 1) {
+    if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) err[b] = 2.302585093f * sqrtf(red[0] / O);
+}
+
+// Label transform: out = log10(max(v, floor)) (FP64 in, FP32 out)
+__global__ void k_log_targets(int64_t n, double floor_v, const double *__restrict__ v, float *out) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = static_cast<float>(log10(fmax(v[i], floor_v)));
+}
+
+// Per-column mean and standard deviation of y [rows][cols] (FP64 accumulation).
+__global__ void k_colstats(int64_t rows, int cols, const float *__restrict__ y, float *mean, float *stdv) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cols) return;
+  double s = 0.0, s2 = 0.0;
+  for (int64_t r = 0; r < rows; ++r) {
+    const double v = y[r * cols + c];
+    s += v;
+    s2 += v * v;
+  }
+  const double mu = rows > 0 ? s / rows : 0.0;
+  const double var = rows > 1 ? (s2 - rows * mu * mu) / (rows - 1) : 0.0;
+  mean[c] = static_cast<float>(mu);
+  stdv[c] = static_cast<float>(sqrt(fmax(var, 1e-12)));
+}
+
+__global__ void k_standardize(int64_t rows, int cols, float *y, const float *mean, const float *stdv, int inverse) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= rows * cols) return;
+  const int c = static_cast<int>(i % cols);
+  y[i] = inverse ? y[i] * stdv[c] + mean[c] : (y[i] - mean[c]) / stdv[c];
+}
+
+inline unsigned nblk(int64_t n, int t = 256) { return static_cast<unsigned>((n + t - 1) / t); }
+
+}  // namespace
+}  // namespace rad
+
+using namespace rad;
+
+struct rad_mlp_s {
+  int n_in = 0, width = 0, depth = 0, n_out = 0;
+  int64_t max_batch = 0;
+  int64_t n_params = 0;
+  // parameter layout in the FP32 buffers: W1 [width][n_in], b1, then for l = 2..depth
+  // W_l [width][width], b_l, then W_out [n_out][width], b_out
+  std::vector<int64_t> w_off, b_off;  // per layer (depth + 1 layers)
+  float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
+  bf16 *wb = nullptr;                  // BF16 copy of all weights (same offsets)
+  float *Z = nullptr;                  // pre-activations [depth][max_batch][width]
+  bf16 *H = nullptr;                   // activations [depth][max_batch][width]
+  bf16 *dZ = nullptr;                  // [2][max_batch][width] ping-pong
+  float *Y = nullptr;                  // [max_batch][n_out]
+  bf16 *dY = nullptr;                  // [max_batch][n_out]
+  float *partial = nullptr;            // loss partials [1024]
+  int64_t step = 0;
+};
+
+namespace {
+
+int64_t layer_in(const rad_mlp_s *h, int l) { return l == 0 ? h->n_in : h->width; }
+int64_t layer_out(const rad_mlp_s *h, int l) { return l == h->depth ? h->n_out : h->width; }
+
+cudaError_t forward_impl(rad_mlp h, const float *x, int64_t B, float *y_out, bool keep, cudaStream_t st) {
+  const int W = h->width, D = h->depth, O = h->n_out;
+  float *Z = keep ? h->Z : nullptr;
+  k_layer1<<<nblk(B * W), 256, 0, st>>>(B, h->n_in, W, x, h->w + h->w_off[0], h->w + h->b_off[0], Z, h->H);
+  cudaError_t e = cudaGetLastError();
+  for (int l = 1; l < D && e == cudaSuccess; ++l) {
+    const bf16 *Hin = h->H + static_cast<int64_t>(l - 1) * h->max_batch * W;
+    EpiHidden epi{h->w + h->b_off[l], keep ? h->Z + static_cast<int64_t>(l) * h->max_batch * W : nullptr,
+                  h->H + static_cast<int64_t>(l) * h->max_batch * W, W};
+    e = gemm<true, true>(static_cast<int>(B), W, W, Hin, W, h->wb + h->w_off[l], W, epi, st);
+  }
+  if (e != cudaSuccess) return e;
+  const bf16 *Hlast = h->H + static_cast<int64_t>(D - 1) * h->max_batch * W;
+  EpiOut epo{h->w + h->b_off[D], y_out, O};
+  return gemm<true, true>(static_cast<int>(B), O, W, Hlast, W, h->wb + h->w_off[D], W, epo, st);
+}
+
+cudaError_t backward_impl(rad_mlp h, const float *x, const float *target, int64_t B, float *loss, cudaStream_t st) {
+  const int W = h->width, D = h->depth, O = h->n_out;
+  cudaError_t e = forward_impl(h, x, B, h->Y, true, st);
+  if (e != cudaSuccess) return e;
+  const int64_t n = B * O;
+  int nb = static_cast<int>(std::min<int64_t>(1024, (n + 255) / 256));
+  const float scale = 1.f / static_cast<float>(n);
+  k_loss<<<nb, 256, 0, st>>>(n, scale, h->Y, target, h->dY, h->partial);
+  if (loss) k_loss_final<<<1, 32, 0, st>>>(nb, scale, h->partial, loss);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // output layer: dW_out = dY^T H_last, db_out = colsum(dY), dH = dY W_out
+  const bf16 *Hlast = h->H + static_cast<int64_t>(D - 1) * h->max_batch * W;
+  EpiStore gW{h->g + h->w_off[D], W};
+  e = gemm<false, false>(O, W, static_cast<int>(B), h->dY, O, Hlast, W, gW, st);
+  if (e != cudaSuccess) return e;
+  k_colsum<<<nblk(O), 256, 0, st>>>(B, O, h->dY, h->g + h->b_off[D]);
+  int cur = 0;
+  {
+    EpiGradAct ga{h->Z + static_cast<int64_t>(D - 1) * h->max_batch * W, h->dZ, W};
+    e = gemm<true, false>(static_cast<int>(B), W, O, h->dY, O, h->wb + h->w_off[D], W, ga, st);
+    if (e != cudaSuccess) return e;
+  }
+  for (int l = D - 1; l >= 1; --l) {
+    const bf16 *dZl = h->dZ + static_cast<int64_t>(cur) * h->max_batch * W;
+    const bf16 *Hin = h->H + static_cast<int64_t>(l - 1) * h->max_batch * W;
+    EpiStore gw{h->g + h->w_off[l], W};
+    e = gemm<false, false>(W, W, static_cast<int>(B), dZl, W, Hin, W, gw, st);
+    if (e != cudaSuccess) return e;
+    k_colsum<<<nblk(W), 256, 0, st>>>(B, W, dZl, h->g + h->b_off[l]);
+    bf16 *dZn = h->dZ + static_cast<int64_t>(cur ^ 1) * h->max_batch * W;
+    EpiGradAct ga{h->Z + static_cast<int64_t>(l - 1) * h->max_batch * W, dZn, W};
+    e = gemm<true, false>(static_cast<int>(B), W, W, dZl, W, h->wb + h->w_off[l], W, ga, st);
+    if (e != cudaSuccess) return e;
+    cur ^= 1;
+  }
+  const bf16 *dZ1 = h->dZ + static_cast<int64_t>(cur) * h->max_batch * W;
+  k_layer1_grad<<<nblk(static_cast<int64_t>(W) * h->n_in), 256, 0, st>>>(B, h->n_in, W, x, dZ1, h->g + h->w_off[0]);
+  k_colsum<<<nblk(W), 256, 0, st>>>(B, W, dZ1, h->g + h->b_off[0]);
+  return cudaGetLastError();
+}
+
+void mlp_free(rad_mlp h) {
+  if (!h) return;
+  cudaFree(h->w);
+  cudaFree(h->g);
+  cudaFree(h->m);
+  cudaFree(h->v);
+  cudaFree(h->wb);
+  cudaFree(h->Z);
+  cudaFree(h->H);
+  cudaFree(h->dZ);
+  cudaFree(h->Y);
+  cudaFree(h->dY);
+  cudaFree(h->partial);
+  delete h;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rad_mlp_create(int n_in, int width, int depth, int n_out, int64_t max_batch, uint64_t seed, rad_mlp *out) {
+  if (!out || n_in < 1 || width < 1 || depth < 1 || n_out < 1 || max_batch < 1) return RAD_EINVAL;
+  if (width % 2 || n_out % 2 || width > 8192 || n_out > (1 << 16) || n_in > 64) return RAD_EINVAL;
+  *out = nullptr;
+  rad_mlp h = new rad_mlp_s();
+  h->n_in = n_in;
+  h->width = width;
+  h->depth = depth;
+  h->n_out = n_out;
+  h->max_batch = max_batch;
+  int64_t off = 0;
+  for (int l = 0; l <= depth; ++l) {
+    h->w_off.push_back(off);
+    off += layer_in(h, l) * layer_out(h, l);
+    h->b_off.push_back(off);
+    off += layer_out(h, l);
+  }
+  h->n_params = off;
+  const size_t pb = sizeof(float) * off;
+  bool ok = cudaMalloc(&h->w, pb) == cudaSuccess && cudaMalloc(&h->g, pb) == cudaSuccess &&
+            cudaMalloc(&h->m, pb) == cudaSuccess && cudaMalloc(&h->v, pb) == cudaSuccess &&
+            cudaMalloc(&h->wb, sizeof(bf16) * off) == cudaSuccess &&
+            cudaMalloc(&h->Z, sizeof(float) * depth * max_batch * width) == cudaSuccess &&
+            cudaMalloc(&h->H, sizeof(bf16) * depth * max_batch * width) == cudaSuccess &&
+            cudaMalloc(&h->dZ, sizeof(bf16) * 2 * max_batch * width) == cudaSuccess &&
+            cudaMalloc(&h->Y, sizeof(float) * max_batch * n_out) == cudaSuccess &&
+            cudaMalloc(&h->dY, sizeof(bf16) * max_batch * n_out) == cudaSuccess &&
+            cudaMalloc(&h->partial, sizeof(float) * 1024) == cudaSuccess;
+  if (!ok) {
+    mlp_free(h);
+    return RAD_ENOMEM;
+  }
+  // initialisation: weights uniform in +-1/sqrt(fan_in) (seeded), biases 0
+  std::vector<float> hw(off, 0.f);
+  std::mt19937_64 rng(seed);
+  for (int l = 0; l <= depth; ++l) {
+    const double bound = 1.0 / std::sqrt(static_cast<double>(layer_in(h, l)));
+    std::uniform_real_distribution<double> U(-bound, bound);
+    for (int64_t i = 0; i < layer_in(h, l) * layer_out(h, l); ++i) hw[h->w_off[l] + i] = static_cast<float>(U(rng));
+  }
+  ok = cudaMemcpy(h->w, hw.data(), pb, cudaMemcpyHostToDevice) == cudaSuccess &&
+       cudaMemset(h->m, 0, pb) == cudaSuccess && cudaMemset(h->v, 0, pb) == cudaSuccess &&
+       cudaMemset(h->g, 0, pb) == cudaSuccess;
+  if (ok) {
+    k_to_bf16<<<nblk(off), 256>>>(off, h->w, h->wb);
+    ok = cudaDeviceSynchronize() == cudaSuccess;
+  }
+  if (!ok) {
+    mlp_free(h);
+    return RAD_ECUDA;
+  }
+  *out = h;
+  return RAD_OK;
+}
+
+int rad_mlp_destroy(rad_mlp h) {
+  cudaDeviceSynchronize();
+  mlp_free(h);
+  return RAD_OK;
+}
+
+int64_t rad_mlp_num_params(rad_mlp h) { return h ? h->n_params : 0; }
+
+int rad_mlp_forward(rad_mlp h, const float *x, int64_t batch, float *y, void *stream) {
+  if (!h || !x || !y || batch < 0) return RAD_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (int64_t b0 = 0; b0 < batch; b0 += h->max_batch) {
+    const int64_t nb = std::min<int64_t>(h->max_batch, batch - b0);
+    if (forward_impl(h, x + b0 * h->n_in, nb, y + b0 * h->n_out, false, st) != cudaSuccess) return RAD_ECUDA;
+  }
+  return RAD_OK;
+}
+
+int rad_mlp_backward(rad_mlp h, const float *x, const float *target, int64_t batch, float *loss, void *stream) {
+  if (!h || !x || !target || batch < 1 || batch > h->max_batch) return RAD_EINVAL;
+  return backward_impl(h, x, target, batch, loss, static_cast<cudaStream_t>(stream)) == cudaSuccess ? RAD_OK
+                                                                                                   : RAD_ECUDA;
+}
+
+int rad_mlp_adamw(rad_mlp h, float lr, float beta1, float beta2, float eps, float weight_decay, void *stream) {
+  if (!h || !(lr >= 0.f) || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f))
+    return RAD_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  h->step += 1;
+  const float bc1 = 1.f - powf(beta1, static_cast<float>(h->step));
+  const float bc2 = 1.f - powf(beta2, static_cast<float>(h->step));
+  k_adamw<<<nblk(h->n_params), 256, 0, st>>>(h->n_params, lr, beta1, beta2, eps, weight_decay, bc1, bc2, h->w, h->g,
+                                             h->m, h->v);
+  k_to_bf16<<<nblk(h->n_params), 256, 0, st>>>(h->n_params, h->w, h->wb);
+  return cudaGetLastError() == cudaSuccess ? RAD_OK : RAD_ECUDA;
+}
+
+int rad_mlp_train_step(rad_mlp h, const float *x, const float *target, int64_t batch, float lr, float weight_decay,
+                       float *loss, void *stream) {
+  int rc = rad_mlp_backward(h, x, target, batch, loss, stream);
+  if (rc) return rc;
+  return rad_mlp_adamw(h, lr, 0.9f, 0.999f, 1e-8f, weight_decay, stream);
+}
+
+int rad_mlp_get(rad_mlp h, int what, float *host_out) {
+  if (!h || !host_out || what < 0 || what > 3) return RAD_EINVAL;
+  const float *src = what == 0 ? h->w : what == 1 ? h->g : what == 2 ? h->m : h->v;
+  return cudaMemcpy(host_out, src, sizeof(float) * h->n_params, cudaMemcpyDeviceToHost) == cudaSuccess ? RAD_OK
+                                                                                                         : RAD_ECUDA;
+}
+
+int rad_mlp_set_params(rad_mlp h, const float *host_in) {
+  if (!h || !host_in) return RAD_EINVAL;
+  if (cudaMemcpy(h->w, host_in, sizeof(float) * h->n_params, cudaMemcpyHostToDevice) != cudaSuccess) return RAD_ECUDA;
+  k_to_bf16<<<nblk(h->n_params), 256>>>(h->n_params, h->w, h->wb);
+  return cudaDeviceSynchronize() == cudaSuccess ? RAD_OK : RAD_ECUDA;
+}
+
+int rad_mlp_ensemble_estimate(const float *preds, int n_models, int64_t batch, int n_out, float *mean, float *err,
+                              void *stream) {
+  if (!preds || !mean || !err || n_models < 1 || batch < 0 || n_out < 1) return RAD_EINVAL;
+  if (batch == 0) return RAD_OK;
+  k_ensemble<<<static_cast<unsigned>(batch), 256, 0, static_cast<cudaStream_t>(stream)>>>(n_models, batch, n_out,
+                                                                                         preds, mean, err);
+  return cudaGetLastError() == cudaSuccess ? RAD_OK : RAD_ECUDA;
+}
+
+int rad_log_targets(const double *values, int64_t n, double floor_value, float *out, void *stream) {
+  if (!values || !out || n < 0 || !(floor_value > 0.0)) return RAD_EINVAL;
+  if (n == 0) return RAD_OK;
+  k_log_targets<<<nblk(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(n, floor_value, values, out);
+  return cudaGetLastError() == cudaSuccess ? RAD_OK : RAD_ECUDA;
+}
+
+int rad_column_stats(const float *y, int64_t rows, int cols, float *mean, float *stdv, void *stream) {
+  if (!y || !mean || !stdv || rows < 0 || cols < 1) return RAD_EINVAL;
+  k_colstats<<<nblk(cols), 256, 0, static_cast<cudaStream_t>(stream)>>>(rows, cols, y, mean, stdv);
+  return cudaGetLastError() == cudaSuccess ? RAD_OK : RAD_ECUDA;
+}
+
+int rad_standardize(float *y, int64_t rows, int cols, const float *mean, const float *stdv, int inverse,
+                    void *stream) {
+  if (!y || !mean || !stdv || rows < 0 || cols < 1) return RAD_EINVAL;
+  if (rows == 0) return RAD_OK;
+  k_standardize<<<nblk(rows * cols), 256, 0, static_cast<cudaStream_t>(stream)>>>(rows, cols, y, mean, stdv,
+                                                                                 inverse ? 1 : 0);
+  return cudaGetLastError() == cudaSuccess ? RAD_OK : RAD_ECUDA;
+}
+
+}  // extern "C"

@@ -162,6 +162,46 @@ __global__ void k_reduce(const Params P, const double *cube_new, const double *d
   }
 }
 
+// Per-particle angle integral and radial bins (S-mode partials, one chunk per particle).
+// Block (32 energies) x (8 direction lanes); grid (energy tiles, particles).
+constexpr int kMaxBinsPP = 16;
+__global__ void k_reduce_particles(const Params P, const double *d_omega, double *out_spectrum,
+                                   const int32_t *bin_of_angle, int n_bins, double *out_bins,
+                                   int *dev_status) {
+  __shared__ double acc[kMaxBinsPP + 1][8][32];
+  const int st = *reinterpret_cast<volatile int *>(P.status);
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0 && st != 0)
+    atomicCAS(dev_status, 0, st);
+  if (st != 0) return;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int64_t p = blockIdx.y;
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * 32 + tx;
+  const double pref = kAlpha / (4.0 * kPi * kPi);
+  for (int b = 0; b <= kMaxBinsPP; ++b) acc[b][ty][tx] = 0.0;
+  if (i < P.n_omega) {
+    for (int64_t j = ty; j < P.n_angles; j += 8) {
+      const double v = P.part[(p * P.n_angles + j) * P.n_omega + i] * d_omega[j];
+      acc[kMaxBinsPP][ty][tx] += v;
+      if (bin_of_angle) {
+        const int32_t b = bin_of_angle[j];
+        if (b >= 0 && b < n_bins) acc[b][ty][tx] += v;
+      }
+    }
+  }
+  __syncthreads();
+  if (ty == 0 && i < P.n_omega) {
+    double s = 0.0;
+    for (int l = 0; l < 8; ++l) s += acc[kMaxBinsPP][l][tx];
+    if (out_spectrum) out_spectrum[p * P.n_omega + i] = pref * s;
+    if (out_bins)
+      for (int b = 0; b < n_bins; ++b) {
+        double sb = 0.0;
+        for (int l = 0; l < 8; ++l) sb += acc[b][l][tx];
+        out_bins[(p * P.n_omega + i) * n_bins + b] = pref * sb;
+      }
+  }
+}
+
 std::mutex g_mu;
 struct DevRes {
   double2 *table = nullptr;
@@ -281,6 +321,19 @@ cudaError_t launch_reduce(const Params &P, const double *cube_new, const double 
   if (P.n_omega == 0 || (!out_spectrum && !out_bins)) return cudaSuccess;
   k_reduce<<<static_cast<unsigned>(P.n_omega), 256, 0, st>>>(P, cube_new, d_omega, out_spectrum,
                                                            bin_of_angle, n_bins, out_bins, accumulate);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_particles(const Params &P, const double *d_omega, double *out_spectrum,
+                                   const int32_t *bin_of_angle, int n_bins, double *out_bins, cudaStream_t st) {
+  if (P.amp_mode || n_bins > kMaxBinsPP) return cudaErrorInvalidValue;
+  if (P.n_omega == 0 || P.n_particles == 0) return cudaSuccess;
+  cudaError_t e;
+  int *ds = device_status_word(&e);
+  if (!ds) return e;
+  dim3 blk(32, 8);
+  dim3 grd(static_cast<unsigned>((P.n_omega + 31) / 32), static_cast<unsigned>(P.n_particles));
+  k_reduce_particles<<<grd, blk, 0, st>>>(P, d_omega, out_spectrum, bin_of_angle, n_bins, out_bins, ds);
   return cudaGetLastError();
 }
 

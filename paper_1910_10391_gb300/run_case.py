@@ -27,6 +27,10 @@ def main(argv=None):
     ap.add_argument("--shape", default="", help="R,NW,T,chunk_mult")
     ap.add_argument("--repeat", type=int, default=2)
     ap.add_argument("--graph", action="store_true", help="replay a captured CUDA graph")
+    ap.add_argument("--autotune-subset", type=int, default=0,
+                    help="autotune the launch shape on the first N particles and apply it")
+    ap.add_argument("--seed", type=int, default=0, help="generator seed (0: the workload's own)")
+    ap.add_argument("--prepass", type=int, default=-1, help="mixed precision: 1 pre-pass kernel, 0 inline")
     a = ap.parse_args(argv)
 
     import torch
@@ -35,17 +39,37 @@ def main(argv=None):
     from paper_1910_10391_gb300 import inputs as I
 
     if a.workload == "ensemble":
-        tr = I.channeling(a.particles, 10e9, +1, a.samples, 5e-9, seed=2)
+        tr = I.channeling(a.particles, 10e9, +1, a.samples, 5e-9, seed=a.seed or 2)
         grid = I._ensemble_grid(10e9, 20.0, a.n_omega, a.n_side)
     elif a.workload == "batch":
-        L = I.lognormal_lengths(a.particles, seed=4)
-        tr = I.channeling(a.particles, 20e9, -1, L, 5e-9, seed=4)
+        L = I.lognormal_lengths(a.particles, seed=a.seed or 4)
+        tr = I.channeling(a.particles, 20e9, -1, L, 5e-9, seed=a.seed or 4)
         grid = I._ensemble_grid(20e9, 20.0, a.n_omega, a.n_side)
     else:
         tr, grid = I.workload_undulator_4096()
     inp = rad.DeviceInputs(tr, grid)
     mode, prec = rad.MODES[a.mode], rad.PRECISIONS[a.precision]
     plan = rad.Plan(inp.n_samples, inp.n_particles, inp.n_omega, inp.n_angles, mode, prec, 1, 0)
+    tuned = None
+    if a.autotune_subset > 0:
+        sub = tr.subset(range(min(a.autotune_subset, tr.n_particles)))
+        si = rad.DeviceInputs(sub, grid)
+        tp = rad.Plan(si.n_samples, si.n_particles, si.n_omega, si.n_angles, mode, prec, 1, 0)
+        tmp = torch.empty(si.n_omega * si.n_angles, dtype=torch.float64, device="cuda")
+        rc = tp.autotune(*si.args(), tmp, None, None, None, budget_ms=120000)
+        if rc:
+            raise rad.RadError(rc, "autotune")
+        d = dict(kv.split("=") for kv in tp.describe().split())
+        tuned = (int(d["R"]), int(d["NW"]), int(d["T"]), 1)
+        tp.close()
+        del si, tmp
+        rc = plan.set_shape(*tuned)
+        if rc:
+            raise rad.RadError(rc, "set_shape")
+    if a.prepass >= 0:
+        rc = plan.set_prepass(a.prepass)
+        if rc:
+            raise rad.RadError(rc, "set_prepass")
     if a.shape:
         rc = plan.set_shape(*[int(x) for x in a.shape.split(",")])
         if rc:
@@ -70,7 +94,8 @@ def main(argv=None):
     terms = int(tr.lengths().sum()) * inp.n_omega * inp.n_angles
     best = min(times)
     print(json.dumps({"case": vars(a), "shape": plan.describe(), "terms": terms, "ms": times,
-                      "terms_per_s": terms / (best * 1e-3), "checksum": float(out.sum().item())}))
+                      "terms_per_s": terms / (best * 1e-3), "spectra_per_s": tr.n_particles / (best * 1e-3),
+                      "samples_total": int(tr.lengths().sum()), "checksum": float(out.sum().item())}))
     if g:
         g.close()
     plan.close()

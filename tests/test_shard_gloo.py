@@ -1,0 +1,76 @@
+"""Multi-rank particle sharding on CPU: 2 gloo ranks, each sums its particle range with the FP64
+oracle, one all-reduce; the result equals the oracle on the whole ensemble."""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+from paper_1910_10391_gb300 import shard
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, out):
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import oracle as O
+    from paper_1910_10391_gb300 import inputs as I
+    from paper_1910_10391_gb300 import shard as S
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    tr = I.channeling(7, 10e9, +1, 300, 5e-9, seed=21)
+    tr.weight = np.full(7, 1.0 / 7)
+    grid = I._ensemble_grid(10e9, 20.0, 6, 4)
+    p0, p1 = S.particle_range(tr.n_particles, world, rank)
+    part = O.spectrum_cube(tr.subset(range(p0, p1)), grid, O.CLASSICAL) if p1 > p0 else np.zeros((6, 16))
+    t = torch.from_numpy(part.copy())
+    S.allreduce_sum(t)
+    if rank == 0:
+        out.put(t.numpy())
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_rank_particle_shards_sum_to_ensemble():
+    import oracle as O
+    from paper_1910_10391_gb300 import inputs as I
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    tr = I.channeling(7, 10e9, +1, 300, 5e-9, seed=21)
+    tr.weight = np.full(7, 1.0 / 7)
+    ref = O.spectrum_cube(tr, I._ensemble_grid(10e9, 20.0, 6, 4), O.CLASSICAL)
+    np.testing.assert_allclose(got, ref, rtol=1e-12)
+
+
+def test_partition_and_batches():
+    for n, w in [(7, 2), (1024, 8), (3, 4)]:
+        ranges = [shard.particle_range(n, w, r) for r in range(w)]
+        assert ranges[0][0] == 0 and ranges[-1][1] == n
+        assert all(a[1] == b[0] for a, b in zip(ranges, ranges[1:]))
+        assert max(b - a for a, b in ranges) - min(b - a for a, b in ranges) <= 1
+    seen = set()
+    for r in range(4):
+        p0, p1 = shard.step_batch(3, r, 4, 32, 1024)
+        assert p1 - p0 == 32 and p0 not in seen
+        seen.add(p0)
+    with pytest.raises(ValueError):
+        shard.particle_range(5, 2, 2)
