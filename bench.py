@@ -338,15 +338,17 @@ def main():
     terms_launch = terms_of(B, grid)
     sfu_ops = 2.0 * terms_launch / (kernel_ms_avg * 1e-3)     # one sin and one cos per term
     sfu_peak = SM_COUNT * SFU_PER_SM_CLK * SM_MAX_MHZ * 1e6
-    # DRAM bytes per launch, scaled from the ncu capture of this kernel on a small case of the same
-    # workload (128 particles x 20000 samples x 64 hw x 256 directions, 38 particle chunks:
-    # 206.2 MB read, 6.89 MB written): reads grow with the samples a launch processes, writes with
-    # the partial sums it stores (chunks x bins).
+    # DRAM bytes per launch of the integral kernel (k_mixed_pp), scaled from its ncu capture on a
+    # small case of the same workload (128 particles x 20000 samples x 64 hw x 256 directions,
+    # 38 particle chunks: 124.9 MB read = the 48-byte pre-pass records once, 6.04 MB written):
+    # reads grow with the samples a launch processes, writes with the partial sums it stores.
     samples_launch = B * N_SAMP
-    chunks = int(dict(kv.split("=") for kv in mixed_desc[modes[0]].split())["chunks"])
-    traffic = (206.2e6 * samples_launch / (128 * N_SAMP)
-               + 6.89e6 * (chunks * no * na) / (38 * 64 * 256))
-    roofline = {"bound": "alu", "pipe": "sfu", "kernel": "k_mixed", "achieved": sfu_ops / 1e12,
+    desc0 = dict(kv.split("=") for kv in mixed_desc[modes[0]].split())
+    chunks = int(desc0["chunks"])
+    traffic = (124.9e6 * samples_launch / (128 * N_SAMP)
+               + 6.04e6 * (chunks * no * na) / (38 * 64 * 256)) if desc0.get("pp") == "1" else None
+    roofline = {"bound": "alu", "pipe": "sfu",
+                "kernel": "k_mixed_pp" if desc0.get("pp") == "1" else "k_mixed", "achieved": sfu_ops / 1e12,
                 "peak": sfu_peak / 1e12, "unit": "Tops/s", "frac": sfu_ops / sfu_peak,
                 "traffic": traffic, "traffic_source": "ncu dram__bytes_read/write.sum of a small case, scaled",
                 "terms_per_launch": terms_launch, "kernel_ms_avg": kernel_ms_avg,

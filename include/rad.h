@@ -285,18 +285,20 @@ int64_t rad_mlp_num_params(rad_mlp mlp);
 /* rad_mlp_forward -- y [batch][n_out] = network(x [batch][n_in]); any batch size. */
 int rad_mlp_forward(rad_mlp mlp, const float *x, int64_t batch, float *y, void *stream);
 
-/* rad_mlp_backward -- forward pass, loss = mean((y - target)^2) written to *loss (device, may be
- * NULL) and the gradient of the loss w.r.t. every parameter kept in the network (batch <= max_batch). */
-int rad_mlp_backward(rad_mlp mlp, const float *x, const float *target, int64_t batch, float *loss,
-                     void *stream);
+/* rad_mlp_backward -- forward pass, loss = mean(mask (y - target)^2) over all batch x n_out
+ * elements written to *loss (device, may be NULL), and the gradient of the loss w.r.t. every
+ * parameter kept in the network (batch <= max_batch). mask [batch][n_out] of 0/1 weights, or
+ * NULL for all ones (masked elements contribute nothing). */
+int rad_mlp_backward(rad_mlp mlp, const float *x, const float *target, const float *mask, int64_t batch,
+                     float *loss, void *stream);
 
 /* rad_mlp_adamw -- one AdamW update of all parameters from the stored gradients. */
 int rad_mlp_adamw(rad_mlp mlp, float lr, float beta1, float beta2, float eps, float weight_decay,
                   void *stream);
 
 /* rad_mlp_train_step -- rad_mlp_backward then rad_mlp_adamw (beta 0.9/0.999, eps 1e-8). */
-int rad_mlp_train_step(rad_mlp mlp, const float *x, const float *target, int64_t batch, float lr,
-                       float weight_decay, float *loss, void *stream);
+int rad_mlp_train_step(rad_mlp mlp, const float *x, const float *target, const float *mask, int64_t batch,
+                       float lr, float weight_decay, float *loss, void *stream);
 
 /* rad_mlp_get -- copies parameters (what 0), gradients (1) or Adam moments (2, 3) to host_out
  * [rad_mlp_num_params]. Layout per layer l = 0..depth: W_l [out][in] row-major, then b_l [out]. */

@@ -51,14 +51,15 @@ def forward(params, x, n_in, width, depth, n_out, keep=False):
     return (y, zs, hs) if keep else y
 
 
-def loss_and_grad(params, x, t, n_in, width, depth, n_out):
-    """(loss, flat gradient) of mean((y - t)^2) over all batch x output elements."""
+def loss_and_grad(params, x, t, n_in, width, depth, n_out, mask=None):
+    """(loss, flat gradient) of mean(mask (y - t)^2) over all batch x output elements."""
     layers = unpack(params, n_in, width, depth, n_out)
     y, zs, hs = forward(params, x, n_in, width, depth, n_out, keep=True)
     t = np.asarray(t, dtype=np.float64)
+    m = np.ones_like(y) if mask is None else np.asarray(mask, dtype=np.float64)
     n = y.size
-    loss = float(np.sum((y - t) ** 2) / n)
-    d = 2.0 * (y - t) / n
+    loss = float(np.sum(m * (y - t) ** 2) / n)
+    d = 2.0 * m * (y - t) / n
     grads = [None] * len(layers)
     for l in range(len(layers) - 1, -1, -1):
         W, _ = layers[l]

@@ -79,11 +79,11 @@ def load(build_if_missing: bool = True):
         lib.rad_mlp_num_params.restype = i64
         lib.rad_mlp_forward.argtypes = [P, P, i64, P, P]
         lib.rad_mlp_forward.restype = c_int
-        lib.rad_mlp_backward.argtypes = [P, P, P, i64, P, P]
+        lib.rad_mlp_backward.argtypes = [P, P, P, P, i64, P, P]
         lib.rad_mlp_backward.restype = c_int
         lib.rad_mlp_adamw.argtypes = [P, f32, f32, f32, f32, f32, P]
         lib.rad_mlp_adamw.restype = c_int
-        lib.rad_mlp_train_step.argtypes = [P, P, P, i64, f32, f32, P, P]
+        lib.rad_mlp_train_step.argtypes = [P, P, P, P, i64, f32, f32, P, P]
         lib.rad_mlp_train_step.restype = c_int
         lib.rad_mlp_get.argtypes = [P, c_int, P]
         lib.rad_mlp_get.restype = c_int
@@ -277,10 +277,11 @@ class MLP:
             raise RadError(rc, "rad_mlp_forward")
         return y
 
-    def backward(self, x, t, loss=None, stream=None):
+    def backward(self, x, t, loss=None, mask=None, stream=None):
         import torch
         rc = load().rad_mlp_backward(self._h, _dev_ptr(x, torch.float32, "x"), _dev_ptr(t, torch.float32, "t"),
-                                     int(x.shape[0]), _dev_ptr(loss, torch.float32, "loss"), _stream(stream))
+                                     _dev_ptr(mask, torch.float32, "mask"), int(x.shape[0]),
+                                     _dev_ptr(loss, torch.float32, "loss"), _stream(stream))
         if rc:
             raise RadError(rc, "rad_mlp_backward")
 
@@ -290,11 +291,11 @@ class MLP:
         if rc:
             raise RadError(rc, "rad_mlp_adamw")
 
-    def train_step(self, x, t, lr, weight_decay=0.0, loss=None, stream=None):
+    def train_step(self, x, t, lr, weight_decay=0.0, loss=None, mask=None, stream=None):
         import torch
         rc = load().rad_mlp_train_step(self._h, _dev_ptr(x, torch.float32, "x"), _dev_ptr(t, torch.float32, "t"),
-                                       int(x.shape[0]), float(lr), float(weight_decay),
-                                       _dev_ptr(loss, torch.float32, "loss"), _stream(stream))
+                                       _dev_ptr(mask, torch.float32, "mask"), int(x.shape[0]), float(lr),
+                                       float(weight_decay), _dev_ptr(loss, torch.float32, "loss"), _stream(stream))
         if rc:
             raise RadError(rc, "rad_mlp_train_step")
 

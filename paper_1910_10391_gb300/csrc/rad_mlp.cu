@@ -1,7 +1,7 @@
 // Surrogate MLP for per-particle spectra: training and inference kernels.
 //
 // Network: x (n_in, FP32) -> [Linear -> GELU] x depth (width) -> Linear -> y (n_out, FP32).
-// The first layer (n_in = 3 inputs) runs in FP32 so the entry conditions are not quantized;
+// The first layer (the input features, n_in <= 64) runs in FP32 so inputs are not quantized;
 // every other layer is a BF16 x BF16 -> FP32 tensor-core GEMM (mma.sync m16n8k16) with the
 // bias, GELU (exact erf form) and their derivatives fused into the GEMM epilogues. FP32 master
 // weights are updated by AdamW (Loshchilov & Hutter, "Decoupled weight decay
@@ -196,13 +196,14 @@ __global__ void k_colsum(int64_t rows, int cols, const bf16 *__restrict__ dZ, fl
   db[n] = s;
 }
 
-// Loss and output gradient: dY = bf16(2 (Y - T) / (B O)); per-block squared-error partials.
-__global__ void k_loss(int64_t n, float scale, const float *__restrict__ Y, const float *__restrict__ T, bf16 *dY,
-                       float *partial) {
+// Loss and output gradient: dY = bf16(2 m (Y - T) / (B O)) with the optional 0/1 mask m;
+// per-block squared-error partials.
+__global__ void k_loss(int64_t n, float scale, const float *__restrict__ Y, const float *__restrict__ T,
+                       const float *__restrict__ mask, bf16 *dY, float *partial) {
   __shared__ float red[256];
   float s = 0.f;
   for (int64_t e = static_cast<int64_t>(blockIdx.x) * 256 + threadIdx.x; e < n; e += static_cast<int64_t>(gridDim.x) * 256) {
-    const float d = Y[e] - T[e];
+    const float d = mask ? (Y[e] - T[e]) * mask[e] : (Y[e] - T[e]);
     dY[e] = __float2bfloat16(2.f * d * scale);
     s = fmaf(d, d, s);
   }
@@ -343,14 +344,15 @@ cudaError_t forward_impl(rad_mlp h, const float *x, int64_t B, float *y_out, boo
   return gemm<true, true>(static_cast<int>(B), O, W, Hlast, W, h->wb + h->w_off[D], W, epo, st);
 }
 
-cudaError_t backward_impl(rad_mlp h, const float *x, const float *target, int64_t B, float *loss, cudaStream_t st) {
+cudaError_t backward_impl(rad_mlp h, const float *x, const float *target, const float *mask, int64_t B, float *loss,
+                          cudaStream_t st) {
   const int W = h->width, D = h->depth, O = h->n_out;
   cudaError_t e = forward_impl(h, x, B, h->Y, true, st);
   if (e != cudaSuccess) return e;
   const int64_t n = B * O;
   int nb = static_cast<int>(std::min<int64_t>(1024, (n + 255) / 256));
   const float scale = 1.f / static_cast<float>(n);
-  k_loss<<<nb, 256, 0, st>>>(n, scale, h->Y, target, h->dY, h->partial);
+  k_loss<<<nb, 256, 0, st>>>(n, scale, h->Y, target, mask, h->dY, h->partial);
   if (loss) k_loss_final<<<1, 32, 0, st>>>(nb, scale, h->partial, loss);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // output layer: dW_out = dY^T H_last, db_out = colsum(dY), dH = dY W_out
@@ -477,10 +479,12 @@ int rad_mlp_forward(rad_mlp h, const float *x, int64_t batch, float *y, void *st
   return RAD_OK;
 }
 
-int rad_mlp_backward(rad_mlp h, const float *x, const float *target, int64_t batch, float *loss, void *stream) {
+int rad_mlp_backward(rad_mlp h, const float *x, const float *target, const float *mask, int64_t batch, float *loss,
+                     void *stream) {
   if (!h || !x || !target || batch < 1 || batch > h->max_batch) return RAD_EINVAL;
-  return backward_impl(h, x, target, batch, loss, static_cast<cudaStream_t>(stream)) == cudaSuccess ? RAD_OK
-                                                                                                   : RAD_ECUDA;
+  return backward_impl(h, x, target, mask, batch, loss, static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? RAD_OK
+             : RAD_ECUDA;
 }
 
 int rad_mlp_adamw(rad_mlp h, float lr, float beta1, float beta2, float eps, float weight_decay, void *stream) {
@@ -496,9 +500,9 @@ int rad_mlp_adamw(rad_mlp h, float lr, float beta1, float beta2, float eps, floa
   return cudaGetLastError() == cudaSuccess ? RAD_OK : RAD_ECUDA;
 }
 
-int rad_mlp_train_step(rad_mlp h, const float *x, const float *target, int64_t batch, float lr, float weight_decay,
-                       float *loss, void *stream) {
-  int rc = rad_mlp_backward(h, x, target, batch, loss, stream);
+int rad_mlp_train_step(rad_mlp h, const float *x, const float *target, const float *mask, int64_t batch, float lr,
+                       float weight_decay, float *loss, void *stream) {
+  int rc = rad_mlp_backward(h, x, target, mask, batch, loss, stream);
   if (rc) return rc;
   return rad_mlp_adamw(h, lr, 0.9f, 0.999f, 1e-8f, weight_decay, stream);
 }

@@ -12,6 +12,15 @@ Angle grid per gamma: 32 x 32 cells over +-(theta_L + 3/gamma); radial bins of |
 [0, theta_L + 3/gamma). Motion without scattering stays in the x-z plane, so the spectrum is
 symmetric in theta_y: only the theta_y > 0 half is computed, with doubled cell solid angles.
 
+Frequency alignment: the spectra are sharp harmonic lines whose positions move with the
+transverse energy and gamma. The fundamental of the transverse motion has a closed form in the
+harmonic well (channeled: 2 theta_L/d_p; over the barrier: 2 pi theta_L/(d_p arcsin(eps^-1/2))),
+which with the mean squared transverse velocity gives the first line hw1 = 2 gamma^2 hbar c
+Omega / (1 + gamma^2 <v^2>). Because the photon-energy grid is log-uniform, shifting an entry's
+labels by the whole number of grid steps that puts hw1 at a fixed index is exact; the network
+predicts on that extended, aligned grid (masked loss outside each entry's window) and sees
+the remaining fraction of a step as an input.
+
   python -m paper_1910_10391_gb300.surrogate --train 200000 --heldout 4096
 """
 from __future__ import annotations
@@ -62,7 +71,7 @@ class Config:
 
     @property
     def n_in(self):
-        return 5 + 2 * self.n_fourier
+        return 6 + 2 * self.n_fourier
 
     @property
     def n_out(self):
@@ -98,6 +107,48 @@ def sample_entries(cfg: Config, n: int, seed: int, discrete_gamma: bool):
     return x0, th, g
 
 
+def first_line_over_E(cfg: Config, u, v, g):
+    """hw1/E of the on-axis first harmonic of the transverse motion (closed form, harmonic well)."""
+    E = g * I.ME_EV
+    thL = np.sqrt(2.0 * cfg.U0_eV / E)
+    eps = u ** 2 + (cfg.theta_frac * v) ** 2
+    over = eps > 1.0
+    es = np.where(over, eps, 2.0)                     # placeholder keeps arcsin defined below
+    asn = np.arcsin(1.0 / np.sqrt(es))
+    omega = np.where(over, 2.0 * np.pi * thL / (cfg.d_p * asn), 2.0 * thL / cfg.d_p)
+    v2 = np.where(over, thL ** 2 * (np.sqrt(np.maximum(es - 1.0, 0.0)) + es * asn) / asn, 0.5 * thL ** 2 * eps)
+    return 2.0 * g ** 2 * I.HBARC_EV_M * omega / (1.0 + g ** 2 * v2) / E
+
+
+def grid_steps(cfg: Config, ratio):
+    """Position of hw/E = ratio on the log grid, in grid steps from its first point."""
+    step = math.log(0.5 / 1e-4) / (cfg.n_omega - 1)
+    return np.log(ratio / 1e-4) / step
+
+
+def alignment(cfg: Config, uvw, g):
+    """(integer shift, fractional remainder) of each entry's first line on the photon-energy grid."""
+    pos = grid_steps(cfg, first_line_over_E(cfg, uvw[:, 0], uvw[:, 1], g))
+    sh = np.rint(pos).astype(np.int64)
+    return sh, pos - sh
+
+
+def shift_range(cfg: Config):
+    """Smallest and largest shift over the input domain (dense scan of eps and gamma)."""
+    ee = np.linspace(0.0, 1.0 + cfg.theta_frac ** 2, 801)
+    gg = np.exp(np.linspace(math.log(cfg.gamma_lo), math.log(cfg.gamma_hi), 201))
+    E2, G2 = np.meshgrid(ee, gg)
+    u = np.sqrt(E2.ravel())
+    v = np.zeros_like(u)
+    sh = np.rint(grid_steps(cfg, first_line_over_E(cfg, u, v, G2.ravel()))).astype(np.int64)
+    return int(sh.min()) - 1, int(sh.max()) + 1
+
+
+def gamma_of(cfg: Config, w):
+    lo, hi = math.log(cfg.gamma_lo), math.log(cfg.gamma_hi)
+    return np.exp(lo + 0.5 * (np.asarray(w) + 1.0) * (hi - lo))
+
+
 def raw_inputs(cfg: Config, x0, th, g):
     """(u, v, w) in [-1, 1]: 2 x0/d_p - 1, theta0/(theta_frac theta_L), scaled log gamma."""
     lo, hi = math.log(cfg.gamma_lo), math.log(cfg.gamma_hi)
@@ -111,9 +162,11 @@ def feature_map(cfg: Config, uvw):
     sin/cos(2 pi B (u, v, w)) with B ~ N(0, sigma^2) fixed by a seed (Tancik et al., NeurIPS 2020)."""
     uvw = np.asarray(uvw, dtype=np.float64)
     eps = uvw[:, 0] ** 2 + (cfg.theta_frac * uvw[:, 1]) ** 2
+    _, frac = alignment(cfg, uvw, gamma_of(cfg, uvw[:, 2]))
     B = np.random.default_rng(cfg.fourier_seed).normal(0.0, cfg.fourier_sigma, (cfg.n_fourier, 3))
     z = 2.0 * np.pi * uvw @ B.T
-    f = np.concatenate([uvw, eps[:, None] / 3.0, np.log(eps + 1e-4)[:, None] / 5.0, np.sin(z), np.cos(z)], 1)
+    f = np.concatenate([uvw, eps[:, None] / 3.0, np.log(eps + 1e-4)[:, None] / 5.0, frac[:, None],
+                        np.sin(z), np.cos(z)], 1)
     return f.astype(np.float32)
 
 
@@ -163,11 +216,24 @@ def kernel_bins(cfg: Config, x0, th, g, stream=None):
 
 
 class Surrogate:
+    """Ensemble of MLPs predicting aligned log10 spectra; see the module docstring."""
+
     def __init__(self, cfg: Config):
         self.cfg = cfg
         self.models = []
-        self.mean = self.std = None
+        self.mu = self.sigma = None
         self.floor = None
+        self.calib = 1.0
+        self.s_lo, self.s_hi = shift_range(cfg)
+        self.n_ext = cfg.n_omega + (self.s_hi - self.s_lo)
+
+    def _window_index(self, uvw, device):
+        """Column indices [n][n_out] of each entry's own 256 x 8 window in the extended output."""
+        import torch
+        sh, _ = alignment(self.cfg, uvw, gamma_of(self.cfg, uvw[:, 2]))
+        off_np = np.clip(self.s_hi - sh, 0, self.s_hi - self.s_lo).astype(np.int64)
+        off = torch.from_numpy(off_np).to(device) * self.cfg.n_rbins
+        return off[:, None] + torch.arange(self.cfg.n_out, device=device)[None, :]
 
     def fit(self, uvw, bins_dev, val_uvw=None, val_bins=None, log=None):
         """Train the ensemble on raw inputs uvw [n][3] and their per-particle bins; a validation
@@ -175,44 +241,52 @@ class Surrogate:
         import torch
         cfg = self.cfg
         n = uvw.shape[0]
-        n_val = 0 if val_uvw is None else val_uvw.shape[0]
         self.floor = float(bins_dev.max().item()) * cfg.floor_rel
         y = torch.empty((n, cfg.n_out), dtype=torch.float32, device="cuda")
         rad.rad_log_targets(bins_dev.reshape(-1).contiguous(), self.floor, y.view(-1))
-        self.mean = torch.empty(cfg.n_out, dtype=torch.float32, device="cuda")
-        self.std = torch.empty(cfg.n_out, dtype=torch.float32, device="cuda")
-        rad.rad_column_stats(y, self.mean, self.std)
-        rad.rad_standardize(y, self.mean, self.std)
-        x = torch.from_numpy(np.concatenate([feature_map(cfg, uvw), feature_map(cfg, mirrored_inputs(uvw))])).cuda()
-        y = torch.cat([y, y])
-        n = x.shape[0]
+        self.mu, self.sigma = float(y.mean().item()), float(y.std().item())
+        y = (y - self.mu) / self.sigma
+        # aligned targets and masks on the extended grid, for the entries and their mirror images
+        uvw2 = np.concatenate([uvw, mirrored_inputs(uvw)])
+        x = torch.from_numpy(feature_map(cfg, uvw2)).cuda()
+        idx = self._window_index(uvw2, "cuda")
+        n2 = uvw2.shape[0]
+        n_ext_out = self.n_ext * cfg.n_rbins
+        yt = torch.zeros((n2, n_ext_out), dtype=torch.float32, device="cuda")
+        mk = torch.zeros((n2, n_ext_out), dtype=torch.float32, device="cuda")
+        yt.scatter_(1, idx, torch.cat([y, y]))
+        mk.scatter_(1, idx, torch.ones((n2, cfg.n_out), dtype=torch.float32, device="cuda"))
+        del y
         loss = torch.zeros(1, dtype=torch.float32, device="cuda")
-        bsz = min(cfg.batch, n)
-        per_epoch = max(n // bsz, 1)
+        bsz = min(cfg.batch, n2)
+        per_epoch = max(n2 // bsz, 1)
         history = []
         for k in range(cfg.n_models):
-            m = rad.MLP(cfg.n_in, cfg.width, cfg.depth, cfg.n_out, bsz, seed=1000 + k)
+            m = rad.MLP(cfg.n_in, cfg.width, cfg.depth, n_ext_out, bsz, seed=1000 + k)
             gen = torch.Generator(device="cuda")
             gen.manual_seed(77 + k)
             perm = None
             for step in range(cfg.steps):
                 if step % per_epoch == 0:
-                    perm = torch.randperm(n, device="cuda", generator=gen)
+                    perm = torch.randperm(n2, device="cuda", generator=gen)
                 j = step % per_epoch
-                idx = perm[j * bsz:(j + 1) * bsz]
+                b = perm[j * bsz:(j + 1) * bsz]
                 lr = cfg.lr_min + 0.5 * (cfg.lr - cfg.lr_min) * (1 + math.cos(math.pi * step / cfg.steps))
-                m.train_step(x[idx].contiguous(), y[idx].contiguous(), lr, cfg.weight_decay, loss)
+                m.train_step(x[b].contiguous(), yt[b].contiguous(), lr, cfg.weight_decay, loss,
+                             mask=mk[b].contiguous())
                 if step == 0 or (step + 1) % max(cfg.steps // 20, 1) == 0:
                     history.append((k, step, float(loss.item())))
                     if log:
                         log(f"model {k} step {step} loss {history[-1][2]:.5f}")
             self.models.append(m)
+        del yt, mk
         # calibration: scale of the ensemble spread so that it covers the actual relative error of
         # calib_quantile of the validation entries
         self.calib = 1.0
-        if n_val > 0 and len(self.models) > 1:
+        if val_uvw is not None and len(val_uvw) > 0 and len(self.models) > 1:
             mean, spread = self.predict(val_uvw, calibrated=False)
-            actual = rel_l2(torch.pow(10.0, mean.double()).cpu().numpy(), val_bins.reshape(n_val, -1).cpu().numpy())
+            nv = len(val_uvw)
+            actual = rel_l2(torch.pow(10.0, mean.double()).cpu().numpy(), val_bins.reshape(nv, -1).cpu().numpy())
             ratio = actual / np.maximum(spread.cpu().numpy(), 1e-12)
             self.calib = float(np.quantile(ratio, cfg.calib_quantile))
         return history
@@ -221,12 +295,16 @@ class Surrogate:
         """(log10 bins mean [n][n_out], relative error estimate [n]) as device tensors."""
         import torch
         cfg = self.cfg
+        uvw = np.asarray(uvw, dtype=np.float64)
         x = torch.from_numpy(feature_map(cfg, uvw)).cuda()
         n = x.shape[0]
+        idx = self._window_index(uvw, "cuda")
+        ext = torch.empty((n, self.n_ext * cfg.n_rbins), dtype=torch.float32, device="cuda")
         preds = torch.empty((len(self.models), n, cfg.n_out), dtype=torch.float32, device="cuda")
         for k, m in enumerate(self.models):
-            m.forward(x, preds[k])
-            rad.rad_standardize(preds[k], self.mean, self.std, inverse=True)
+            m.forward(x, ext)
+            torch.gather(ext, 1, idx, out=preds[k])
+        preds.mul_(self.sigma).add_(self.mu)
         mean = torch.empty((n, cfg.n_out), dtype=torch.float32, device="cuda")
         err = torch.empty(n, dtype=torch.float32, device="cuda")
         rad.rad_mlp_ensemble_estimate(preds, mean, err)

@@ -38,10 +38,11 @@ def test_forward_and_gradients_match_reference():
     y_ref = M.forward(p, x, n_in, width, depth, n_out)
     assert np.abs(y - y_ref).max() <= 2e-2 * np.abs(y_ref).max()
     loss = torch.zeros(1, dtype=torch.float32, device="cuda")
-    m.backward(dx, dt, loss)
+    mask = (rng.random((B, n_out)) < 0.7).astype(np.float32)
+    m.backward(dx, dt, loss, mask=torch.from_numpy(mask).cuda())
     torch.cuda.synchronize()
     g = m.get(1).astype(np.float64)
-    l_ref, g_ref = M.loss_and_grad(p, x, t, n_in, width, depth, n_out)
+    l_ref, g_ref = M.loss_and_grad(p, x, t, n_in, width, depth, n_out, mask=mask)
     assert abs(loss.item() - l_ref) <= 1e-2 * l_ref
     lay, _ = M.layout(n_in, width, depth, n_out)
     for (wo, bo, fo, fi) in lay:
