@@ -276,7 +276,8 @@ int rad_graph_destroy(rad_graph graph);
 typedef struct rad_mlp_s *rad_mlp;
 
 /* rad_mlp_create -- allocates a network for batches of up to max_batch rows (width and n_out
- * even); weights uniform in +-1/sqrt(fan_in) from `seed`, biases 0. */
+ * even, width <= 8192, n_out <= 65536, n_in <= 64, max_batch <= 4,194,240; RAD_EINVAL
+ * otherwise); weights uniform in +-1/sqrt(fan_in) from `seed`, biases 0. */
 int rad_mlp_create(int n_in, int width, int depth, int n_out, int64_t max_batch, uint64_t seed,
                    rad_mlp *out);
 int rad_mlp_destroy(rad_mlp mlp);
@@ -287,8 +288,8 @@ int rad_mlp_forward(rad_mlp mlp, const float *x, int64_t batch, float *y, void *
 
 /* rad_mlp_backward -- forward pass, loss = mean(mask (y - target)^2) over all batch x n_out
  * elements written to *loss (device, may be NULL), and the gradient of the loss w.r.t. every
- * parameter kept in the network (batch <= max_batch). mask [batch][n_out] of 0/1 weights, or
- * NULL for all ones (masked elements contribute nothing). */
+ * parameter kept in the network (batch <= max_batch). mask [batch][n_out] of nonnegative
+ * weights m (loss = sum m (y - target)^2 / (batch n_out)), or NULL for all ones. */
 int rad_mlp_backward(rad_mlp mlp, const float *x, const float *target, const float *mask, int64_t batch,
                      float *loss, void *stream);
 
@@ -307,8 +308,9 @@ int rad_mlp_get(rad_mlp mlp, int what, float *host_out);
 int rad_mlp_set_params(rad_mlp mlp, const float *host_in);
 
 /* rad_mlp_ensemble_estimate -- preds [n_models][batch][n_out] of log10 spectra -> mean
- * [batch][n_out] and err[batch] = ln(10) sqrt(mean over outputs of the models' variance), the
- * relative spectrum error implied by the ensemble spread (the surrogate's error estimate). */
+ * [batch][n_out] (mu_o) and err[batch] = ln(10) sqrt(sum_o s_o^2 var_o / sum_o s_o^2) with
+ * s_o = 10^mu_o and var_o the unbiased variance over models: the relative L2 error of the
+ * spectrum implied, to first order, by the ensemble spread (the surrogate's error estimate). */
 int rad_mlp_ensemble_estimate(const float *preds, int n_models, int64_t batch, int n_out, float *mean,
                               float *err, void *stream);
 
@@ -319,6 +321,61 @@ int rad_column_stats(const float *y, int64_t rows, int cols, float *mean, float 
 /* rad_standardize -- y = (y - mean) / std per column, or the inverse when inverse != 0. */
 int rad_standardize(float *y, int64_t rows, int cols, const float *mean, const float *stdv, int inverse,
                     void *stream);
+
+/* ---- trajectories on the GPU (Sec. III) ---- */
+
+/* Flags of rad_channel.flags */
+#define RAD_TRAJ_MS 1      /* multiple Coulomb scattering kicks after every step            */
+#define RAD_TRAJ_LL 2      /* radiation-reaction drag (leading Landau-Lifshitz term)        */
+#define RAD_TRAJ_MS_LOSS 4 /* energy loss of each kick, m alpha/(2 pi) gamma^3 theta^2       */
+
+/* Planar channel of the trajectory integrator: a harmonic well U(s) = U0 (2 s / d_p)^2 in the
+ * distance s to the nearest channel centre (a stand-in for the planar continuum potential of
+ * Sec. III, whose Doyle-Turner tables the paper does not print), and the nuclear
+ * multiple-scattering model of Sec. III. */
+typedef struct {
+  double U0_eV;    /* well depth, eV (>= 0)                                                 */
+  double d_p;      /* interplanar distance, m (> 0)                                         */
+  double eps_s_eV; /* scattering energy constant (10.6 MeV in Sec. III), eV                 */
+  double X0;       /* radiation length, m (> 0 with RAD_TRAJ_MS)                             */
+  double rho;      /* thermal amplitude of the Gaussian plane density, m (> 0 with MS)       */
+  double mass_eV;  /* rest energy of the particle, eV (> 0)                                  */
+  int charge_sign; /* +1: channel centres mid-way between planes; -1: centres on the planes */
+  int flags;       /* RAD_TRAJ_* bits                                                        */
+} rad_channel;
+
+/*
+ * rad_channeling_trajectories -- integrates n_particles trajectories in the channel `ch` and
+ * writes their records in the layout every rad_spectrum* entry point reads (Sec. II
+ * variables), one thread per particle.
+ *   Equations (c = 1, metres, eV): dx/dt = v_x, dy/dt = v_y, dv_x/dt = F(x)/E with
+ *   F = -8 U0 s/d_p^2, dv_y/dt = 0, d(dz)/dt = v_z - beta0 with beta0 = 1 - 1/(2 gamma0^2)
+ *   from the entry energy, v_z = sqrt(1 - 1/gamma^2 - v_perp^2), and with RAD_TRAJ_LL
+ *   dE/dt = -(2/3) alpha hbar c gamma^2 F^2/m^2 (Sec. III, Landau-Lifshitz force). One
+ *   classical Runge-Kutta (RK4) step of dt between samples. With RAD_TRAJ_MS, after every
+ *   step both angles get Gaussian kicks of variance (1/2)(eps_s/E)^2 (dt/X0) n(x)/N, n(x)/N =
+ *   d_p/(sqrt(pi) rho) sum over the two nearest planes of exp(-r^2/rho^2); the next sample's
+ *   acceleration carries the kick as delta_v/dt; with RAD_TRAJ_MS_LOSS the kick costs
+ *   m alpha/(2 pi) gamma^3 theta^2 of energy (Sec. III). Normals: Philox4x32-10 (Salmon et
+ *   al., SC'11), counter (id low word, step, 1, id high word), key (seed low, seed high);
+ *   u = ((a >> 5) 2^26 + (b >> 6) + 1/2) 2^-53 from output words (0,1) and (2,3); Box-Muller
+ *   z0 = r cos(2 pi u2), z1 = r sin(2 pi u2), r = sqrt(-2 ln u1).
+ *   Records: t = k dt, x, y, dz, v_x, v_y, dvz = v_z - beta0, a_x = F/E + kick, a_y = kick,
+ *   a_z = (dgamma/dt / gamma^3 - v_perp . a_perp)/v_z. Particle p owns records
+ *   offsets[p] .. offsets[p+1]-1 (device int64, n_particles + 1 values, within
+ *   [0, n_samples_total]) and starts at x0[p], v_x = thx0[p], v_y = thy0[p] (thy0 may be NULL
+ *   for 0), y = dz = 0, energy energy_eV[p] (> mass); particle_ids[p] (device, may be NULL for
+ *   p) selects its random stream. All arrays are device memory; out holds n_samples_total
+ *   records; energy_out (optional, n_samples_total doubles) receives the energy at every
+ *   sample. Asynchronous on `stream`; host checks (null pointers, dt > 0, channel values,
+ *   unknown flags) return RAD_EINVAL before anything is enqueued; a particle with bad
+ *   offsets, non-finite entry values or energy <= mass is skipped and RAD_EDATA is recorded
+ *   for rad_device_status().
+ */
+int rad_channeling_trajectories(const rad_channel *ch, int64_t n_particles, const int64_t *offsets,
+                                int64_t n_samples_total, const double *energy_eV, const double *x0,
+                                const double *thx0, const double *thy0, const int64_t *particle_ids,
+                                double dt, uint64_t seed, double *out, double *energy_out, void *stream);
 
 /*
  * rad_device_status -- waits for the current device to finish, returns the first

@@ -1,7 +1,8 @@
 """FP64 numpy reference of the surrogate MLP -- test infrastructure only.
 
 Same network as the CUDA surrogate: x -> depth x [Linear -> GELU] -> Linear, GELU in its
-exact form 0.5 z (1 + erf(z / sqrt 2)), loss = mean((y - t)^2). Parameters use the CUDA
+exact form 0.5 z (1 + erf(z / sqrt 2)), loss = mean(m (y - t)^2) with optional nonnegative
+weights m. Parameters use the CUDA
 library's flat layout: for each layer l = 0..depth, W_l [out][in] row-major then b_l [out].
 Gradients come from the chain rule written out layer by layer (plain backpropagation).
 Pinned in tests by central finite differences of the loss (tests/test_mlp_reference.py).

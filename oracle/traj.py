@@ -1,0 +1,180 @@
+"""FP64 CPU oracle for planar-channeling trajectories -- test infrastructure only.
+
+Only the tests, the smoke check and the benchmark's CPU-baseline leg may import this module;
+the CUDA integrator never calls it and the two share no code.
+
+What it computes (arXiv:1910.10391, Sec. III, with the harmonic stand-in for the planar
+continuum potential, whose Doyle-Turner tables the paper does not print):
+  * potential energy U(s) = U0 (2 s / d_p)^2, s = distance to the nearest channel centre
+    (positrons: centres mid-way between planes at (m + 1/2) d_p; electrons: on the planes);
+    transverse force F = -dU/ds = -8 U0 s / d_p^2 (eV/m);
+  * ultra-relativistic equation of motion with c = 1, lengths and times in metres:
+      dx/dt = v_x, dy/dt = v_y, dv_x/dt = F / E, dv_y/dt = 0,
+      d(dz)/dt = v_z - beta0, beta0 := 1 - 1/(2 gamma0^2) with gamma0 the entry value,
+      v_z = sqrt(1 - 1/gamma^2 - v_perp^2);
+  * radiation reaction (Landau-Lifshitz force, Sec. III; its leading term for a static
+    transverse field is a drag along the velocity with the relativistic Larmor power):
+      dE/dt = -(2/3) alpha hbar c gamma^2 F^2 / (m c^2)^2;
+  * one classical Runge-Kutta (RK4) step of dt on (x, y, v_x, v_y, dz, E) between samples;
+  * multiple Coulomb scattering on nuclei (Sec. III, nuclear term only): after each step,
+    independent Gaussian kicks of both transverse angles with variance
+      (1/2) (eps_s / E)^2 (dt / X0) n(x)/N,  n(x)/N = d_p/(sqrt(pi) rho) sum over the two
+      nearest planes of exp(-r^2/rho^2),
+    added to v_perp; the next sample's acceleration carries the kick as delta_v / dt, and
+    with scattering loss the kick costs dE = m alpha/(2 pi) gamma^3 theta^2 (Sec. III);
+  * normals from Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), counter
+    (particle low word, step, 1, particle high word), key (seed low, seed high), by
+    Box-Muller on two 53-bit uniforms ((top 27 bits of word a) * 2^26 + top 26 of word b
+    + 1/2) / 2^53, z0 = r cos(2 pi u2), z1 = r sin(2 pi u2), r = sqrt(-2 ln u1).
+Records (the radiation integral's input, Sec. II variables): t = k dt, x, y, dz, v_x, v_y,
+dvz = v_z - beta0, a_x = F/E + kick, a_y = kick, a_z = (dgamma/dt / gamma^3 - v_perp.a_perp)/v_z.
+
+Pinned in tests/test_traj_oracle.py: Philox published vectors, the closed-form harmonic
+solution and its dz, transverse-energy conservation, the Larmor integral of the energy loss,
+the per-kick scattering loss, kick statistics, and agreement with the input generator.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+ALPHA = 7.2973525693e-3
+HBARC_EV_M = 1.973269804e-7
+
+_M0, _M1 = np.uint64(0xD2511F53), np.uint64(0xCD9E8D57)
+_W0, _W1 = np.uint32(0x9E3779B9), np.uint32(0xBB67AE85)
+_MASK = np.uint64(0xFFFFFFFF)
+
+
+def philox4x32_10(c0, c1, c2, c3, k0, k1):
+    """Ten Philox4x32 rounds on uint32 arrays (broadcast): each round multiplies words 0 and 2
+    by the two round constants (64-bit products split into high and low halves), mixes with
+    words 1 and 3 and the key, then bumps the key by the two Weyl constants."""
+    c = [np.asarray(x, dtype=np.uint32) for x in (c0, c1, c2, c3)]
+    k = [np.asarray(k0, dtype=np.uint32), np.asarray(k1, dtype=np.uint32)]
+    for r in range(10):
+        p0 = c[0].astype(np.uint64) * _M0
+        p1 = c[2].astype(np.uint64) * _M1
+        hi0, lo0 = (p0 >> np.uint64(32)).astype(np.uint32), (p0 & _MASK).astype(np.uint32)
+        hi1, lo1 = (p1 >> np.uint64(32)).astype(np.uint32), (p1 & _MASK).astype(np.uint32)
+        c = [hi1 ^ c[1] ^ k[0], lo1, hi0 ^ c[3] ^ k[1], lo0]
+        if r < 9:  # key bump modulo 2^32
+            k = [((k[0].astype(np.uint64) + np.uint64(_W0)) & _MASK).astype(np.uint32),
+                 ((k[1].astype(np.uint64) + np.uint64(_W1)) & _MASK).astype(np.uint32)]
+    return c
+
+
+def _u53(a, b):
+    m = ((a >> np.uint32(5)).astype(np.uint64) << np.uint64(26)) | (b >> np.uint32(6)).astype(np.uint64)
+    return (m.astype(np.float64) + 0.5) * (1.0 / 9007199254740992.0)
+
+
+def kick_normals(seed: int, particles, step: int):
+    """(z0, z1) standard normals of the scattering kick after `step` for each particle index."""
+    p = np.asarray(particles, dtype=np.uint64)
+    r = philox4x32_10(p & _MASK, np.full(p.shape, step & 0xFFFFFFFF, np.uint32), np.full(p.shape, 1, np.uint32),
+                      p >> np.uint64(32), np.uint32(seed & 0xFFFFFFFF), np.uint32((seed >> 32) & 0xFFFFFFFF))
+    u1, u2 = _u53(r[0], r[1]), _u53(r[2], r[3])
+    rad = np.sqrt(-2.0 * np.log(u1))
+    ang = 2.0 * math.pi * u2
+    return rad * np.cos(ang), rad * np.sin(ang)
+
+
+def force(x, U0_eV, d_p, charge):
+    """Transverse force F (eV/m) of the harmonic planar well."""
+    centre = 0.5 * d_p if charge > 0 else 0.0
+    u = (x - centre) / d_p
+    s = (u - np.floor(u + 0.5)) * d_p
+    return -8.0 * U0_eV * s / (d_p * d_p)
+
+
+def plane_density(x, d_p, rho):
+    """n(x)/N: Gaussian plane density (thermal amplitude rho) summed over the two nearest planes."""
+    m = np.floor(x / d_p)
+    r1, r2 = x - m * d_p, (m + 1.0) * d_p - x
+    return d_p / (math.sqrt(math.pi) * rho) * (np.exp(-(r1 * r1) / (rho * rho)) + np.exp(-(r2 * r2) / (rho * rho)))
+
+
+def trajectories(x0, thx0, thy0, E0_eV, n_samples: int, dt: float, seed: int, *, charge=+1,
+                 U0_eV=20.0, d_p=1.92e-10, eps_s_eV=10.6e6, X0=0.0937, rho=0.075e-10, ms=True,
+                 ll=False, ms_loss=False, mass_eV=0.51099895e6, particle_ids=None, energies=False):
+    """Records [n][n_samples][10] of n particles with entry (x0, thx0, thy0) and energy E0
+    (scalar or per particle); particle_ids index the random streams (default 0..n-1).
+    With energies=True also returns the energy at every sample [n][n_samples]."""
+    x0 = np.asarray(x0, dtype=np.float64)
+    n = x0.shape[0]
+    pid = np.arange(n, dtype=np.uint64) if particle_ids is None else np.asarray(particle_ids, dtype=np.uint64)
+    E0 = np.broadcast_to(np.asarray(E0_eV, dtype=np.float64), (n,)).copy()
+    g0 = E0 / mass_eV
+    beta0 = 1.0 - 1.0 / (2.0 * g0 * g0)
+    s = np.stack([x0, np.zeros(n), np.asarray(thx0, np.float64), np.broadcast_to(np.asarray(thy0, np.float64), (n,)),
+                  np.zeros(n), E0], 1)
+
+    def dvz_of(g, vp2, vz):
+        # v_z - beta0 without cancellation: (v_z^2 - beta0^2)/(v_z + beta0) with
+        # v_z^2 - beta0^2 = (1/gamma0^2 - 1/gamma^2) - v_perp^2 - 1/(4 gamma0^4)
+        d_inv = ((g - g0) * (g + g0)) / ((g * g) * (g0 * g0))
+        return (d_inv - vp2 - 1.0 / (4.0 * g0 ** 4)) / (vz + beta0)
+
+    def gamma_dot(F, E):
+        g = E / mass_eV
+        return -(2.0 / 3.0) * ALPHA * HBARC_EV_M * g * g * (F / mass_eV) ** 2 / mass_eV
+
+    def deriv(st):
+        g = st[:, 5] / mass_eV
+        vp2 = st[:, 2] ** 2 + st[:, 3] ** 2
+        vz = np.sqrt(1.0 - 1.0 / (g * g) - vp2)
+        F = force(st[:, 0], U0_eV, d_p, charge)
+        d = np.empty_like(st)
+        d[:, 0] = st[:, 2]
+        d[:, 1] = st[:, 3]
+        d[:, 2] = F / st[:, 5]
+        d[:, 3] = 0.0
+        d[:, 4] = dvz_of(g, vp2, vz)
+        d[:, 5] = gamma_dot(F, st[:, 5]) * mass_eV if ll else 0.0
+        return d
+
+    out = np.empty((n, n_samples, 10))
+    Es = np.empty((n, n_samples))
+    kick = np.zeros((n, 2))
+    for k in range(n_samples):
+        g = s[:, 5] / mass_eV
+        vp2 = s[:, 2] ** 2 + s[:, 3] ** 2
+        vz = np.sqrt(1.0 - 1.0 / (g * g) - vp2)
+        F = force(s[:, 0], U0_eV, d_p, charge)
+        ax = F / s[:, 5] + kick[:, 0]
+        ay = kick[:, 1]
+        gd = gamma_dot(F, s[:, 5]) if ll else np.zeros(n)
+        rec = out[:, k]
+        rec[:, 0] = k * dt
+        rec[:, 1] = s[:, 0]
+        rec[:, 2] = s[:, 1]
+        rec[:, 3] = s[:, 4]
+        rec[:, 4] = s[:, 2]
+        rec[:, 5] = s[:, 3]
+        rec[:, 6] = dvz_of(g, vp2, vz)
+        rec[:, 7] = ax
+        rec[:, 8] = ay
+        rec[:, 9] = (gd / g ** 3 - (s[:, 2] * ax + s[:, 3] * ay)) / vz
+        Es[:, k] = s[:, 5]
+        kick[:] = 0.0
+        if k == n_samples - 1:
+            break
+        k1 = deriv(s)
+        k2 = deriv(s + 0.5 * dt * k1)
+        k3 = deriv(s + 0.5 * dt * k2)
+        k4 = deriv(s + dt * k3)
+        s = s + dt / 6.0 * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
+        if ms:
+            E = s[:, 5]
+            var = 0.5 * (eps_s_eV / E) ** 2 * (dt / X0) * plane_density(s[:, 0], d_p, rho)
+            z0, z1 = kick_normals(seed, pid, k)
+            dthx, dthy = np.sqrt(var) * z0, np.sqrt(var) * z1
+            kick[:, 0], kick[:, 1] = dthx / dt, dthy / dt
+            s[:, 2] += dthx
+            s[:, 3] += dthy
+            if ms_loss:
+                gk = E / mass_eV
+                s[:, 5] = E - mass_eV * ALPHA / (2.0 * math.pi) * gk ** 3 * (dthx * dthx + dthy * dthy)
+    return (out, Es) if energies else out

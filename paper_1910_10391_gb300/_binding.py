@@ -21,6 +21,14 @@ RAD_OK, RAD_EINVAL, RAD_ENOMEM, RAD_ECUDA, RAD_ETIMEOUT, RAD_EUNSUPPORTED, RAD_E
 RAD_CLASSICAL, RAD_SPIN0, RAD_SPIN_HALF = 0, 1, 2
 RAD_FP64, RAD_MIXED = 0, 1
 RAD_NREC = 10
+RAD_TRAJ_MS, RAD_TRAJ_LL, RAD_TRAJ_MS_LOSS = 1, 2, 4
+
+
+class RadChannel(ctypes.Structure):
+    """rad_channel: harmonic planar well and scattering model of the trajectory integrator."""
+    _fields_ = [("U0_eV", ctypes.c_double), ("d_p", ctypes.c_double), ("eps_s_eV", ctypes.c_double),
+                ("X0", ctypes.c_double), ("rho", ctypes.c_double), ("mass_eV", ctypes.c_double),
+                ("charge_sign", ctypes.c_int), ("flags", ctypes.c_int)]
 MODES = {"classical": RAD_CLASSICAL, "spin0": RAD_SPIN0, "spin_half": RAD_SPIN_HALF}
 PRECISIONS = {"fp64": RAD_FP64, "mixed": RAD_MIXED}
 
@@ -71,6 +79,9 @@ def load(build_if_missing: bool = True):
                                                i32, P, P]
         lib.rad_spectrum_particles.restype = c_int
         u64, f32 = ctypes.c_uint64, ctypes.c_float
+        lib.rad_channeling_trajectories.argtypes = [ctypes.POINTER(RadChannel), i64, P, i64, P, P, P, P, P,
+                                                    ctypes.c_double, u64, P, P, P]
+        lib.rad_channeling_trajectories.restype = c_int
         lib.rad_mlp_create.argtypes = [c_int, c_int, c_int, c_int, i64, u64, ctypes.POINTER(P)]
         lib.rad_mlp_create.restype = c_int
         lib.rad_mlp_destroy.argtypes = [P]
@@ -250,6 +261,18 @@ def rad_spectrum_particles(samples, offsets, gamma, energy_eV, weight, hbar_omeg
         _numel(theta_x), int(mode), int(precision), _dev_ptr(out_spectrum, f64, "out_spectrum"),
         _dev_ptr(bin_of_angle, torch.int32, "bin_of_angle"), int(n_bins), _dev_ptr(out_bins, f64, "out_bins"),
         _stream(stream))
+
+
+def rad_channeling_trajectories(channel, offsets, energy_eV, x0, thx0, out, dt, seed, thy0=None,
+                                particle_ids=None, energy_out=None, stream=None) -> int:
+    """Records of every particle into `out` [n_samples_total][10] (device tensors throughout)."""
+    import torch
+    f64 = torch.float64
+    return load().rad_channeling_trajectories(
+        ctypes.byref(channel), _numel(offsets) - 1, _dev_ptr(offsets, torch.int64, "offsets"), _numel(out) // RAD_NREC,
+        _dev_ptr(energy_eV, f64, "energy_eV"), _dev_ptr(x0, f64, "x0"), _dev_ptr(thx0, f64, "thx0"),
+        _dev_ptr(thy0, f64, "thy0"), _dev_ptr(particle_ids, torch.int64, "particle_ids"), float(dt), int(seed),
+        _dev_ptr(out, f64, "out"), _dev_ptr(energy_out, f64, "energy_out"), _stream(stream))
 
 
 class MLP:

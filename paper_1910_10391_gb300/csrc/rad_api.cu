@@ -35,6 +35,10 @@ struct Choice {
 
 }  // namespace
 
+namespace rad {
+int cuda_status(cudaError_t e) { return cuda_fail(e); }
+}  // namespace rad
+
 struct rad_plan_s {
   int device = 0;
   int sms = 0;

@@ -33,6 +33,9 @@ constexpr int kTabN = 1 << kTabBits;
 
 // Bounded waits: give up after this many nanoseconds of %globaltimer (and a
 // backstop iteration count), record RAD_ETIMEOUT and return.
+// Largest grid y extent; kernels with a y dimension stride over y beyond it.
+constexpr int64_t kMaxGridY = 65535;
+inline unsigned grid_y(int64_t n) { return static_cast<unsigned>(n < kMaxGridY ? n : kMaxGridY); }
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;
 constexpr unsigned long long kWaitLimitIter = 400000000ull;
 
@@ -251,6 +254,7 @@ cudaError_t launch_zero_outputs(const Params &P, double *out_cube, double *out_s
                                 int n_bins, double *out_bins, cudaStream_t st);
 const double2 *device_table(cudaError_t *err);  // per-device FP64 sincos table
 int *device_status_word(cudaError_t *err);      // per-device sticky status word
+int cuda_status(cudaError_t e);                 // records e for rad_status_string; RAD_ENOMEM or RAD_ECUDA
 
 inline int ncomp_of(int mode) { return mode == RAD_SPIN_HALF ? 8 : 6; }
 

@@ -37,9 +37,8 @@ __device__ __forceinline__ void tile_of(const Params &P, int64_t L, int64_t k, i
   km = k0 + (n - 1) / 2;
 }
 
-__global__ void k_prep_samples(const Params P, int T, float *__restrict__ out) {
-  if (*reinterpret_cast<volatile int *>(P.status) != 0) return;  // device data check failed
-  const int64_t p = blockIdx.y;
+// One particle's records: grid x strides over its samples.
+__device__ __forceinline__ void prep_particle(const Params &P, int T, int64_t p, float *__restrict__ out) {
   const int64_t off = P.offsets[p];
   const int64_t L = P.offsets[p + 1] - off;
   const double g = P.gamma[p];
@@ -73,6 +72,11 @@ __global__ void k_prep_samples(const Params P, int T, float *__restrict__ out) {
     reinterpret_cast<float4 *>(o)[1] = b;
     reinterpret_cast<float4 *>(o)[2] = c;
   }
+}
+
+__global__ void k_prep_samples(const Params P, int T, float *__restrict__ out) {
+  if (*reinterpret_cast<volatile int *>(P.status) != 0) return;  // device data check failed
+  for (int64_t p = blockIdx.y; p < P.n_particles; p += gridDim.y) prep_particle(P, T, p, out);
 }
 
 template <int MODE, int R, int NW, int T>
@@ -410,7 +414,7 @@ bool shape_supported_mixed_pp(int R, int NW, int T) {
 
 cudaError_t launch_prep_samples(const Params &P, int T, float *prep, cudaStream_t st) {
   if (P.n_particles == 0) return cudaSuccess;
-  dim3 grd(8, static_cast<unsigned>(P.n_particles));
+  dim3 grd(8, grid_y(P.n_particles));
   k_prep_samples<<<grd, 256, 0, st>>>(P, T, prep);
   return cudaGetLastError();
 }

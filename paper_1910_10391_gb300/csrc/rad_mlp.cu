@@ -196,16 +196,17 @@ __global__ void k_colsum(int64_t rows, int cols, const bf16 *__restrict__ dZ, fl
   db[n] = s;
 }
 
-// Loss and output gradient: dY = bf16(2 m (Y - T) / (B O)) with the optional 0/1 mask m;
-// per-block squared-error partials.
+// Loss and output gradient: loss terms m (Y - T)^2 and dY = bf16(2 m (Y - T) / (B O)) with the
+// optional nonnegative weights m (all ones when absent); per-block loss partials.
 __global__ void k_loss(int64_t n, float scale, const float *__restrict__ Y, const float *__restrict__ T,
                        const float *__restrict__ mask, bf16 *dY, float *partial) {
   __shared__ float red[256];
   float s = 0.f;
   for (int64_t e = static_cast<int64_t>(blockIdx.x) * 256 + threadIdx.x; e < n; e += static_cast<int64_t>(gridDim.x) * 256) {
-    const float d = mask ? (Y[e] - T[e]) * mask[e] : (Y[e] - T[e]);
-    dY[e] = __float2bfloat16(2.f * d * scale);
-    s = fmaf(d, d, s);
+    const float d = Y[e] - T[e];
+    const float md = mask ? mask[e] * d : d;
+    dY[e] = __float2bfloat16(2.f * md * scale);
+    s = fmaf(md, d, s);
   }
   red[threadIdx.x] = s;
   __syncthreads();
@@ -244,28 +245,53 @@ __global__ void k_to_bf16(int64_t n, const float *__restrict__ a, bf16 *b) {
 
 // Ensemble estimate: preds [K][B][O] -> mean [B][O], err[b] = ln(10) * sqrt(mean_o var_k),
 // the relative error of the spectrum implied by the models' spread of log10 predictions.
+// Ensemble mean of log10 predictions and the relative L2 spectrum error implied by the models'
+// spread: with mu_o the mean, var_o the unbiased variance over models and s_o = 10^mu_o,
+// err = ln(10) sqrt(sum_o s_o^2 var_o / sum_o s_o^2) (first order in the log-space spread).
 __global__ void k_ensemble(int K, int64_t B, int O, const float *__restrict__ preds, float *mean, float *err) {
   __shared__ float red[256];
+  __shared__ float red2[256];
   const int64_t b = blockIdx.x;
-  float acc = 0.f;
+  float mx = -INFINITY;
   for (int o = threadIdx.x; o < O; o += 256) {
-    float s = 0.f, s2 = 0.f;
-    for (int k = 0; k < K; ++k) {
-      const float p = preds[(static_cast<int64_t>(k) * B + b) * O + o];
-      s += p;
-      s2 = fmaf(p, p, s2);
-    }
+    float s = 0.f;
+    for (int k = 0; k < K; ++k) s += preds[(static_cast<int64_t>(k) * B + b) * O + o];
     const float mu = s / K;
     mean[b * O + o] = mu;
-    acc += fmaxf(s2 / K - mu * mu, 0.f) * (K > 1 ? static_cast<float>(K) / (K - 1) : 0.f);
+    mx = fmaxf(mx, mu);
   }
-  red[threadIdx.x] = acc;
+  red[threadIdx.x] = mx;
   __syncthreads();
   for (int k = 128; k > 0; k >>= 1) {
-    if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+    if (threadIdx.x < k) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + k]);
     __syncthreads();
   }
-  if (threadIdx.x == 0) err[b] = 2.302585093f * sqrtf(red[0] / O);
+  mx = red[0];
+  __syncthreads();
+  float aw = 0.f, an = 0.f;
+  for (int o = threadIdx.x; o < O; o += 256) {
+    const float mu = mean[b * O + o];
+    float v = 0.f;
+    for (int k = 0; k < K; ++k) {
+      const float d = preds[(static_cast<int64_t>(k) * B + b) * O + o] - mu;
+      v = fmaf(d, d, v);
+    }
+    v = K > 1 ? v / (K - 1) : 0.f;
+    const float w = exp10f(2.f * (mu - mx));  // (s_o / max s)^2
+    aw = fmaf(w, v, aw);
+    an += w;
+  }
+  red[threadIdx.x] = aw;
+  red2[threadIdx.x] = an;
+  __syncthreads();
+  for (int k = 128; k > 0; k >>= 1) {
+    if (threadIdx.x < k) {
+      red[threadIdx.x] += red[threadIdx.x + k];
+      red2[threadIdx.x] += red2[threadIdx.x + k];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) err[b] = 2.302585093f * sqrtf(red2[0] > 0.f ? red[0] / red2[0] : 0.f);
 }
 
 // Label transform: out = log10(max(v, floor)) (FP64 in, FP32 out)
@@ -409,6 +435,7 @@ extern "C" {
 int rad_mlp_create(int n_in, int width, int depth, int n_out, int64_t max_batch, uint64_t seed, rad_mlp *out) {
   if (!out || n_in < 1 || width < 1 || depth < 1 || n_out < 1 || max_batch < 1) return RAD_EINVAL;
   if (width % 2 || n_out % 2 || width > 8192 || n_out > (1 << 16) || n_in > 64) return RAD_EINVAL;
+  if (max_batch > 64 * 65535) return RAD_EINVAL;  // GEMM grid y = batch rows / 64
   *out = nullptr;
   rad_mlp h = new rad_mlp_s();
   h->n_in = n_in;

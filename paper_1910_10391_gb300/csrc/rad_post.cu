@@ -68,8 +68,10 @@ __global__ void k_finalize(const Params P, double *cube_new, double *out_cube, i
     atomicCAS(dev_status, 0, st);
   if (st != 0) return;  // leave the outputs untouched
   const int64_t i0 = static_cast<int64_t>(blockIdx.x) * 32;  // energy tile
-  const int64_t j0 = static_cast<int64_t>(blockIdx.y) * 32;  // direction tile
   const double pref = kAlpha / (4.0 * kPi * kPi);
+  const int64_t n_jt = (P.n_angles + 31) / 32;
+  for (int64_t jt = blockIdx.y; jt < n_jt; jt += gridDim.y) {  // direction tiles
+  const int64_t j0 = jt * 32;
   // read phase: thread (x, y) reads i = i0 + x, j = j0 + y + 8k
   for (int kk = 0; kk < 32; kk += 8) {
     const int64_t i = i0 + threadIdx.x, j = j0 + threadIdx.y + kk;
@@ -120,6 +122,8 @@ __global__ void k_finalize(const Params P, double *cube_new, double *out_cube, i
       cube_new[e] = v;
       if (out_cube) out_cube[e] = accumulate ? out_cube[e] + v : v;
     }
+  }
+  __syncthreads();  // the tile is rewritten by the next direction tile
   }
 }
 
@@ -174,9 +178,9 @@ __global__ void k_reduce_particles(const Params P, const double *d_omega, double
     atomicCAS(dev_status, 0, st);
   if (st != 0) return;
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int64_t p = blockIdx.y;
   const int64_t i = static_cast<int64_t>(blockIdx.x) * 32 + tx;
   const double pref = kAlpha / (4.0 * kPi * kPi);
+  for (int64_t p = blockIdx.y; p < P.n_particles; p += gridDim.y) {
   for (int b = 0; b <= kMaxBinsPP; ++b) acc[b][ty][tx] = 0.0;
   if (i < P.n_omega) {
     for (int64_t j = ty; j < P.n_angles; j += 8) {
@@ -199,6 +203,8 @@ __global__ void k_reduce_particles(const Params P, const double *d_omega, double
         for (int l = 0; l < 8; ++l) sb += acc[b][l][tx];
         out_bins[(p * P.n_omega + i) * n_bins + b] = pref * sb;
       }
+  }
+  __syncthreads();  // acc is cleared for the next particle
   }
 }
 
@@ -294,7 +300,7 @@ cudaError_t launch_finalize(const Params &P, double *cube_new, double *out_cube,
   int *ds = device_status_word(&e);
   if (!ds) return e;
   dim3 blk(32, 8);
-  dim3 grd(static_cast<unsigned>((P.n_omega + 31) / 32), static_cast<unsigned>((P.n_angles + 31) / 32));
+  dim3 grd(static_cast<unsigned>((P.n_omega + 31) / 32), grid_y((P.n_angles + 31) / 32));
   if (grd.x == 0 || grd.y == 0) return cudaSuccess;
   if (!P.amp_mode)
     k_finalize<false, 6><<<grd, blk, 0, st>>>(P, cube_new, out_cube, accumulate, ds);
@@ -308,7 +314,7 @@ cudaError_t launch_finalize(const Params &P, double *cube_new, double *out_cube,
 cudaError_t launch_finalize_status(const Params &P, double *cube_new, double *out_cube, int accumulate,
                                    int *publish_status, cudaStream_t st) {
   dim3 blk(32, 8);
-  dim3 grd(static_cast<unsigned>((P.n_omega + 31) / 32), static_cast<unsigned>((P.n_angles + 31) / 32));
+  dim3 grd(static_cast<unsigned>((P.n_omega + 31) / 32), grid_y((P.n_angles + 31) / 32));
   if (grd.x == 0 || grd.y == 0) return cudaSuccess;
   if (P.amp_mode) return cudaErrorInvalidValue;
   k_finalize<false, 6><<<grd, blk, 0, st>>>(P, cube_new, out_cube, accumulate, publish_status);
@@ -332,7 +338,7 @@ cudaError_t launch_reduce_particles(const Params &P, const double *d_omega, doub
   int *ds = device_status_word(&e);
   if (!ds) return e;
   dim3 blk(32, 8);
-  dim3 grd(static_cast<unsigned>((P.n_omega + 31) / 32), static_cast<unsigned>(P.n_particles));
+  dim3 grd(static_cast<unsigned>((P.n_omega + 31) / 32), grid_y(P.n_particles));
   k_reduce_particles<<<grd, blk, 0, st>>>(P, d_omega, out_spectrum, bin_of_angle, n_bins, out_bins, ds);
   return cudaGetLastError();
 }

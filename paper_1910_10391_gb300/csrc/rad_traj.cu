@@ -1,0 +1,229 @@
+// Planar-channeling trajectories on the GPU (Sec. III): one thread integrates one particle
+// with classical RK4 steps and writes the records the radiation kernels consume (Sec. II
+// variables), so an ensemble goes from entry conditions to spectra without leaving HBM.
+//
+// Model (harmonic stand-in for the planar continuum potential, c = 1, metres, eV):
+//   U(s) = U0 (2 s / d_p)^2, s = distance to the nearest channel centre (positrons: mid-way
+//   between planes; electrons: on the planes); F = -8 U0 s / d_p^2;
+//   dx/dt = v_x, dy/dt = v_y, dv_x/dt = F / E, dv_y/dt = 0, d(dz)/dt = v_z - beta0,
+//   beta0 := 1 - 1/(2 gamma0^2) (entry energy), v_z = sqrt(1 - 1/gamma^2 - v_perp^2);
+//   optional radiation-reaction drag (leading Landau-Lifshitz term for a static transverse
+//   field): dE/dt = -(2/3) alpha hbar c gamma^2 F^2 / m^2;
+//   optional multiple scattering on nuclei after every step: Gaussian kicks of both angles
+//   with variance (1/2)(eps_s/E)^2 (dt/X0) n(x)/N, n(x)/N the Gaussian plane density of the
+//   two nearest planes; the next sample's acceleration carries the kick as delta_v/dt; with
+//   scattering loss each kick costs m alpha/(2 pi) gamma^3 theta^2.
+// Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) with counter
+// (particle low, step, 1, particle high) and key (seed low, seed high); two 53-bit uniforms
+// per block and Box-Muller normals.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "rad_internal.cuh"
+
+namespace rad {
+namespace {
+
+struct Chan {
+  double U0, d_p, eps_s, X0, rho, mass, centre, inv_d, force_k, dens_pref, inv_rho2, var_k, loss_k, ll_k;
+  int ms, ll, ms_loss;
+};
+
+// ---------------- Philox4x32-10 ----------------
+__device__ __forceinline__ void philox(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c[0], hi0 = __umulhi(0xD2511F53u, c[0]);
+    const uint32_t lo1 = 0xCD9E8D57u * c[2], hi1 = __umulhi(0xCD9E8D57u, c[2]);
+    const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+
+__device__ __forceinline__ double u53(uint32_t a, uint32_t b) {
+  const uint64_t m = (static_cast<uint64_t>(a >> 5) << 26) | static_cast<uint64_t>(b >> 6);
+  return (static_cast<double>(m) + 0.5) * (1.0 / 9007199254740992.0);
+}
+
+__device__ __forceinline__ void kick_normals(uint64_t seed, uint64_t pid, uint64_t step, double &z0, double &z1) {
+  uint32_t c[4] = {static_cast<uint32_t>(pid), static_cast<uint32_t>(step), 1u, static_cast<uint32_t>(pid >> 32)};
+  philox(c, static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32));
+  const double u1 = u53(c[0], c[1]), u2 = u53(c[2], c[3]);
+  const double r = sqrt(-2.0 * log(u1));
+  double s, co;
+  sincospi(2.0 * u2, &s, &co);
+  z0 = r * co;
+  z1 = r * s;
+}
+
+// ---------------- field ----------------
+__device__ __forceinline__ double force(const Chan &C, double x) {
+  const double u = (x - C.centre) * C.inv_d;
+  const double s = (u - floor(u + 0.5)) * C.d_p;
+  return C.force_k * s;  // -8 U0 s / d_p^2
+}
+
+__device__ __forceinline__ double plane_density(const Chan &C, double x) {
+  const double m = floor(x * C.inv_d);
+  const double r1 = x - m * C.d_p, r2 = (m + 1.0) * C.d_p - x;
+  return C.dens_pref * (exp(-(r1 * r1) * C.inv_rho2) + exp(-(r2 * r2) * C.inv_rho2));
+}
+
+// v_z - beta0 without cancellation: ((1/g0^2 - 1/g^2) - vp2 - 1/(4 g0^4)) / (v_z + beta0)
+__device__ __forceinline__ double dvz_of(double g, double g0, double q0, double beta0, double vp2, double &vz) {
+  vz = sqrt(1.0 - 1.0 / (g * g) - vp2);
+  const double d_inv = ((g - g0) * (g + g0)) / ((g * g) * (g0 * g0));
+  return (d_inv - vp2 - q0) / (vz + beta0);
+}
+
+struct State {
+  double x, y, vx, vy, dz, E;
+};
+
+__device__ __forceinline__ State deriv(const Chan &C, double g0, double q0, double beta0, const State &s) {
+  const double g = s.E / C.mass;
+  const double vp2 = s.vx * s.vx + s.vy * s.vy;
+  double vz;
+  const double dvz = dvz_of(g, g0, q0, beta0, vp2, vz);
+  const double F = force(C, s.x);
+  State d;
+  d.x = s.vx;
+  d.y = s.vy;
+  d.vx = F / s.E;
+  d.vy = 0.0;
+  d.dz = dvz;
+  d.E = C.ll ? C.ll_k * (g * g) * (F * F) : 0.0;
+  return d;
+}
+
+__device__ __forceinline__ State axpy(const State &s, double h, const State &d) {
+  return State{s.x + h * d.x, s.y + h * d.y, s.vx + h * d.vx, s.vy + h * d.vy, s.dz + h * d.dz, s.E + h * d.E};
+}
+
+__global__ void k_channel(const Chan C, int64_t n_particles, const int64_t *__restrict__ offsets,
+                          int64_t n_total, const double *__restrict__ energy, const double *__restrict__ x0,
+                          const double *__restrict__ thx0, const double *__restrict__ thy0,
+                          const int64_t *__restrict__ ids, double dt, uint64_t seed, double *__restrict__ out,
+                          double *__restrict__ e_out, int *dev_status) {
+  for (int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; p < n_particles;
+       p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t off = offsets[p], L = offsets[p + 1] - off;
+    const double E0 = energy[p];
+    if (off < 0 || L < 1 || off + L > n_total || !(E0 > C.mass) || !isfinite(E0) || !isfinite(x0[p]) ||
+        !isfinite(thx0[p]) || (thy0 && !isfinite(thy0[p]))) {
+      atomicCAS(dev_status, 0, RAD_EDATA);
+      continue;
+    }
+    const uint64_t pid = ids ? static_cast<uint64_t>(ids[p]) : static_cast<uint64_t>(p);
+    const double g0 = E0 / C.mass;
+    const double beta0 = 1.0 - 1.0 / (2.0 * g0 * g0);
+    const double q0 = 1.0 / (4.0 * (g0 * g0) * (g0 * g0));
+    State s{x0[p], 0.0, thx0[p], thy0 ? thy0[p] : 0.0, 0.0, E0};
+    double kx = 0.0, ky = 0.0;
+    double *rec = out + off * kRec;
+    for (int64_t k = 0; k < L; ++k, rec += kRec) {
+      // record k
+      const double g = s.E / C.mass;
+      const double vp2 = s.vx * s.vx + s.vy * s.vy;
+      double vz;
+      const double dvz = dvz_of(g, g0, q0, beta0, vp2, vz);
+      const double F = force(C, s.x);
+      const double ax = F / s.E + kx, ay = ky;
+      const double gdot = C.ll ? C.ll_k * (g * g) * (F * F) / C.mass : 0.0;
+      rec[F_T] = static_cast<double>(k) * dt;
+      rec[F_X] = s.x;
+      rec[F_Y] = s.y;
+      rec[F_DZ] = s.dz;
+      rec[F_VX] = s.vx;
+      rec[F_VY] = s.vy;
+      rec[F_DVZ] = dvz;
+      rec[F_AX] = ax;
+      rec[F_AY] = ay;
+      rec[F_AZ] = (gdot / (g * g * g) - (s.vx * ax + s.vy * ay)) / vz;
+      if (e_out) e_out[off + k] = s.E;
+      kx = ky = 0.0;
+      if (k == L - 1) break;
+      // RK4 step
+      const State k1 = deriv(C, g0, q0, beta0, s);
+      const State k2 = deriv(C, g0, q0, beta0, axpy(s, 0.5 * dt, k1));
+      const State k3 = deriv(C, g0, q0, beta0, axpy(s, 0.5 * dt, k2));
+      const State k4 = deriv(C, g0, q0, beta0, axpy(s, dt, k3));
+      const double h6 = dt / 6.0;
+      s.x += h6 * (k1.x + 2.0 * k2.x + 2.0 * k3.x + k4.x);
+      s.y += h6 * (k1.y + 2.0 * k2.y + 2.0 * k3.y + k4.y);
+      s.vx += h6 * (k1.vx + 2.0 * k2.vx + 2.0 * k3.vx + k4.vx);
+      s.vy += h6 * (k1.vy + 2.0 * k2.vy + 2.0 * k3.vy + k4.vy);
+      s.dz += h6 * (k1.dz + 2.0 * k2.dz + 2.0 * k3.dz + k4.dz);
+      s.E += h6 * (k1.E + 2.0 * k2.E + 2.0 * k3.E + k4.E);
+      if (C.ms) {
+        const double E = s.E;
+        const double var = C.var_k / (E * E) * plane_density(C, s.x);
+        double z0, z1;
+        kick_normals(seed, pid, static_cast<uint64_t>(k), z0, z1);
+        const double sd = sqrt(var);
+        const double dthx = sd * z0, dthy = sd * z1;
+        kx = dthx / dt;
+        ky = dthy / dt;
+        s.vx += dthx;
+        s.vy += dthy;
+        if (C.ms_loss) {
+          const double gk = E / C.mass;
+          s.E = E - C.loss_k * (gk * gk * gk) * (dthx * dthx + dthy * dthy);
+        }
+      }
+    }
+  }
+}
+
+}  // namespace
+}  // namespace rad
+
+extern "C" int rad_channeling_trajectories(const rad_channel *ch, int64_t n_particles, const int64_t *offsets,
+                                           int64_t n_samples_total, const double *energy_eV, const double *x0,
+                                           const double *thx0, const double *thy0, const int64_t *particle_ids,
+                                           double dt, uint64_t seed, double *out, double *energy_out,
+                                           void *stream) {
+  using namespace rad;
+  if (!ch || n_particles < 0 || n_samples_total < 0) return RAD_EINVAL;
+  if (n_particles == 0) return RAD_OK;
+  if (!offsets || !energy_eV || !x0 || !thx0 || !out) return RAD_EINVAL;
+  if (!(dt > 0.0) || !isfinite(dt) || !(ch->d_p > 0.0) || !(ch->mass_eV > 0.0) || !(ch->U0_eV >= 0.0) ||
+      (ch->charge_sign != 1 && ch->charge_sign != -1) || (ch->flags & ~7))
+    return RAD_EINVAL;
+  if ((ch->flags & RAD_TRAJ_MS) && !(ch->X0 > 0.0 && ch->rho > 0.0 && ch->eps_s_eV >= 0.0)) return RAD_EINVAL;
+  cudaError_t e;
+  int *ds = device_status_word(&e);
+  if (!ds) return cuda_status(e);
+  Chan C;
+  C.U0 = ch->U0_eV;
+  C.d_p = ch->d_p;
+  C.eps_s = ch->eps_s_eV;
+  C.X0 = ch->X0;
+  C.rho = ch->rho;
+  C.mass = ch->mass_eV;
+  C.centre = ch->charge_sign > 0 ? 0.5 * ch->d_p : 0.0;
+  C.inv_d = 1.0 / ch->d_p;
+  C.force_k = -8.0 * ch->U0_eV / (ch->d_p * ch->d_p);
+  C.dens_pref = (ch->flags & RAD_TRAJ_MS) ? ch->d_p / (sqrt(kPi) * ch->rho) : 0.0;
+  C.inv_rho2 = (ch->flags & RAD_TRAJ_MS) ? 1.0 / (ch->rho * ch->rho) : 0.0;
+  C.var_k = (ch->flags & RAD_TRAJ_MS) ? 0.5 * ch->eps_s_eV * ch->eps_s_eV * (dt / ch->X0) : 0.0;
+  C.loss_k = ch->mass_eV * kAlpha / (2.0 * kPi);
+  C.ll_k = -(2.0 / 3.0) * kAlpha * kHbarC * ch->mass_eV / (ch->mass_eV * ch->mass_eV * ch->mass_eV);
+  C.ms = (ch->flags & RAD_TRAJ_MS) != 0;
+  C.ll = (ch->flags & RAD_TRAJ_LL) != 0;
+  C.ms_loss = (ch->flags & RAD_TRAJ_MS_LOSS) != 0;
+  const int block = 64;
+  int64_t grid = (n_particles + block - 1) / block;
+  if (grid > 1 << 20) grid = 1 << 20;
+  k_channel<<<static_cast<unsigned>(grid), block, 0, static_cast<cudaStream_t>(stream)>>>(
+      C, n_particles, offsets, n_samples_total, energy_eV, x0, thx0, thy0, particle_ids, dt, seed, out, energy_out,
+      ds);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? RAD_OK : cuda_status(e);
+}

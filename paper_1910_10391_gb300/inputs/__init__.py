@@ -57,6 +57,11 @@ def _load():
             lib.tg_channeling.restype = i32
             lib.tg_channeling_given.argtypes = [P, d, i32, d, d, d, d, d, i32, d, u64, i64, P, P, P, P]
             lib.tg_channeling_given.restype = i32
+            lib.tg_channeling_loss.argtypes = [d, d, i32, d, d, d, d, d, d, i32, i32, i32, d, u64, i64, P,
+                                               i64, P, P, P, P, P, P, P, P]
+            lib.tg_channeling_loss.restype = i32
+            lib.tg_section_count.argtypes = [i64, i64]
+            lib.tg_section_count.restype = i64
             lib.tg_lognormal_lengths.argtypes = [u64, i64, d, d, i64, i64, P]
             lib.tg_lognormal_lengths.restype = i32
             lib.tg_philox4x32_10.argtypes = [P, P, P]
@@ -311,6 +316,71 @@ def channeling_given(x0, thx0, gammas, n_samples: int, dt: float, charge: int = 
     return Trajectories(out, off, E / mass_eV, E, np.full(n, 1.0 / max(n, 1)))
 
 
+@dataclasses.dataclass
+class Sectioned:
+    """Sections of an ensemble with energy loss: each section is one entry of `traj` (its own
+    gamma and E, weight of its particle); parent[j] is the particle of section j."""
+    traj: Trajectories
+    parent: np.ndarray          # [n_sections] int64
+    sec_offsets: np.ndarray     # [n_particles + 1] first section of each particle
+    energy_samples: np.ndarray | None = None   # [sum L] energy at every sample (optional)
+    sample_offsets: np.ndarray | None = None   # [n_particles + 1]
+
+
+def formation_length_m(E_eV: float, hw_eV: float, mass_eV: float = ME_EV) -> float:
+    """Coherence (formation) length of emitting hw from energy E, 2 gamma^2 (E - hw) / (E omega)
+    in metres (hbar c restored): a section must be longer than this at the photon energies of
+    interest (Sec. II)."""
+    g = E_eV / mass_eV
+    return 2.0 * g * g * (E_eV - hw_eV) / E_eV * HBARC_EV_M / hw_eV
+
+
+def channeling_sections(n_particles: int, E_eV: float, charge: int, lengths, dt: float, seed: int,
+                        section_samples: int, ll: bool = True, ms_loss: bool = True, ms: bool = True,
+                        U0_eV: float = 20.0, d_p: float = SI110_DP, sigma_theta_frac: float = 0.3,
+                        mass_eV: float = ME_EV, keep_energy: bool = False) -> Sectioned:
+    """Planar-channeling ensemble (entries as `channeling` with the same seed) integrated with
+    radiation-reaction drag (Landau-Lifshitz, leading term) and the multiple-scattering energy
+    loss of Sec. III, cut into sections of `section_samples` samples that share boundary
+    samples; each section enters the radiation integral with the energy it starts with."""
+    lens = np.broadcast_to(np.asarray(lengths, dtype=np.int64), (n_particles,)).copy()
+    S = int(section_samples)
+    if S < 2 or np.any(lens < 2):
+        raise ValueError("sections need >= 2 samples and particles >= 2 samples")
+    nsec = (lens - 2) // (S - 1) + 1
+    rec_off = np.zeros(n_particles + 1, dtype=np.int64)
+    rec_off[1:] = np.cumsum(lens + nsec - 1)
+    sec_off = np.zeros(n_particles + 1, dtype=np.int64)
+    sec_off[1:] = np.cumsum(nsec)
+    samp_off = np.zeros(n_particles + 1, dtype=np.int64)
+    samp_off[1:] = np.cumsum(lens)
+    out = np.empty((int(rec_off[-1]), NREC), dtype=np.float64)
+    secE = np.empty(int(sec_off[-1]), dtype=np.float64)
+    eS = np.empty(int(samp_off[-1]), dtype=np.float64) if keep_energy else None
+    theta_L = math.sqrt(2.0 * U0_eV / E_eV)
+    rc = _load().tg_channeling_loss(E_eV, mass_eV, int(charge), U0_eV, d_p, sigma_theta_frac * theta_L,
+                                    EPS_S_EV, SI_X0, RHO_THERMAL, int(bool(ms)), int(bool(ll)),
+                                    int(bool(ms_loss)), dt, int(seed), n_particles, _ptr(lens), S,
+                                    _ptr(rec_off), _ptr(sec_off), _ptr(samp_off), _ptr(out), _ptr(secE),
+                                    _ptr(eS) if eS is not None else None, None, None)
+    if rc != 0:
+        raise RuntimeError("tg_channeling_loss failed")
+    # section record ranges: particle p's sections are consecutive; all but the last have S records
+    ns = int(sec_off[-1])
+    parent = np.repeat(np.arange(n_particles, dtype=np.int64), nsec)
+    first = sec_off[parent]
+    j_in = np.arange(ns, dtype=np.int64) - first
+    start = rec_off[parent] + j_in * S
+    last = j_in == nsec[parent] - 1
+    slen = np.where(last, (lens[parent] + nsec[parent] - 1) - j_in * S, S)
+    off = np.zeros(ns + 1, dtype=np.int64)
+    off[1:] = start + slen
+    off[:-1] = start
+    w = np.full(ns, 1.0 / max(n_particles, 1))
+    tr = Trajectories(out, off, secE / mass_eV, secE, w)
+    return Sectioned(tr, parent, sec_off, eS, samp_off if keep_energy else None)
+
+
 def lognormal_lengths(n: int, seed: int, median: float = 20000.0, sigma: float = math.log(10) / 3,
                       lo: int = 2000, hi: int = 200000) -> np.ndarray:
     out = np.empty(n, dtype=np.int64)
@@ -418,3 +488,15 @@ def workload_electron_batch(n_particles=4096, seed=4, n_omega=1024, n_side=32, m
         tr = tr.subset(particles)
         tr.weight = np.full(tr.n_particles, 1.0 / n_particles)
     return tr, _ensemble_grid(E, 20.0, n_omega, n_side)
+
+
+def workload_strong_undulator(samples_per_period: int = 2048, n_omega: int = 256, n_side: int = 8,
+                              half_angle_gammas: float = 0.5):
+    """The paper's integral test (Sec. IV): 2 GeV electron, planar undulator with 53 mm period,
+    20 periods, B0 = 1 T (K = 4.95); photon energies 0-500 eV (linear grid from 2 eV) and a small
+    direction grid around the axis (+-half_angle_gammas/gamma)."""
+    g = 2.0e9 / ME_EV
+    K = undulator_K(1.0, 0.053)
+    tr = planar_undulator(g, K, 0.053, 20, samples_per_period)
+    grid = make_grid(omega_linear(n_omega, 500.0), n_side, n_side, half_angle_gammas / g)
+    return tr, grid

@@ -5,8 +5,13 @@ Entry conditions (x0/d_p, theta0/theta_L, gamma) of a positron in the harmonic p
 radial bins of the emission angle, at 256 photon energies hw/E log-spaced in [1e-4, 0.5]
 (BCK spin-1/2 model). Training spectra come from rad_spectrum_particles; the network (3 ->
 256 -> 256 -> 256 -> 2048, GELU) is trained with the library's own BF16 tensor-core kernels.
-An ensemble of networks gives an error estimate per entry; entries whose estimate exceeds
-`fallback_rel` are recomputed with the exact kernel.
+An ensemble of networks gives error estimates: per entry (entries whose estimate exceeds
+`fallback_rel` are recomputed with the exact kernel), and for the weighted mean spectrum of a
+beam of entries (the entries with the largest estimated error contributions are recomputed with
+the kernel until the mean's estimate is at most `fallback_rel`). Both estimates are calibrated on
+validation entries the networks do not train on. The loss weights each output by the square of
+its value relative to the entry's maximum (plus a floor): to first order that is the relative L2
+error of the spectrum that the log-space error causes.
 
 Angle grid per gamma: 32 x 32 cells over +-(theta_L + 3/gamma); radial bins of |theta| in
 [0, theta_L + 3/gamma). Motion without scattering stays in the x-z plane, so the spectrum is
@@ -68,6 +73,10 @@ class Config:
     fourier_seed: int = 11
     n_val: int = 2048
     calib_quantile: float = 0.95
+    loss_floor_w: float = 0.02
+    beams_val: int = 32
+    calib_subsets: int = 8
+    calib_gamma_bins: int = 4
 
     @property
     def n_in(self):
@@ -105,6 +114,20 @@ def sample_entries(cfg: Config, n: int, seed: int, discrete_gamma: bool):
     else:
         g = np.exp(rng.uniform(lo, hi, n))
     return x0, th, g
+
+
+def sample_beams(cfg: Config, n_beams: int, per_beam: int, seed: int):
+    """Beams of entries: each beam has one Lorentz factor, log-uniform in [gamma_lo, gamma_hi];
+    its entries have x0/d_p ~ U[0, 1) and theta0/theta_L ~ U[-theta_frac, theta_frac].
+    Returns (x0, theta0/theta_L, gamma, beam index) per entry."""
+    rng = np.random.default_rng(seed)
+    lo, hi = math.log(cfg.gamma_lo), math.log(cfg.gamma_hi)
+    gb = np.exp(rng.uniform(lo, hi, n_beams))
+    n = n_beams * per_beam
+    x0 = rng.uniform(0.0, 1.0, n)
+    th = rng.uniform(-cfg.theta_frac, cfg.theta_frac, n)
+    beam = np.repeat(np.arange(n_beams), per_beam)
+    return x0, th, gb[beam], beam
 
 
 def first_line_over_E(cfg: Config, u, v, g):
@@ -202,16 +225,20 @@ def kernel_bins(cfg: Config, x0, th, g, stream=None):
         d_boa = torch.from_numpy(boa).cuda()
         for c0 in range(a, b, cfg.chunk):
             idx = order[c0:min(b, c0 + cfg.chunk)]
-            tr = I.channeling_given(x0[idx] * cfg.d_p, th[idx] * thL, np.full(len(idx), gamma), cfg.n_samples, dt,
+            m = len(idx)
+            # pad to a multiple of 32 entries (repeating the last) so that the library sees a
+            # bounded set of batch shapes and reuses their plans
+            pad = np.concatenate([idx, np.full((-m) % 32, idx[-1])])
+            tr = I.channeling_given(x0[pad] * cfg.d_p, th[pad] * thL, np.full(len(pad), gamma), cfg.n_samples, dt,
                                     charge=+1, U0_eV=cfg.U0_eV, d_p=cfg.d_p, ms=False)
             inp = rad.DeviceInputs(tr, grid)
-            w = torch.ones(len(idx), dtype=torch.float64, device="cuda")
-            o = torch.empty((len(idx), cfg.n_omega, cfg.n_rbins), dtype=torch.float64, device="cuda")
+            w = torch.ones(len(pad), dtype=torch.float64, device="cuda")
+            o = torch.empty((len(pad), cfg.n_omega, cfg.n_rbins), dtype=torch.float64, device="cuda")
             rc = rad.rad_spectrum_particles(inp.samples, inp.offsets, inp.gamma, inp.energy, w, d_hw, d_tx, d_ty,
                                             d_dom, cfg.mode, cfg.precision, None, d_boa, cfg.n_rbins, o, stream)
             if rc:
                 raise rad.RadError(rc, "rad_spectrum_particles")
-            out[torch.from_numpy(idx).cuda()] = o
+            out[torch.from_numpy(idx).cuda()] = o[:m]
     return out
 
 
@@ -223,7 +250,8 @@ class Surrogate:
         self.models = []
         self.mu = self.sigma = None
         self.floor = None
-        self.calib = 1.0
+        self.calib = np.ones(cfg.calib_gamma_bins)
+        self.calib_ens = np.ones(cfg.calib_gamma_bins)
         self.s_lo, self.s_hi = shift_range(cfg)
         self.n_ext = cfg.n_omega + (self.s_hi - self.s_lo)
 
@@ -235,9 +263,17 @@ class Surrogate:
         off = torch.from_numpy(off_np).to(device) * self.cfg.n_rbins
         return off[:, None] + torch.arange(self.cfg.n_out, device=device)[None, :]
 
-    def fit(self, uvw, bins_dev, val_uvw=None, val_bins=None, log=None):
+    def gamma_bin(self, g):
+        """Calibration bin of Lorentz factors g: equal widths in log gamma over the input domain."""
+        cfg = self.cfg
+        lo, hi = math.log(cfg.gamma_lo), math.log(cfg.gamma_hi)
+        b = np.floor((np.log(np.asarray(g, dtype=np.float64)) - lo) / (hi - lo) * cfg.calib_gamma_bins)
+        return np.clip(b, 0, cfg.calib_gamma_bins - 1).astype(np.int64)
+
+    def fit(self, uvw, bins_dev, val_uvw=None, val_bins=None, val_beam=None, log=None):
         """Train the ensemble on raw inputs uvw [n][3] and their per-particle bins; a validation
-        set (entries the ensemble does not train on) calibrates the error estimate."""
+        set (entries the ensemble does not train on, grouped in beams by val_beam) calibrates the
+        per-entry and the beam-mean error estimates."""
         import torch
         cfg = self.cfg
         n = uvw.shape[0]
@@ -246,6 +282,8 @@ class Surrogate:
         rad.rad_log_targets(bins_dev.reshape(-1).contiguous(), self.floor, y.view(-1))
         self.mu, self.sigma = float(y.mean().item()), float(y.std().item())
         y = (y - self.mu) / self.sigma
+        flat = bins_dev.reshape(n, -1)
+        wt = (flat / flat.amax(1, keepdim=True).clamp_min(1e-300)).pow(2).add_(cfg.loss_floor_w).float()
         # aligned targets and masks on the extended grid, for the entries and their mirror images
         uvw2 = np.concatenate([uvw, mirrored_inputs(uvw)])
         x = torch.from_numpy(feature_map(cfg, uvw2)).cuda()
@@ -255,8 +293,8 @@ class Surrogate:
         yt = torch.zeros((n2, n_ext_out), dtype=torch.float32, device="cuda")
         mk = torch.zeros((n2, n_ext_out), dtype=torch.float32, device="cuda")
         yt.scatter_(1, idx, torch.cat([y, y]))
-        mk.scatter_(1, idx, torch.ones((n2, cfg.n_out), dtype=torch.float32, device="cuda"))
-        del y
+        mk.scatter_(1, idx, torch.cat([wt, wt]))
+        del y, wt
         loss = torch.zeros(1, dtype=torch.float32, device="cuda")
         bsz = min(cfg.batch, n2)
         per_epoch = max(n2 // bsz, 1)
@@ -280,19 +318,51 @@ class Surrogate:
                         log(f"model {k} step {step} loss {history[-1][2]:.5f}")
             self.models.append(m)
         del yt, mk
-        # calibration: scale of the ensemble spread so that it covers the actual relative error of
-        # calib_quantile of the validation entries
-        self.calib = 1.0
+        # calibration, per bin of log gamma: scales of the ensemble spreads so that they cover the
+        # actual relative errors of calib_quantile of the validation entries, and of validation
+        # beam means (every beam and half-size subsets of it); a bin with too few validation
+        # beams takes the largest factor of the other bins
+        nb = cfg.calib_gamma_bins
+        self.calib = np.ones(nb)
+        self.calib_ens = np.ones(nb)
         if val_uvw is not None and len(val_uvw) > 0 and len(self.models) > 1:
-            mean, spread = self.predict(val_uvw, calibrated=False)
             nv = len(val_uvw)
-            actual = rel_l2(torch.pow(10.0, mean.double()).cpu().numpy(), val_bins.reshape(nv, -1).cpu().numpy())
+            members = self.members(val_uvw)
+            mean, spread = self._estimate(members)
+            served = torch.pow(10.0, mean.double())
+            truth = val_bins.reshape(nv, -1)
+            actual = rel_l2(served.cpu().numpy(), truth.cpu().numpy())
             ratio = actual / np.maximum(spread.cpu().numpy(), 1e-12)
-            self.calib = float(np.quantile(ratio, cfg.calib_quantile))
+            gb = self.gamma_bin(gamma_of(cfg, np.asarray(val_uvw)[:, 2]))
+            glob = float(np.quantile(ratio, cfg.calib_quantile))
+            for k in range(nb):
+                sel = gb == k
+                self.calib[k] = np.quantile(ratio[sel], cfg.calib_quantile) if sel.sum() >= 20 else np.nan
+            self.calib = np.where(np.isnan(self.calib), max(glob, float(np.nanmax(np.r_[self.calib, glob]))),
+                                  self.calib)
+            if val_beam is not None:
+                rng = np.random.default_rng(cfg.fourier_seed + 1)
+                ratios = [[] for _ in range(nb)]
+                for b in np.unique(val_beam):
+                    sel = np.flatnonzero(val_beam == b)
+                    k = int(gb[sel[0]])
+                    for j in range(cfg.calib_subsets):
+                        sub = sel if j == 0 else np.sort(rng.choice(sel, size=max(len(sel) // 2, 2), replace=False))
+                        st = torch.from_numpy(sub).cuda()
+                        w = torch.full((len(sub),), 1.0 / len(sub), dtype=torch.float64, device="cuda")
+                        est = float(self._fallback_curve(members[:, st], w, torch.arange(len(sub), device="cuda"))[0])
+                        act = rel_l2(served[st].mean(0, keepdim=True).cpu().numpy(),
+                                     truth[st].mean(0, keepdim=True).cpu().numpy())[0]
+                        ratios[k].append(act / max(est, 1e-12))
+                glob = float(np.quantile(np.concatenate([np.asarray(r) for r in ratios]), cfg.calib_quantile))
+                self.calib_ens = np.array([np.quantile(r, cfg.calib_quantile) if len(r) >= 3 * cfg.calib_subsets
+                                           else np.nan for r in ratios])
+                fill = max(glob, float(np.nanmax(np.r_[self.calib_ens, glob])))
+                self.calib_ens = np.where(np.isnan(self.calib_ens), fill, self.calib_ens)
         return history
 
-    def predict(self, uvw, calibrated=True):
-        """(log10 bins mean [n][n_out], relative error estimate [n]) as device tensors."""
+    def members(self, uvw):
+        """log10 bins of every model [n_models][n][n_out] (device float32)."""
         import torch
         cfg = self.cfg
         uvw = np.asarray(uvw, dtype=np.float64)
@@ -304,12 +374,64 @@ class Surrogate:
         for k, m in enumerate(self.models):
             m.forward(x, ext)
             torch.gather(ext, 1, idx, out=preds[k])
-        preds.mul_(self.sigma).add_(self.mu)
-        mean = torch.empty((n, cfg.n_out), dtype=torch.float32, device="cuda")
+        return preds.mul_(self.sigma).add_(self.mu)
+
+    def _estimate(self, members):
+        import torch
+        n = members.shape[1]
+        mean = torch.empty((n, self.cfg.n_out), dtype=torch.float32, device="cuda")
         err = torch.empty(n, dtype=torch.float32, device="cuda")
-        rad.rad_mlp_ensemble_estimate(preds, mean, err)
+        rad.rad_mlp_ensemble_estimate(members, mean, err)
+        return mean, err
+
+    def _fallback_curve(self, members, w, order):
+        """Uncalibrated relative error estimate of the weighted mean spectrum when the first j
+        entries of `order` come from the kernel, for j = 0..n: the L2 norm of the models' spread
+        (standard deviation over models) of the remaining entries' weighted sum, over the L2
+        norm of the mean spectrum."""
+        import torch
+        lin = torch.pow(10.0, members[:, order].double()) * w[order][None, :, None]
+        tail = torch.flip(torch.cumsum(torch.flip(lin, [1]), 1), [1])     # tail[:, j] = sum over i >= j
+        sd = torch.cat([tail.var(0, unbiased=True).sum(1), tail.new_zeros(1)]).sqrt_()
+        served = (torch.pow(10.0, members.double().mean(0)) * w[:, None]).sum(0)
+        return sd / torch.linalg.norm(served).clamp_min(1e-300)
+
+    def ensemble_average(self, x0, th, g, weight=None, fallback_rel=None):
+        """Weighted mean bins [n_omega][n_rbins] (device float64) of one beam's entries and a dict
+        (n_fallback, estimate, estimate_surrogate_only): surrogate predictions, with the entries of
+        largest estimated error contribution recomputed by the kernel until the calibrated
+        estimate of the mean's relative L2 error is at most fallback_rel."""
+        import torch
+        cfg = self.cfg
+        bar = cfg.fallback_rel if fallback_rel is None else fallback_rel
+        n = len(x0)
+        w_np = np.full(n, 1.0 / n) if weight is None else np.asarray(weight, np.float64) / np.sum(weight)
+        w = torch.from_numpy(w_np).cuda()
+        members = self.members(raw_inputs(cfg, x0, th, g))
+        mean, err = self._estimate(members)
+        served = torch.pow(10.0, mean.double())
+        ce = torch.from_numpy(self.calib[self.gamma_bin(g)]).cuda()
+        contrib = err.double() * ce * w * torch.linalg.norm(served, dim=1)
+        order = torch.argsort(contrib, descending=True)
+        g_beam = float(np.exp(np.sum(w_np * np.log(g))))  # weighted geometric mean Lorentz factor
+        curve = float(self.calib_ens[self.gamma_bin(g_beam)]) * self._fallback_curve(members, w, order)
+        j = int(torch.nonzero(curve <= bar)[0, 0].item())
+        keep = order[j:]
+        total = (served[keep] * w[keep, None]).sum(0)
+        if j:
+            fb = order[:j].cpu().numpy()
+            exact = kernel_bins(cfg, x0[fb], th[fb], g[fb]).view(j, -1)
+            total += (exact * w[order[:j], None]).sum(0)
+        info = {"n_fallback": j, "estimate": float(curve[j].item()), "estimate_surrogate_only": float(curve[0].item())}
+        return total.view(cfg.n_omega, cfg.n_rbins), info
+
+    def predict(self, uvw, calibrated=True):
+        """(log10 bins mean [n][n_out], relative error estimate [n]) as device tensors."""
+        import torch
+        mean, err = self._estimate(self.members(uvw))
         if calibrated:
-            err *= self.calib
+            k = self.gamma_bin(gamma_of(self.cfg, np.asarray(uvw)[:, 2]))
+            err *= torch.from_numpy(self.calib[k].astype(np.float32)).cuda()
         return mean, err
 
     def close(self):
@@ -324,50 +446,81 @@ def rel_l2(pred, truth):
     return np.sqrt(((pred - truth) ** 2 * sig).sum(1) / np.maximum((truth ** 2 * sig).sum(1), 1e-300))
 
 
-def evaluate(sur: Surrogate, x0, th, g, log=None):
-    """Surrogate with fallback vs the exact kernel on held-out entries; returns a report dict."""
+def evaluate(sur: Surrogate, x0, th, g, beam, log=None):
+    """Surrogate with fallback vs the exact kernel on held-out beams; returns a report dict.
+
+    Per entry: the surrogate's relative L2 error, its calibrated estimate, and the merged result
+    with per-entry fallback. Per beam: the uniform-weight mean spectrum from ensemble_average
+    (fallback until the estimate is at most fallback_rel) against the kernel's, with the time
+    of each path; gain = kernel time / surrogate-with-fallback time over all beams."""
     import torch
     cfg = sur.cfg
-    xf = raw_inputs(cfg, x0, th, g)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    truth = kernel_bins(cfg, x0, th, g)
-    torch.cuda.synchronize()
-    t_kernel = time.perf_counter() - t0
+    beams = np.unique(beam)
+    # warm-up of every step on two entries (first-call costs are not steady state)
+    kernel_bins(cfg, x0[:2], th[:2], g[:2])
+    sur.ensemble_average(x0[:2], th[:2], g[:2], fallback_rel=0.0)
+    truth = torch.empty((len(x0), cfg.n_omega, cfg.n_rbins), dtype=torch.float64, device="cuda")
+    t_kernel, t_sur, ens = [], [], []
+    for b in beams:
+        sel = np.flatnonzero(beam == b)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        truth[torch.from_numpy(sel).cuda()] = kernel_bins(cfg, x0[sel], th[sel], g[sel])
+        torch.cuda.synchronize()
+        t_kernel.append(time.perf_counter() - t0)
+        t0 = time.perf_counter()
+        avg, info = sur.ensemble_average(x0[sel], th[sel], g[sel])
+        torch.cuda.synchronize()
+        t_sur.append(time.perf_counter() - t0)
+        ref = truth[torch.from_numpy(sel).cuda()].mean(0).reshape(1, -1).cpu().numpy()
+        info["error"] = float(rel_l2(avg.reshape(1, -1).cpu().numpy(), ref)[0])
+        m_only, _ = sur.predict(raw_inputs(cfg, x0[sel], th[sel], g[sel]))
+        info["error_surrogate_only"] = float(rel_l2(torch.pow(10.0, m_only.double()).mean(0, keepdim=True).cpu().numpy(),
+                                                    ref)[0])
+        info["gamma"] = float(g[sel[0]])
+        info["entries"] = int(len(sel))
+        ens.append(info)
 
-    sur.predict(xf[:1])  # warm-up (first-call costs are not part of the steady state)
-    torch.cuda.synchronize()
     t0 = time.perf_counter()
-    mean, err = sur.predict(xf)
+    mean, err = sur.predict(raw_inputs(cfg, x0, th, g))
     err_np = err.cpu().numpy()
     t_predict = time.perf_counter() - t0
-    fb = np.flatnonzero(err_np > cfg.fallback_rel)
-    pred = torch.pow(10.0, mean.double()).view(-1, cfg.n_omega, cfg.n_rbins)
-    if fb.size:
-        pred[torch.from_numpy(fb).cuda()] = kernel_bins(cfg, x0[fb], th[fb], g[fb])
-    torch.cuda.synchronize()
-    t_sur = time.perf_counter() - t0
-
     tr = truth.cpu().numpy().reshape(len(x0), -1)
-    pr = pred.cpu().numpy().reshape(len(x0), -1)
     sur_only = (10.0 ** mean.double().cpu().numpy()).reshape(len(x0), -1)
     err_sur = rel_l2(sur_only, tr)
-    err_merged = rel_l2(pr, tr)
-    ens_t, ens_p = tr.mean(0), pr.mean(0)
-    s_ens = ens_t >= 1e-3 * ens_t.max()
-    ens_err = np.abs(ens_p - ens_t)[s_ens] / ens_t[s_ens]
-    # calibration: fraction of entries whose estimate is at least their actual error
-    calibrated = float(np.mean(err_np >= err_sur))
+    fb = err_np > cfg.fallback_rel
+    merged = np.where(fb[:, None], tr, sur_only)
+    err_merged = rel_l2(merged, tr)
+    e_err = np.array([e["error"] for e in ens])
+    eps = (2.0 * x0 - 1.0) ** 2 + th ** 2
+    by_eps = {}
+    for lo, hi in ((0.0, 0.5), (0.5, 0.9), (0.9, 1.1), (1.1, 10.0)):
+        sel = (eps >= lo) & (eps < hi)
+        if sel.any():
+            by_eps[f"{lo}-{hi}"] = [int(sel.sum()), float(np.median(err_sur[sel])), float(np.quantile(err_sur[sel], 0.9))]
+    gbin = sur.gamma_bin(g)
+    by_gamma = {int(k): [int((gbin == k).sum()), float(np.median(err_sur[gbin == k]))] for k in np.unique(gbin)}
+    e_est = np.array([e["estimate"] for e in ens])
+    n_fb = sum(e["n_fallback"] for e in ens)
     report = {
-        "heldout": int(len(x0)), "fallback_fraction": float(fb.size / len(x0)),
-        "rel_l2_surrogate_median": float(np.median(err_sur)), "rel_l2_surrogate_p90": float(np.quantile(err_sur, 0.9)),
-        "rel_l2_merged_max": float(err_merged.max()), "rel_l2_merged_median": float(np.median(err_merged)),
-        "rel_l2_merged_p99": float(np.quantile(err_merged, 0.99)), "calibration_factor": sur.calib,
-        "estimate_covers_error_fraction": calibrated,
-        "ensemble_spectrum_max_rel_err": float(ens_err.max()), "ensemble_spectrum_mean_rel_err": float(ens_err.mean()),
-        "t_kernel_s": t_kernel, "t_predict_s": t_predict, "t_surrogate_with_fallback_s": t_sur,
-        "gain": t_kernel / t_sur,
-        "spectra_per_s_kernel": len(x0) / t_kernel, "spectra_per_s_surrogate": len(x0) / t_sur,
+        "heldout": int(len(x0)), "beams": int(len(beams)), "fallback_rel": cfg.fallback_rel,
+        "calibration_factor": [float(c) for c in sur.calib], "calibration_factor_mean": [float(c) for c in sur.calib_ens],
+        "entry_rel_l2_by_eps": by_eps, "entry_rel_l2_by_gamma_bin": by_gamma,
+        "mean_error_surrogate_only_median": float(np.median([e["error_surrogate_only"] for e in ens])),
+        "mean_error_surrogate_only_max": float(np.max([e["error_surrogate_only"] for e in ens])),
+        "entry_rel_l2_surrogate_median": float(np.median(err_sur)),
+        "entry_rel_l2_surrogate_p90": float(np.quantile(err_sur, 0.9)),
+        "entry_estimate_covers_error_fraction": float(np.mean(err_np >= err_sur)),
+        "entry_fallback_fraction": float(fb.mean()), "entry_rel_l2_merged_max": float(err_merged.max()),
+        "mean_error_max": float(e_err.max()), "mean_error_median": float(np.median(e_err)),
+        "mean_estimate_max": float(e_est.max()),
+        "mean_estimate_covers_error_fraction": float(np.mean(e_est >= e_err)),
+        "mean_surrogate_only_estimate_median": float(np.median([e["estimate_surrogate_only"] for e in ens])),
+        "mean_fallback_fraction": float(n_fb / len(x0)),
+        "t_kernel_s": float(sum(t_kernel)), "t_surrogate_with_fallback_s": float(sum(t_sur)),
+        "t_predict_all_s": t_predict, "gain": float(sum(t_kernel) / sum(t_sur)),
+        "spectra_per_s_kernel": len(x0) / sum(t_kernel), "spectra_per_s_surrogate": len(x0) / sum(t_sur),
+        "per_beam": ens,
     }
     if log:
         log(json.dumps(report))
@@ -381,6 +534,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--models", type=int, default=4)
     ap.add_argument("--n-gamma", type=int, default=64)
+    ap.add_argument("--beams", type=int, default=16)
+    ap.add_argument("--save", default="")
     ap.add_argument("--quiet", action="store_true")
     a = ap.parse_args(argv)
     import torch
@@ -394,21 +549,24 @@ def main(argv=None):
     t_data = time.perf_counter() - t0
     terms = a.train * cfg.n_samples * cfg.n_omega * (cfg.n_side * cfg.n_side // 2)
     log(json.dumps({"data_s": t_data, "terms": terms, "terms_per_s": terms / t_data}))
-    vx0, vth, vg = sample_entries(cfg, cfg.n_val, seed=7, discrete_gamma=False)
+    vx0, vth, vg, vbeam = sample_beams(cfg, cfg.beams_val, cfg.n_val // cfg.beams_val, seed=7)
     vbins = kernel_bins(cfg, vx0, vth, vg)
     sur = Surrogate(cfg)
     t0 = time.perf_counter()
-    hist = sur.fit(raw_inputs(cfg, x0, th, g), bins, raw_inputs(cfg, vx0, vth, vg), vbins,
+    hist = sur.fit(raw_inputs(cfg, x0, th, g), bins, raw_inputs(cfg, vx0, vth, vg), vbins, vbeam,
                    log=None if a.quiet else log)
     torch.cuda.synchronize()
     t_fit = time.perf_counter() - t0
     del bins
-    hx0, hth, hg = sample_entries(cfg, a.heldout, seed=6, discrete_gamma=False)
-    rep = evaluate(sur, hx0, hth, hg)
+    hx0, hth, hg, hbeam = sample_beams(cfg, a.beams, a.heldout // a.beams, seed=6)
+    rep = evaluate(sur, hx0, hth, hg, hbeam)
     rep.update({"train": a.train, "steps": cfg.steps, "models": cfg.n_models, "fit_s": t_fit, "data_s": t_data,
                 "final_losses": [h[2] for h in hist if h[1] == cfg.steps - 1],
                 "first_losses": [h[2] for h in hist if h[1] == 0]})
     print(json.dumps(rep))
+    if a.save:
+        with open(a.save, "w") as f:
+            json.dump(rep, f, indent=1)
     st = rad.rad_device_status(1)
     if st:
         raise rad.RadError(st, "device status")

@@ -1,6 +1,7 @@
 """Shared helpers of the GPU parity tests: run the CUDA path through the C ABI and compare
 with the FP64 oracle under the tolerances stated in the tests."""
 import numpy as np
+from scipy.special import jv
 
 import oracle as O
 import paper_1910_10391_gb300 as rad
@@ -75,3 +76,14 @@ def assert_mixed_close(got, ref, rel=1e-4, level=1e-3):
     # everywhere else the absolute error stays below rel * level * peak
     assert np.all(np.abs(got - ref)[~sel] <= rel * level * peak * 10), "small bins off"
     return stats
+
+
+def strong_undulator_on_axis(n, K, gamma, N):
+    """Textbook on-axis line height of harmonic n of a planar undulator (classical):
+    d2I/dhw dOmega = alpha N^2 gamma^2 F_n(K), F_n = n^2 K^2/(1+K^2/2)^2
+    [J_{(n-1)/2}(xi) - J_{(n+1)/2}(xi)]^2 with xi = n K^2/(4 (1+K^2/2)) for odd n, 0 for even n."""
+    if n % 2 == 0:
+        return 0.0
+    xi = n * K * K / (4 * (1 + K * K / 2))
+    Fn = n * n * K * K / (1 + K * K / 2) ** 2 * (jv((n - 1) // 2, xi) - jv((n + 1) // 2, xi)) ** 2
+    return O.ALPHA * N * N * gamma * gamma * Fn

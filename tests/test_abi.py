@@ -43,3 +43,22 @@ def test_invalid_shapes_rejected_before_device_work(lib):
     rc = lib.rad_spectrum(None, 0, None, 0, None, None, None, None, 1, None, None, None, 1, 5, 0,
                           None, None, None, 0, None, 0, None)
     assert rc == rad.RAD_EINVAL
+
+
+def test_trajectory_argument_checks(lib):
+    """rad_channeling_trajectories rejects bad host arguments before any device work."""
+    ch = rad.RadChannel(20.0, 1.92e-10, 10.6e6, 0.0937, 0.075e-10, 0.51099895e6, 1, rad.RAD_TRAJ_MS)
+    P = ctypes.c_void_p(16)  # never dereferenced: every call below fails its host checks
+    args = lambda c, n, dt: (c, n, P, 10, P, P, P, None, None, dt, 1, P, None, None)
+    assert lib.rad_channeling_trajectories(*args(None, 1, 5e-9)) == rad.RAD_EINVAL
+    assert lib.rad_channeling_trajectories(*args(ctypes.byref(ch), -1, 5e-9)) == rad.RAD_EINVAL
+    assert lib.rad_channeling_trajectories(*args(ctypes.byref(ch), 1, 0.0)) == rad.RAD_EINVAL
+    assert lib.rad_channeling_trajectories(*args(ctypes.byref(ch), 0, 5e-9)) == rad.RAD_OK
+    for bad in (dict(flags=8), dict(charge_sign=0), dict(d_p=0.0), dict(mass_eV=-1.0), dict(U0_eV=-1.0),
+                dict(rho=0.0), dict(X0=0.0)):
+        c2 = rad.RadChannel(20.0, 1.92e-10, 10.6e6, 0.0937, 0.075e-10, 0.51099895e6, 1, rad.RAD_TRAJ_MS)
+        for k, v in bad.items():
+            setattr(c2, k, v)
+        assert lib.rad_channeling_trajectories(*args(ctypes.byref(c2), 1, 5e-9)) == rad.RAD_EINVAL, bad
+    r = lib.rad_channeling_trajectories(ctypes.byref(ch), 1, None, 10, P, P, P, None, None, 5e-9, 1, P, None, None)
+    assert r == rad.RAD_EINVAL  # null offsets

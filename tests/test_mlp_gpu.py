@@ -38,7 +38,7 @@ def test_forward_and_gradients_match_reference():
     y_ref = M.forward(p, x, n_in, width, depth, n_out)
     assert np.abs(y - y_ref).max() <= 2e-2 * np.abs(y_ref).max()
     loss = torch.zeros(1, dtype=torch.float32, device="cuda")
-    mask = (rng.random((B, n_out)) < 0.7).astype(np.float32)
+    mask = np.where(rng.random((B, n_out)) < 0.7, rng.uniform(0.05, 2.0, (B, n_out)), 0.0).astype(np.float32)
     m.backward(dx, dt, loss, mask=torch.from_numpy(mask).cuda())
     torch.cuda.synchronize()
     g = m.get(1).astype(np.float64)
@@ -103,5 +103,10 @@ def test_label_and_ensemble_kernels():
     err = torch.empty(20, dtype=torch.float32, device="cuda")
     rad.rad_mlp_ensemble_estimate(dp, mu, err)
     np.testing.assert_allclose(mu.cpu().numpy(), preds.mean(0), rtol=1e-5, atol=1e-7)
-    ref = np.log(10) * np.sqrt(preds.astype(np.float64).var(0, ddof=1).mean(1))
+    p64 = preds.astype(np.float64)
+    p64 = (p64 + np.linspace(-3, 0, 30)[None, None, :]).astype(np.float32).astype(np.float64)  # three decades
+    dp.copy_(torch.from_numpy(p64.astype(np.float32)))
+    rad.rad_mlp_ensemble_estimate(dp, mu, err)
+    s2 = 10.0 ** (2 * p64.mean(0))
+    ref = np.log(10) * np.sqrt((s2 * p64.var(0, ddof=1)).sum(1) / s2.sum(1))
     np.testing.assert_allclose(err.cpu().numpy(), ref, rtol=1e-4)
