@@ -328,6 +328,7 @@ int rad_standardize(float *y, int64_t rows, int cols, const float *mean, const f
 #define RAD_TRAJ_MS 1      /* multiple Coulomb scattering kicks after every step            */
 #define RAD_TRAJ_LL 2      /* radiation-reaction drag (leading Landau-Lifshitz term)        */
 #define RAD_TRAJ_MS_LOSS 4 /* energy loss of each kick, m alpha/(2 pi) gamma^3 theta^2       */
+#define RAD_TRAJ_FP32 8    /* FP32 arithmetic with double-float state (else FP64 throughout)  */
 
 /* Planar channel of the trajectory integrator: a harmonic well U(s) = U0 (2 s / d_p)^2 in the
  * distance s to the nearest channel centre (a stand-in for the planar continuum potential of
@@ -372,6 +373,11 @@ typedef struct {
  *   offsets, non-finite entry values or energy <= mass is skipped and RAD_EDATA is recorded
  *   for rad_device_status().
  */
+/*   Precision: FP64 throughout by default. With RAD_TRAJ_FP32 the stages are evaluated in FP32
+ *   and every state variable is kept as a double-float (hi + lo, about 48 bits) updated with
+ *   error-free sums and products; the channel offset replaces the absolute position (channel
+ *   index + offset); records are then within about 1e-7 relative of the FP64 form for
+ *   channeled motion (dvz, a_x, a_y, a_z carry FP32 precision). */
 int rad_channeling_trajectories(const rad_channel *ch, int64_t n_particles, const int64_t *offsets,
                                 int64_t n_samples_total, const double *energy_eV, const double *x0,
                                 const double *thx0, const double *thy0, const int64_t *particle_ids,

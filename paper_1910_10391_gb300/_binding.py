@@ -21,7 +21,7 @@ RAD_OK, RAD_EINVAL, RAD_ENOMEM, RAD_ECUDA, RAD_ETIMEOUT, RAD_EUNSUPPORTED, RAD_E
 RAD_CLASSICAL, RAD_SPIN0, RAD_SPIN_HALF = 0, 1, 2
 RAD_FP64, RAD_MIXED = 0, 1
 RAD_NREC = 10
-RAD_TRAJ_MS, RAD_TRAJ_LL, RAD_TRAJ_MS_LOSS = 1, 2, 4
+RAD_TRAJ_MS, RAD_TRAJ_LL, RAD_TRAJ_MS_LOSS, RAD_TRAJ_FP32 = 1, 2, 4, 8
 
 
 class RadChannel(ctypes.Structure):

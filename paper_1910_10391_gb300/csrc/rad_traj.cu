@@ -181,6 +181,207 @@ __global__ void k_channel(const Chan C, int64_t n_particles, const int64_t *__re
   }
 }
 
+// ------------------------------------------------------------------------------------
+// Mixed precision (RAD_TRAJ_FP32): FP32 arithmetic with double-float state
+// ------------------------------------------------------------------------------------
+// GB300 issues FP32 at 72x its FP64 rate, so this form evaluates the RK4 stages in FP32 and
+// keeps every state variable as an unevaluated sum hi + lo of two floats (about 48 bits),
+// updated with error-free transformations (Knuth's two-sum, FMA two-product). The position is
+// kept as (channel index m, offset s from the channel centre) so that s stays below d_p/2 in
+// magnitude however far the particle drifts. The x and y increments h v use a double-float
+// product of the step h and the double-float velocity; the other increments are FP32.
+// Records are formed in FP64 from the double-float values.
+struct Chan32 {
+  float d_f, half_d, kf_hi, kf_lo, dt_hi, dt_lo, dt6_hi, dt6_lo, h2_6, h_half, ll_k, loss_k, dens_pref, nexp2_rho,
+      var_k, inv_mass;
+  double d_p, centre, dt, mass;
+  int ms, ll, ms_loss;
+};
+
+struct DF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ DF df_of(double v) {
+  const float h = static_cast<float>(v);
+  return DF{h, static_cast<float>(v - static_cast<double>(h))};
+}
+
+__device__ __forceinline__ double df_val(const DF &a) { return static_cast<double>(a.hi) + static_cast<double>(a.lo); }
+
+// a += d (two-sum, then renormalise)
+__device__ __forceinline__ void df_add(DF &a, float d) {
+  const float s = __fadd_rn(a.hi, d);
+  const float bb = __fsub_rn(s, a.hi);
+  const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(d, bb));
+  const float l = __fadd_rn(a.lo, err);
+  const float h2 = __fadd_rn(s, l);
+  a.lo = __fsub_rn(l, __fsub_rn(h2, s));
+  a.hi = h2;
+}
+
+// a += (h_hi + h_lo) * (v.hi + v.lo), the product to about 46 bits (two-product of the high parts)
+__device__ __forceinline__ void df_add_prod(DF &a, float h_hi, float h_lo, const DF &v) {
+  const float p = __fmul_rn(h_hi, v.hi);
+  const float pe = __fmaf_rn(h_hi, v.hi, -p);
+  const float tail = __fmaf_rn(h_hi, v.lo, __fmaf_rn(h_lo, v.hi, pe));
+  df_add(a, p);
+  df_add(a, tail);
+}
+
+struct D32 {
+  float vx, vy, a, dvz, dE;
+};
+
+// stage derivative at offset s (any value; wrapped into the channel), velocity (vx, vy), energy
+// offset dE from the entry energy E0 (for 1/gamma0^2 - 1/gamma^2), reciprocal energy (iE_hi, iE_lo)
+__device__ __forceinline__ D32 deriv32(const Chan32 &C, float s, float vx, float vy, float dEoff, float g,
+                                       float g0, float q0, float iE_hi, float iE_lo) {
+  float sw = s;
+  if (sw >= C.half_d) sw -= C.d_f;
+  else if (sw < -C.half_d) sw += C.d_f;
+  const float F = -__fmaf_rn(C.kf_hi, sw, C.kf_lo * sw);  // -8 U0 s / d_p^2, eV/m
+  D32 d;
+  d.vx = vx;
+  d.vy = vy;
+  d.a = __fmaf_rn(F, iE_hi, F * iE_lo);
+  // v_z - beta0 = ((1/g0^2 - 1/g^2) - v_perp^2 - 1/(4 g0^4)) / (v_z + beta0), with
+  // v_z + beta0 = 2 - O(1e-8): the FP32 quotient is half the numerator
+  const float dg = dEoff * C.inv_mass;  // gamma - gamma0
+  const float dinv = (dg * (g + g0)) / ((g * g) * (g0 * g0));
+  d.dvz = 0.5f * (dinv - __fmaf_rn(vx, vx, vy * vy) - q0);
+  d.dE = C.ll ? C.ll_k * (g * g) * (F * F) : 0.f;
+  return d;
+}
+
+__global__ void k_channel_mixed(const Chan32 C, int64_t n_particles, const int64_t *__restrict__ offsets,
+                                int64_t n_total, const double *__restrict__ energy, const double *__restrict__ x0,
+                                const double *__restrict__ thx0, const double *__restrict__ thy0,
+                                const int64_t *__restrict__ ids, uint64_t seed, double *__restrict__ out,
+                                double *__restrict__ e_out, int *dev_status) {
+  for (int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; p < n_particles;
+       p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t off = offsets[p], L = offsets[p + 1] - off;
+    const double E0 = energy[p];
+    if (off < 0 || L < 1 || off + L > n_total || !(E0 > C.mass) || !isfinite(E0) || !isfinite(x0[p]) ||
+        !isfinite(thx0[p]) || (thy0 && !isfinite(thy0[p]))) {
+      atomicCAS(dev_status, 0, RAD_EDATA);
+      continue;
+    }
+    const uint64_t pid = ids ? static_cast<uint64_t>(ids[p]) : static_cast<uint64_t>(p);
+    const double g0d = E0 / C.mass;
+    const float g0 = static_cast<float>(g0d);
+    const float q0 = static_cast<float>(1.0 / (4.0 * (g0d * g0d) * (g0d * g0d)));
+    // position as channel index and offset from its centre
+    const double u = (x0[p] - C.centre) / C.d_p;
+    double m = floor(u + 0.5);
+    DF s = df_of((x0[p] - C.centre) - m * C.d_p);
+    DF y{0.f, 0.f}, dz{0.f, 0.f};
+    DF vx = df_of(thx0[p]), vy = df_of(thy0 ? thy0[p] : 0.0);
+    DF E = df_of(E0);
+    const DF E0f = E;
+    float kx = 0.f, ky = 0.f;
+    double *rec = out + off * kRec;
+    for (int64_t k = 0; k < L; ++k, rec += kRec) {
+      const float dEoff = __fadd_rn(__fsub_rn(E.hi, E0f.hi), __fsub_rn(E.lo, E0f.lo));
+      const float g = __fmaf_rn(dEoff, C.inv_mass, g0);
+      // 1/E to about 46 bits: one Newton correction of the FP32 reciprocal
+      const float r = __frcp_rn(E.hi);
+      const float res = __fmaf_rn(-E.lo, r, __fmaf_rn(-E.hi, r, 1.0f));
+      const float iE_hi = r, iE_lo = res * r;
+      // record k
+      const D32 d0 = deriv32(C, s.hi + s.lo, vx.hi, vy.hi, dEoff, g, g0, q0, iE_hi, iE_lo);
+      const float ax = d0.a + kx, ay = ky;
+      const float gdot = C.ll ? d0.dE * C.inv_mass : 0.f;
+      rec[F_T] = static_cast<double>(k) * C.dt;
+      rec[F_X] = (m * C.d_p + C.centre) + df_val(s);
+      rec[F_Y] = df_val(y);
+      rec[F_DZ] = df_val(dz);
+      rec[F_VX] = df_val(vx);
+      rec[F_VY] = df_val(vy);
+      rec[F_DVZ] = static_cast<double>(d0.dvz);
+      rec[F_AX] = static_cast<double>(ax);
+      rec[F_AY] = static_cast<double>(ay);
+      // a_z = (dgamma/dt / gamma^3 - v_perp . a_perp) / v_z with v_z = 1 to FP32 precision
+      rec[F_AZ] = static_cast<double>(gdot / (g * g * g) - __fmaf_rn(vx.hi, ax, vy.hi * ay));
+      if (e_out) e_out[off + k] = df_val(E);
+      kx = ky = 0.f;
+      if (k == L - 1) break;
+      // RK4 stages in FP32 around the double-float state
+      const float h2 = C.h_half, h = C.dt_hi;
+      const D32 k1 = d0;
+      const D32 k2 = deriv32(C, s.hi + (s.lo + h2 * k1.vx), vx.hi + (vx.lo + h2 * k1.a), vy.hi + vy.lo,
+                             dEoff + h2 * k1.dE, g, g0, q0, iE_hi, iE_lo);
+      const D32 k3 = deriv32(C, s.hi + (s.lo + h2 * k2.vx), vx.hi + (vx.lo + h2 * k2.a), vy.hi + vy.lo,
+                             dEoff + h2 * k2.dE, g, g0, q0, iE_hi, iE_lo);
+      const D32 k4 = deriv32(C, s.hi + (s.lo + h * k3.vx), vx.hi + (vx.lo + h * k3.a), vy.hi + vy.lo,
+                             dEoff + h * k3.dE, g, g0, q0, iE_hi, iE_lo);
+      // x' = v is linear in the stages: sum/6 = v + h (a1 + a2 + a3)/6. Every factor that
+      // multiplies all steps alike (dt, dt/6) is a double-float pair: an FP32-rounded constant
+      // would scale every increment by the same relative error and the oscillation's phase
+      // would drift with it.
+      df_add_prod(s, C.dt_hi, C.dt_lo, vx);
+      df_add(s, C.h2_6 * (k1.a + k2.a + k3.a));
+      df_add_prod(y, C.dt_hi, C.dt_lo, vy);
+      const float sa = k1.a + 2.f * k2.a + 2.f * k3.a + k4.a;
+      df_add(vx, __fmaf_rn(sa, C.dt6_hi, sa * C.dt6_lo));
+      const float sz = k1.dvz + 2.f * k2.dvz + 2.f * k3.dvz + k4.dvz;
+      df_add(dz, __fmaf_rn(sz, C.dt6_hi, sz * C.dt6_lo));
+      if (C.ll) {
+        const float se = k1.dE + 2.f * k2.dE + 2.f * k3.dE + k4.dE;
+        df_add(E, __fmaf_rn(se, C.dt6_hi, se * C.dt6_lo));
+      }
+      // keep the offset inside the channel
+      if (s.hi >= C.half_d) {
+        m += 1.0;
+        df_add(s, -C.d_f);
+        df_add(s, -static_cast<float>(C.d_p - static_cast<double>(C.d_f)));
+      } else if (s.hi < -C.half_d) {
+        m -= 1.0;
+        df_add(s, C.d_f);
+        df_add(s, static_cast<float>(C.d_p - static_cast<double>(C.d_f)));
+      }
+      if (C.ms) {
+        // distances to the two nearest planes from the offset (planes at +-d/2 around a
+        // positron channel centre, at 0 and +-d around an electron channel centre)
+        const float sc = s.hi + s.lo;
+        float r1, r2;
+        if (C.centre != 0.0) {
+          r1 = C.half_d + sc;
+          r2 = C.half_d - sc;
+        } else {
+          r1 = sc >= 0.f ? sc : C.d_f + sc;
+          r2 = C.d_f - r1;
+        }
+        const float n = C.dens_pref * (exp2f(C.nexp2_rho * r1 * r1) + exp2f(C.nexp2_rho * r2 * r2));
+        const float var = (C.var_k * n) / (E.hi * E.hi);
+        if (var > 0.f) {
+          uint32_t c[4] = {static_cast<uint32_t>(pid), static_cast<uint32_t>(k), 1u, static_cast<uint32_t>(pid >> 32)};
+          philox(c, static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32));
+          // the 53-bit uniforms of the FP64 form, rounded to FP32 (never 0)
+          const float u1 = __fmaf_rn(static_cast<float>(c[1] >> 6) + 0.5f, 1.1102230246251565e-16f,
+                                     static_cast<float>(c[0] >> 5) * 7.450580596923828e-09f);
+          const float u2 = __fmaf_rn(static_cast<float>(c[3] >> 6) + 0.5f, 1.1102230246251565e-16f,
+                                     static_cast<float>(c[2] >> 5) * 7.450580596923828e-09f);
+          const float rad = sqrtf(-2.0f * logf(u1));
+          float sn, cs;
+          sincospif(2.0f * u2, &sn, &cs);
+          const float sd = sqrtf(var);
+          const float dthx = sd * (rad * cs), dthy = sd * (rad * sn);
+          kx = dthx / C.dt_hi;
+          ky = dthy / C.dt_hi;
+          df_add(vx, dthx);
+          df_add(vy, dthy);
+          if (C.ms_loss) {
+            const float gk = E.hi * C.inv_mass;
+            df_add(E, -C.loss_k * (gk * gk * gk) * __fmaf_rn(dthx, dthx, dthy * dthy));
+          }
+        }
+      }
+    }
+  }
+}
+
 }  // namespace
 }  // namespace rad
 
@@ -194,7 +395,7 @@ extern "C" int rad_channeling_trajectories(const rad_channel *ch, int64_t n_part
   if (n_particles == 0) return RAD_OK;
   if (!offsets || !energy_eV || !x0 || !thx0 || !out) return RAD_EINVAL;
   if (!(dt > 0.0) || !isfinite(dt) || !(ch->d_p > 0.0) || !(ch->mass_eV > 0.0) || !(ch->U0_eV >= 0.0) ||
-      (ch->charge_sign != 1 && ch->charge_sign != -1) || (ch->flags & ~7))
+      (ch->charge_sign != 1 && ch->charge_sign != -1) || (ch->flags & ~15))
     return RAD_EINVAL;
   if ((ch->flags & RAD_TRAJ_MS) && !(ch->X0 > 0.0 && ch->rho > 0.0 && ch->eps_s_eV >= 0.0)) return RAD_EINVAL;
   cudaError_t e;
@@ -218,12 +419,44 @@ extern "C" int rad_channeling_trajectories(const rad_channel *ch, int64_t n_part
   C.ms = (ch->flags & RAD_TRAJ_MS) != 0;
   C.ll = (ch->flags & RAD_TRAJ_LL) != 0;
   C.ms_loss = (ch->flags & RAD_TRAJ_MS_LOSS) != 0;
-  const int block = 64;
+  // one thread per particle; small ensembles spread one warp per SM (the integration is a
+  // dependent chain per thread), large ones fill the SMs with 128-thread blocks
+  const int block = n_particles < 152 * 4 * 32 ? 32 : 128;
   int64_t grid = (n_particles + block - 1) / block;
   if (grid > 1 << 20) grid = 1 << 20;
-  k_channel<<<static_cast<unsigned>(grid), block, 0, static_cast<cudaStream_t>(stream)>>>(
-      C, n_particles, offsets, n_samples_total, energy_eV, x0, thx0, thy0, particle_ids, dt, seed, out, energy_out,
-      ds);
+  if (ch->flags & RAD_TRAJ_FP32) {
+    Chan32 M;
+    M.d_p = ch->d_p;
+    M.centre = C.centre;
+    M.dt = dt;
+    M.mass = ch->mass_eV;
+    M.d_f = static_cast<float>(ch->d_p);
+    M.half_d = 0.5f * M.d_f;
+    const double kf = 8.0 * ch->U0_eV / (ch->d_p * ch->d_p);
+    M.kf_hi = static_cast<float>(kf);
+    M.kf_lo = static_cast<float>(kf - static_cast<double>(M.kf_hi));
+    M.dt_hi = static_cast<float>(dt);
+    M.dt_lo = static_cast<float>(dt - static_cast<double>(M.dt_hi));
+    M.h_half = static_cast<float>(0.5 * dt);
+    M.dt6_hi = static_cast<float>(dt / 6.0);
+    M.dt6_lo = static_cast<float>(dt / 6.0 - static_cast<double>(M.dt6_hi));
+    M.h2_6 = static_cast<float>(dt * dt / 6.0);
+    M.ll_k = static_cast<float>(C.ll_k);
+    M.loss_k = static_cast<float>(C.loss_k);
+    M.dens_pref = static_cast<float>(C.dens_pref);
+    M.nexp2_rho = static_cast<float>(-C.inv_rho2 / log(2.0));
+    M.var_k = static_cast<float>(C.var_k);
+    M.inv_mass = static_cast<float>(1.0 / ch->mass_eV);
+    M.ms = C.ms;
+    M.ll = C.ll;
+    M.ms_loss = C.ms_loss;
+    k_channel_mixed<<<static_cast<unsigned>(grid), block, 0, static_cast<cudaStream_t>(stream)>>>(
+        M, n_particles, offsets, n_samples_total, energy_eV, x0, thx0, thy0, particle_ids, seed, out, energy_out, ds);
+  } else {
+    k_channel<<<static_cast<unsigned>(grid), block, 0, static_cast<cudaStream_t>(stream)>>>(
+        C, n_particles, offsets, n_samples_total, energy_eV, x0, thx0, thy0, particle_ids, dt, seed, out,
+        energy_out, ds);
+  }
   e = cudaGetLastError();
   return e == cudaSuccess ? RAD_OK : cuda_status(e);
 }

@@ -8,10 +8,12 @@ radial bins of the emission angle, at 256 photon energies hw/E log-spaced in [1e
 An ensemble of networks gives error estimates: per entry (entries whose estimate exceeds
 `fallback_rel` are recomputed with the exact kernel), and for the weighted mean spectrum of a
 beam of entries (the entries with the largest estimated error contributions are recomputed with
-the kernel until the mean's estimate is at most `fallback_rel`). Both estimates are calibrated on
-validation entries the networks do not train on. The loss weights each output by the square of
-its value relative to the entry's maximum (plus a floor): to first order that is the relative L2
-error of the spectrum that the log-space error causes.
+the kernel until the mean's estimate is at most `fallback_rel`). Both estimates are calibrated,
+per bin of log gamma, on validation beams the networks do not train on. Entries with transverse
+energy above `eps_gate` (near or over the barrier, where plane crossings change the spectrum's
+character) always take the kernel. The loss weights each output by the square of its value
+relative to the entry's maximum (plus a floor): to first order that is the relative L2 error of
+the spectrum that the log-space error causes.
 
 Angle grid per gamma: 32 x 32 cells over +-(theta_L + 3/gamma); radial bins of |theta| in
 [0, theta_L + 3/gamma). Motion without scattering stays in the x-z plane, so the spectrum is
@@ -26,7 +28,7 @@ labels by the whole number of grid steps that puts hw1 at a fixed index is exact
 predicts on that extended, aligned grid (masked loss outside each entry's window) and sees
 the remaining fraction of a step as an input.
 
-  python -m paper_1910_10391_gb300.surrogate --train 200000 --heldout 4096
+  python -m paper_1910_10391_gb300.surrogate --train 200000 --heldout 4096 --beams 16 --steps 40000
 """
 from __future__ import annotations
 
@@ -77,6 +79,8 @@ class Config:
     beams_val: int = 32
     calib_subsets: int = 8
     calib_gamma_bins: int = 4
+    beam_divergence: float = 0.3
+    eps_gate: float = 0.9
 
     @property
     def n_in(self):
@@ -116,16 +120,21 @@ def sample_entries(cfg: Config, n: int, seed: int, discrete_gamma: bool):
     return x0, th, g
 
 
-def sample_beams(cfg: Config, n_beams: int, per_beam: int, seed: int):
+def sample_beams(cfg: Config, n_beams: int, per_beam: int, seed: int, divergence=None):
     """Beams of entries: each beam has one Lorentz factor, log-uniform in [gamma_lo, gamma_hi];
-    its entries have x0/d_p ~ U[0, 1) and theta0/theta_L ~ U[-theta_frac, theta_frac].
+    its entries have x0/d_p ~ U[0, 1) and theta0/theta_L ~ N(0, divergence^2) clipped to
+    [-theta_frac, theta_frac] (a beam with the ensemble workloads' divergence, 0.3 theta_L), or
+    ~ U[-theta_frac, theta_frac] when divergence is None (the training coverage).
     Returns (x0, theta0/theta_L, gamma, beam index) per entry."""
     rng = np.random.default_rng(seed)
     lo, hi = math.log(cfg.gamma_lo), math.log(cfg.gamma_hi)
     gb = np.exp(rng.uniform(lo, hi, n_beams))
     n = n_beams * per_beam
     x0 = rng.uniform(0.0, 1.0, n)
-    th = rng.uniform(-cfg.theta_frac, cfg.theta_frac, n)
+    if divergence is None:
+        th = rng.uniform(-cfg.theta_frac, cfg.theta_frac, n)
+    else:
+        th = np.clip(rng.normal(0.0, divergence, n), -cfg.theta_frac, cfg.theta_frac)
     beam = np.repeat(np.arange(n_beams), per_beam)
     return x0, th, gb[beam], beam
 
@@ -176,6 +185,13 @@ def raw_inputs(cfg: Config, x0, th, g):
     """(u, v, w) in [-1, 1]: 2 x0/d_p - 1, theta0/(theta_frac theta_L), scaled log gamma."""
     lo, hi = math.log(cfg.gamma_lo), math.log(cfg.gamma_hi)
     return np.stack([2.0 * x0 - 1.0, th / cfg.theta_frac, 2.0 * (np.log(g) - lo) / (hi - lo) - 1.0], 1)
+
+
+def transverse_energy(cfg: Config, uvw):
+    """Transverse energy in units of the well depth, eps = u^2 + (theta_frac v)^2 (eps > 1: over
+    the barrier)."""
+    uvw = np.asarray(uvw, dtype=np.float64)
+    return uvw[:, 0] ** 2 + (cfg.theta_frac * uvw[:, 1]) ** 2
 
 
 def feature_map(cfg: Config, uvw):
@@ -343,15 +359,25 @@ class Surrogate:
             if val_beam is not None:
                 rng = np.random.default_rng(cfg.fourier_seed + 1)
                 ratios = [[] for _ in range(nb)]
+                gated_all = transverse_energy(cfg, val_uvw) > cfg.eps_gate
                 for b in np.unique(val_beam):
                     sel = np.flatnonzero(val_beam == b)
                     k = int(gb[sel[0]])
                     for j in range(cfg.calib_subsets):
                         sub = sel if j == 0 else np.sort(rng.choice(sel, size=max(len(sel) // 2, 2), replace=False))
+                        # gated entries come from the kernel (exact); the estimate and the error
+                        # are those of the mean with the rest from the surrogate
+                        gsub = gated_all[sub]
+                        if gsub.all():
+                            continue
+                        order = torch.from_numpy(np.r_[np.flatnonzero(gsub), np.flatnonzero(~gsub)]).cuda()
                         st = torch.from_numpy(sub).cuda()
                         w = torch.full((len(sub),), 1.0 / len(sub), dtype=torch.float64, device="cuda")
-                        est = float(self._fallback_curve(members[:, st], w, torch.arange(len(sub), device="cuda"))[0])
-                        act = rel_l2(served[st].mean(0, keepdim=True).cpu().numpy(),
+                        est = float(self._fallback_curve(members[:, st], w, order)[int(gsub.sum())])
+                        mix = served[st].clone()
+                        gi = torch.from_numpy(np.flatnonzero(gsub)).cuda()
+                        mix[gi] = truth[st][gi]
+                        act = rel_l2(mix.mean(0, keepdim=True).cpu().numpy(),
                                      truth[st].mean(0, keepdim=True).cpu().numpy())[0]
                         ratios[k].append(act / max(est, 1e-12))
                 glob = float(np.quantile(np.concatenate([np.asarray(r) for r in ratios]), cfg.calib_quantile))
@@ -407,15 +433,21 @@ class Surrogate:
         n = len(x0)
         w_np = np.full(n, 1.0 / n) if weight is None else np.asarray(weight, np.float64) / np.sum(weight)
         w = torch.from_numpy(w_np).cuda()
-        members = self.members(raw_inputs(cfg, x0, th, g))
+        uvw = raw_inputs(cfg, x0, th, g)
+        members = self.members(uvw)
         mean, err = self._estimate(members)
         served = torch.pow(10.0, mean.double())
         ce = torch.from_numpy(self.calib[self.gamma_bin(g)]).cuda()
         contrib = err.double() * ce * w * torch.linalg.norm(served, dim=1)
+        # entries near or over the barrier always take the kernel: their spectra change character
+        # there (plane crossings) and the network does not reach percent accuracy on them
+        gated = torch.from_numpy(transverse_energy(cfg, uvw) > cfg.eps_gate).cuda()
+        contrib = torch.where(gated, torch.full_like(contrib, float("inf")), contrib)
         order = torch.argsort(contrib, descending=True)
+        j0 = int(gated.sum().item())
         g_beam = float(np.exp(np.sum(w_np * np.log(g))))  # weighted geometric mean Lorentz factor
         curve = float(self.calib_ens[self.gamma_bin(g_beam)]) * self._fallback_curve(members, w, order)
-        j = int(torch.nonzero(curve <= bar)[0, 0].item())
+        j = j0 + int(torch.nonzero(curve[j0:] <= bar)[0, 0].item())
         keep = order[j:]
         total = (served[keep] * w[keep, None]).sum(0)
         if j:
@@ -488,7 +520,7 @@ def evaluate(sur: Surrogate, x0, th, g, beam, log=None):
     tr = truth.cpu().numpy().reshape(len(x0), -1)
     sur_only = (10.0 ** mean.double().cpu().numpy()).reshape(len(x0), -1)
     err_sur = rel_l2(sur_only, tr)
-    fb = err_np > cfg.fallback_rel
+    fb = (err_np > cfg.fallback_rel) | (transverse_energy(cfg, raw_inputs(cfg, x0, th, g)) > cfg.eps_gate)
     merged = np.where(fb[:, None], tr, sur_only)
     err_merged = rel_l2(merged, tr)
     e_err = np.array([e["error"] for e in ens])
@@ -549,7 +581,8 @@ def main(argv=None):
     t_data = time.perf_counter() - t0
     terms = a.train * cfg.n_samples * cfg.n_omega * (cfg.n_side * cfg.n_side // 2)
     log(json.dumps({"data_s": t_data, "terms": terms, "terms_per_s": terms / t_data}))
-    vx0, vth, vg, vbeam = sample_beams(cfg, cfg.beams_val, cfg.n_val // cfg.beams_val, seed=7)
+    vx0, vth, vg, vbeam = sample_beams(cfg, cfg.beams_val, cfg.n_val // cfg.beams_val, seed=7,
+                                       divergence=cfg.beam_divergence)
     vbins = kernel_bins(cfg, vx0, vth, vg)
     sur = Surrogate(cfg)
     t0 = time.perf_counter()
@@ -558,8 +591,18 @@ def main(argv=None):
     torch.cuda.synchronize()
     t_fit = time.perf_counter() - t0
     del bins
-    hx0, hth, hg, hbeam = sample_beams(cfg, a.beams, a.heldout // a.beams, seed=6)
+    hx0, hth, hg, hbeam = sample_beams(cfg, a.beams, a.heldout // a.beams, seed=6, divergence=cfg.beam_divergence)
     rep = evaluate(sur, hx0, hth, hg, hbeam)
+    # per-entry accuracy over the whole training domain (uniform coverage), no fallback
+    ux0, uth, ug, _ = sample_beams(cfg, 64, 16, seed=8)
+    mean_u, _ = sur.predict(raw_inputs(cfg, ux0, uth, ug))
+    tru = kernel_bins(cfg, ux0, uth, ug).reshape(len(ux0), -1).cpu().numpy()
+    err_u = rel_l2(10.0 ** mean_u.double().cpu().numpy(), tru)
+    eps_u = (2.0 * ux0 - 1.0) ** 2 + uth ** 2
+    rep["coverage_entry_rel_l2"] = {
+        "entries": int(len(ux0)), "median": float(np.median(err_u)),
+        "median_channeled": float(np.median(err_u[eps_u < 0.9])),
+        "median_over_barrier": float(np.median(err_u[eps_u > 1.1]))}
     rep.update({"train": a.train, "steps": cfg.steps, "models": cfg.n_models, "fit_s": t_fit, "data_s": t_data,
                 "final_losses": [h[2] for h in hist if h[1] == cfg.steps - 1],
                 "first_losses": [h[2] for h in hist if h[1] == 0]})

@@ -54,7 +54,7 @@ def test_trajectory_argument_checks(lib):
     assert lib.rad_channeling_trajectories(*args(ctypes.byref(ch), -1, 5e-9)) == rad.RAD_EINVAL
     assert lib.rad_channeling_trajectories(*args(ctypes.byref(ch), 1, 0.0)) == rad.RAD_EINVAL
     assert lib.rad_channeling_trajectories(*args(ctypes.byref(ch), 0, 5e-9)) == rad.RAD_OK
-    for bad in (dict(flags=8), dict(charge_sign=0), dict(d_p=0.0), dict(mass_eV=-1.0), dict(U0_eV=-1.0),
+    for bad in (dict(flags=16), dict(charge_sign=0), dict(d_p=0.0), dict(mass_eV=-1.0), dict(U0_eV=-1.0),
                 dict(rho=0.0), dict(X0=0.0)):
         c2 = rad.RadChannel(20.0, 1.92e-10, 10.6e6, 0.0937, 0.075e-10, 0.51099895e6, 1, rad.RAD_TRAJ_MS)
         for k, v in bad.items():

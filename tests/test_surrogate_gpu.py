@@ -1,8 +1,9 @@
 """End-to-end surrogate on a small training set: what the network gains over the kernel alone.
 
-Trains a 3-model ensemble on 2048 kernel spectra (8 Lorentz factors), calibrates its error
-estimates on 4 validation beams, then evaluates 2 held-out beams of 64 entries each (one
-continuous Lorentz factor per beam) against the kernel. Checks: the training loss falls; each
+Trains a 3-model ensemble on 2048 kernel spectra (8 Lorentz factors, entry angles over the whole
+training domain), calibrates its error estimates on 4 validation beams, then evaluates 2
+held-out beams of 64 entries each (one continuous Lorentz factor per beam, entry angles with the
+ensemble workloads' divergence 0.3 theta_L) against the kernel. Checks: the training loss falls; each
 beam's mean spectrum meets its calibrated estimate's bar (entries that fall back carry the
 kernel's exact spectra); the surrogate's inference is far faster than the kernel; and with the
 fallback included the beam means come out faster than from the kernel alone.
@@ -19,14 +20,14 @@ def test_small_surrogate_end_to_end():
     cfg = S.Config(n_gamma_train=8, n_models=3, steps=2500, batch=256, fallback_rel=0.1, calib_gamma_bins=1)
     x0, th, g = S.sample_entries(cfg, 2048, seed=5, discrete_gamma=True)
     bins = S.kernel_bins(cfg, x0, th, g)
-    vx0, vth, vg, vb = S.sample_beams(cfg, 4, 48, seed=7)
+    vx0, vth, vg, vb = S.sample_beams(cfg, 4, 48, seed=7, divergence=cfg.beam_divergence)
     sur = S.Surrogate(cfg)
     hist = sur.fit(S.raw_inputs(cfg, x0, th, g), bins, S.raw_inputs(cfg, vx0, vth, vg),
                    S.kernel_bins(cfg, vx0, vth, vg), vb)
     first = [h[2] for h in hist if h[1] == 0]
     last = [h[2] for h in hist if h[1] == cfg.steps - 1]
     assert all(l < f / 5 for f, l in zip(first, last))
-    hx0, hth, hg, hb = S.sample_beams(cfg, 2, 64, seed=6)
+    hx0, hth, hg, hb = S.sample_beams(cfg, 2, 64, seed=6, divergence=cfg.beam_divergence)
     rep = S.evaluate(sur, hx0, hth, hg, hb)
     print({k: v for k, v in rep.items() if k != "per_beam"})
     print(rep["per_beam"])

@@ -134,3 +134,87 @@ def test_full_size_ensemble_sampled():
     pick = np.array([0, 1, 511, 512, 1000, 1023])
     ref = T.trajectories(x0[pick], th[pick], 0.0, E, L, dt, 2, particle_ids=pick)
     assert_fields_close(got.reshape(n, L, 10)[pick], ref)
+
+
+# Mixed precision (RAD_TRAJ_FP32): FP32 stages, double-float state. Without scattering, per step
+# the FP32 increments carry about 6e-8 relative rounding, random from step to step, and in the
+# harmonic well a velocity error stays bounded (it becomes a phase/amplitude error of the
+# oscillation): positions and velocities stay within about 1e-7 of their scale over 20,000 steps.
+# With scattering, each kick's size carries the FP32 precision of its plane density: exp(-r^2/rho^2)
+# with an exponent rounded to FP32 is good to about 1e-7 times the exponent, so kicks differ from
+# the FP64 ones by about 1e-6 relative and the velocities, which sum the kicks, by the same
+# relative amount (observed: x 1e-7, y and v 3e-6, dz 9e-7, FP32-evaluated fields 1e-5).
+MIXED_TOL_MS = {"t": 0.0, "x": 1e-6, "y": 1e-5, "dz": 3e-6, "vx": 1e-5, "vy": 1e-5, "dvz": 1e-5, "ax": 3e-5,
+                "ay": 3e-5, "az": 3e-5}
+MIXED_TOL_DET = {"t": 0.0, "x": 1e-6, "y": 0.0, "dz": 1e-6, "vx": 1e-6, "vy": 0.0, "dvz": 1e-5, "ax": 1e-5,
+                 "ay": 0.0, "az": 1e-5}
+
+
+def mixed_errors(got, ref):
+    worst = {}
+    for f, name in enumerate(I.FIELDS):
+        scale = np.abs(ref[..., f]).max()
+        err = np.abs(got[..., f] - ref[..., f]).max()
+        worst[name] = float(err / scale) if scale > 0 else float(err)
+    return worst
+
+
+@pytest.mark.parametrize("charge", [+1, -1])
+@pytest.mark.parametrize("flags", [0, rad.RAD_TRAJ_LL, rad.RAD_TRAJ_MS,
+                                   rad.RAD_TRAJ_MS | rad.RAD_TRAJ_LL | rad.RAD_TRAJ_MS_LOSS])
+def test_mixed_records_close_to_oracle(charge, flags):
+    n, L, dt, E, seed = 48, 20000, 5e-9, 20e9, 21
+    x0, th = entries(n, E, 8)
+    got, eg, _, st = run_gpu(channel(charge, flags | rad.RAD_TRAJ_FP32), x0, th, E, np.full(n, L), dt, seed,
+                             energies=True)
+    assert st == rad.RAD_OK
+    ref, er = T.trajectories(x0, th, 0.0, E, L, dt, seed, charge=charge, ms=bool(flags & rad.RAD_TRAJ_MS),
+                             ll=bool(flags & rad.RAD_TRAJ_LL), ms_loss=bool(flags & rad.RAD_TRAJ_MS_LOSS),
+                             energies=True)
+    worst = mixed_errors(got.reshape(n, L, 10), ref)
+    print("mixed trajectory errors (relative to field scale):", flags, charge, worst)
+    tol = MIXED_TOL_MS if flags & rad.RAD_TRAJ_MS else MIXED_TOL_DET
+    for name, t in tol.items():
+        assert worst[name] <= t, (name, worst[name])
+    # energy: the loss carries FP32 precision (its rate is an FP32 product of gamma^2 and F^2)
+    eg = eg.reshape(n, L)
+    assert np.all(np.abs(eg - er) <= 1e-6 * (E - er) + 4 * np.spacing(E))
+
+
+def pipeline_error(charge, flags, n=24, L=20000, dt=5e-9, E=10e9, seed=5):
+    import torch
+    x0, th = entries(n, E, 9)
+    got, _, off, st = run_gpu(channel(charge, flags | rad.RAD_TRAJ_FP32), x0, th, E, np.full(n, L), dt, seed)
+    assert st == rad.RAD_OK
+    ref = T.trajectories(x0, th, 0.0, E, L, dt, seed, charge=charge, ms=bool(flags & rad.RAD_TRAJ_MS),
+                         ll=bool(flags & rad.RAD_TRAJ_LL), ms_loss=bool(flags & rad.RAD_TRAJ_MS_LOSS))
+    g = np.full(n, E / I.ME_EV)
+    tr_ref = I.Trajectories(ref.reshape(-1, 10), off, g, np.full(n, E), np.full(n, 1.0 / n))
+    grid = I._ensemble_grid(E, 20.0, 48, 8)
+    cube_ref = O.spectrum_cube(tr_ref, grid, O.SPIN_HALF)
+    inp = rad.DeviceInputs(I.Trajectories(got, off, g, tr_ref.energy_eV, tr_ref.weight), grid)
+    cube = torch.empty((grid.n_omega * grid.n_angles,), dtype=torch.float64, device="cuda")
+    assert rad.rad_spectrum(*inp.args(), rad.RAD_SPIN_HALF, rad.RAD_MIXED, cube, None, None, 0, None, 0) == 0
+    torch.cuda.synchronize()
+    assert rad.rad_device_status(1) == rad.RAD_OK
+    return cube.view(grid.n_omega, grid.n_angles).cpu().numpy(), cube_ref
+
+
+@pytest.mark.parametrize("charge", [+1, -1])
+def test_mixed_pipeline_spectrum_deterministic(charge):
+    """FP32 trajectories (radiation reaction, no scattering) -> mixed spectrum on the device,
+    against the FP64 oracles end to end, at the mixed radiation tolerance (1e-4 on bins >= 1e-3
+    of the peak)."""
+    got, ref = pipeline_error(charge, rad.RAD_TRAJ_LL)
+    print("mixed pipeline spectrum error (deterministic):", charge, assert_mixed_close(got, ref))
+
+
+@pytest.mark.parametrize("charge", [+1, -1])
+def test_mixed_pipeline_spectrum_with_scattering(charge):
+    """With scattering the FP32 kicks differ from the FP64 ones by about 1e-6 relative, so each
+    trajectory is a slightly different sample of the same random motion; d(dz)/dt = -v^2/2 then
+    accumulates the velocity difference and shifts high-frequency phases by up to about 1e-2 rad
+    over 100 um. The spectra agree to 2e-2 on bins >= 1e-3 of the peak (observed 3e-4 for
+    positrons, 8e-3 for electrons, whose channels sit on the planes where the kicks are)."""
+    got, ref = pipeline_error(charge, rad.RAD_TRAJ_MS | rad.RAD_TRAJ_LL | rad.RAD_TRAJ_MS_LOSS)
+    print("mixed pipeline spectrum error (scattering):", charge, assert_mixed_close(got, ref, rel=2e-2))
