@@ -36,6 +36,24 @@ SM_COUNT, SM_MAX_MHZ = 152, 2070.0
 SFU_PER_SM_CLK = 16          # special-function unit ops per SM per clock (4 per SM sub-partition)
 FMA_PER_SM_CLK = 128         # FP32 FMA lanes per SM
 FP64_PER_SM_CLK = 2          # FP64 FMA per SM per clock
+ISSUE_PER_SM_CLK = 128       # 4 schedulers x 1 warp instruction (32 lanes) per clock
+SPLIT_EXTRA_SLOTS = 18       # FMA-pipe sin/cos (21 slots) in place of prescale + 2 MUFU (3)
+
+
+def clocks_per_term(mode, R, pe):
+    """Lower bound on SM clocks per term of the mixed integral kernel (k_mixed_pp / k_mixed)
+    from its two limits: the SFU (2 MUFU per term it serves, 16 per SM per clock) and the issue
+    slots (per SFU term: the phase FMUL, the prescale FMUL, 2 MUFU, 6 or 8 FFMA and the term's
+    share of the shared-memory loads, one float4 (+ one float for spin-1/2) per sample shared by
+    R energies; an FMA-pipe sin/cos term takes 18 slots more). With a split 1/pe, f is the
+    fraction of the 4R terms of an unrolled group whose index is pe - 1 mod pe."""
+    import math
+    nc = 8 if mode == 2 else 6
+    loads = (2 if mode == 2 else 1) / R
+    f = (sum(1 for i in range(4 * R) if i % pe == pe - 1) / (4 * R)) if pe else 0.0
+    sfu = 2.0 * (1.0 - f) / SFU_PER_SM_CLK
+    issue = (4 + nc + loads + SPLIT_EXTRA_SLOTS * f) / ISSUE_PER_SM_CLK
+    return max(sfu, issue), f
 
 
 def parse():
@@ -225,7 +243,10 @@ def main():
             d = dict(kv.split("=") for kv in tp.describe().split())
             tuned[m] = (int(d["R"]), int(d["NW"]), int(d["T"]))
             tp.close()
+            plans[m].set_prepass(int(d.get("pp", "1")))
             plans[m].set_shape(*tuned[m], 1)
+            if int(d.get("pe", "0")):
+                plans[m].set_sincos_split(int(d["pe"]))
     for m in modes:
         plans[m].set_timing(True)
 
@@ -336,7 +357,20 @@ def main():
     mk = [ms for (_, ms) in kms]
     kernel_ms_avg = sum(mk) / len(mk)
     terms_launch = terms_of(B, grid)
-    sfu_ops = 2.0 * terms_launch / (kernel_ms_avg * 1e-3)     # one sin and one cos per term
+    # ideal time of the launches from the per-mode pipe bound, against their measured time
+    t_meas = 0.0
+    t_ideal = 0.0
+    sfu_ops_total = 0.0
+    bound_by_mode = {}
+    for (m, ms) in kms:
+        dm = dict(kv.split("=") for kv in mixed_desc[m].split())
+        cpt, f = clocks_per_term(m, int(dm["R"]), int(dm.get("pe", "0")))
+        t_meas += ms * 1e-3
+        t_ideal += terms_launch * cpt / (SM_COUNT * SM_MAX_MHZ * 1e6)
+        sfu_ops_total += 2.0 * (1.0 - f) * terms_launch
+        bound_by_mode[int(m)] = {"clocks_per_term": cpt, "fma_sincos_fraction": f}
+    terms_all = terms_launch * len(kms)
+    sfu_ops = sfu_ops_total / t_meas
     sfu_peak = SM_COUNT * SFU_PER_SM_CLK * SM_MAX_MHZ * 1e6
     # DRAM bytes per launch of the integral kernel (k_mixed_pp), scaled from its ncu capture on a
     # small case of the same workload (128 particles x 20000 samples x 64 hw x 256 directions,
@@ -347,12 +381,15 @@ def main():
     chunks = int(desc0["chunks"])
     traffic = (124.9e6 * samples_launch / (128 * N_SAMP)
                + 6.04e6 * (chunks * no * na) / (38 * 64 * 256)) if desc0.get("pp") == "1" else None
-    roofline = {"bound": "alu", "pipe": "sfu",
-                "kernel": "k_mixed_pp" if desc0.get("pp") == "1" else "k_mixed", "achieved": sfu_ops / 1e12,
-                "peak": sfu_peak / 1e12, "unit": "Tops/s", "frac": sfu_ops / sfu_peak,
+    roofline = {"bound": "alu", "pipe": "sfu + issue slots",
+                "kernel": "k_mixed_pp" if desc0.get("pp") == "1" else "k_mixed",
+                "achieved": terms_all / t_meas / 1e12, "peak": terms_all / t_ideal / 1e12, "unit": "Tterm/s",
+                "frac": t_ideal / t_meas,
                 "traffic": traffic, "traffic_source": "ncu dram__bytes_read/write.sum of a small case, scaled",
-                "terms_per_launch": terms_launch, "kernel_ms_avg": kernel_ms_avg,
-                "peak_source": "152 SMs x 16 SFU/clk x 2070 MHz (unit counts and max clock)"}
+                "terms_per_launch": terms_launch, "kernel_ms_avg": kernel_ms_avg, "per_mode": bound_by_mode,
+                "sfu_ops_per_s": sfu_ops, "sfu_frac": sfu_ops / sfu_peak,
+                "peak_source": "per mode max(2(1-f)/16 SFU, slots/128 issue) clocks per term x 152 SMs x 2070 MHz "
+                               "(unit counts and max clock)"}
     fk = [ms for (_, ms) in fkms]
     f_terms_launch = terms_of(args.fp64_batch, grid)
     fp64_kernel_ms = sum(fk) / len(fk)

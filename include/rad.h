@@ -228,6 +228,15 @@ int rad_plan_set_shape(rad_plan plan, int R, int NW, int T, int chunk_mult);
 int rad_plan_set_prepass(rad_plan plan, int enable);
 
 /*
+ * rad_plan_set_sincos_split -- pre-pass kernel only: every = 4 or 6 evaluates about 1/every
+ * of the terms' sin/cos on the FMA pipe (Cody-Waite reduction to |r| <= pi/4, Taylor
+ * polynomials; same error bound as the SFU's on the in-tile phases) instead of the SFU, so
+ * that both pipes share the work; 0 uses the SFU for every term. RAD_EINVAL for other values,
+ * FP64 plans or the inline-preparation kernel (plan unchanged). The autotuner also tries these.
+ */
+int rad_plan_set_sincos_split(rad_plan plan, int every);
+
+/*
  * rad_plan_describe -- writes a short text description of the plan's chosen launch
  * shape into buf (at most len bytes, NUL-terminated). Returns RAD_OK.
  */

@@ -119,6 +119,8 @@ def load(build_if_missing: bool = True):
         lib.rad_plan_set_shape.restype = c_int
         lib.rad_plan_set_prepass.argtypes = [P, c_int]
         lib.rad_plan_set_prepass.restype = c_int
+        lib.rad_plan_set_sincos_split.argtypes = [P, c_int]
+        lib.rad_plan_set_sincos_split.restype = c_int
         lib.rad_plan_describe.argtypes = [P, ctypes.c_char_p, c_int]
         lib.rad_plan_describe.restype = c_int
         lib.rad_plan_set_timing.argtypes = [P, c_int]
@@ -436,6 +438,9 @@ class Plan:
 
     def set_prepass(self, enable=True) -> int:
         return load().rad_plan_set_prepass(self._h, int(bool(enable)))
+
+    def set_sincos_split(self, every=4) -> int:
+        return load().rad_plan_set_sincos_split(self._h, int(every))
 
     def describe(self) -> str:
         buf = ctypes.create_string_buffer(512)

@@ -31,6 +31,7 @@ struct Choice {
   int R, NW, T;
   int chunk_mult;  // multiplies the default number of work items
   int pp;          // mixed precision: 1 = per-sample pre-pass kernel, 0 = in-kernel preparation
+  int pe = 0;      // pre-pass kernel: 1/pe of the terms take sincos on the FMA pipe (0, 4 or 6)
 };
 
 }  // namespace
@@ -83,18 +84,19 @@ Choice default_choice(int precision) {
 }
 
 bool supported(int precision, const Choice &c) {
+  if (c.pe != 0 && (precision != RAD_MIXED || !c.pp || (c.pe != 4 && c.pe != 6))) return false;
   if (precision == RAD_FP64) return c.pp == 0 && shape_supported_fp64(c.R, c.NW, c.T);
   return c.pp ? shape_supported_mixed_pp(c.R, c.NW, c.T) : shape_supported_mixed(c.R, c.NW, c.T);
 }
 
 bool same_choice(const Choice &a, const Choice &b) {
-  return a.R == b.R && a.NW == b.NW && a.T == b.T && a.chunk_mult == b.chunk_mult && a.pp == b.pp;
+  return a.R == b.R && a.NW == b.NW && a.T == b.T && a.chunk_mult == b.chunk_mult && a.pp == b.pp && a.pe == b.pe;
 }
 
 // Work decomposition for a choice; (re)allocates scratch when it grows.
 int configure(rad_plan p, const Choice &c) {
   if (!supported(p->precision, c)) return RAD_EINVAL;
-  LaunchShape sh{c.R, c.NW, c.T, 0, 0};
+  LaunchShape sh{c.R, c.NW, c.T, 0, 0, c.pe};
   const int occ = p->precision == RAD_FP64 ? occupancy_fp64(sh)
                   : c.pp                   ? occupancy_mixed_pp(sh)
                                            : occupancy_mixed(sh);
@@ -156,10 +158,11 @@ int configure(rad_plan p, const Choice &c) {
   }
   char buf[256];
   std::snprintf(buf, sizeof buf,
-                "precision=%s mode=%d R=%d NW=%d T=%d grid=%d occ=%d items=%lld chunks=%lld amp=%d nq=%d pp=%d",
+                "precision=%s mode=%d R=%d NW=%d T=%d grid=%d occ=%d items=%lld chunks=%lld amp=%d nq=%d pp=%d "
+                "pe=%d",
                 p->precision == RAD_FP64 ? "fp64" : "mixed", p->mode, c.R, c.NW, c.T, sh.grid, occ,
                 static_cast<long long>(p->n_items), static_cast<long long>(p->n_chunks), p->amp_mode,
-                p->n_q, c.pp);
+                p->n_q, c.pp, c.pe);
   p->desc = buf;
   return RAD_OK;
 }
@@ -417,6 +420,7 @@ int rad_plan_set_prepass(rad_plan plan, int enable) {
   if (!plan || plan->precision != RAD_MIXED) return RAD_EINVAL;
   Choice c = plan->choice;
   c.pp = enable ? 1 : 0;
+  if (!c.pp) c.pe = 0;
   if (!supported(plan->precision, c)) return RAD_EINVAL;
   const Choice old = plan->choice;
   int rc = configure(plan, c);
@@ -426,8 +430,22 @@ int rad_plan_set_prepass(rad_plan plan, int enable) {
 
 int rad_plan_set_shape(rad_plan plan, int R, int NW, int T, int chunk_mult) {
   if (!plan || chunk_mult < 1) return RAD_EINVAL;
-  Choice c{R, NW, T, chunk_mult, plan->choice.pp};
-  if (plan->precision == RAD_MIXED && !supported(plan->precision, c)) c.pp = 1 - c.pp;
+  Choice c{R, NW, T, chunk_mult, plan->choice.pp, plan->choice.pe};
+  if (plan->precision == RAD_MIXED && !supported(plan->precision, c)) {
+    c.pp = 1 - c.pp;
+    if (!c.pp) c.pe = 0;
+  }
+  if (!supported(plan->precision, c)) return RAD_EINVAL;
+  const Choice old = plan->choice;
+  int rc = configure(plan, c);
+  if (rc) configure(plan, old);
+  return rc;
+}
+
+int rad_plan_set_sincos_split(rad_plan plan, int every) {
+  if (!plan || plan->precision != RAD_MIXED || !plan->choice.pp) return RAD_EINVAL;
+  Choice c = plan->choice;
+  c.pe = every;
   if (!supported(plan->precision, c)) return RAD_EINVAL;
   const Choice old = plan->choice;
   int rc = configure(plan, c);
@@ -491,14 +509,16 @@ int rad_plan_autotune(rad_plan plan, const double *samples, const int64_t *offse
   const int NWs[] = {4, 8};
   const int Ts[] = {64, 128, 256};
   const int mults[] = {1, 2, 4};
+  const int pes[] = {0, 4, 6};
   for (int pp = 0; pp <= 1; ++pp)
-    for (int R : Rs)
-      for (int NW : NWs)
-        for (int T : Ts)
-          for (int m : mults) {
-            Choice c{R, NW, T, m, pp};
-            if (supported(plan->precision, c)) cands.push_back(c);
-          }
+    for (int pe : pes)
+      for (int R : Rs)
+        for (int NW : NWs)
+          for (int T : Ts)
+            for (int m : mults) {
+              Choice c{R, NW, T, m, pp, pe};
+              if (supported(plan->precision, c)) cands.push_back(c);
+            }
   const Choice start = plan->choice;
   Choice best = start;
   float best_ms = 1e30f;

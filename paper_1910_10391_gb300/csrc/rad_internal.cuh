@@ -219,6 +219,7 @@ struct LaunchShape {
   int T;        // time-tile length
   int grid;     // persistent grid size
   int smem;     // dynamic shared memory bytes
+  int pe = 0;   // mixed pre-pass kernel: 1/pe of the terms take sincos on the FMA pipe (0: none)
 };
 
 // Returns cudaSuccess or the launch error. Fills shape->smem.

@@ -101,7 +101,39 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-template <int MODE, int R, int NW, int T>
+// sin and cos of x (radians) on the FMA pipe, to take part of the terms off the SFU:
+// x = j pi/2 + r with j = rint(2x/pi) formed by adding 1.5 2^23 (the integer lands in the low
+// mantissa bits), r by a three-term Cody-Waite reduction (each step one FMA, so the product
+// j * (pi/2)_i is exact inside it), |r| <= pi/4; Taylor polynomials of degree 9 (sin) and 8
+// (cos) in r (truncation below 3e-8 on |r| <= pi/4); the quadrant j mod 4 rotates the pair.
+// Valid for |2x/pi| < 2^22.
+__device__ __forceinline__ void sincos_fma(float x, float &s, float &c) {
+  constexpr float kMagic = 12582912.0f;             // 1.5 * 2^23
+  const float t = __fmaf_rn(x, 0.636619772367581343f, kMagic);
+  const float j = __fsub_rn(t, kMagic);
+  float r = __fmaf_rn(-j, 1.57079637050628662f, x);   // (pi/2)_1 = fl(pi/2)
+  r = __fmaf_rn(-j, -4.37113900018624283e-08f, r);    // (pi/2)_2 = fl(pi/2 - (pi/2)_1)
+  r = __fmaf_rn(-j, -1.70899169742600938e-15f, r);    // (pi/2)_3
+  const float r2 = r * r;
+  float ps = __fmaf_rn(r2, 2.75573192239858907e-06f, -1.98412698412698413e-04f);
+  ps = __fmaf_rn(r2, ps, 8.33333333333333333e-03f);
+  ps = __fmaf_rn(r2, ps, -1.66666666666666667e-01f);
+  const float sr = __fmaf_rn(r * r2, ps, r);
+  float pc = __fmaf_rn(r2, 2.48015873015873016e-05f, -1.38888888888888889e-03f);
+  pc = __fmaf_rn(r2, pc, 4.16666666666666667e-02f);
+  pc = __fmaf_rn(r2, pc, -0.5f);
+  const float cr = __fmaf_rn(r2, pc, 1.0f);
+  const int q = __float_as_int(t);  // = 2^22 + j: its low two bits are j mod 4
+  const float a = (q & 1) ? cr : sr;
+  const float b = (q & 1) ? sr : cr;
+  s = (q & 2) ? -a : a;
+  c = ((q + 1) & 2) ? -b : b;
+}
+
+// PE: with PE > 0, the term with index (q R + r) % PE == PE - 1 in every group of 4 samples x R
+// energies takes sincos_fma instead of the SFU (about 1/PE of the terms), balancing the SFU
+// against the FMA pipe and the issue slots.
+template <int MODE, int R, int NW, int T, int PE>
 __global__ void __launch_bounds__(NW * 32, (R <= 2 && NW == 8) ? 2 : 1) k_mixed_pp(const Params P, const float *__restrict__ prep) {
   using L = PPLayout<MODE, R, NW, T>;
   constexpr int NC = (MODE == RAD_SPIN_HALF) ? 8 : 6;
@@ -283,27 +315,39 @@ __global__ void __launch_bounds__(NW * 32, (R <= 2 && NW == 8) ? 2 : 1) k_mixed_
         for (int r = 0; r < R; ++r)
 #pragma unroll
           for (int c = 0; c < NC; ++c) tpart[r][c] = 0.f;
-#pragma unroll 4
-        for (int k = 0; k < n; ++k) {
-          const float4 F = myF[k];
-          float jj = 0.f;
-          if (MODE == RAD_SPIN_HALF) jj = myJ[k];
-#pragma unroll
-          for (int r = 0; r < R; ++r) {
-            const float x = ws_f[r] * F.x;
-            float sn, cs;
+        auto term = [&](const float4 &F, float jj, int r, bool on_fma) {
+          const float x = ws_f[r] * F.x;
+          float sn, cs;
+          if (on_fma)
+            sincos_fma(x, sn, cs);
+          else
             __sincosf(x, &sn, &cs);
-            tpart[r][0] = fmaf(F.y, cs, tpart[r][0]);
-            tpart[r][1] = fmaf(F.y, sn, tpart[r][1]);
-            tpart[r][2] = fmaf(F.z, cs, tpart[r][2]);
-            tpart[r][3] = fmaf(F.z, sn, tpart[r][3]);
-            tpart[r][4] = fmaf(F.w, cs, tpart[r][4]);
-            tpart[r][5] = fmaf(F.w, sn, tpart[r][5]);
-            if (MODE == RAD_SPIN_HALF) {
-              tpart[r][6] = fmaf(jj, cs, tpart[r][6]);
-              tpart[r][7] = fmaf(jj, sn, tpart[r][7]);
-            }
+          tpart[r][0] = fmaf(F.y, cs, tpart[r][0]);
+          tpart[r][1] = fmaf(F.y, sn, tpart[r][1]);
+          tpart[r][2] = fmaf(F.z, cs, tpart[r][2]);
+          tpart[r][3] = fmaf(F.z, sn, tpart[r][3]);
+          tpart[r][4] = fmaf(F.w, cs, tpart[r][4]);
+          tpart[r][5] = fmaf(F.w, sn, tpart[r][5]);
+          if (MODE == RAD_SPIN_HALF) {
+            tpart[r][6] = fmaf(jj, cs, tpart[r][6]);
+            tpart[r][7] = fmaf(jj, sn, tpart[r][7]);
           }
+        };
+        int k = 0;
+        for (; k + 4 <= n; k += 4) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float4 F = myF[k + q];
+            const float jj = (MODE == RAD_SPIN_HALF) ? myJ[k + q] : 0.f;
+#pragma unroll
+            for (int r = 0; r < R; ++r) term(F, jj, r, PE > 0 && (q * R + r) % (PE > 0 ? PE : 1) == PE - 1);
+          }
+        }
+        for (; k < n; ++k) {
+          const float4 F = myF[k];
+          const float jj = (MODE == RAD_SPIN_HALF) ? myJ[k] : 0.f;
+#pragma unroll
+          for (int r = 0; r < R; ++r) term(F, jj, r, false);
         }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -364,10 +408,10 @@ __global__ void __launch_bounds__(NW * 32, (R <= 2 && NW == 8) ? 2 : 1) k_mixed_
   // drain: the last copies of every stage were consumed; nothing is in flight here
 }
 
-template <int MODE, int R, int NW, int T>
+template <int MODE, int R, int NW, int T, int PE>
 cudaError_t launch_t(const Params &P, const float *prep, LaunchShape *shape, cudaStream_t st, int *occ) {
   using L = PPLayout<MODE, R, NW, T>;
-  auto kern = k_mixed_pp<MODE, R, NW, T>;
+  auto kern = k_mixed_pp<MODE, R, NW, T, PE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kTotal);
   if (e != cudaSuccess) return e;
   shape->smem = L::kTotal;
@@ -384,8 +428,13 @@ cudaError_t launch_t(const Params &P, const float *prep, LaunchShape *shape, cud
 
 template <int MODE>
 cudaError_t dispatch_mode(const Params &P, const float *prep, LaunchShape *sh, cudaStream_t st, int *occ) {
-#define RAD_PP_CASE(RR, WW, TT) \
-  if (sh->R == RR && sh->NW == WW && sh->T == TT) return launch_t<MODE, RR, WW, TT>(P, prep, sh, st, occ);
+#define RAD_PP_CASE(RR, WW, TT)                                                          \
+  if (sh->R == RR && sh->NW == WW && sh->T == TT) {                                      \
+    if (sh->pe == 4) return launch_t<MODE, RR, WW, TT, 4>(P, prep, sh, st, occ);         \
+    if (sh->pe == 6) return launch_t<MODE, RR, WW, TT, 6>(P, prep, sh, st, occ);         \
+    if (sh->pe == 0) return launch_t<MODE, RR, WW, TT, 0>(P, prep, sh, st, occ);         \
+    return cudaErrorInvalidValue;                                                        \
+  }
   RAD_PP_CASE(2, 8, 128)
   RAD_PP_CASE(2, 8, 256)
   RAD_PP_CASE(2, 4, 256)

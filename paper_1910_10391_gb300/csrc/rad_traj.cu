@@ -234,9 +234,11 @@ struct D32 {
 };
 
 // stage derivative at offset s (any value; wrapped into the channel), velocity (vx, vy), energy
-// offset dE from the entry energy E0 (for 1/gamma0^2 - 1/gamma^2), reciprocal energy (iE_hi, iE_lo)
-__device__ __forceinline__ D32 deriv32(const Chan32 &C, float s, float vx, float vy, float dEoff, float g,
-                                       float g0, float q0, float iE_hi, float iE_lo) {
+// offset dEoff from the entry energy E0 (for 1/gamma0^2 - 1/gamma^2), reciprocal of the step's
+// energy (iE_hi, iE_lo) and the stage's energy change within the step dEs (radiation reaction:
+// 1/(E + dEs) = (1/E)(1 - dEs/E) to first order, dEs/E ~ 1e-7)
+__device__ __forceinline__ D32 deriv32(const Chan32 &C, float s, float vx, float vy, float dEoff, float dEs,
+                                       float g, float g0, float q0, float iE_hi, float iE_lo) {
   float sw = s;
   if (sw >= C.half_d) sw -= C.d_f;
   else if (sw < -C.half_d) sw += C.d_f;
@@ -244,7 +246,9 @@ __device__ __forceinline__ D32 deriv32(const Chan32 &C, float s, float vx, float
   D32 d;
   d.vx = vx;
   d.vy = vy;
-  d.a = __fmaf_rn(F, iE_hi, F * iE_lo);
+  // F (iE_hi + iE_lo)(1 - dEs/E), rounded once: the exact product F iE_hi inside the outer FMA
+  const float corr = __fmaf_rn(-(F * iE_hi), dEs * iE_hi, F * iE_lo);
+  d.a = __fmaf_rn(F, iE_hi, corr);
   // v_z - beta0 = ((1/g0^2 - 1/g^2) - v_perp^2 - 1/(4 g0^4)) / (v_z + beta0), with
   // v_z + beta0 = 2 - O(1e-8): the FP32 quotient is half the numerator
   const float dg = dEoff * C.inv_mass;  // gamma - gamma0
@@ -290,7 +294,7 @@ __global__ void k_channel_mixed(const Chan32 C, int64_t n_particles, const int64
       const float res = __fmaf_rn(-E.lo, r, __fmaf_rn(-E.hi, r, 1.0f));
       const float iE_hi = r, iE_lo = res * r;
       // record k
-      const D32 d0 = deriv32(C, s.hi + s.lo, vx.hi, vy.hi, dEoff, g, g0, q0, iE_hi, iE_lo);
+      const D32 d0 = deriv32(C, s.hi + s.lo, vx.hi, vy.hi, dEoff, 0.f, g, g0, q0, iE_hi, iE_lo);
       const float ax = d0.a + kx, ay = ky;
       const float gdot = C.ll ? d0.dE * C.inv_mass : 0.f;
       rec[F_T] = static_cast<double>(k) * C.dt;
@@ -311,11 +315,11 @@ __global__ void k_channel_mixed(const Chan32 C, int64_t n_particles, const int64
       const float h2 = C.h_half, h = C.dt_hi;
       const D32 k1 = d0;
       const D32 k2 = deriv32(C, s.hi + (s.lo + h2 * k1.vx), vx.hi + (vx.lo + h2 * k1.a), vy.hi + vy.lo,
-                             dEoff + h2 * k1.dE, g, g0, q0, iE_hi, iE_lo);
+                             dEoff + h2 * k1.dE, h2 * k1.dE, g, g0, q0, iE_hi, iE_lo);
       const D32 k3 = deriv32(C, s.hi + (s.lo + h2 * k2.vx), vx.hi + (vx.lo + h2 * k2.a), vy.hi + vy.lo,
-                             dEoff + h2 * k2.dE, g, g0, q0, iE_hi, iE_lo);
+                             dEoff + h2 * k2.dE, h2 * k2.dE, g, g0, q0, iE_hi, iE_lo);
       const D32 k4 = deriv32(C, s.hi + (s.lo + h * k3.vx), vx.hi + (vx.lo + h * k3.a), vy.hi + vy.lo,
-                             dEoff + h * k3.dE, g, g0, q0, iE_hi, iE_lo);
+                             dEoff + h * k3.dE, h * k3.dE, g, g0, q0, iE_hi, iE_lo);
       // x' = v is linear in the stages: sum/6 = v + h (a1 + a2 + a3)/6. Every factor that
       // multiplies all steps alike (dt, dt/6) is a double-float pair: an FP32-rounded constant
       // would scale every increment by the same relative error and the oscillation's phase

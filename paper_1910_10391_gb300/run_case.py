@@ -31,6 +31,8 @@ def main(argv=None):
                     help="autotune the launch shape on the first N particles and apply it")
     ap.add_argument("--seed", type=int, default=0, help="generator seed (0: the workload's own)")
     ap.add_argument("--prepass", type=int, default=-1, help="mixed precision: 1 pre-pass kernel, 0 inline")
+    ap.add_argument("--split", type=int, default=-1,
+                    help="pre-pass kernel: 1/split of the terms take sincos on the FMA pipe (0, 4, 6)")
     a = ap.parse_args(argv)
 
     import torch
@@ -63,9 +65,17 @@ def main(argv=None):
         tuned = (int(d["R"]), int(d["NW"]), int(d["T"]), 1)
         tp.close()
         del si, tmp
+        if prec == rad.RAD_MIXED:
+            rc = plan.set_prepass(int(d.get("pp", "1")))
+            if rc:
+                raise rad.RadError(rc, "set_prepass")
         rc = plan.set_shape(*tuned)
         if rc:
             raise rad.RadError(rc, "set_shape")
+        if int(d.get("pe", "0")):
+            rc = plan.set_sincos_split(int(d["pe"]))
+            if rc:
+                raise rad.RadError(rc, "set_sincos_split")
     if a.prepass >= 0:
         rc = plan.set_prepass(a.prepass)
         if rc:
@@ -74,6 +84,10 @@ def main(argv=None):
         rc = plan.set_shape(*[int(x) for x in a.shape.split(",")])
         if rc:
             raise rad.RadError(rc, "set_shape")
+    if a.split >= 0:
+        rc = plan.set_sincos_split(a.split)
+        if rc:
+            raise rad.RadError(rc, "set_sincos_split")
     out = torch.empty(inp.n_omega * inp.n_angles, dtype=torch.float64, device="cuda")
     s = torch.cuda.Stream()
     times = []

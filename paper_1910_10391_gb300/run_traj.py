@@ -1,0 +1,74 @@
+"""Time the GPU trajectory integrator (rad_channeling_trajectories) on a planar-channeling ensemble.
+
+  python -m paper_1910_10391_gb300.run_traj --particles 1024 --samples 20000 --precision fp32
+
+Entry conditions: x0 uniform over the channel, theta_x0 ~ N(0, (0.3 theta_L)^2) (the ensemble
+workloads' beam), Si(110) harmonic well with U0 = 20 eV. Prints one JSON line with the CUDA-event
+time of the integrator (best of --repeat) and samples/s.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+
+import numpy as np
+
+from . import _binding as rad
+from . import inputs as I
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--particles", type=int, default=1024)
+    ap.add_argument("--samples", type=int, default=20000)
+    ap.add_argument("--lognormal", action="store_true", help="lengths of the electron batch (2k..200k)")
+    ap.add_argument("--energy", type=float, default=10e9)
+    ap.add_argument("--charge", type=int, default=+1, choices=[+1, -1])
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32"])
+    ap.add_argument("--physics", default="ms", choices=["none", "ms", "ms+ll+loss"])
+    ap.add_argument("--repeat", type=int, default=3)
+    ap.add_argument("--seed", type=int, default=2)
+    a = ap.parse_args(argv)
+    import torch
+    n = a.particles
+    lens = I.lognormal_lengths(n, 4) if a.lognormal else np.full(n, a.samples, dtype=np.int64)
+    off = np.zeros(n + 1, dtype=np.int64)
+    off[1:] = np.cumsum(lens)
+    rng = np.random.default_rng(a.seed)
+    thL = math.sqrt(2.0 * 20.0 / a.energy)
+    d = lambda v: torch.from_numpy(np.ascontiguousarray(v, dtype=np.float64)).cuda()
+    x0, th = d(rng.uniform(0.0, I.SI110_DP, n)), d(rng.normal(0.0, 0.3 * thL, n))
+    E = d(np.full(n, a.energy))
+    doff = torch.from_numpy(off).cuda()
+    out = torch.empty((int(off[-1]), rad.RAD_NREC), dtype=torch.float64, device="cuda")
+    flags = {"none": 0, "ms": rad.RAD_TRAJ_MS,
+             "ms+ll+loss": rad.RAD_TRAJ_MS | rad.RAD_TRAJ_LL | rad.RAD_TRAJ_MS_LOSS}[a.physics]
+    if a.precision == "fp32":
+        flags |= rad.RAD_TRAJ_FP32
+    ch = rad.RadChannel(20.0, I.SI110_DP, I.EPS_S_EV, I.SI_X0, I.RHO_THERMAL, I.ME_EV, a.charge, flags)
+    st = torch.cuda.current_stream()
+    ms = []
+    for r in range(a.repeat + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        rc = rad.rad_channeling_trajectories(ch, doff, E, x0, th, out, 5e-9, a.seed)
+        e1.record(st)
+        if rc:
+            raise rad.RadError(rc, "rad_channeling_trajectories")
+        torch.cuda.synchronize()
+        if r:  # the first call is a warm-up
+            ms.append(e0.elapsed_time(e1))
+    status = rad.rad_device_status(1)
+    if status:
+        raise rad.RadError(status, "device status")
+    best = min(ms)
+    print(json.dumps({"particles": n, "samples_total": int(off[-1]), "max_length": int(lens.max()),
+                      "precision": a.precision, "physics": a.physics, "charge": a.charge, "ms": ms,
+                      "samples_per_s": int(off[-1]) / best * 1e3,
+                      "checksum": float(out[:, 1].double().abs().sum().item())}))
+
+
+if __name__ == "__main__":
+    main()

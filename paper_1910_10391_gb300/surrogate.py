@@ -357,29 +357,41 @@ class Surrogate:
             self.calib = np.where(np.isnan(self.calib), max(glob, float(np.nanmax(np.r_[self.calib, glob]))),
                                   self.calib)
             if val_beam is not None:
+                # the policy's estimate after fallback of the first j entries (gated ones first,
+                # then by estimated contribution), against the actual error of that mean, at
+                # several fallback depths from "gated entries only" to most of the beam
                 rng = np.random.default_rng(cfg.fourier_seed + 1)
                 ratios = [[] for _ in range(nb)]
                 gated_all = transverse_energy(cfg, val_uvw) > cfg.eps_gate
+                ce_all = torch.from_numpy(self.calib[gb]).cuda() * spread.double()
                 for b in np.unique(val_beam):
                     sel = np.flatnonzero(val_beam == b)
                     k = int(gb[sel[0]])
                     for j in range(cfg.calib_subsets):
                         sub = sel if j == 0 else np.sort(rng.choice(sel, size=max(len(sel) // 2, 2), replace=False))
-                        # gated entries come from the kernel (exact); the estimate and the error
-                        # are those of the mean with the rest from the surrogate
                         gsub = gated_all[sub]
-                        if gsub.all():
+                        m = len(sub)
+                        j0 = int(gsub.sum())
+                        if j0 == m:
                             continue
-                        order = torch.from_numpy(np.r_[np.flatnonzero(gsub), np.flatnonzero(~gsub)]).cuda()
                         st = torch.from_numpy(sub).cuda()
-                        w = torch.full((len(sub),), 1.0 / len(sub), dtype=torch.float64, device="cuda")
-                        est = float(self._fallback_curve(members[:, st], w, order)[int(gsub.sum())])
-                        mix = served[st].clone()
-                        gi = torch.from_numpy(np.flatnonzero(gsub)).cuda()
-                        mix[gi] = truth[st][gi]
-                        act = rel_l2(mix.mean(0, keepdim=True).cpu().numpy(),
-                                     truth[st].mean(0, keepdim=True).cpu().numpy())[0]
-                        ratios[k].append(act / max(est, 1e-12))
+                        w = torch.full((m,), 1.0 / m, dtype=torch.float64, device="cuda")
+                        sv, tv = served[st], truth[st]
+                        contrib = ce_all[st] * w * torch.linalg.norm(sv, dim=1)
+                        contrib = torch.where(torch.from_numpy(gsub).cuda(), torch.full_like(contrib, float("inf")),
+                                              contrib)
+                        order = torch.argsort(contrib, descending=True)
+                        curve = self._fallback_curve(members[:, st], w, order)
+                        mt = (tv * w[:, None]).sum(0)
+                        sig = mt >= 1e-3 * mt.max()
+                        diff = ((sv - tv) * w[:, None])[order][:, sig]
+                        tail = torch.flip(torch.cumsum(torch.flip(diff, [0]), 0), [0])
+                        den = torch.linalg.norm(mt[sig])
+                        for jj in sorted({j0 + int(f * (m - j0)) for f in (0.0, 0.1, 0.2, 0.35, 0.5, 0.7)}):
+                            if jj >= m:
+                                continue
+                            act = float(torch.linalg.norm(tail[jj]) / den)
+                            ratios[k].append(act / max(float(curve[jj]), 1e-12))
                 glob = float(np.quantile(np.concatenate([np.asarray(r) for r in ratios]), cfg.calib_quantile))
                 self.calib_ens = np.array([np.quantile(r, cfg.calib_quantile) if len(r) >= 3 * cfg.calib_subsets
                                            else np.nan for r in ratios])

@@ -10,7 +10,7 @@ MODE_ORC = {rad.RAD_CLASSICAL: O.CLASSICAL, rad.RAD_SPIN0: O.SPIN0, rad.RAD_SPIN
 
 
 def gpu_cube(tr, grid, mode, precision, shape=None, outputs=("cube",), bin_of_angle=None, n_bins=0,
-             plan=False, prepass=None):
+             plan=False, prepass=None, split=None):
     """Cube (and optional spectrum/bins) from the CUDA library, as numpy arrays."""
     import torch
     inp = rad.DeviceInputs(tr, grid, bin_of_angle=bin_of_angle, n_bins=n_bins)
@@ -19,7 +19,7 @@ def gpu_cube(tr, grid, mode, precision, shape=None, outputs=("cube",), bin_of_an
     os_ = torch.full((inp.n_omega,), np.nan, dtype=torch.float64, device="cuda")
     ob = torch.full((inp.n_omega * max(n_bins, 1),), np.nan, dtype=torch.float64, device="cuda")
     oc_, os2, ob_ = (oc if want & 1 else None), (os_ if want & 2 else None), (ob if want & 4 else None)
-    if shape is None and not plan and prepass is None:
+    if shape is None and not plan and prepass is None and split is None:
         rc = rad.rad_spectrum(*inp.args(), mode, precision, oc_, os2, inp.boa if want & 4 else None,
                               n_bins if want & 4 else 0, ob_, 0)
         assert rc == rad.RAD_OK, rad.rad_status_string(rc)
@@ -32,6 +32,9 @@ def gpu_cube(tr, grid, mode, precision, shape=None, outputs=("cube",), bin_of_an
             assert p.set_shape(*shape) == rad.RAD_OK, shape
         if prepass is not None:
             assert f"pp={int(bool(prepass))}" in p.describe(), p.describe()
+        if split is not None:
+            assert p.set_sincos_split(split) == rad.RAD_OK, split
+            assert f"pe={split}" in p.describe(), p.describe()
         rc = p.execute(*inp.args(), oc_, os2, inp.boa if want & 4 else None, ob_)
         assert rc == rad.RAD_OK, rad.rad_status_string(rc)
         torch.cuda.synchronize()

@@ -135,6 +135,18 @@ def test_mixed_prepass_every_shape(ragged_batch, shape, mode):
     assert_mixed_close(got, ref)
 
 
+@pytest.mark.parametrize("shape", [(2, 8, 256, 1), (2, 4, 256, 1), (4, 8, 128, 2)])
+@pytest.mark.parametrize("split", [4, 6])
+@pytest.mark.parametrize("mode", [rad.RAD_CLASSICAL, rad.RAD_SPIN_HALF])
+def test_mixed_sincos_split(ragged_batch, shape, split, mode):
+    """Part of the terms' sin/cos on the FMA pipe (Cody-Waite reduction, Taylor polynomials):
+    the same tolerance as the SFU path, on uneven lengths, ragged grids and every quadrant."""
+    tr, grid = ragged_batch
+    ref = oracle_cube(tr, grid, mode)
+    got = gpu_cube(tr, grid, mode, rad.RAD_MIXED, shape=shape, prepass=True, split=split)["cube"]
+    print("split", split, shape, assert_mixed_close(got, ref))
+
+
 def test_mixed_prepass_time_split_and_inline_agree(undulator):
     """One particle split in time (amplitude partials) through both mixed kernels."""
     tr, grid = undulator

@@ -176,9 +176,11 @@ def test_mixed_records_close_to_oracle(charge, flags):
     tol = MIXED_TOL_MS if flags & rad.RAD_TRAJ_MS else MIXED_TOL_DET
     for name, t in tol.items():
         assert worst[name] <= t, (name, worst[name])
-    # energy: the loss carries FP32 precision (its rate is an FP32 product of gamma^2 and F^2)
+    # energy: the loss carries FP32 precision (its rate is an FP32 product of gamma^2 and F^2;
+    # with scattering loss, each kick's cost carries the kick's 1e-6 precision)
     eg = eg.reshape(n, L)
-    assert np.all(np.abs(eg - er) <= 1e-6 * (E - er) + 4 * np.spacing(E))
+    rel_loss = 1e-5 if flags & rad.RAD_TRAJ_MS_LOSS else 1e-6
+    assert np.all(np.abs(eg - er) <= rel_loss * (E - er) + 4 * np.spacing(E))
 
 
 def pipeline_error(charge, flags, n=24, L=20000, dt=5e-9, E=10e9, seed=5):
