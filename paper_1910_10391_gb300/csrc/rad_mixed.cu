@@ -15,14 +15,10 @@
 //   - Tile sums are rotated by e^{i Phi0} and added to Kahan-compensated FP32 running sums
 //     (W. Kahan, "Further remarks on reducing truncation errors", CACM 8 (1965)).
 // Per term: 2 SFU ops (sin, cos) and 8 (classical/spin-0) or 10 (spin-1/2) FMA-pipe ops.
-#include "rad_internal.cuh"
+#include "rad_mixed_common.cuh"
 
 namespace rad {
 namespace {
-
-constexpr float kMagicF = 12582912.0f;  // 1.5 * 2^23
-constexpr float kTwoPiF = 6.28318530717958647692f;
-constexpr double kInvTwoPi = 0.159154943091895335768883763372514362;
 
 template <int MODE, int R, int NW, int T>
 struct MixLayout {
@@ -37,13 +33,6 @@ struct MixLayout {
   static constexpr int kMisc = kBar + 16;
   static constexpr int kTotal = kMisc + 16;
 };
-
-__device__ __forceinline__ void kahan_add(float &s, float &c, float v) {
-  const float y = __fsub_rn(v, c);
-  const float t = __fadd_rn(s, y);
-  c = __fsub_rn(__fsub_rn(t, s), y);
-  s = t;
-}
 
 template <int MODE, int R, int NW, int T>
 __global__ void __launch_bounds__(NW * 32) k_mixed(const Params P) {

@@ -10,15 +10,10 @@
 //                   each warp computes f, j and the in-tile phase for its own direction, releases
 //                   the stage through an mbarrier, and runs its term loop. There is no block-wide
 //                   barrier per tile: warps only meet when a new work item is fetched.
-#include "rad_internal.cuh"
+#include "rad_mixed_common.cuh"
 
 namespace rad {
 namespace {
-
-constexpr int kPP = 12;  // floats per prepared record (10 used + 2 pad: 48 B, 16-byte aligned)
-constexpr float kMagicF = 12582912.0f;
-constexpr float kTwoPiF = 6.28318530717958647692f;
-constexpr double kInvTwoPi = 0.159154943091895335768883763372514362;
 
 // Tile geometry shared by the pre-pass and the kernel: sample k of particle p (length L)
 // belongs to the tile starting at k0 with n samples; its reference is the tile's middle sample.
@@ -89,17 +84,6 @@ struct PPLayout {
   static constexpr int kMisc = kBar + 32;
   static constexpr int kTotal = kMisc + 16;
 };
-
-__device__ __forceinline__ void kahan_add(float &s, float &c, float v) {
-  const float y = __fsub_rn(v, c);
-  const float t = __fadd_rn(s, y);
-  c = __fsub_rn(__fsub_rn(t, s), y);
-  s = t;
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
 
 // sin and cos of x (radians) on the FMA pipe, to take part of the terms off the SFU:
 // x = j pi/2 + r with j = rint(2x/pi) formed by adding 1.5 2^23 (the integer lands in the low
@@ -294,21 +278,7 @@ __global__ void __launch_bounds__(NW * 32, (R <= 2 && NW == 8) ? 2 : 1) k_mixed_
         a0l = __shfl_sync(0xffffffffu, a0l, 0);
         float c0[R], s0[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-          const float p = wt_hi[r] * a0h;
-          float e = fmaf(wt_hi[r], a0h, -p);
-          e = fmaf(wt_hi[r], a0l, e);
-          e = fmaf(wt_lo[r], a0h, e);
-          float rr;
-          if (fabsf(p) < 2097152.0f) {
-            const float nr = __fsub_rn(__fadd_rn(p, kMagicF), kMagicF);
-            rr = __fadd_rn(__fsub_rn(p, nr), e);
-          } else {
-            const double ph = ws[r] * (static_cast<double>(a0h) + static_cast<double>(a0l)) * kInvTwoPi;
-            rr = static_cast<float>(ph - rint(ph));
-          }
-          __sincosf(rr * kTwoPiF, &s0[r], &c0[r]);
-        }
+        for (int r = 0; r < R; ++r) tile_base_sincos(wt_hi[r], wt_lo[r], a0h, a0l, ws[r], s0[r], c0[r]);
 
         float tpart[R][NC];
 #pragma unroll
