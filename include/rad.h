@@ -237,27 +237,6 @@ int rad_plan_set_prepass(rad_plan plan, int enable);
 int rad_plan_set_sincos_split(rad_plan plan, int every);
 
 /*
- * rad_plan_set_angle_grid -- mixed precision only: declares that the plan's directions form a
- * row-major tensor grid with n_x columns, i.e. direction j = row * n_x + column has theta_x
- * equal to theta_x[column] and theta_y equal to theta_y[row * n_x] (a cell-centred rectangular
- * grid, Sec. IV's N_x x N_y directions). The plan then uses the separable kernel: the phase of
- * Sec. II, w*((1/(2 gamma^2) + theta^2/2) t - dz - n_x x - n_y y), is a sum of a part common to
- * a 2 x 2 block of directions and one part per direction component, so e^{i phi} of the four
- * directions is formed from three sin/cos pairs and three complex products. The result is the
- * same sum as the list-of-directions kernel within the mixed-precision tolerance.
- *   n_x        > 0 with n_angles % n_x == 0 (at least 1 row); 0 returns to the list kernel.
- * Each execute checks on the device that theta_x and theta_y have this structure (exact
- * equality); a violation is a device data check failure (RAD_EDATA in the status word, outputs
- * unchanged). Selects the kernel's default shape (R = 1, NW = 4, T = 256; rad_plan_set_shape
- * may choose NW = 8 with T = 128, or NW = 4 with T = 128; other shapes switch back to the list
- * kernel). The autotuner tries both kernels on a plan with a grid. RAD_EINVAL for FP64 plans,
- * a negative n_x or one that does not divide n_angles (plan unchanged). May reallocate
- * scratch (waits for the device); not allowed during stream capture. rad_spectrum_host detects
- * such grids on its host arrays and uses this kernel by itself.
- */
-int rad_plan_set_angle_grid(rad_plan plan, int64_t n_x);
-
-/*
  * rad_plan_describe -- writes a short text description of the plan's chosen launch
  * shape into buf (at most len bytes, NUL-terminated). Returns RAD_OK.
  */

@@ -121,8 +121,6 @@ def load(build_if_missing: bool = True):
         lib.rad_plan_set_prepass.restype = c_int
         lib.rad_plan_set_sincos_split.argtypes = [P, c_int]
         lib.rad_plan_set_sincos_split.restype = c_int
-        lib.rad_plan_set_angle_grid.argtypes = [P, i64]
-        lib.rad_plan_set_angle_grid.restype = c_int
         lib.rad_plan_describe.argtypes = [P, ctypes.c_char_p, c_int]
         lib.rad_plan_describe.restype = c_int
         lib.rad_plan_set_timing.argtypes = [P, c_int]
@@ -443,9 +441,6 @@ class Plan:
 
     def set_sincos_split(self, every=4) -> int:
         return load().rad_plan_set_sincos_split(self._h, int(every))
-
-    def set_angle_grid(self, n_x) -> int:
-        return load().rad_plan_set_angle_grid(self._h, int(n_x))
 
     def describe(self) -> str:
         buf = ctypes.create_string_buffer(512)

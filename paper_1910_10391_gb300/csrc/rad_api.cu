@@ -32,7 +32,6 @@ struct Choice {
   int chunk_mult;  // multiplies the default number of work items
   int pp;          // mixed precision: 1 = per-sample pre-pass kernel, 0 = in-kernel preparation
   int pe = 0;      // pre-pass kernel: 1/pe of the terms take sincos on the FMA pipe (0, 4 or 6)
-  int sep = 0;     // mixed precision on a tensor direction grid: 1 = separable kernel (k_mixed_sep)
 };
 
 }  // namespace
@@ -47,7 +46,6 @@ struct rad_plan_s {
   int64_t n_samples_total = 0, n_particles = 0, n_omega = 0, n_angles = 0;
   int mode = 0, precision = 0, want = 0;
   int32_t n_bins = 0;
-  int64_t grid_nx = 0;  // > 0: directions form a tensor grid with grid_nx columns (rad_plan_set_angle_grid)
   Choice choice{};
   LaunchShape shape{};
   int n_wt = 0, n_nt = 0, amp_mode = 0, n_q = 1;
@@ -71,71 +69,41 @@ struct rad_graph_s {
 namespace {
 
 std::mutex g_mu;
-using ShapeKey = std::tuple<int, int64_t, int64_t, int64_t, int64_t, int, int, int, int, int64_t>;
+using ShapeKey = std::tuple<int, int64_t, int64_t, int64_t, int64_t, int, int, int, int>;
 std::map<ShapeKey, Choice> g_tuned;                                  // autotuned choices
 std::map<std::tuple<ShapeKey, void *>, rad_plan> g_plans;            // rad_spectrum cache
 
 ShapeKey key_of(int dev, int64_t ns, int64_t np, int64_t no, int64_t na, int mode, int prec, int want,
-                int nb, int64_t grid_nx) {
-  return ShapeKey{dev, ns, np, no, na, mode, prec, want, nb, grid_nx};
+                int nb) {
+  return ShapeKey{dev, ns, np, no, na, mode, prec, want, nb};
 }
 
-Choice default_choice(int precision, int64_t grid_nx) {
+Choice default_choice(int precision) {
   if (precision == RAD_FP64) return Choice{2, 8, 64, 1, 0};
-  if (grid_nx > 0) return Choice{1, 4, 256, 1, 1, 0, 1};
   return Choice{2, 8, 256, 1, 1};
 }
 
 bool supported(int precision, const Choice &c) {
-  if (c.pe != 0 && (precision != RAD_MIXED || !c.pp || c.sep || (c.pe != 4 && c.pe != 6))) return false;
-  if (c.sep) return precision == RAD_MIXED && c.pp && shape_supported_mixed_sep(c.R, c.NW, c.T);
+  if (c.pe != 0 && (precision != RAD_MIXED || !c.pp || (c.pe != 4 && c.pe != 6))) return false;
   if (precision == RAD_FP64) return c.pp == 0 && shape_supported_fp64(c.R, c.NW, c.T);
   return c.pp ? shape_supported_mixed_pp(c.R, c.NW, c.T) : shape_supported_mixed(c.R, c.NW, c.T);
 }
 
-// the separable kernel also needs the plan's tensor-grid declaration
-bool supported_by(const rad_plan p, const Choice &c) {
-  return supported(p->precision, c) && (!c.sep || p->grid_nx > 0);
-}
-
 bool same_choice(const Choice &a, const Choice &b) {
-  return a.R == b.R && a.NW == b.NW && a.T == b.T && a.chunk_mult == b.chunk_mult && a.pp == b.pp && a.pe == b.pe &&
-         a.sep == b.sep;
-}
-
-// Host-side detection of a row-major tensor grid: theta_y constant along the first row fixes
-// n_x; every direction must then repeat its column's theta_x and its row's theta_y exactly.
-// Returns n_x, or 0 when the directions are not such a grid (or the grid is narrower than 2 x 2).
-int64_t detect_tensor_grid(const double *tx, const double *ty, int64_t n) {
-  if (!tx || !ty || n < 4) return 0;
-  int64_t nx = 1;
-  while (nx < n && ty[nx] == ty[0]) ++nx;
-  if (nx < 2 || n % nx != 0 || n / nx < 2) return 0;
-  for (int64_t j = 0; j < n; ++j) {
-    const int64_t ix = j % nx;
-    if (tx[j] != tx[ix] || ty[j] != ty[j - ix]) return 0;
-  }
-  return nx;
+  return a.R == b.R && a.NW == b.NW && a.T == b.T && a.chunk_mult == b.chunk_mult && a.pp == b.pp && a.pe == b.pe;
 }
 
 // Work decomposition for a choice; (re)allocates scratch when it grows.
 int configure(rad_plan p, const Choice &c) {
-  if (!supported_by(p, c)) return RAD_EINVAL;
+  if (!supported(p->precision, c)) return RAD_EINVAL;
   LaunchShape sh{c.R, c.NW, c.T, 0, 0, c.pe};
   const int occ = p->precision == RAD_FP64 ? occupancy_fp64(sh)
-                  : c.sep                  ? occupancy_mixed_sep(sh)
                   : c.pp                   ? occupancy_mixed_pp(sh)
                                            : occupancy_mixed(sh);
   if (occ <= 0) return RAD_EUNSUPPORTED;
   const int64_t resident = static_cast<int64_t>(p->sms) * occ;
   p->n_wt = static_cast<int>((p->n_omega + 32 * c.R - 1) / (32 * c.R));
-  if (c.sep) {  // work tiles of NW blocks of 2 x 2 directions
-    const int64_t ny = p->n_angles / p->grid_nx;
-    const int64_t n_blocks = ((p->grid_nx + 1) / 2) * ((ny + 1) / 2);
-    p->n_nt = static_cast<int>((n_blocks + c.NW - 1) / c.NW);
-  } else {
-    p->n_nt = static_cast<int>((p->n_angles + c.NW - 1) / c.NW);
-  }
+  p->n_nt = static_cast<int>((p->n_angles + c.NW - 1) / c.NW);
   const int64_t tiles = static_cast<int64_t>(p->n_wt) * p->n_nt;
   const int64_t target = resident * 4 * std::max(1, c.chunk_mult);
   p->amp_mode = 0;
@@ -191,10 +159,10 @@ int configure(rad_plan p, const Choice &c) {
   char buf[256];
   std::snprintf(buf, sizeof buf,
                 "precision=%s mode=%d R=%d NW=%d T=%d grid=%d occ=%d items=%lld chunks=%lld amp=%d nq=%d pp=%d "
-                "pe=%d sep=%d",
+                "pe=%d",
                 p->precision == RAD_FP64 ? "fp64" : "mixed", p->mode, c.R, c.NW, c.T, sh.grid, occ,
                 static_cast<long long>(p->n_items), static_cast<long long>(p->n_chunks), p->amp_mode,
-                p->n_q, c.pp, c.pe, c.sep);
+                p->n_q, c.pp, c.pe);
   p->desc = buf;
   return RAD_OK;
 }
@@ -243,7 +211,6 @@ Params make_params(rad_plan p, const double *samples, const int64_t *offsets, co
   P.counter = p->ctrl;
   P.status = p->ctrl + 1;
   P.table = table;
-  P.grid_nx = p->choice.sep ? p->grid_nx : 0;
   return P;
 }
 
@@ -305,8 +272,6 @@ int execute(rad_plan p, const double *samples, const int64_t *offsets, const dou
   }
   if (p->precision == RAD_FP64) {
     e = launch_fp64(P, &sh, st);
-  } else if (p->choice.sep) {
-    e = launch_mixed_sep(P, p->prep, &sh, st);
   } else if (p->choice.pp) {
     e = launch_mixed_pp(P, p->prep, &sh, st);
   } else {
@@ -331,7 +296,7 @@ int execute(rad_plan p, const double *samples, const int64_t *offsets, const dou
 }
 
 int plan_create(int64_t ns, int64_t np, int64_t no, int64_t na, int mode, int prec, int want, int32_t nb,
-                int64_t grid_nx, rad_plan *out) {
+                rad_plan *out) {
   if (!out) return RAD_EINVAL;
   *out = nullptr;
   int rc = check_shape(ns, np, no, na, mode, prec, want, nb);
@@ -354,7 +319,6 @@ int plan_create(int64_t ns, int64_t np, int64_t no, int64_t na, int mode, int pr
   p->precision = prec;
   p->want = want;
   p->n_bins = (want & 4) ? nb : 0;
-  p->grid_nx = grid_nx;
   e = cudaMalloc(&p->ctrl, 2 * sizeof(int));
   if (e != cudaSuccess) {
     delete p;
@@ -367,10 +331,10 @@ int plan_create(int64_t ns, int64_t np, int64_t no, int64_t na, int mode, int pr
     delete p;
     return cuda_fail(e);
   }
-  Choice c = default_choice(prec, grid_nx);
+  Choice c = default_choice(prec);
   {
     std::lock_guard<std::mutex> lk(g_mu);
-    auto it = g_tuned.find(key_of(dev, ns, np, no, na, mode, prec, want, p->n_bins, grid_nx));
+    auto it = g_tuned.find(key_of(dev, ns, np, no, na, mode, prec, want, p->n_bins));
     if (it != g_tuned.end()) c = it->second;
   }
   rc = configure(p, c);
@@ -438,7 +402,7 @@ const char *rad_status_string(int status) {
 
 int rad_plan_create(int64_t n_samples_total, int64_t n_particles, int64_t n_omega, int64_t n_angles,
                     int mode, int precision, int want, int32_t n_bins, rad_plan *plan) {
-  return plan_create(n_samples_total, n_particles, n_omega, n_angles, mode, precision, want, n_bins, 0, plan);
+  return plan_create(n_samples_total, n_particles, n_omega, n_angles, mode, precision, want, n_bins, plan);
 }
 
 int rad_plan_execute(rad_plan plan, const double *samples, const int64_t *offsets, const double *gamma,
@@ -456,8 +420,8 @@ int rad_plan_set_prepass(rad_plan plan, int enable) {
   if (!plan || plan->precision != RAD_MIXED) return RAD_EINVAL;
   Choice c = plan->choice;
   c.pp = enable ? 1 : 0;
-  if (!c.pp) c.pe = c.sep = 0;
-  if (!supported_by(plan, c)) return RAD_EINVAL;
+  if (!c.pp) c.pe = 0;
+  if (!supported(plan->precision, c)) return RAD_EINVAL;
   const Choice old = plan->choice;
   int rc = configure(plan, c);
   if (rc) configure(plan, old);
@@ -466,13 +430,12 @@ int rad_plan_set_prepass(rad_plan plan, int enable) {
 
 int rad_plan_set_shape(rad_plan plan, int R, int NW, int T, int chunk_mult) {
   if (!plan || chunk_mult < 1) return RAD_EINVAL;
-  Choice c{R, NW, T, chunk_mult, plan->choice.pp, plan->choice.pe, plan->choice.sep};
-  if (plan->precision == RAD_MIXED && c.sep && !supported_by(plan, c)) c.sep = 0;  // a list-kernel shape
-  if (plan->precision == RAD_MIXED && !supported_by(plan, c)) {
+  Choice c{R, NW, T, chunk_mult, plan->choice.pp, plan->choice.pe};
+  if (plan->precision == RAD_MIXED && !supported(plan->precision, c)) {
     c.pp = 1 - c.pp;
     if (!c.pp) c.pe = 0;
   }
-  if (!supported_by(plan, c)) return RAD_EINVAL;
+  if (!supported(plan->precision, c)) return RAD_EINVAL;
   const Choice old = plan->choice;
   int rc = configure(plan, c);
   if (rc) configure(plan, old);
@@ -480,31 +443,13 @@ int rad_plan_set_shape(rad_plan plan, int R, int NW, int T, int chunk_mult) {
 }
 
 int rad_plan_set_sincos_split(rad_plan plan, int every) {
-  if (!plan || plan->precision != RAD_MIXED || !plan->choice.pp || plan->choice.sep) return RAD_EINVAL;
+  if (!plan || plan->precision != RAD_MIXED || !plan->choice.pp) return RAD_EINVAL;
   Choice c = plan->choice;
   c.pe = every;
-  if (!supported_by(plan, c)) return RAD_EINVAL;
+  if (!supported(plan->precision, c)) return RAD_EINVAL;
   const Choice old = plan->choice;
   int rc = configure(plan, c);
   if (rc) configure(plan, old);
-  return rc;
-}
-
-int rad_plan_set_angle_grid(rad_plan plan, int64_t n_x) {
-  if (!plan || n_x < 0) return RAD_EINVAL;
-  if (n_x > 0 && (plan->precision != RAD_MIXED || plan->n_angles <= 0 || plan->n_angles % n_x != 0))
-    return RAD_EINVAL;
-  const int64_t old_nx = plan->grid_nx;
-  const Choice old = plan->choice;
-  plan->grid_nx = n_x;
-  Choice c = default_choice(plan->precision, n_x);
-  c.chunk_mult = old.chunk_mult;
-  if (n_x == 0 && !old.sep) c = old;  // nothing to switch back from
-  int rc = configure(plan, c);
-  if (rc) {
-    plan->grid_nx = old_nx;
-    configure(plan, old);
-  }
   return rc;
 }
 
@@ -565,16 +510,15 @@ int rad_plan_autotune(rad_plan plan, const double *samples, const int64_t *offse
   const int Ts[] = {64, 128, 256};
   const int mults[] = {1, 2, 4};
   const int pes[] = {0, 4, 6};
-  for (int sep = 0; sep <= 1; ++sep)
-    for (int pp = 0; pp <= 1; ++pp)
-      for (int pe : pes)
-        for (int R : Rs)
-          for (int NW : NWs)
-            for (int T : Ts)
-              for (int m : mults) {
-                Choice c{R, NW, T, m, pp, pe, sep};
-                if (supported_by(plan, c)) cands.push_back(c);
-              }
+  for (int pp = 0; pp <= 1; ++pp)
+    for (int pe : pes)
+      for (int R : Rs)
+        for (int NW : NWs)
+          for (int T : Ts)
+            for (int m : mults) {
+              Choice c{R, NW, T, m, pp, pe};
+              if (supported(plan->precision, c)) cands.push_back(c);
+            }
   const Choice start = plan->choice;
   Choice best = start;
   float best_ms = 1e30f;
@@ -616,7 +560,7 @@ int rad_plan_autotune(rad_plan plan, const double *samples, const int64_t *offse
     std::lock_guard<std::mutex> lk(g_mu);
     // cached rad_spectrum plans of this shape pick up the choice on their next call
     g_tuned[key_of(plan->device, plan->n_samples_total, plan->n_particles, plan->n_omega, plan->n_angles,
-                   plan->mode, plan->precision, plan->want, plan->n_bins, plan->grid_nx)] = plan->choice;
+                   plan->mode, plan->precision, plan->want, plan->n_bins)] = plan->choice;
   }
   // leave a result of the chosen shape in the outputs
   if (rc == RAD_OK)
@@ -629,16 +573,12 @@ int rad_plan_autotune(rad_plan plan, const double *samples, const int64_t *offse
   return rc;
 }
 
-}  // extern "C"
-
-namespace {
-// rad_spectrum through the per-(shape, stream) plan cache; grid_nx > 0 declares a tensor direction grid
-int spectrum_cached(const double *samples, int64_t n_samples_total, const int64_t *offsets, int64_t n_particles,
-                    const double *gamma, const double *energy_eV, const double *weight,
-                    const double *hbar_omega_eV, int64_t n_omega, const double *theta_x, const double *theta_y,
-                    const double *d_omega, int64_t n_angles, int mode, int precision, double *out_cube,
-                    double *out_spectrum, const int32_t *bin_of_angle, int32_t n_bins, double *out_bins,
-                    int accumulate, void *stream, int64_t grid_nx) {
+int rad_spectrum(const double *samples, int64_t n_samples_total, const int64_t *offsets, int64_t n_particles,
+                 const double *gamma, const double *energy_eV, const double *weight,
+                 const double *hbar_omega_eV, int64_t n_omega, const double *theta_x, const double *theta_y,
+                 const double *d_omega, int64_t n_angles, int mode, int precision, double *out_cube,
+                 double *out_spectrum, const int32_t *bin_of_angle, int32_t n_bins, double *out_bins,
+                 int accumulate, void *stream) {
   const int want = (out_cube ? 1 : 0) | (out_spectrum ? 2 : 0) | (out_bins ? 4 : 0);
   int rc = check_shape(n_samples_total, n_particles, n_omega, n_angles, mode, precision, want, n_bins);
   if (rc) return rc;
@@ -646,7 +586,7 @@ int spectrum_cached(const double *samples, int64_t n_samples_total, const int64_
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e);
   const int32_t nb = (want & 4) ? n_bins : 0;
-  const ShapeKey k = key_of(dev, n_samples_total, n_particles, n_omega, n_angles, mode, precision, want, nb, grid_nx);
+  const ShapeKey k = key_of(dev, n_samples_total, n_particles, n_omega, n_angles, mode, precision, want, nb);
   rad_plan p = nullptr;
   Choice tuned{};
   bool have_tuned = false;
@@ -667,7 +607,7 @@ int spectrum_cached(const double *samples, int64_t n_samples_total, const int64_
     if (rc) return rc;
   }
   if (!p) {
-    rc = plan_create(n_samples_total, n_particles, n_omega, n_angles, mode, precision, want, nb, grid_nx, &p);
+    rc = plan_create(n_samples_total, n_particles, n_omega, n_angles, mode, precision, want, nb, &p);
     if (rc) return rc;
     std::lock_guard<std::mutex> lk(g_mu);
     auto ins = g_plans.emplace(std::make_tuple(k, stream), p);
@@ -678,21 +618,6 @@ int spectrum_cached(const double *samples, int64_t n_samples_total, const int64_
   }
   return execute(p, samples, offsets, gamma, energy_eV, weight, hbar_omega_eV, theta_x, theta_y, d_omega,
                  out_cube, out_spectrum, bin_of_angle, out_bins, accumulate, static_cast<cudaStream_t>(stream));
-}
-
-}  // namespace
-
-extern "C" {
-
-int rad_spectrum(const double *samples, int64_t n_samples_total, const int64_t *offsets, int64_t n_particles,
-                 const double *gamma, const double *energy_eV, const double *weight,
-                 const double *hbar_omega_eV, int64_t n_omega, const double *theta_x, const double *theta_y,
-                 const double *d_omega, int64_t n_angles, int mode, int precision, double *out_cube,
-                 double *out_spectrum, const int32_t *bin_of_angle, int32_t n_bins, double *out_bins,
-                 int accumulate, void *stream) {
-  return spectrum_cached(samples, n_samples_total, offsets, n_particles, gamma, energy_eV, weight, hbar_omega_eV,
-                         n_omega, theta_x, theta_y, d_omega, n_angles, mode, precision, out_cube, out_spectrum,
-                         bin_of_angle, n_bins, out_bins, accumulate, stream, 0);
 }
 
 int rad_spectrum_particles(const double *samples, int64_t n_samples_total, const int64_t *offsets,
@@ -709,7 +634,7 @@ int rad_spectrum_particles(const double *samples, int64_t n_samples_total, const
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e);
   const int32_t nb = (want & 4) ? n_bins : 0;
-  const ShapeKey k = key_of(dev, n_samples_total, n_particles, n_omega, n_angles, mode, precision, want, nb, 0);
+  const ShapeKey k = key_of(dev, n_samples_total, n_particles, n_omega, n_angles, mode, precision, want, nb);
   rad_plan p = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_mu);
@@ -717,7 +642,7 @@ int rad_spectrum_particles(const double *samples, int64_t n_samples_total, const
     if (it != g_plans.end()) p = it->second;
   }
   if (!p) {
-    rc = plan_create(n_samples_total, n_particles, n_omega, n_angles, mode, precision, want, nb, 0, &p);
+    rc = plan_create(n_samples_total, n_particles, n_omega, n_angles, mode, precision, want, nb, &p);
     if (rc) return rc;
     std::lock_guard<std::mutex> lk(g_mu);
     auto ins = g_plans.emplace(std::make_tuple(k, stream), p);
@@ -796,14 +721,12 @@ int rad_spectrum_host(const double *samples, int64_t n_samples_total, const int6
     if (e == cudaSuccess && d_bins) e = cudaMemcpyAsync(d_bins, out_bins, sz[11], cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e);
   }
-  // mixed precision on a tensor direction grid takes the separable kernel
-  const int64_t grid_nx = precision == RAD_MIXED ? detect_tensor_grid(theta_x, theta_y, n_angles) : 0;
-  rc = spectrum_cached(static_cast<const double *>(b->ptr[0]), n_samples_total,
+  rc = rad_spectrum(static_cast<const double *>(b->ptr[0]), n_samples_total,
                     static_cast<const int64_t *>(b->ptr[1]), n_particles, static_cast<const double *>(b->ptr[2]),
                     static_cast<const double *>(b->ptr[3]), weight ? static_cast<const double *>(b->ptr[4]) : nullptr,
                     static_cast<const double *>(b->ptr[5]), n_omega, static_cast<const double *>(b->ptr[6]),
                     static_cast<const double *>(b->ptr[7]), d_omega ? static_cast<const double *>(b->ptr[8]) : nullptr,
-                    n_angles, mode, precision, d_cube, d_spec, d_boa, n_bins, d_bins, accumulate, stream, grid_nx);
+                    n_angles, mode, precision, d_cube, d_spec, d_boa, n_bins, d_bins, accumulate, stream);
   if (rc) return rc;
   // read the call's device status through the cached plan's control word
   if (d_cube) e = cudaMemcpyAsync(out_cube, d_cube, sz[9], cudaMemcpyDeviceToHost, st);
@@ -815,7 +738,7 @@ int rad_spectrum_host(const double *samples, int64_t n_samples_total, const int6
     rad_plan p = nullptr;
     std::lock_guard<std::mutex> lk(g_mu);
     auto it = g_plans.find({key_of(dev, n_samples_total, n_particles, n_omega, n_angles, mode, precision, want,
-                                   static_cast<int>(nb), grid_nx),
+                                   static_cast<int>(nb)),
                             stream});
     if (it != g_plans.end()) p = it->second;
     if (p && n_omega > 0 && n_angles > 0) {

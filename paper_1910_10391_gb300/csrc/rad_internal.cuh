@@ -65,10 +65,6 @@ struct Params {
   int *counter;    // work counter (zeroed before launch)
   int *status;     // per-call status word (zeroed before launch)
   const double2 *table;  // FP64 sincos table in global memory (kTabN entries)
-  // > 0: the directions form a row-major tensor grid with grid_nx columns (direction
-  // j = row * grid_nx + column, theta_x a function of the column, theta_y of the row); the
-  // separable mixed kernel (rad_mixed_sep.cu) runs and k_validate checks the structure
-  int64_t grid_nx;
 };
 
 // ------------------------------------------------------------------------------------
@@ -239,10 +235,6 @@ bool shape_supported_mixed_pp(int R, int NW, int T);
 int occupancy_mixed_pp(const LaunchShape &s);
 cudaError_t launch_prep_samples(const Params &P, int T, float *prep, cudaStream_t st);
 cudaError_t launch_mixed_pp(const Params &P, const float *prep, LaunchShape *shape, cudaStream_t st);
-// mixed kernel for tensor-product direction grids (rad_mixed_sep.cu); same pre-pass records
-bool shape_supported_mixed_sep(int R, int NW, int T);
-int occupancy_mixed_sep(const LaunchShape &s);
-cudaError_t launch_mixed_sep(const Params &P, const float *prep, LaunchShape *shape, cudaStream_t st);
 
 // post-processing kernels (rad_post.cu)
 cudaError_t launch_validate(const Params &P, const double *d_omega, bool need_domega,

@@ -1,4 +1,4 @@
-// Pieces shared by the mixed-precision kernels (rad_mixed.cu, rad_mixed_pp.cu, rad_mixed_sep.cu).
+// Pieces shared by the mixed-precision kernels (rad_mixed.cu, rad_mixed_pp.cu).
 #pragma once
 #include "rad_internal.cuh"
 

@@ -49,10 +49,6 @@ __global__ void k_validate(const Params P, const double *d_omega, int need_domeg
   for (int64_t j = t0; j < P.n_angles; j += stride) {
     if (!finite_d(P.theta_x[j]) || !finite_d(P.theta_y[j])) bad = true;
     if (need_domega && !finite_d(d_omega[j])) bad = true;
-    if (P.grid_nx > 0) {  // tensor grid: theta_x equal down each column, theta_y along each row
-      const int64_t ix = j % P.grid_nx;
-      if (P.theta_x[j] != P.theta_x[ix] || P.theta_y[j] != P.theta_y[j - ix]) bad = true;
-    }
   }
   // trajectory records
   const int64_t nv = P.n_samples_total * kRec;

@@ -33,8 +33,6 @@ def main(argv=None):
     ap.add_argument("--prepass", type=int, default=-1, help="mixed precision: 1 pre-pass kernel, 0 inline")
     ap.add_argument("--split", type=int, default=-1,
                     help="pre-pass kernel: 1/split of the terms take sincos on the FMA pipe (0, 4, 6)")
-    ap.add_argument("--grid", type=int, default=0,
-                    help="mixed precision: 1 declares the tensor direction grid (separable kernel)")
     a = ap.parse_args(argv)
 
     import torch
@@ -54,18 +52,11 @@ def main(argv=None):
     inp = rad.DeviceInputs(tr, grid)
     mode, prec = rad.MODES[a.mode], rad.PRECISIONS[a.precision]
     plan = rad.Plan(inp.n_samples, inp.n_particles, inp.n_omega, inp.n_angles, mode, prec, 1, 0)
-    n_x = 16 if a.workload == "undulator" else a.n_side
-    if a.grid:
-        rc = plan.set_angle_grid(n_x)
-        if rc:
-            raise rad.RadError(rc, "set_angle_grid")
     tuned = None
     if a.autotune_subset > 0:
         sub = tr.subset(range(min(a.autotune_subset, tr.n_particles)))
         si = rad.DeviceInputs(sub, grid)
         tp = rad.Plan(si.n_samples, si.n_particles, si.n_omega, si.n_angles, mode, prec, 1, 0)
-        if a.grid:
-            tp.set_angle_grid(n_x)
         tmp = torch.empty(si.n_omega * si.n_angles, dtype=torch.float64, device="cuda")
         rc = tp.autotune(*si.args(), tmp, None, None, None, budget_ms=120000)
         if rc:
@@ -74,8 +65,6 @@ def main(argv=None):
         tuned = (int(d["R"]), int(d["NW"]), int(d["T"]), 1)
         tp.close()
         del si, tmp
-        if a.grid and d.get("sep") == "0":
-            plan.set_angle_grid(0)
         if prec == rad.RAD_MIXED:
             rc = plan.set_prepass(int(d.get("pp", "1")))
             if rc:
