@@ -243,6 +243,17 @@ __global__ void __launch_bounds__(NW * 32, (R <= 2 && NW == 8) ? 2 : 1) k_mixed_
         const int n = static_cast<int>((cur.ke - cur.k0) < T ? (cur.ke - cur.k0) : T);
         const int km = (n - 1) >> 1;
 
+        // base phase at the reference (middle) sample, FP64 by lane 0, as a double-float pair;
+        // started here and consumed after the term loop, so its global load and FP64 chain overlap
+        // the tile's FP32 work
+        float a0h = 0.f, a0l = 0.f;
+        if (lane == 0) {
+          const double *r0 = P.samples + (P.offsets[cur.p] + cur.k0 + km) * kRec;
+          const double A0 = ((cn * r0[F_T] - r0[F_DZ]) - nx * r0[F_X]) - ny * r0[F_Y];
+          a0h = static_cast<float>(A0);
+          a0l = static_cast<float>(A0 - static_cast<double>(a0h));
+        }
+
         // per (n, k): weighted f, j and the FP32 phase offset for this warp's direction
         for (int k = lane; k < n; k += 32) {
           const float4 ra = reinterpret_cast<const float4 *>(st + k * kPP)[0];
@@ -265,20 +276,6 @@ __global__ void __launch_bounds__(NW * 32, (R <= 2 && NW == 8) ? 2 : 1) k_mixed_
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);  // this warp is done with the stage
-
-        // base phase at the reference (middle) sample, FP64 by lane 0, as a double-float pair
-        float a0h = 0.f, a0l = 0.f;
-        if (lane == 0) {
-          const double *r0 = P.samples + (P.offsets[cur.p] + cur.k0 + km) * kRec;
-          const double A0 = ((cn * r0[F_T] - r0[F_DZ]) - nx * r0[F_X]) - ny * r0[F_Y];
-          a0h = static_cast<float>(A0);
-          a0l = static_cast<float>(A0 - static_cast<double>(a0h));
-        }
-        a0h = __shfl_sync(0xffffffffu, a0h, 0);
-        a0l = __shfl_sync(0xffffffffu, a0l, 0);
-        float c0[R], s0[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) tile_base_sincos(wt_hi[r], wt_lo[r], a0h, a0l, ws[r], s0[r], c0[r]);
 
         float tpart[R][NC];
 #pragma unroll
@@ -305,10 +302,14 @@ __global__ void __launch_bounds__(NW * 32, (R <= 2 && NW == 8) ? 2 : 1) k_mixed_
         };
         int k = 0;
         for (; k + 4 <= n; k += 4) {
+          // j of the four samples in one 16-byte load (k is a multiple of 4 here)
+          const float4 J4 = (MODE == RAD_SPIN_HALF) ? reinterpret_cast<const float4 *>(myJ)[k >> 2]
+                                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+          const float jq[4] = {J4.x, J4.y, J4.z, J4.w};
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
             const float4 F = myF[k + q];
-            const float jj = (MODE == RAD_SPIN_HALF) ? myJ[k + q] : 0.f;
+            const float jj = jq[q];
 #pragma unroll
             for (int r = 0; r < R; ++r) term(F, jj, r, PE > 0 && (q * R + r) % (PE > 0 ? PE : 1) == PE - 1);
           }
@@ -319,6 +320,11 @@ __global__ void __launch_bounds__(NW * 32, (R <= 2 && NW == 8) ? 2 : 1) k_mixed_
 #pragma unroll
           for (int r = 0; r < R; ++r) term(F, jj, r, false);
         }
+        a0h = __shfl_sync(0xffffffffu, a0h, 0);
+        a0l = __shfl_sync(0xffffffffu, a0l, 0);
+        float c0[R], s0[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) tile_base_sincos(wt_hi[r], wt_lo[r], a0h, a0l, ws[r], s0[r], c0[r]);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
 #pragma unroll

@@ -133,3 +133,70 @@ def test_electron_batch_full_size_sampled():
     print("electron batch full size: sampled bins", int(sel.sum()), "max rel err", rel.max())
     assert rel.max() <= 1e-4, rel.max()
     assert np.all(np.abs(got - ref)[~sel] <= 1e-7 * peak)
+
+
+def test_positron_ensemble_full_size_sampled():
+    """The full positron ensemble (1024 e+ x 20 000 samples, 512 hw x 64 x 64, classical and
+    spin-1/2) in the benchmark's launch configuration: shape autotuned on a 2-particle batch,
+    32-particle batches added into one cube (accumulate). 32 seeded bins per model over all
+    1024 particles (24 of them in the emission cone) against the oracle at the mixed tolerance;
+    the plain FP64 kernel on particle 0 over every energy x 64 seeded directions at the FP64
+    tolerance."""
+    import torch
+    tr, grid = I.workload_positron_ensemble()
+    inp = rad.DeviceInputs(tr, grid)
+    no, na, L = inp.n_omega, inp.n_angles, 20000
+    rng = np.random.default_rng(12)
+    a2 = inp.args()
+
+    def part(p0, n):  # particles p0 .. p0+n-1 of the resident ensemble, as one call's arguments
+        w = a2[4]
+        return (a2[0][p0 * L:(p0 + n) * L], torch.arange(n + 1, dtype=torch.int64, device="cuda") * L,
+                a2[2][p0:p0 + n], a2[3][p0:p0 + n], None if w is None else w[p0:p0 + n]) + tuple(a2[5:])
+
+    for mode, omode in ((rad.RAD_CLASSICAL, O.CLASSICAL), (rad.RAD_SPIN_HALF, O.SPIN_HALF)):
+        tp = rad.Plan(2 * L, 2, no, na, mode, rad.RAD_MIXED, 3, 0)
+        tmp = torch.empty(no * na, dtype=torch.float64, device="cuda")
+        tmps = torch.empty(no, dtype=torch.float64, device="cuda")
+        assert tp.autotune(*part(0, 2), tmp, tmps, None, None, budget_ms=4000) == 0
+        d = dict(kv.split("=") for kv in tp.describe().split())
+        tp.close()
+        plan = rad.Plan(32 * L, 32, no, na, mode, rad.RAD_MIXED, 3, 0)
+        assert plan.set_prepass(int(d["pp"])) == 0
+        assert plan.set_shape(int(d["R"]), int(d["NW"]), int(d["T"]), 1) == 0
+        if int(d.get("pe", "0")):
+            assert plan.set_sincos_split(int(d["pe"])) == 0
+        cube = torch.zeros(no * na, dtype=torch.float64, device="cuda")
+        spec = torch.zeros(no, dtype=torch.float64, device="cuda")
+        for b in range(32):
+            assert plan.execute(*part(32 * b, 32), cube, spec, None, None, accumulate=1) == 0
+        torch.cuda.synchronize()
+        assert rad.rad_device_status(1) == rad.RAD_OK
+        plan.close()
+        got_cube = cube.view(no, na).cpu().numpy()
+        # sample locations: 24 seeded bins among those above 1e-2 of the peak (the emission cone
+        # covers a small part of the grid) and 8 seeded bins anywhere
+        big = np.flatnonzero(got_cube.ravel() >= 1e-2 * got_cube.max())
+        flat = np.r_[rng.choice(big, 24, replace=False), rng.integers(0, no * na, 8)]
+        bi, bj = flat // na, flat % na
+        ref = O.spectrum_bins(tr, grid, omode, bi, bj)
+        got = got_cube[bi, bj]
+        peak = got_cube.max()
+        sel = ref >= 1e-3 * peak
+        assert sel.sum() >= 12
+        rel = np.abs(got[sel] - ref[sel]) / ref[sel]
+        print("positron ensemble full size, mode", mode, d, "sampled bins", int(sel.sum()), "max rel err",
+              rel.max())
+        assert rel.max() <= 1e-4, rel.max()
+        assert np.all(np.abs(got - ref)[~sel] <= 1e-7 * peak)
+        # spectrum = sum_j cube dOmega (the angle integral of the same launches)
+        dom = grid.d_omega
+        assert np.allclose(spec.cpu().numpy(), (got_cube * dom[None, :]).sum(1), rtol=1e-12, atol=0)
+    # plain FP64: particle 0, full grid, 64 directions x every energy
+    one = tr.subset([0])
+    ref_j = rng.integers(0, na, 64)
+    out = gpu_cube(one, grid, rad.RAD_SPIN_HALF, rad.RAD_FP64)["cube"]
+    bi2 = np.repeat(np.arange(no), 64)
+    bj2 = np.tile(ref_j, no)
+    ref = O.spectrum_bins(one, grid, O.SPIN_HALF, bi2, bj2).reshape(no, 64)
+    assert_fp64_close(out[:, ref_j], ref)
