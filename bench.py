@@ -29,6 +29,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "integrand terms/s (ω·n·t) & spectra/s: plain FP64 vs chosen form at stated err"
 N_PART, N_SAMP, N_OMEGA, N_SIDE = 1024, 20000, 512, 64
+TUNE_PARTICLES = 8
+# launch shapes (R, NW, T) of the mixed kernel per model, the fastest on 32-particle launches of this
+# workload in a sweep of the autotuner's candidates; --autotune re-derives them on the box
+SHAPES = {0: (2, 8, 256), 2: (2, 4, 256)}
 WORKLOAD = ("positron ensemble: 1024 e+ at 10 GeV, harmonic planar well (U0 = 20 eV, d_p = 1.92 A), "
             "RK4 + scattering kicks, 20000 samples over 100 um; 512 log hw in [1e-4 E, 0.5 E] x 64x64 "
             "directions within +-(theta_L + 3/gamma); classical + spin-1/2")
@@ -67,7 +71,8 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--autotune", action="store_true",
+                    help="choose the launch shapes with the library's autotuner instead of SHAPES")
     return ap.parse_args()
 
 
@@ -232,11 +237,12 @@ def main():
 
     plans = make_plans(rad.RAD_MIXED, B)
     tuned = {}
-    if not args.no_autotune:
-        # tune the launch shape on a 2-particle slice of the same grids, then apply it
-        sub = batch_args(0, 2)
+    if args.autotune:
+        # tune the launch shape on an 8-particle slice of the same grids (long enough per work item
+        # to rank the shapes as the 32-particle launches do), then apply it
+        sub = batch_args(0, TUNE_PARTICLES)
         for m in modes:
-            tp = rad.Plan(2 * N_SAMP, 2, no, na, m, rad.RAD_MIXED, 3, 0)
+            tp = rad.Plan(TUNE_PARTICLES * N_SAMP, TUNE_PARTICLES, no, na, m, rad.RAD_MIXED, 3, 0)
             tmp_c = torch.empty(no * na, dtype=torch.float64, device=dev)
             tmp_s = torch.empty(no, dtype=torch.float64, device=dev)
             tp.autotune(*sub, tmp_c, tmp_s, None, None, budget_ms=60000)
@@ -247,6 +253,11 @@ def main():
             plans[m].set_shape(*tuned[m], 1)
             if int(d.get("pe", "0")):
                 plans[m].set_sincos_split(int(d["pe"]))
+    else:
+        for m in modes:
+            rc = plans[m].set_shape(*SHAPES[m], 1)
+            if rc:
+                raise rad.RadError(rc, "rad_plan_set_shape")
     for m in modes:
         plans[m].set_timing(True)
 
@@ -374,13 +385,14 @@ def main():
     sfu_peak = SM_COUNT * SFU_PER_SM_CLK * SM_MAX_MHZ * 1e6
     # DRAM bytes per launch of the integral kernel (k_mixed_pp), scaled from its ncu capture on a
     # small case of the same workload (128 particles x 20000 samples x 64 hw x 256 directions,
-    # 38 particle chunks: 124.9 MB read = the 48-byte pre-pass records once, 6.04 MB written):
+    # shape R=2 NW=4 T=256, 29 particle chunks: 124.88 MB read = the 48-byte pre-pass records once,
+    # 5.46 MB written):
     # reads grow with the samples a launch processes, writes with the partial sums it stores.
     samples_launch = B * N_SAMP
     desc0 = dict(kv.split("=") for kv in mixed_desc[modes[0]].split())
     chunks = int(desc0["chunks"])
-    traffic = (124.9e6 * samples_launch / (128 * N_SAMP)
-               + 6.04e6 * (chunks * no * na) / (38 * 64 * 256)) if desc0.get("pp") == "1" else None
+    traffic = (124.88e6 * samples_launch / (128 * N_SAMP)
+               + 5.46e6 * (chunks * no * na) / (29 * 64 * 256)) if desc0.get("pp") == "1" else None
     roofline = {"bound": "alu", "pipe": "sfu + issue slots",
                 "kernel": "k_mixed_pp" if desc0.get("pp") == "1" else "k_mixed",
                 "achieved": terms_all / t_meas / 1e12, "peak": terms_all / t_ideal / 1e12, "unit": "Tterm/s",
