@@ -30,8 +30,9 @@ sys.path.insert(0, ROOT)
 METRIC = "integrand terms/s (ω·n·t) & spectra/s: plain FP64 vs chosen form at stated err"
 N_PART, N_SAMP, N_OMEGA, N_SIDE = 1024, 20000, 512, 64
 TUNE_PARTICLES = 8
-# launch shapes (R, NW, T) of the mixed kernel per model, the fastest on 32-particle launches of this
-# workload in a sweep of the autotuner's candidates; --autotune re-derives them on the box
+# launch shapes (R, NW, T) of the mixed kernel per model: the fastest of the shapes timed on
+# 32-particle launches of this workload (R=2 or 4, NW=4 or 8, T=128 or 256); --autotune lets the
+# library's autotuner choose instead
 SHAPES = {0: (2, 8, 256), 2: (2, 4, 256)}
 WORKLOAD = ("positron ensemble: 1024 e+ at 10 GeV, harmonic planar well (U0 = 20 eV, d_p = 1.92 A), "
             "RK4 + scattering kicks, 20000 samples over 100 um; 512 log hw in [1e-4 E, 0.5 E] x 64x64 "
@@ -50,11 +51,11 @@ def clocks_per_term(mode, R, pe):
     slots (per SFU term: the phase FMUL, the prescale FMUL, 2 MUFU, 6 or 8 FFMA and the term's
     share of the shared-memory loads, one float4 (+ one float for spin-1/2) per sample shared by
     R energies; an FMA-pipe sin/cos term takes 18 slots more). With a split 1/pe, f is the
-    fraction of the 4R terms of an unrolled group whose index is pe - 1 mod pe."""
+    fraction of the 8R terms of an unrolled group whose index is pe - 1 mod pe."""
     import math
     nc = 8 if mode == 2 else 6
     loads = (2 if mode == 2 else 1) / R
-    f = (sum(1 for i in range(4 * R) if i % pe == pe - 1) / (4 * R)) if pe else 0.0
+    f = (sum(1 for i in range(8 * R) if i % pe == pe - 1) / (8 * R)) if pe else 0.0
     sfu = 2.0 * (1.0 - f) / SFU_PER_SM_CLK
     issue = (4 + nc + loads + SPLIT_EXTRA_SLOTS * f) / ISSUE_PER_SM_CLK
     return max(sfu, issue), f
@@ -385,14 +386,14 @@ def main():
     sfu_peak = SM_COUNT * SFU_PER_SM_CLK * SM_MAX_MHZ * 1e6
     # DRAM bytes per launch of the integral kernel (k_mixed_pp), scaled from its ncu capture on a
     # small case of the same workload (128 particles x 20000 samples x 64 hw x 256 directions,
-    # shape R=2 NW=4 T=256, 29 particle chunks: 124.88 MB read = the 48-byte pre-pass records once,
-    # 5.46 MB written):
+    # shape R=2 NW=4 T=256, 29 particle chunks: 125.39 MB read = the 48-byte pre-pass records once,
+    # 5.24 MB written):
     # reads grow with the samples a launch processes, writes with the partial sums it stores.
     samples_launch = B * N_SAMP
     desc0 = dict(kv.split("=") for kv in mixed_desc[modes[0]].split())
     chunks = int(desc0["chunks"])
-    traffic = (124.88e6 * samples_launch / (128 * N_SAMP)
-               + 5.46e6 * (chunks * no * na) / (29 * 64 * 256)) if desc0.get("pp") == "1" else None
+    traffic = (125.39e6 * samples_launch / (128 * N_SAMP)
+               + 5.24e6 * (chunks * no * na) / (29 * 64 * 256)) if desc0.get("pp") == "1" else None
     roofline = {"bound": "alu", "pipe": "sfu + issue slots",
                 "kernel": "k_mixed_pp" if desc0.get("pp") == "1" else "k_mixed",
                 "achieved": terms_all / t_meas / 1e12, "peak": terms_all / t_ideal / 1e12, "unit": "Tterm/s",

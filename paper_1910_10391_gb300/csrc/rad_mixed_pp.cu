@@ -114,11 +114,11 @@ __device__ __forceinline__ void sincos_fma(float x, float &s, float &c) {
   c = ((q + 1) & 2) ? -b : b;
 }
 
-// PE: with PE > 0, the term with index (q R + r) % PE == PE - 1 in every group of 4 samples x R
+// PE: with PE > 0, the term with index (q R + r) % PE == PE - 1 in every group of 8 samples x R
 // energies takes sincos_fma instead of the SFU (about 1/PE of the terms), balancing the SFU
 // against the FMA pipe and the issue slots.
 template <int MODE, int R, int NW, int T, int PE>
-__global__ void __launch_bounds__(NW * 32, (R <= 2 && NW == 8) ? 2 : 1) k_mixed_pp(const Params P, const float *__restrict__ prep) {
+__global__ void __launch_bounds__(NW * 32, NW == 8 ? (R <= 2 ? 2 : 1) : 3) k_mixed_pp(const Params P, const float *__restrict__ prep) {
   using L = PPLayout<MODE, R, NW, T>;
   constexpr int NC = (MODE == RAD_SPIN_HALF) ? 8 : 6;
   extern __shared__ __align__(128) unsigned char sm[];
@@ -301,13 +301,15 @@ __global__ void __launch_bounds__(NW * 32, (R <= 2 && NW == 8) ? 2 : 1) k_mixed_
           }
         };
         int k = 0;
-        for (; k + 4 <= n; k += 4) {
-          // j of the four samples in one 16-byte load (k is a multiple of 4 here)
+        for (; k + 8 <= n; k += 8) {
+          // j of the eight samples in two 16-byte loads (k is a multiple of 8 here)
           const float4 J4 = (MODE == RAD_SPIN_HALF) ? reinterpret_cast<const float4 *>(myJ)[k >> 2]
                                                     : make_float4(0.f, 0.f, 0.f, 0.f);
-          const float jq[4] = {J4.x, J4.y, J4.z, J4.w};
+          const float4 J5 = (MODE == RAD_SPIN_HALF) ? reinterpret_cast<const float4 *>(myJ)[(k >> 2) + 1]
+                                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+          const float jq[8] = {J4.x, J4.y, J4.z, J4.w, J5.x, J5.y, J5.z, J5.w};
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
+          for (int q = 0; q < 8; ++q) {
             const float4 F = myF[k + q];
             const float jj = jq[q];
 #pragma unroll
