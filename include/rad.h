@@ -399,6 +399,16 @@ int rad_channeling_trajectories(const rad_channel *ch, int64_t n_particles, cons
  */
 int rad_device_status(int reset);
 
+/*
+ * rad_selftest_bounded_wait -- failure-detection self-test (the paper has no counterpart):
+ * enqueues on `stream` a one-thread kernel that waits, with the same bounded wait the staging
+ * kernels use for their bulk copies, on an mbarrier phase that nothing completes. After the
+ * wait's time limit (about 2 s) the kernel records RAD_ETIMEOUT in the device status word and
+ * returns; the context stays usable. Returns RAD_OK when the kernel was enqueued; read the
+ * outcome with rad_device_status. Shows that a stalled copy ends in an error status, not a hang.
+ */
+int rad_selftest_bounded_wait(void *stream);
+
 /* rad_status_string -- static description of a status code (RAD_ECUDA: last CUDA error). */
 const char *rad_status_string(int status);
 

@@ -139,6 +139,8 @@ def load(build_if_missing: bool = True):
         lib.rad_graph_destroy.restype = c_int
         lib.rad_device_status.argtypes = [c_int]
         lib.rad_device_status.restype = c_int
+        lib.rad_selftest_bounded_wait.argtypes = [P]
+        lib.rad_selftest_bounded_wait.restype = c_int
         lib.rad_status_string.argtypes = [c_int]
         lib.rad_status_string.restype = ctypes.c_char_p
         lib.rad_version.argtypes = []
@@ -385,6 +387,10 @@ def rad_standardize(y, mean, stdv, inverse=False, stream=None):
                                 int(bool(inverse)), _stream(stream))
     if rc:
         raise RadError(rc, "rad_standardize")
+
+
+def rad_selftest_bounded_wait(stream=None) -> int:
+    return load().rad_selftest_bounded_wait(_stream(stream))
 
 
 def rad_device_status(reset: int = 1) -> int:

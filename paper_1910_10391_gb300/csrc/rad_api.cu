@@ -805,6 +805,11 @@ int rad_graph_destroy(rad_graph graph) {
   return RAD_OK;
 }
 
+int rad_selftest_bounded_wait(void *stream) {
+  const cudaError_t e = launch_wait_selftest(static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? RAD_OK : cuda_fail(e);
+}
+
 int rad_device_status(int reset) {
   cudaError_t e;
   int *ds = device_status_word(&e);

@@ -255,6 +255,7 @@ cudaError_t launch_zero_outputs(const Params &P, double *out_cube, double *out_s
                                 int n_bins, double *out_bins, cudaStream_t st);
 const double2 *device_table(cudaError_t *err);  // per-device FP64 sincos table
 int *device_status_word(cudaError_t *err);      // per-device sticky status word
+cudaError_t launch_wait_selftest(cudaStream_t st);  // a bounded wait that runs out (RAD_ETIMEOUT)
 int cuda_status(cudaError_t e);                 // records e for rad_status_string; RAD_ENOMEM or RAD_ECUDA
 
 inline int ncomp_of(int mode) { return mode == RAD_SPIN_HALF ? 8 : 6; }

@@ -39,10 +39,11 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1
 // C[M x N] = sum_k A(m, k) B(k, n), BF16 inputs, FP32 accumulation, epilogue epi(m, n, value).
 //   A(m, k) = A_KM ? A[m * lda + k] : A[k * lda + m]
 //   B(k, n) = B_KN ? B[n * ldb + k] : B[k * ldb + n]
-// Block tile 64 x 64 x 32, 4 warps (2 x 2), warp tile 32 x 32 (2 x 4 mma tiles).
+// Block tile 64 x 64 x 32, 4 warps (2 x 2), warp tile 32 x 32 (2 x 4 mma tiles). Block z covers
+// the K range [z k_chunk, min(K, (z + 1) k_chunk)) (split K; k_chunk a multiple of 32).
 template <bool A_KM, bool B_KN, class Epi>
 __global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const bf16 *__restrict__ A, int lda,
-                                              const bf16 *__restrict__ B, int ldb, Epi epi) {
+                                              const bf16 *__restrict__ B, int ldb, Epi epi, int k_chunk) {
   __shared__ __align__(16) bf16 As[64][40];
   __shared__ __align__(16) bf16 Bs[64][40];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -56,7 +57,9 @@ __global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const bf16 *_
 #pragma unroll
       for (int c = 0; c < 4; ++c) acc[i][j][c] = 0.f;
   const bf16 zero = __float2bfloat16(0.f);
-  for (int k0 = 0; k0 < K; k0 += 32) {
+  const int k_begin = blockIdx.z * k_chunk;
+  const int k_end = min(K, k_begin + k_chunk);
+  for (int k0 = k_begin; k0 < k_end; k0 += 32) {
     for (int e = tid; e < 64 * 32; e += 128) {
       int mm, kk;
       if (A_KM) {
@@ -67,7 +70,7 @@ __global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const bf16 *_
         mm = e & 63;
       }
       const int m = m0 + mm, k = k0 + kk;
-      As[mm][kk] = (m < M && k < K) ? (A_KM ? A[static_cast<int64_t>(m) * lda + k]
+      As[mm][kk] = (m < M && k < k_end) ? (A_KM ? A[static_cast<int64_t>(m) * lda + k]
                                             : A[static_cast<int64_t>(k) * lda + m])
                                     : zero;
       int nn, kb;
@@ -79,7 +82,7 @@ __global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const bf16 *_
         nn = e & 63;
       }
       const int n = n0 + nn, k2 = k0 + kb;
-      Bs[nn][kb] = (n < N && k2 < K) ? (B_KN ? B[static_cast<int64_t>(n) * ldb + k2]
+      Bs[nn][kb] = (n < N && k2 < k_end) ? (B_KN ? B[static_cast<int64_t>(n) * ldb + k2]
                                              : B[static_cast<int64_t>(k2) * ldb + n])
                                      : zero;
     }
@@ -155,11 +158,52 @@ struct EpiStore {  // plain FP32 store
   __device__ void operator()(int m, int n, float v) const { C[static_cast<int64_t>(m) * ld + n] = v; }
 };
 
+struct EpiPartial {  // split K: FP32 partial sums of K range z at ws[z][m][n]
+  float *ws;
+  int64_t mn;
+  int ld;
+  __device__ void operator()(int m, int n, float v) const {
+    ws[blockIdx.z * mn + static_cast<int64_t>(m) * ld + n] = v;
+  }
+};
+
+// Sum of the split-K partials in a fixed order, then the GEMM's own epilogue.
+template <class Epi>
+__global__ void k_splitk_reduce(int M, int N, int S, const float *__restrict__ ws, Epi epi) {
+  const int64_t mn = static_cast<int64_t>(M) * N;
+  for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < mn;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    float v = 0.f;
+    for (int z = 0; z < S; ++z) v += ws[z * mn + e];
+    epi(static_cast<int>(e / N), static_cast<int>(e % N), v);
+  }
+}
+
+// Split-K workspace: a grid of fewer than kSplitTarget blocks is split in K until about that
+// many blocks run; then S x M x N <= 2 kSplitTarget x 64 x 64 floats.
+constexpr int kSplitTarget = 2 * 152;
+constexpr int64_t kSplitWsFloats = 2ll * kSplitTarget * 64 * 64;
+
 template <bool A_KM, bool B_KN, class Epi>
-cudaError_t gemm(int M, int N, int K, const bf16 *A, int lda, const bf16 *B, int ldb, Epi epi, cudaStream_t st) {
+cudaError_t gemm(int M, int N, int K, const bf16 *A, int lda, const bf16 *B, int ldb, Epi epi, float *ws,
+                 cudaStream_t st) {
   if (M <= 0 || N <= 0) return cudaSuccess;
-  dim3 grd((N + 63) / 64, (M + 63) / 64);
-  k_gemm<A_KM, B_KN, Epi><<<grd, 128, 0, st>>>(M, N, K, A, lda, B, ldb, epi);
+  const int gx = (N + 63) / 64, gy = (M + 63) / 64;
+  const int blocks = gx * gy;
+  const int kt = (K + 31) / 32;
+  int S = 1;
+  if (ws && blocks < kSplitTarget && kt > 1) S = std::min(kt, (kSplitTarget + blocks - 1) / blocks);
+  const int k_chunk = ((kt + S - 1) / S) * 32;
+  S = (K + k_chunk - 1) / k_chunk;
+  if (S <= 1) {
+    k_gemm<A_KM, B_KN, Epi><<<dim3(gx, gy, 1), 128, 0, st>>>(M, N, K, A, lda, B, ldb, epi, kt * 32);
+    return cudaGetLastError();
+  }
+  EpiPartial part{ws, static_cast<int64_t>(M) * N, N};
+  k_gemm<A_KM, B_KN, EpiPartial><<<dim3(gx, gy, S), 128, 0, st>>>(M, N, K, A, lda, B, ldb, part, k_chunk);
+  const int64_t mn = static_cast<int64_t>(M) * N;
+  k_splitk_reduce<Epi><<<static_cast<unsigned>(std::min<int64_t>((mn + 255) / 256, 4096)), 256, 0, st>>>(
+      M, N, S, ws, epi);
   return cudaGetLastError();
 }
 
@@ -345,6 +389,7 @@ struct rad_mlp_s {
   float *Y = nullptr;                  // [max_batch][n_out]
   bf16 *dY = nullptr;                  // [max_batch][n_out]
   float *partial = nullptr;            // loss partials [1024]
+  float *splitk = nullptr;             // split-K partial sums [kSplitWsFloats]
   int64_t step = 0;
 };
 
@@ -362,12 +407,12 @@ cudaError_t forward_impl(rad_mlp h, const float *x, int64_t B, float *y_out, boo
     const bf16 *Hin = h->H + static_cast<int64_t>(l - 1) * h->max_batch * W;
     EpiHidden epi{h->w + h->b_off[l], keep ? h->Z + static_cast<int64_t>(l) * h->max_batch * W : nullptr,
                   h->H + static_cast<int64_t>(l) * h->max_batch * W, W};
-    e = gemm<true, true>(static_cast<int>(B), W, W, Hin, W, h->wb + h->w_off[l], W, epi, st);
+    e = gemm<true, true>(static_cast<int>(B), W, W, Hin, W, h->wb + h->w_off[l], W, epi, h->splitk, st);
   }
   if (e != cudaSuccess) return e;
   const bf16 *Hlast = h->H + static_cast<int64_t>(D - 1) * h->max_batch * W;
   EpiOut epo{h->w + h->b_off[D], y_out, O};
-  return gemm<true, true>(static_cast<int>(B), O, W, Hlast, W, h->wb + h->w_off[D], W, epo, st);
+  return gemm<true, true>(static_cast<int>(B), O, W, Hlast, W, h->wb + h->w_off[D], W, epo, h->splitk, st);
 }
 
 cudaError_t backward_impl(rad_mlp h, const float *x, const float *target, const float *mask, int64_t B, float *loss,
@@ -384,25 +429,25 @@ cudaError_t backward_impl(rad_mlp h, const float *x, const float *target, const 
   // output layer: dW_out = dY^T H_last, db_out = colsum(dY), dH = dY W_out
   const bf16 *Hlast = h->H + static_cast<int64_t>(D - 1) * h->max_batch * W;
   EpiStore gW{h->g + h->w_off[D], W};
-  e = gemm<false, false>(O, W, static_cast<int>(B), h->dY, O, Hlast, W, gW, st);
+  e = gemm<false, false>(O, W, static_cast<int>(B), h->dY, O, Hlast, W, gW, h->splitk, st);
   if (e != cudaSuccess) return e;
   k_colsum<<<nblk(O), 256, 0, st>>>(B, O, h->dY, h->g + h->b_off[D]);
   int cur = 0;
   {
     EpiGradAct ga{h->Z + static_cast<int64_t>(D - 1) * h->max_batch * W, h->dZ, W};
-    e = gemm<true, false>(static_cast<int>(B), W, O, h->dY, O, h->wb + h->w_off[D], W, ga, st);
+    e = gemm<true, false>(static_cast<int>(B), W, O, h->dY, O, h->wb + h->w_off[D], W, ga, h->splitk, st);
     if (e != cudaSuccess) return e;
   }
   for (int l = D - 1; l >= 1; --l) {
     const bf16 *dZl = h->dZ + static_cast<int64_t>(cur) * h->max_batch * W;
     const bf16 *Hin = h->H + static_cast<int64_t>(l - 1) * h->max_batch * W;
     EpiStore gw{h->g + h->w_off[l], W};
-    e = gemm<false, false>(W, W, static_cast<int>(B), dZl, W, Hin, W, gw, st);
+    e = gemm<false, false>(W, W, static_cast<int>(B), dZl, W, Hin, W, gw, h->splitk, st);
     if (e != cudaSuccess) return e;
     k_colsum<<<nblk(W), 256, 0, st>>>(B, W, dZl, h->g + h->b_off[l]);
     bf16 *dZn = h->dZ + static_cast<int64_t>(cur ^ 1) * h->max_batch * W;
     EpiGradAct ga{h->Z + static_cast<int64_t>(l - 1) * h->max_batch * W, dZn, W};
-    e = gemm<true, false>(static_cast<int>(B), W, W, dZl, W, h->wb + h->w_off[l], W, ga, st);
+    e = gemm<true, false>(static_cast<int>(B), W, W, dZl, W, h->wb + h->w_off[l], W, ga, h->splitk, st);
     if (e != cudaSuccess) return e;
     cur ^= 1;
   }
@@ -425,6 +470,7 @@ void mlp_free(rad_mlp h) {
   cudaFree(h->Y);
   cudaFree(h->dY);
   cudaFree(h->partial);
+  cudaFree(h->splitk);
   delete h;
 }
 
@@ -460,7 +506,8 @@ int rad_mlp_create(int n_in, int width, int depth, int n_out, int64_t max_batch,
             cudaMalloc(&h->dZ, sizeof(bf16) * 2 * max_batch * width) == cudaSuccess &&
             cudaMalloc(&h->Y, sizeof(float) * max_batch * n_out) == cudaSuccess &&
             cudaMalloc(&h->dY, sizeof(bf16) * max_batch * n_out) == cudaSuccess &&
-            cudaMalloc(&h->partial, sizeof(float) * 1024) == cudaSuccess;
+            cudaMalloc(&h->partial, sizeof(float) * 1024) == cudaSuccess &&
+            cudaMalloc(&h->splitk, sizeof(float) * kSplitWsFloats) == cudaSuccess;
   if (!ok) {
     mlp_free(h);
     return RAD_ENOMEM;

@@ -267,7 +267,27 @@ DevRes *dev_res(cudaError_t *err) {
   return &r;
 }
 
+// Self-test of the bounded mbarrier wait that every staging kernel uses to wait for its bulk
+// copies: one thread waits on a phase of an mbarrier that nothing ever completes. The wait gives
+// up after its time limit (kWaitLimitNs), the kernel records RAD_ETIMEOUT in the device status
+// word and returns, and the context stays usable.
+__global__ void k_wait_selftest(int *dev_status) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  fence_mbar_init();
+  if (!mbar_wait_bounded(&bar, 0u)) set_status(dev_status, RAD_ETIMEOUT);
+}
+
 }  // namespace
+
+cudaError_t launch_wait_selftest(cudaStream_t st) {
+  cudaError_t e;
+  int *ds = device_status_word(&e);
+  if (!ds) return e;
+  k_wait_selftest<<<1, 32, 0, st>>>(ds);
+  return cudaGetLastError();
+}
 
 const double2 *device_table(cudaError_t *err) {
   DevRes *r = dev_res(err);

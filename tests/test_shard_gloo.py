@@ -74,3 +74,37 @@ def test_partition_and_batches():
         seen.add(p0)
     with pytest.raises(ValueError):
         shard.particle_range(5, 2, 2)
+
+
+def _worker_leaves(rank, world, port, out):
+    """Rank 1 leaves after the rendezvous, between steps; rank 0's next collective must fail with
+    an error within the process group's timeout instead of hanging."""
+    import datetime
+    import time
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=10))
+    if rank == 1:
+        os._exit(0)  # leaves without joining the reduction of the next step
+    t0 = time.perf_counter()
+    try:
+        shard.allreduce_sum(torch.zeros(4, dtype=torch.float64))
+        out.put(("no error", time.perf_counter() - t0))
+    except Exception as e:  # the failure is detected on the host
+        out.put((type(e).__name__, time.perf_counter() - t0))
+
+
+def test_rank_that_leaves_is_detected_by_the_next_collective():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker_leaves, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    kind, dt = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=60)
+        if p.is_alive():
+            p.kill()
+    assert kind != "no error", "the all-reduce with a departed rank returned normally"
+    assert dt < 60.0
