@@ -73,6 +73,10 @@ extern "C" {
 
 #define RAD_FP64 0  /* every operation in FP64 (the paper's precision, Sec. IV)          */
 #define RAD_MIXED 1 /* FP64 phase base and particle sums; FP32 sincos, f and tile sums   */
+/* RAD_FP64_DF: FP64 accuracy with the FP64 phase product and its reduction as in RAD_FP64,
+ * then double-float FP32 arithmetic (float pairs) for sin, cos, f and compensated tile sums,
+ * and FP64 particle sums: the RAD_FP64 tolerance with about a quarter of its FP64 instructions. */
+#define RAD_FP64_DF 2
 
 #define RAD_NREC 10 /* float64 fields per trajectory record */
 
@@ -92,7 +96,7 @@ extern "C" {
  *   d_omega          device, [n_angles] solid angle of each direction cell; may be NULL
  *                    when neither out_spectrum nor out_bins is requested
  *   mode             RAD_CLASSICAL | RAD_SPIN0 | RAD_SPIN_HALF
- *   precision        RAD_FP64 | RAD_MIXED
+ *   precision        RAD_FP64 | RAD_MIXED | RAD_FP64_DF
  *   out_cube         device, [n_omega * n_angles] or NULL
  *   out_spectrum     device, [n_omega] or NULL
  *   bin_of_angle     device, [n_angles] int32 or NULL (required when out_bins != NULL)

@@ -19,7 +19,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "rad.h")
 
 RAD_OK, RAD_EINVAL, RAD_ENOMEM, RAD_ECUDA, RAD_ETIMEOUT, RAD_EUNSUPPORTED, RAD_EDATA, RAD_ETOOBIG = range(8)
 RAD_CLASSICAL, RAD_SPIN0, RAD_SPIN_HALF = 0, 1, 2
-RAD_FP64, RAD_MIXED = 0, 1
+RAD_FP64, RAD_MIXED, RAD_FP64_DF = 0, 1, 2
 RAD_NREC = 10
 RAD_TRAJ_MS, RAD_TRAJ_LL, RAD_TRAJ_MS_LOSS, RAD_TRAJ_FP32 = 1, 2, 4, 8
 
@@ -30,7 +30,7 @@ class RadChannel(ctypes.Structure):
                 ("X0", ctypes.c_double), ("rho", ctypes.c_double), ("mass_eV", ctypes.c_double),
                 ("charge_sign", ctypes.c_int), ("flags", ctypes.c_int)]
 MODES = {"classical": RAD_CLASSICAL, "spin0": RAD_SPIN0, "spin_half": RAD_SPIN_HALF}
-PRECISIONS = {"fp64": RAD_FP64, "mixed": RAD_MIXED}
+PRECISIONS = {"fp64": RAD_FP64, "mixed": RAD_MIXED, "fp64_df": RAD_FP64_DF}
 
 _lock = threading.Lock()
 _lib = None

@@ -82,7 +82,7 @@ ShapeKey key_of(int dev, int64_t ns, int64_t np, int64_t no, int64_t na, int mod
 // 64 x 64 directions, 32 particles per launch). Spin-1/2 (8 accumulators per energy) runs best with
 // 4 warps per block, 3 blocks per SM; the other models with 8 warps, 2 blocks per SM.
 Choice default_choice(int precision, int mode) {
-  if (precision == RAD_FP64) return Choice{2, 8, 64, 1, 0};
+  if (precision == RAD_FP64 || precision == RAD_FP64_DF) return Choice{2, 8, 64, 1, 0};
   if (mode == RAD_SPIN_HALF) return Choice{2, 4, 256, 1, 1};
   return Choice{2, 8, 256, 1, 1};
 }
@@ -90,6 +90,7 @@ Choice default_choice(int precision, int mode) {
 bool supported(int precision, const Choice &c) {
   if (c.pe != 0 && (precision != RAD_MIXED || !c.pp || (c.pe != 4 && c.pe != 6))) return false;
   if (precision == RAD_FP64) return c.pp == 0 && shape_supported_fp64(c.R, c.NW, c.T);
+  if (precision == RAD_FP64_DF) return c.pp == 0 && shape_supported_df(c.R, c.NW, c.T);
   return c.pp ? shape_supported_mixed_pp(c.R, c.NW, c.T) : shape_supported_mixed(c.R, c.NW, c.T);
 }
 
@@ -101,9 +102,10 @@ bool same_choice(const Choice &a, const Choice &b) {
 int configure(rad_plan p, const Choice &c) {
   if (!supported(p->precision, c)) return RAD_EINVAL;
   LaunchShape sh{c.R, c.NW, c.T, 0, 0, c.pe};
-  const int occ = p->precision == RAD_FP64 ? occupancy_fp64(sh)
-                  : c.pp                   ? occupancy_mixed_pp(sh)
-                                           : occupancy_mixed(sh);
+  const int occ = p->precision == RAD_FP64      ? occupancy_fp64(sh)
+                  : p->precision == RAD_FP64_DF ? occupancy_df(sh)
+                  : c.pp                        ? occupancy_mixed_pp(sh)
+                                                : occupancy_mixed(sh);
   if (occ <= 0) return RAD_EUNSUPPORTED;
   const int64_t resident = static_cast<int64_t>(p->sms) * occ;
   p->n_wt = static_cast<int>((p->n_omega + 32 * c.R - 1) / (32 * c.R));
@@ -164,7 +166,8 @@ int configure(rad_plan p, const Choice &c) {
   std::snprintf(buf, sizeof buf,
                 "precision=%s mode=%d R=%d NW=%d T=%d grid=%d occ=%d items=%lld chunks=%lld amp=%d nq=%d pp=%d "
                 "pe=%d",
-                p->precision == RAD_FP64 ? "fp64" : "mixed", p->mode, c.R, c.NW, c.T, sh.grid, occ,
+                p->precision == RAD_FP64 ? "fp64" : p->precision == RAD_FP64_DF ? "fp64_df" : "mixed", p->mode, c.R,
+                c.NW, c.T, sh.grid, occ,
                 static_cast<long long>(p->n_items), static_cast<long long>(p->n_chunks), p->amp_mode,
                 p->n_q, c.pp, c.pe);
   p->desc = buf;
@@ -175,7 +178,7 @@ int check_shape(int64_t ns, int64_t np, int64_t no, int64_t na, int mode, int pr
                 int32_t nb) {
   if (ns < 0 || np < 0 || no < 0 || na < 0) return RAD_EINVAL;
   if (mode < RAD_CLASSICAL || mode > RAD_SPIN_HALF) return RAD_EINVAL;
-  if (prec != RAD_FP64 && prec != RAD_MIXED) return RAD_EINVAL;
+  if (prec != RAD_FP64 && prec != RAD_MIXED && prec != RAD_FP64_DF) return RAD_EINVAL;
   if (want < 0 || want > 15) return RAD_EINVAL;
   if ((want & 4) && nb < 1) return RAD_EINVAL;
   if (want & RAD_PER_PARTICLE) {
@@ -276,6 +279,8 @@ int execute(rad_plan p, const double *samples, const int64_t *offsets, const dou
   }
   if (p->precision == RAD_FP64) {
     e = launch_fp64(P, &sh, st);
+  } else if (p->precision == RAD_FP64_DF) {
+    e = launch_df(P, &sh, st);
   } else if (p->choice.pp) {
     e = launch_mixed_pp(P, p->prep, &sh, st);
   } else {

@@ -1,0 +1,411 @@
+// FP64-accurate radiation-integral kernel that spends the FP64 pipe only where the result needs
+// it (sm_103a). GB300 executes FP64 at 1/64 of its FP32 rate, and the plain FP64 kernel
+// (rad_fp64.cu) spends about 20 FP64 instructions per term. Here a term costs 5:
+//   phi = w* A_k(n)                      one FP64 multiply: the same double as the oracle's phase
+//                                        (A_k(n) is formed in the oracle's IEEE order, FP64)
+//   phi = j 2 pi/4096 + r                the table index j and a two-part Cody-Waite reduction,
+//                                        FP64 (one FMA with a rounding constant, one subtraction,
+//                                        two FMAs), as in the plain kernel
+// and everything after the reduction runs in double-float FP32 arithmetic (T. J. Dekker, Numer.
+// Math. 18 (1971); error-free products by FMA and sums by Knuth's TwoSum):
+//   r -> (r_hi, r_lo)                    split by integer operations on r's bits
+//   sin r, cos r - 1                     Taylor series on |r| <= pi/4096, FP32 beyond the leading
+//                                        term of sin
+//   sin phi, cos phi                     with the (cos, sin)(2 pi j/4096) table held as float pairs,
+//                                        one error-free product and one TwoSum each
+//   sum_k f_k e^{i phi_k}                 f as float pairs, accumulated with the compensated dot
+//                                        product of Ogita, Rump and Oishi ("Accurate sum and dot
+//                                        product", SIAM J. Sci. Comput. 26 (2005), Dot2): per term
+//                                        and component an error-free product, a TwoSum and the
+//                                        errors summed in FP32
+// Tile sums are added into FP64 particle amplitudes. The per-term error is about 1e-14 of |f|,
+// far inside the FP64 form's tolerance (1e-9 of a bin, floor 1e-6 of the peak).
+#include <cstdio>
+
+#include "rad_internal.cuh"
+
+namespace rad {
+namespace {
+
+constexpr double kPiHi = 3.141592653589793116;
+constexpr double kPiLo = 1.2246467991473531772e-16;
+constexpr double kC1 = kPiHi / 2048.0;
+constexpr double kC2 = kPiLo / 2048.0;
+constexpr double kInvStep = 2048.0 / 3.141592653589793238462643383279502884;  // 4096/(2 pi)
+constexpr double kMagic = 6755399441055744.0;  // 1.5 * 2^52
+
+// hi = r rounded to FP32, lo = (r - hi) rounded to FP32, from r's bits with integer operations.
+// Valid for |r| < 2^100; |r| < 2^-126 gives (0, 0), an error below 1.2e-38.
+__device__ __forceinline__ void split_df(double r, float &hi, float &lo) {
+  const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(r));
+  const unsigned sign = static_cast<unsigned>(u >> 32) & 0x80000000u;
+  const int e = static_cast<int>((u >> 52) & 0x7ffull);
+  if (e < 1023 - 126) {
+    hi = 0.f;
+    lo = 0.f;
+    return;
+  }
+  const unsigned long long m = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);  // 53-bit significand
+  unsigned long long mh = (m + (1ull << 28)) >> 29;                      // rounded to 24 bits
+  const long long d = static_cast<long long>(m) - static_cast<long long>(mh << 29);  // |d| <= 2^28
+  int eh = e;
+  if (mh >> 24) {  // rounding carried into a 25th bit
+    mh >>= 1;
+    ++eh;
+  }
+  hi = __int_as_float(static_cast<int>(sign | (static_cast<unsigned>(eh - 1023 + 127) << 23) |
+                                       (static_cast<unsigned>(mh) & 0x7FFFFFu)));
+  // r - hi = sign * d * 2^(e - 1075) exactly; its FP32 rounding (0 when below 2^-98)
+  if (e >= 949) {
+    const float scale = __int_as_float((e - 948) << 23);  // 2^(e - 1075)
+    const float l = __int2float_rn(static_cast<int>(d)) * scale;
+    lo = sign ? -l : l;
+  } else {
+    lo = 0.f;
+  }
+}
+
+// s + t = a + b exactly (Knuth)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &t) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  t = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// one Dot2 step: (S, C) += (fh + fl)(eh + el)
+__device__ __forceinline__ void dot2(float &S, float &C, float fh, float fl, float eh, float el) {
+  const float p = __fmul_rn(fh, eh);
+  float q = __fmaf_rn(fh, eh, -p);                 // exact error of the product
+  q = __fmaf_rn(fh, el, __fmaf_rn(fl, eh, q));     // cross terms
+  float s, t;
+  two_sum(S, p, s, t);
+  S = s;
+  C = __fadd_rn(C, __fadd_rn(t, q));
+}
+
+template <int MODE>
+struct DfNcomp {
+  static constexpr int value = (MODE == RAD_SPIN_HALF) ? 8 : 6;
+};
+
+template <int MODE, int R, int NW, int T>
+struct DfLayout {
+  static constexpr int kStageDoubles = (T + 2) * kRec;
+  static constexpr int kTable = 0;                                   // float4 [kTabN]
+  static constexpr int kStage = kTable + kTabN * 16;
+  static constexpr int kNk = kStage + 2 * kStageDoubles * 8;         // per warp: A [T] double,
+  static constexpr int kNkWarp = T * 8 + T * 32;                     // Fa, Fb [T] float4
+  static constexpr int kBar = kNk + NW * kNkWarp;
+  static constexpr int kMisc = kBar + 16;
+  static constexpr int kTotal = kMisc + 16;
+};
+
+template <int MODE, int R, int NW, int T>
+__global__ void __launch_bounds__(NW * 32) k_df(const Params P) {
+  using L = DfLayout<MODE, R, NW, T>;
+  constexpr int NC = DfNcomp<MODE>::value;
+  extern __shared__ __align__(128) unsigned char sm[];
+  float4 *tab = reinterpret_cast<float4 *>(sm + L::kTable);
+  double *stage_base = reinterpret_cast<double *>(sm + L::kStage);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(sm + L::kBar);
+  int *s_item = reinterpret_cast<int *>(sm + L::kMisc);
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_item[1] = *reinterpret_cast<volatile int *>(P.status);
+  __syncthreads();
+  if (s_item[1] != 0) return;
+
+  // (cos, sin)(2 pi j / 4096) as float pairs (c_hi, c_lo, s_hi, s_lo) from the FP64 table
+  for (int i = tid; i < kTabN; i += NW * 32) {
+    const double2 t = P.table[i];
+    const float ch = __double2float_rn(t.x), sh = __double2float_rn(t.y);
+    tab[i] = make_float4(ch, __double2float_rn(t.x - static_cast<double>(ch)), sh,
+                         __double2float_rn(t.y - static_cast<double>(sh)));
+  }
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  uint32_t parity[2] = {0u, 0u};
+  unsigned char *myNk = sm + L::kNk + warp * L::kNkWarp;
+  double *myA = reinterpret_cast<double *>(myNk);
+  float4 *myFa = reinterpret_cast<float4 *>(myNk + T * 8);   // (fx_hi, fx_lo, fy_hi, fy_lo)
+  float4 *myFb = reinterpret_cast<float4 *>(myNk + T * 24);  // (fz_hi, fz_lo, j_hi, j_lo)
+
+  const int64_t per_chunk = static_cast<int64_t>(P.n_wt) * P.n_nt;
+  int s = 0;
+
+  for (;;) {
+    if (tid == 0) s_item[0] = atomicAdd(P.counter, 1);
+    __syncthreads();
+    const int64_t item = s_item[0];
+    __syncthreads();
+    if (item >= P.n_items) break;
+    const int64_t chunk = item / per_chunk;
+    const int64_t rem = item % per_chunk;
+    const int nt = static_cast<int>(rem / P.n_wt), wt = static_cast<int>(rem % P.n_wt);
+    const int64_t jdir = static_cast<int64_t>(nt) * NW + warp;
+    const bool jvalid = jdir < P.n_angles;
+    const double nx = jvalid ? P.theta_x[jdir] : 0.0;
+    const double ny = jvalid ? P.theta_y[jdir] : 0.0;
+    const double th2h = __dmul_rn(__dadd_rn(__dmul_rn(nx, nx), __dmul_rn(ny, ny)), 0.5);
+
+    int64_t iw[R];
+    double hwv[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      iw[r] = static_cast<int64_t>(wt) * 32 * R + r * 32 + lane;
+      hwv[r] = iw[r] < P.n_omega ? P.hw[iw[r]] : 1.0;
+    }
+    double S_acc[R];
+    double amp[R][NC];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      S_acc[r] = 0.0;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) amp[r][c] = 0.0;
+    }
+
+    int64_t p0, p1;
+    int q;
+    chunk_range(P, chunk, p0, p1, q);
+    TileCursor cur;
+    cur.p = p0;
+    cur.p_end = p1;
+    cursor_settle(P, cur, q);
+
+    if (cur.valid) {
+      if (tid == 0) issue_tile<T>(P, cur, stage_base + s * L::kStageDoubles, &bar[s]);
+      int64_t cur_p = -1;
+      double ws[R];
+      double inv2g2 = 0.0, cn = 0.0, wp = 1.0, gam = 2.0, En = 1.0;
+      for (;;) {
+        TileCursor nxt = cur;
+        cursor_next<T>(P, nxt, q);
+        if (nxt.valid && tid == 0)
+          issue_tile<T>(P, nxt, stage_base + (s ^ 1) * L::kStageDoubles, &bar[s ^ 1]);
+        if (cur.p != cur_p) {  // new particle: per-particle constants, fresh amplitudes
+          cur_p = cur.p;
+          gam = P.gamma[cur_p];
+          En = P.energy[cur_p];
+          wp = P.weight ? P.weight[cur_p] : 1.0;
+          inv2g2 = __ddiv_rn(1.0, __dmul_rn(__dmul_rn(2.0, gam), gam));
+          cn = __dadd_rn(inv2g2, th2h);
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const double w = __ddiv_rn(hwv[r], kHbarC);
+            if (MODE == RAD_CLASSICAL) {
+              ws[r] = w;
+            } else {
+              const double u = __ddiv_rn(hwv[r], En);
+              ws[r] = __ddiv_rn(w, __dsub_rn(1.0, u));
+            }
+#pragma unroll
+            for (int c = 0; c < NC; ++c) amp[r][c] = 0.0;
+          }
+        }
+        const bool ok = mbar_wait_bounded(&bar[s], parity[s]);
+        parity[s] ^= 1u;
+        if (__syncthreads_or(!ok)) {  // bounded wait ran out: record, drain, leave
+          if (tid == 0) {
+            set_status(P.status, RAD_ETIMEOUT);
+            mbar_wait_bounded(&bar[s], parity[s] ^ 1u);
+            if (nxt.valid) mbar_wait_bounded(&bar[s ^ 1], parity[s ^ 1]);
+          }
+          return;
+        }
+        const double *st = stage_base + s * L::kStageDoubles;
+        const int n = static_cast<int>((cur.ke - cur.k0) < T ? (cur.ke - cur.k0) : T);
+
+        // per (n, k): phase A in the oracle's IEEE order (FP64), weighted f and j as float pairs
+        for (int k = lane; k < n; k += 32) {
+          const double *rc = st + (k + 1) * kRec;
+          const int64_t K = cur.k0 + k;
+          const double tm = (K == 0) ? rc[F_T] : st[k * kRec + F_T];
+          const double tp = (K == cur.L - 1) ? rc[F_T] : st[(k + 2) * kRec + F_T];
+          const double w = 0.5 * (tp - tm);
+          double A = __dmul_rn(cn, rc[F_T]);
+          A = __dsub_rn(A, rc[F_DZ]);
+          A = __dsub_rn(A, __dmul_rn(nx, rc[F_X]));
+          A = __dsub_rn(A, __dmul_rn(ny, rc[F_Y]));
+          const double vx = rc[F_VX], vy = rc[F_VY], dvz = rc[F_DVZ];
+          const double ax = rc[F_AX], ay = rc[F_AY], az = rc[F_AZ];
+          const double D = cn - dvz - nx * vx - ny * vy;  // 1 - n.beta (Sec. II, g)
+          const double gw = w / (D * D);
+          const double a = nx - vx, b = ny - vy;
+          const double m = az + nx * ax + ny * ay;         // n.beta_dot
+          const double cz = inv2g2 - th2h - dvz;           // n_z - beta_z
+          const double fx = (a * m - ax * D) * gw, fy = (b * m - ay * D) * gw, fz = (cz * m - az * D) * gw;
+          const double fj = (MODE == RAD_SPIN_HALF) ? m * gw : 0.0;
+          const float fxh = __double2float_rn(fx), fyh = __double2float_rn(fy);
+          const float fzh = __double2float_rn(fz), fjh = __double2float_rn(fj);
+          myA[k] = A;
+          myFa[k] = make_float4(fxh, __double2float_rn(fx - fxh), fyh, __double2float_rn(fy - fyh));
+          myFb[k] = make_float4(fzh, __double2float_rn(fz - fzh), fjh, __double2float_rn(fj - fjh));
+        }
+        __syncwarp();
+
+        // tile sums (S + C per component), compensated
+        float tS[R][NC], tC[R][NC];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+          for (int c = 0; c < NC; ++c) tS[r][c] = tC[r][c] = 0.f;
+        for (int k = 0; k < n; ++k) {
+          const double A = myA[k];
+          const float4 Fa = myFa[k], Fb = myFb[k];
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const double phi = __dmul_rn(ws[r], A);
+            const double y = fma(phi, kInvStep, kMagic);
+            const int j = __double2loint(y);
+            const double jd = y - kMagic;
+            double rr = fma(-jd, kC1, phi);
+            rr = fma(-jd, kC2, rr);
+            float xh, xl;
+            split_df(rr, xh, xl);
+            const float4 t = tab[j & (kTabN - 1)];  // (C_hi, C_lo, S_hi, S_lo)
+            const float x2 = __fmul_rn(xh, xh);
+            const float x2e = __fmaf_rn(xh, xh, -x2);  // xh^2 = x2 + x2e exactly
+            // cos x - 1 and the part of sin x below xh
+            const float cm = __fmaf_rn(-0.5f, x2e, __fmaf_rn(-xh, xl, __fmul_rn(x2, __fmaf_rn(x2, 1.0f / 24.0f, -0.5f))));
+            const float sxl = __fmaf_rn(__fmul_rn(-xh, x2), __fmaf_rn(x2, -1.0f / 120.0f, 1.0f / 6.0f), xl);
+            // sin(phi) = S + S cm + C xh + C sxl
+            float sh, sl;
+            {
+              const float p = __fmul_rn(t.x, xh);
+              const float pe = __fmaf_rn(t.x, xh, -p);
+              float v;
+              two_sum(t.z, p, sh, v);
+              sl = __fadd_rn(v, __fadd_rn(pe, __fmaf_rn(t.y, xh, __fmaf_rn(t.x, sxl, __fmaf_rn(t.z, cm, t.w)))));
+            }
+            // cos(phi) = C + C cm - S xh - S sxl
+            float ch, cl;
+            {
+              const float p = __fmul_rn(-t.z, xh);
+              const float pe = __fmaf_rn(-t.z, xh, -p);
+              float v;
+              two_sum(t.x, p, ch, v);
+              cl = __fadd_rn(v, __fadd_rn(pe, __fmaf_rn(-t.w, xh, __fmaf_rn(-t.z, sxl, __fmaf_rn(t.x, cm, t.y)))));
+            }
+            dot2(tS[r][0], tC[r][0], Fa.x, Fa.y, ch, cl);
+            dot2(tS[r][1], tC[r][1], Fa.x, Fa.y, sh, sl);
+            dot2(tS[r][2], tC[r][2], Fa.z, Fa.w, ch, cl);
+            dot2(tS[r][3], tC[r][3], Fa.z, Fa.w, sh, sl);
+            dot2(tS[r][4], tC[r][4], Fb.x, Fb.y, ch, cl);
+            dot2(tS[r][5], tC[r][5], Fb.x, Fb.y, sh, sl);
+            if (MODE == RAD_SPIN_HALF) {
+              dot2(tS[r][6], tC[r][6], Fb.z, Fb.w, ch, cl);
+              dot2(tS[r][7], tC[r][7], Fb.z, Fb.w, sh, sl);
+            }
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+          for (int c = 0; c < NC; ++c)
+            amp[r][c] += static_cast<double>(tS[r][c]) + static_cast<double>(tC[r][c]);
+
+        const bool last_of_particle = !nxt.valid || nxt.p != cur.p;
+        if (last_of_particle && !P.amp_mode) {
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            double I2 = 0.0;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) I2 = fma(amp[r][c], amp[r][c], I2);
+            double Sv;
+            if (MODE == RAD_CLASSICAL) {
+              Sv = I2;
+            } else {
+              const double u = hwv[r] / En;
+              if (MODE == RAD_SPIN0) {
+                Sv = (1.0 - u) * I2;
+              } else {
+                const double J2 = amp[r][6] * amp[r][6] + amp[r][7] * amp[r][7];
+                Sv = 0.5 * (1.0 + (1.0 - u) * (1.0 - u)) * I2 + (u * u) / (2.0 * gam * gam) * J2;
+              }
+            }
+            S_acc[r] = fma(wp, Sv, S_acc[r]);
+          }
+        }
+        __syncthreads();  // stage s and the per-warp arrays are free again
+        s ^= 1;
+        if (!nxt.valid) break;
+        cur = nxt;
+      }
+    }
+    if (jvalid) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        if (iw[r] >= P.n_omega) continue;
+        if (!P.amp_mode) {
+          P.part[(chunk * P.n_angles + jdir) * P.n_omega + iw[r]] = S_acc[r];
+        } else {
+#pragma unroll
+          for (int c = 0; c < NC; ++c)
+            P.part[((chunk * NC + c) * P.n_angles + jdir) * P.n_omega + iw[r]] = amp[r][c];
+        }
+      }
+    }
+  }
+}
+
+template <int MODE, int R, int NW>
+cudaError_t launch_t(const Params &P, LaunchShape *shape, cudaStream_t st, int *occ) {
+  constexpr int T = 64;
+  using L = DfLayout<MODE, R, NW, T>;
+  auto kern = k_df<MODE, R, NW, T>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kTotal);
+  if (e != cudaSuccess) return e;
+  shape->smem = L::kTotal;
+  if (occ) {
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, NW * 32, L::kTotal);
+    *occ = (e == cudaSuccess) ? nb : 0;
+    return e;
+  }
+  if (shape->grid <= 0) return cudaErrorInvalidConfiguration;
+  kern<<<shape->grid, NW * 32, L::kTotal, st>>>(P);
+  return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t dispatch_mode(const Params &P, LaunchShape *sh, cudaStream_t st, int *occ) {
+  if (sh->T != 64) return cudaErrorInvalidValue;
+  if (sh->R == 1 && sh->NW == 8) return launch_t<MODE, 1, 8>(P, sh, st, occ);
+  if (sh->R == 2 && sh->NW == 4) return launch_t<MODE, 2, 4>(P, sh, st, occ);
+  if (sh->R == 2 && sh->NW == 8) return launch_t<MODE, 2, 8>(P, sh, st, occ);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t dispatch(const Params &P, LaunchShape *sh, cudaStream_t st, int *occ) {
+  switch (P.mode) {
+    case RAD_CLASSICAL: return dispatch_mode<RAD_CLASSICAL>(P, sh, st, occ);
+    case RAD_SPIN0: return dispatch_mode<RAD_SPIN0>(P, sh, st, occ);
+    case RAD_SPIN_HALF: return dispatch_mode<RAD_SPIN_HALF>(P, sh, st, occ);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+bool shape_supported_df(int R, int NW, int T) {
+  return T == 64 && ((R == 1 && NW == 8) || (R == 2 && (NW == 4 || NW == 8)));
+}
+
+cudaError_t launch_df(const Params &P, LaunchShape *shape, cudaStream_t st) {
+  return dispatch(P, shape, st, nullptr);
+}
+
+int occupancy_df(const LaunchShape &s) {
+  Params P{};
+  P.mode = RAD_SPIN_HALF;
+  LaunchShape sh = s;
+  int occ = 0;
+  if (dispatch(P, &sh, nullptr, &occ) != cudaSuccess) return 0;
+  return occ;
+}
+
+}  // namespace rad

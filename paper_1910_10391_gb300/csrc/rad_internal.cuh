@@ -236,6 +236,11 @@ int occupancy_mixed_pp(const LaunchShape &s);
 cudaError_t launch_prep_samples(const Params &P, int T, float *prep, cudaStream_t st);
 cudaError_t launch_mixed_pp(const Params &P, const float *prep, LaunchShape *shape, cudaStream_t st);
 
+// FP64-accurate kernel with double-float FP32 arithmetic after the FP64 phase (rad_df.cu)
+bool shape_supported_df(int R, int NW, int T);
+int occupancy_df(const LaunchShape &s);
+cudaError_t launch_df(const Params &P, LaunchShape *shape, cudaStream_t st);
+
 // post-processing kernels (rad_post.cu)
 cudaError_t launch_validate(const Params &P, const double *d_omega, bool need_domega,
                             const int32_t *bin_of_angle, cudaStream_t st);

@@ -23,7 +23,7 @@ def main(argv=None):
     ap.add_argument("--n-omega", type=int, default=512)
     ap.add_argument("--n-side", type=int, default=64)
     ap.add_argument("--mode", default="classical", choices=["classical", "spin0", "spin_half"])
-    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed", "fp64_df"])
     ap.add_argument("--shape", default="", help="R,NW,T,chunk_mult")
     ap.add_argument("--repeat", type=int, default=2)
     ap.add_argument("--graph", action="store_true", help="replay a captured CUDA graph")
