@@ -34,6 +34,9 @@ TUNE_PARTICLES = 8
 # 32-particle launches of this workload (R=2 or 4, NW=4 or 8, T=128 or 256); --autotune lets the
 # library's autotuner choose instead
 SHAPES = {0: (2, 8, 256), 2: (2, 4, 256)}
+# FP64 instructions per term of the double-float kernel per model, counted by ncu
+# (smsp__inst_executed_pipe_fp64 on 1 particle x 20000 samples x 128 hw x 32 x 32 directions)
+DF_FP64_OPS_PER_TERM = {0: 6.11, 2: 6.36}
 WORKLOAD = ("positron ensemble: 1024 e+ at 10 GeV, harmonic planar well (U0 = 20 eV, d_p = 1.92 A), "
             "RK4 + scattering kicks, 20000 samples over 100 um; 512 log hw in [1e-4 E, 0.5 E] x 64x64 "
             "directions within +-(theta_L + 3/gamma); classical + spin-1/2")
@@ -326,6 +329,15 @@ def main():
     f_terms = len(modes) * terms_of(args.fp64_batch, grid)
     fp64_value = world * f_terms / (fms_step * 1e-3)
 
+    # ---- FP64-accurate double-float form on the same inputs (same tolerance as plain FP64) ----
+    dfp = make_plans(rad.RAD_FP64_DF, args.fp64_batch)
+    for m in modes:
+        dfp[m].set_timing(True)
+    dkms = []
+    dms, _ = timed(dfp, args.fp64_batch, args.fp64_steps, 1, dkms)
+    dms_step = dms / args.fp64_steps
+    df_value = world * f_terms / (dms_step * 1e-3)
+
     # ---- end to end through the host-buffer entry point (pinned memory, copies timed) ----
     nb_e = B
     p0 = (rank * nb_e) % N_PART
@@ -411,6 +423,17 @@ def main():
                  "fp64_ops_per_term": 20,
                  "frac_fp64_pipe": 20 * f_terms_launch / (fp64_kernel_ms * 1e-3) /
                  (SM_COUNT * FP64_PER_SM_CLK * SM_MAX_MHZ * 1e6)}
+    dk = [ms for (_, ms) in dkms]
+    df_kernel_ms = sum(dk) / len(dk)
+    df_fp64_s = sum(DF_FP64_OPS_PER_TERM[int(m)] * f_terms_launch for (m, _) in dkms) / (sum(dk) * 1e-3)
+    # FP64 instructions per term of k_df: the phase product, the rounding-constant FMA, the
+    # subtraction and two Cody-Waite FMAs (5), plus the per-(direction, sample) preparation of the
+    # phase and f shared by 64 energies and the conversion of the tile sums into the FP64 particle
+    # amplitudes (DF_FP64_OPS_PER_TERM, counted by ncu)
+    df_roof = {"kernel": "k_df", "kernel_ms_avg": df_kernel_ms,
+               "terms_per_s": f_terms_launch / (df_kernel_ms * 1e-3),
+               "fp64_ops_per_term": DF_FP64_OPS_PER_TERM,
+               "frac_fp64_pipe": df_fp64_s / (SM_COUNT * FP64_PER_SM_CLK * SM_MAX_MHZ * 1e6)}
 
     line = {
         "metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": world, "steps": args.steps,
@@ -424,6 +447,10 @@ def main():
         "plain_fp64": {"value": fp64_value, "unit": "terms/s", "particles_per_step": args.fp64_batch,
                        "ms_per_step": fms_step, "spectra_per_s": world * len(modes) * args.fp64_batch /
                        (fms_step * 1e-3), "shape": {m: fp[m].describe() for m in modes}, "kernel": fp64_roof},
+        "fp64_df": {"value": df_value, "unit": "terms/s", "particles_per_step": args.fp64_batch,
+                    "ms_per_step": dms_step, "spectra_per_s": world * len(modes) * args.fp64_batch /
+                    (dms_step * 1e-3), "shape": {m: dfp[m].describe() for m in modes}, "kernel": df_roof,
+                    "tolerance": "as plain FP64: 1e-9 of a bin, floor 1e-6 of the peak"},
         "mixed_over_fp64": value / fp64_value,
         "roofline": roofline,
         "e2e": {"value": e2e_value, "unit": "terms/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -439,7 +466,7 @@ def main():
         vals, bi, bj, terms, dt, cores = run_oracle_sample(tr, grid, n_dirs, modes)
         one = batch_args(0, 1)
         errs = {}
-        for prec, name in ((rad.RAD_MIXED, "mixed"), (rad.RAD_FP64, "fp64")):
+        for prec, name in ((rad.RAD_MIXED, "mixed"), (rad.RAD_FP64, "fp64"), (rad.RAD_FP64_DF, "fp64_df")):
             for m in modes:
                 p1 = rad.Plan(N_SAMP, 1, no, na, m, prec, 1, 0)
                 c1 = torch.empty(no * na, dtype=torch.float64, device=dev)

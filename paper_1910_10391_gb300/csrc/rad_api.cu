@@ -82,7 +82,8 @@ ShapeKey key_of(int dev, int64_t ns, int64_t np, int64_t no, int64_t na, int mod
 // 64 x 64 directions, 32 particles per launch). Spin-1/2 (8 accumulators per energy) runs best with
 // 4 warps per block, 3 blocks per SM; the other models with 8 warps, 2 blocks per SM.
 Choice default_choice(int precision, int mode) {
-  if (precision == RAD_FP64 || precision == RAD_FP64_DF) return Choice{2, 8, 64, 1, 0};
+  if (precision == RAD_FP64) return Choice{2, 8, 64, 1, 0};
+  if (precision == RAD_FP64_DF) return Choice{2, 4, 64, 1, 0};
   if (mode == RAD_SPIN_HALF) return Choice{2, 4, 256, 1, 1};
   return Choice{2, 8, 256, 1, 1};
 }

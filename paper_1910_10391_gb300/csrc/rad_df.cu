@@ -3,15 +3,15 @@
 // (rad_fp64.cu) spends about 20 FP64 instructions per term. Here a term costs 5:
 //   phi = w* A_k(n)                      one FP64 multiply: the same double as the oracle's phase
 //                                        (A_k(n) is formed in the oracle's IEEE order, FP64)
-//   phi = j 2 pi/4096 + r                the table index j and a two-part Cody-Waite reduction,
+//   phi = j 2 pi/2048 + r                the table index j and a two-part Cody-Waite reduction,
 //                                        FP64 (one FMA with a rounding constant, one subtraction,
 //                                        two FMAs), as in the plain kernel
 // and everything after the reduction runs in double-float FP32 arithmetic (T. J. Dekker, Numer.
 // Math. 18 (1971); error-free products by FMA and sums by Knuth's TwoSum):
 //   r -> (r_hi, r_lo)                    split by integer operations on r's bits
-//   sin r, cos r - 1                     Taylor series on |r| <= pi/4096, FP32 beyond the leading
+//   sin r, cos r - 1                     Taylor series on |r| <= pi/2048, FP32 beyond the leading
 //                                        term of sin
-//   sin phi, cos phi                     with the (cos, sin)(2 pi j/4096) table held as float pairs,
+//   sin phi, cos phi                     with a (cos, sin)(2 pi j/2048) table held as float pairs,
 //                                        one error-free product and one TwoSum each
 //   sum_k f_k e^{i phi_k}                 f as float pairs, accumulated with the compensated dot
 //                                        product of Ogita, Rump and Oishi ("Accurate sum and dot
@@ -29,9 +29,10 @@ namespace {
 
 constexpr double kPiHi = 3.141592653589793116;
 constexpr double kPiLo = 1.2246467991473531772e-16;
-constexpr double kC1 = kPiHi / 2048.0;
-constexpr double kC2 = kPiLo / 2048.0;
-constexpr double kInvStep = 2048.0 / 3.141592653589793238462643383279502884;  // 4096/(2 pi)
+constexpr int kDfTabN = 2048;  // table of (cos, sin)(2 pi j / 2048): every other FP64 table entry
+constexpr double kC1 = kPiHi / 1024.0;
+constexpr double kC2 = kPiLo / 1024.0;
+constexpr double kInvStep = 1024.0 / 3.141592653589793238462643383279502884;  // 2048/(2 pi)
 constexpr double kMagic = 6755399441055744.0;  // 1.5 * 2^52
 
 // hi = r rounded to FP32, lo = (r - hi) rounded to FP32, from r's bits with integer operations.
@@ -91,8 +92,8 @@ struct DfNcomp {
 template <int MODE, int R, int NW, int T>
 struct DfLayout {
   static constexpr int kStageDoubles = (T + 2) * kRec;
-  static constexpr int kTable = 0;                                   // float4 [kTabN]
-  static constexpr int kStage = kTable + kTabN * 16;
+  static constexpr int kTable = 0;                                   // float4 [kDfTabN]
+  static constexpr int kStage = kTable + kDfTabN * 16;
   static constexpr int kNk = kStage + 2 * kStageDoubles * 8;         // per warp: A [T] double,
   static constexpr int kNkWarp = T * 8 + T * 32;                     // Fa, Fb [T] float4
   static constexpr int kBar = kNk + NW * kNkWarp;
@@ -115,9 +116,10 @@ __global__ void __launch_bounds__(NW * 32) k_df(const Params P) {
   __syncthreads();
   if (s_item[1] != 0) return;
 
-  // (cos, sin)(2 pi j / 4096) as float pairs (c_hi, c_lo, s_hi, s_lo) from the FP64 table
-  for (int i = tid; i < kTabN; i += NW * 32) {
-    const double2 t = P.table[i];
+  // (cos, sin)(2 pi j / 2048) as float pairs (c_hi, c_lo, s_hi, s_lo) from every other entry of the
+  // FP64 table (2048 entries, 32 KB: three blocks of 4 warps fit on an SM)
+  for (int i = tid; i < kDfTabN; i += NW * 32) {
+    const double2 t = P.table[2 * i];
     const float ch = __double2float_rn(t.x), sh = __double2float_rn(t.y);
     tab[i] = make_float4(ch, __double2float_rn(t.x - static_cast<double>(ch)), sh,
                          __double2float_rn(t.y - static_cast<double>(sh)));
@@ -266,7 +268,7 @@ __global__ void __launch_bounds__(NW * 32) k_df(const Params P) {
             rr = fma(-jd, kC2, rr);
             float xh, xl;
             split_df(rr, xh, xl);
-            const float4 t = tab[j & (kTabN - 1)];  // (C_hi, C_lo, S_hi, S_lo)
+            const float4 t = tab[j & (kDfTabN - 1)];  // (C_hi, C_lo, S_hi, S_lo)
             const float x2 = __fmul_rn(xh, xh);
             const float x2e = __fmaf_rn(xh, xh, -x2);  // xh^2 = x2 + x2e exactly
             // cos x - 1 and the part of sin x below xh
