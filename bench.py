@@ -36,7 +36,7 @@ TUNE_PARTICLES = 8
 SHAPES = {0: (2, 8, 256), 2: (2, 4, 256)}
 # FP64 instructions per term of the double-float kernel per model, counted by ncu
 # (smsp__inst_executed_pipe_fp64 on 1 particle x 20000 samples x 128 hw x 32 x 32 directions)
-DF_FP64_OPS_PER_TERM = {0: 6.11, 2: 6.36}
+DF_FP64_OPS_PER_TERM = {0: 5.12, 2: 5.36}
 WORKLOAD = ("positron ensemble: 1024 e+ at 10 GeV, harmonic planar well (U0 = 20 eV, d_p = 1.92 A), "
             "RK4 + scattering kicks, 20000 samples over 100 um; 512 log hw in [1e-4 E, 0.5 E] x 64x64 "
             "directions within +-(theta_L + 3/gamma); classical + spin-1/2")
@@ -427,7 +427,7 @@ def main():
     df_kernel_ms = sum(dk) / len(dk)
     df_fp64_s = sum(DF_FP64_OPS_PER_TERM[int(m)] * f_terms_launch for (m, _) in dkms) / (sum(dk) * 1e-3)
     # FP64 instructions per term of k_df: the phase product, the rounding-constant FMA, the
-    # subtraction and two Cody-Waite FMAs (5), plus the per-(direction, sample) preparation of the
+    # subtraction and the first Cody-Waite FMA (4), plus the per-(direction, sample) preparation of the
     # phase and f shared by 64 energies and the conversion of the tile sums into the FP64 particle
     # amplitudes (DF_FP64_OPS_PER_TERM, counted by ncu)
     df_roof = {"kernel": "k_df", "kernel_ms_avg": df_kernel_ms,

@@ -1,11 +1,12 @@
 // FP64-accurate radiation-integral kernel that spends the FP64 pipe only where the result needs
 // it (sm_103a). GB300 executes FP64 at 1/64 of its FP32 rate, and the plain FP64 kernel
-// (rad_fp64.cu) spends about 20 FP64 instructions per term. Here a term costs 5:
+// (rad_fp64.cu) spends about 20 FP64 instructions per term. Here a term costs 4:
 //   phi = w* A_k(n)                      one FP64 multiply: the same double as the oracle's phase
 //                                        (A_k(n) is formed in the oracle's IEEE order, FP64)
-//   phi = j 2 pi/2048 + r                the table index j and a two-part Cody-Waite reduction,
-//                                        FP64 (one FMA with a rounding constant, one subtraction,
-//                                        two FMAs), as in the plain kernel
+//   phi = j 2 pi/2048 + r                the table index j and a two-part Cody-Waite reduction:
+//                                        FP64 for the rounding-constant FMA, the subtraction and the
+//                                        first step (phi - j C1); the second step (j C2, below
+//                                        6e-11 rad) in FP32
 // and everything after the reduction runs in double-float FP32 arithmetic (T. J. Dekker, Numer.
 // Math. 18 (1971); error-free products by FMA and sums by Knuth's TwoSum):
 //   r -> (r_hi, r_lo)                    split by integer operations on r's bits
@@ -34,6 +35,7 @@ constexpr double kC1 = kPiHi / 1024.0;
 constexpr double kC2 = kPiLo / 1024.0;
 constexpr double kInvStep = 1024.0 / 3.141592653589793238462643383279502884;  // 2048/(2 pi)
 constexpr double kMagic = 6755399441055744.0;  // 1.5 * 2^52
+constexpr float kC2f = static_cast<float>(kC2);
 
 // hi = r rounded to FP32, lo = (r - hi) rounded to FP32, from r's bits with integer operations.
 // Valid for |r| < 2^100; |r| < 2^-126 gives (0, 0), an error below 1.2e-38.
@@ -102,7 +104,7 @@ struct DfLayout {
 };
 
 template <int MODE, int R, int NW, int T>
-__global__ void __launch_bounds__(NW * 32) k_df(const Params P) {
+__global__ void __launch_bounds__(NW * 32, NW == 4 ? 3 : 1) k_df(const Params P) {
   using L = DfLayout<MODE, R, NW, T>;
   constexpr int NC = DfNcomp<MODE>::value;
   extern __shared__ __align__(128) unsigned char sm[];
@@ -264,10 +266,16 @@ __global__ void __launch_bounds__(NW * 32) k_df(const Params P) {
             const double y = fma(phi, kInvStep, kMagic);
             const int j = __double2loint(y);
             const double jd = y - kMagic;
-            double rr = fma(-jd, kC1, phi);
-            rr = fma(-jd, kC2, rr);
+            const double r1 = fma(-jd, kC1, phi);  // phi - j C1, one rounding
             float xh, xl;
-            split_df(rr, xh, xl);
+            if ((__double2hiint(phi) & 0x7FF00000) < ((1023 + 22) << 20)) {  // |phi| < 2^22, by its bits
+              // second Cody-Waite step in FP32: |j C2| < 2^31 * 6.0e-20, so its FP32 product and
+              // the conversion of j are accurate to ~1e-17 rad
+              split_df(r1, xh, xl);
+              xl = __fmaf_rn(-__int2float_rn(j), kC2f, xl);
+            } else {
+              split_df(fma(-jd, kC2, r1), xh, xl);
+            }
             const float4 t = tab[j & (kDfTabN - 1)];  // (C_hi, C_lo, S_hi, S_lo)
             const float x2 = __fmul_rn(xh, xh);
             const float x2e = __fmaf_rn(xh, xh, -x2);  // xh^2 = x2 + x2e exactly
