@@ -34,9 +34,11 @@ TUNE_PARTICLES = 8
 # 32-particle launches of this workload (R=2 or 4, NW=4 or 8, T=128 or 256); --autotune lets the
 # library's autotuner choose instead
 SHAPES = {0: (2, 8, 256), 2: (2, 4, 256)}
-# FP64 instructions per term of the double-float kernel per model, counted by ncu
-# (smsp__inst_executed_pipe_fp64 on 1 particle x 20000 samples x 128 hw x 32 x 32 directions)
-DF_FP64_OPS_PER_TERM = {0: 5.12, 2: 5.36}
+# FP64 instructions per term and warp instructions per 32 terms of the double-float kernel per
+# model, counted by ncu (smsp__inst_executed_pipe_fp64, smsp__inst_executed on 1 particle x 20000
+# samples x 128 hw x 32 x 32 directions)
+DF_FP64_OPS_PER_TERM = {0: 2.12, 2: 2.36}
+DF_INST_PER_32_TERMS = {0: 182.8, 2: 210.0}
 WORKLOAD = ("positron ensemble: 1024 e+ at 10 GeV, harmonic planar well (U0 = 20 eV, d_p = 1.92 A), "
             "RK4 + scattering kicks, 20000 samples over 100 um; 512 log hw in [1e-4 E, 0.5 E] x 64x64 "
             "directions within +-(theta_L + 3/gamma); classical + spin-1/2")
@@ -426,14 +428,16 @@ def main():
     dk = [ms for (_, ms) in dkms]
     df_kernel_ms = sum(dk) / len(dk)
     df_fp64_s = sum(DF_FP64_OPS_PER_TERM[int(m)] * f_terms_launch for (m, _) in dkms) / (sum(dk) * 1e-3)
-    # FP64 instructions per term of k_df: the phase product, the rounding-constant FMA, the
-    # subtraction and the first Cody-Waite FMA (4), plus the per-(direction, sample) preparation of the
-    # phase and f shared by 64 energies and the conversion of the tile sums into the FP64 particle
-    # amplitudes (DF_FP64_OPS_PER_TERM, counted by ncu)
+    df_inst_s = sum(DF_INST_PER_32_TERMS[int(m)] * f_terms_launch / 32 for (m, _) in dkms) / (sum(dk) * 1e-3)
+    # k_df: one FP64 instruction per term (the phase product; the reduction is integer
+    # arithmetic) plus the per-(direction, sample) preparation shared by 64 energies and the
+    # conversion of the tile sums into FP64 particle amplitudes; it is bound by the issue slots
+    # (4 warp instructions per SM per clock), the FP64 pipe second
     df_roof = {"kernel": "k_df", "kernel_ms_avg": df_kernel_ms,
                "terms_per_s": f_terms_launch / (df_kernel_ms * 1e-3),
-               "fp64_ops_per_term": DF_FP64_OPS_PER_TERM,
-               "frac_fp64_pipe": df_fp64_s / (SM_COUNT * FP64_PER_SM_CLK * SM_MAX_MHZ * 1e6)}
+               "fp64_ops_per_term": DF_FP64_OPS_PER_TERM, "warp_inst_per_32_terms": DF_INST_PER_32_TERMS,
+               "frac_fp64_pipe": df_fp64_s / (SM_COUNT * FP64_PER_SM_CLK * SM_MAX_MHZ * 1e6),
+               "frac_issue": df_inst_s / (SM_COUNT * ISSUE_PER_SM_CLK / 32 * SM_MAX_MHZ * 1e6)}
 
     line = {
         "metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": world, "steps": args.steps,

@@ -73,9 +73,10 @@ extern "C" {
 
 #define RAD_FP64 0  /* every operation in FP64 (the paper's precision, Sec. IV)          */
 #define RAD_MIXED 1 /* FP64 phase base and particle sums; FP32 sincos, f and tile sums   */
-/* RAD_FP64_DF: FP64 accuracy with the FP64 phase product and its reduction as in RAD_FP64,
- * then double-float FP32 arithmetic (float pairs) for sin, cos, f and compensated tile sums,
- * and FP64 particle sums: the RAD_FP64 tolerance with about a quarter of its FP64 instructions. */
+/* RAD_FP64_DF: FP64 accuracy with the FP64 phase product of RAD_FP64, reduced exactly by
+ * fixed-point integer arithmetic, then double-float FP32 arithmetic (float pairs) for sin, cos,
+ * f and compensated tile sums, and FP64 particle sums: the RAD_FP64 tolerance with a small
+ * fraction of its FP64 instructions (GB300 runs FP64 at 1/64 of FP32). */
 #define RAD_FP64_DF 2
 
 #define RAD_NREC 10 /* float64 fields per trajectory record */

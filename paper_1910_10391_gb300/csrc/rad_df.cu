@@ -1,15 +1,13 @@
 // FP64-accurate radiation-integral kernel that spends the FP64 pipe only where the result needs
 // it (sm_103a). GB300 executes FP64 at 1/64 of its FP32 rate, and the plain FP64 kernel
-// (rad_fp64.cu) spends about 20 FP64 instructions per term. Here a term costs 4:
+// (rad_fp64.cu) spends about 20 FP64 instructions per term. Here a term costs one:
 //   phi = w* A_k(n)                      one FP64 multiply: the same double as the oracle's phase
 //                                        (A_k(n) is formed in the oracle's IEEE order, FP64)
-//   phi = j 2 pi/2048 + r                the table index j and a two-part Cody-Waite reduction:
-//                                        FP64 for the rounding-constant FMA, the subtraction and the
-//                                        first step (phi - j C1); the second step (j C2, below
-//                                        6e-11 rad) in FP32
+//   phi = j 2 pi/2048 + r                the table index j and the reduced phase by a fixed-point
+//                                        (Payne-Hanek) reduction of phi's bits with integer multiplies
 // and everything after the reduction runs in double-float FP32 arithmetic (T. J. Dekker, Numer.
 // Math. 18 (1971); error-free products by FMA and sums by Knuth's TwoSum):
-//   r -> (r_hi, r_lo)                    split by integer operations on r's bits
+//   r = (r_hi, r_lo)                     the reduction's fraction times pi/1024 as a float pair
 //   sin r, cos r - 1                     Taylor series on |r| <= pi/2048, FP32 beyond the leading
 //                                        term of sin
 //   sin phi, cos phi                     with a (cos, sin)(2 pi j/2048) table held as float pairs,
@@ -35,7 +33,6 @@ constexpr double kC1 = kPiHi / 1024.0;
 constexpr double kC2 = kPiLo / 1024.0;
 constexpr double kInvStep = 1024.0 / 3.141592653589793238462643383279502884;  // 2048/(2 pi)
 constexpr double kMagic = 6755399441055744.0;  // 1.5 * 2^52
-constexpr float kC2f = static_cast<float>(kC2);
 
 // hi = r rounded to FP32, lo = (r - hi) rounded to FP32, from r's bits with integer operations.
 // Valid for |r| < 2^100; |r| < 2^-126 gives (0, 0), an error below 1.2e-38.
@@ -66,6 +63,54 @@ __device__ __forceinline__ void split_df(double r, float &hi, float &lo) {
   } else {
     lo = 0.f;
   }
+}
+
+// 1024/pi = kKH + kKL 2^-64 (fixed point, truncation below 2^-64) and pi/1024 = kChf + kClf
+// (float pair, residual 3e-18 relative)
+constexpr unsigned long long kKH = 325ull;
+constexpr unsigned long long kKL = 17511926765934236664ull;
+constexpr float kChf = 0.003067961661145091f;
+constexpr float kClf = -8.537380524753502e-11f;
+
+// phi = j pi/1024 + r with |r| <= pi/2048; returns j, r as the float pair (xh, xl).
+// For 2^-10 <= |phi| < 2^22 by a fixed-point (Payne-Hanek) reduction of phi's bits with integer
+// multiplies: |phi| = m 2^(e-1075) with the 53-bit significand m, and phi 1024/pi = m K 2^(e-1139)
+// with K = 1024/pi 2^64 as a 73-bit integer, formed as a 128-bit product; its integer part gives j
+// (rounded to nearest) and the top 48 bits of its fraction F give r = F pi/1024, absolute error
+// below 3e-16 rad. Below 2^-10, r = phi; from 2^22 on, the FP64 Cody-Waite reduction.
+__device__ __forceinline__ int reduce_phase(double phi, float &xh, float &xl) {
+  const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(phi));
+  const int e = static_cast<int>((u >> 52) & 0x7ffull);
+  if (e < 1013) {  // |phi| < 2^-10 < pi/2048
+    split_df(phi, xh, xl);
+    return 0;
+  }
+  if (e > 1044) {  // |phi| >= 2^22
+    const double y = fma(phi, kInvStep, kMagic);
+    const double jd = y - kMagic;
+    split_df(fma(-jd, kC2, fma(-jd, kC1, phi)), xh, xl);
+    return __double2loint(y);
+  }
+  const unsigned long long m = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const int a = 1075 - e;  // 31 .. 62: the integer part starts at bit 64 + a of m K
+  const unsigned long long L = m * kKL;
+  const unsigned long long H = __umul64hi(m, kKL) + m * kKH;  // m K = H 2^64 + L, H < 2^62
+  const unsigned long long I = H >> a;
+  const unsigned long long Ff = (H << (64 - a)) | (L >> a);   // F in units of 2^-64
+  const long long fs = static_cast<long long>(Ff);            // F - 1 when F >= 1/2
+  int j = static_cast<int>(I + (Ff >> 63));
+  const float fa = __int2float_rn(static_cast<int>(fs >> 40)) * 5.9604644775390625e-8f;            // 2^-24
+  const float fb = __int2float_rn(static_cast<int>((fs >> 16) & 0xFFFFFF)) * 3.552713678800501e-15f;  // 2^-48
+  float p = __fmul_rn(fa, kChf);
+  float lo = __fadd_rn(__fmaf_rn(fa, kChf, -p), __fmaf_rn(fa, kClf, __fmul_rn(fb, kChf)));
+  if (u >> 63) {
+    p = -p;
+    lo = -lo;
+    j = -j;
+  }
+  xh = p;
+  xl = lo;
+  return j;
 }
 
 // s + t = a + b exactly (Knuth)
@@ -263,19 +308,8 @@ __global__ void __launch_bounds__(NW * 32, NW == 4 ? 3 : 1) k_df(const Params P)
 #pragma unroll
           for (int r = 0; r < R; ++r) {
             const double phi = __dmul_rn(ws[r], A);
-            const double y = fma(phi, kInvStep, kMagic);
-            const int j = __double2loint(y);
-            const double jd = y - kMagic;
-            const double r1 = fma(-jd, kC1, phi);  // phi - j C1, one rounding
             float xh, xl;
-            if ((__double2hiint(phi) & 0x7FF00000) < ((1023 + 22) << 20)) {  // |phi| < 2^22, by its bits
-              // second Cody-Waite step in FP32: |j C2| < 2^31 * 6.0e-20, so its FP32 product and
-              // the conversion of j are accurate to ~1e-17 rad
-              split_df(r1, xh, xl);
-              xl = __fmaf_rn(-__int2float_rn(j), kC2f, xl);
-            } else {
-              split_df(fma(-jd, kC2, r1), xh, xl);
-            }
+            const int j = reduce_phase(phi, xh, xl);
             const float4 t = tab[j & (kDfTabN - 1)];  // (C_hi, C_lo, S_hi, S_lo)
             const float x2 = __fmul_rn(xh, xh);
             const float x2e = __fmaf_rn(xh, xh, -x2);  // xh^2 = x2 + x2e exactly
