@@ -1,8 +1,8 @@
 """Parity of the FP64-accurate double-float form (RAD_FP64_DF) with the FP64 oracle, through the
 C ABI, at the FP64 tolerance:
   |S_gpu - S_ref| <= 1e-9 * max(S_ref, 1e-6 * peak) per bin (peak = max of the output).
-The phase product w* A_k(n) and its reduction are FP64 as in RAD_FP64; sin, cos, f and the tile
-sums run in float pairs with error-free products and sums.
+The phase product w* A_k(n) is FP64 as in RAD_FP64 and is reduced exactly with integer
+arithmetic; sin, cos, f and the tile sums run in float pairs with error-free products and sums.
 """
 import numpy as np
 import pytest
@@ -103,3 +103,15 @@ def test_df_full_grid_particle_of_the_ensemble():
         out = gpu_cube(tr, grid, mode, DF)["cube"]
         ref = O.spectrum_bins(tr, grid, omode, bi, bj).reshape(grid.n_omega, 64)
         print("df full grid max rel", mode, assert_fp64_close(out[:, js], ref))
+
+
+def test_phases_beyond_2_pow_22_rad():
+    """Half-millimetre trajectories seen up to 1 mrad off axis at hw up to 0.45 E: phases w* A
+    reach ~1e7 rad, beyond the integer reduction's range (2^22 rad), where the double-float kernel
+    takes the FP64 Cody-Waite reduction; it stays within the FP64 tolerance."""
+    tr = I.channeling(2, 10e9, +1, 20000, 25e-9, seed=31)
+    hw = I.omega_log(16, 1e-3 * 10e9, 0.45 * 10e9)
+    grid = I.make_grid(hw, 4, 4, 1.0e-3)
+    ref = O.spectrum_cube(tr, grid, O.SPIN_HALF)
+    got = gpu_cube(tr, grid, rad.RAD_SPIN_HALF, DF)["cube"]
+    print("df large phases max rel", assert_fp64_close(got, ref))
