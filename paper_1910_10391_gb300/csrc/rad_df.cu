@@ -1,6 +1,6 @@
 // FP64-accurate radiation-integral kernel that spends the FP64 pipe only where the result needs
 // it (sm_103a). GB300 executes FP64 at 1/64 of its FP32 rate, and the plain FP64 kernel
-// (rad_fp64.cu) spends about 20 FP64 instructions per term. Here a term costs one:
+// (rad_fp64.cu) spends about 20 FP64 instructions per term. Here a term costs one FP64 instruction:
 //   phi = w* A_k(n)                      one FP64 multiply: the same double as the oracle's phase
 //                                        (A_k(n) is formed in the oracle's IEEE order, FP64)
 //   phi = j 2 pi/2048 + r                the table index j and the reduced phase by a fixed-point
