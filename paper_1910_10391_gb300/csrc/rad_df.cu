@@ -302,6 +302,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 4 ? 3 : 1) k_df(const Params P)
         for (int r = 0; r < R; ++r)
 #pragma unroll
           for (int c = 0; c < NC; ++c) tS[r][c] = tC[r][c] = 0.f;
+#pragma unroll 2
         for (int k = 0; k < n; ++k) {
           const double A = myA[k];
           const float4 Fa = myFa[k], Fb = myFb[k];
