@@ -343,6 +343,7 @@ int rad_standardize(float *y, int64_t rows, int cols, const float *mean, const f
 #define RAD_TRAJ_LL 2      /* radiation-reaction drag (leading Landau-Lifshitz term)        */
 #define RAD_TRAJ_MS_LOSS 4 /* energy loss of each kick, m alpha/(2 pi) gamma^3 theta^2       */
 #define RAD_TRAJ_FP32 8    /* FP32 arithmetic with double-float state (else FP64 throughout)  */
+#define RAD_TRAJ_MS_EL 16  /* scattering on valence electrons too (rad_crystal_trajectories)  */
 
 /* Planar channel of the trajectory integrator: a harmonic well U(s) = U0 (2 s / d_p)^2 in the
  * distance s to the nearest channel centre (a stand-in for the planar continuum potential of
@@ -358,6 +359,31 @@ typedef struct {
   int charge_sign; /* +1: channel centres mid-way between planes; -1: centres on the planes */
   int flags;       /* RAD_TRAJ_* bits                                                        */
 } rad_channel;
+
+/* Thermally averaged Doyle-Turner continuum potential of a family of planes (Sec. III, Eq. plane)
+ * and the valence-electron density of the same planes (Sec. III). The fit coefficients are the
+ * caller's (the paper prints no tables). Planes sit at x = m d_p; a unit positive charge feels
+ *   U(x) = 2 sqrt(pi) e^2 a0 N d_p sum_planes sum_i a[i] / sqrt(C_i) exp(-r^2 / C_i),
+ *   C_i = b[i] / (4 pi^2) + rho^2 (rho of rad_channel), r = distance to the plane,
+ * summed over the 2 n_neighbours planes m0 - n_neighbours + 1 .. m0 + n_neighbours around the
+ * cell m0 = floor(x / d_p) that holds x. A particle of charge sign q feels q U. With
+ * RAD_TRAJ_MS_EL the electron density
+ *   n_el(x) = (N d_p / sqrt(pi)) sum_planes sum_i ax[i] / sqrt(CX_i) exp(-r^2 / CX_i)
+ *             + cx N n(x)/N,   CX_i = bx[i] / (4 pi^2) + rho^2,
+ * (n(x)/N the nuclear plane density of rad_channel's scattering model) sets a second kick
+ * variance per angle, (1/2) dt pi r0^2 / (gamma^2 beta^4) max(ln(2 m_e gamma^2 beta^2 / I) -
+ * beta^2, 0) n_el(x) (Sec. III, the paper's electron term with its factor 2 removed). */
+typedef struct {
+  int n_terms;      /* Gaussian terms of each fit, 1 .. 8 (the paper's fits have 4)              */
+  int n_neighbours; /* planes summed on each side of the particle's cell, 1 .. 8                */
+  double N;         /* atom density, m^-3 (> 0)                                                 */
+  double a[8];      /* potential fit a_i, m (finite)                                            */
+  double b[8];      /* potential fit b_i, m^2 (C_i must be > 0)                                 */
+  double ax[8];     /* X-ray fit a_i^(X), electrons (finite; used with RAD_TRAJ_MS_EL)          */
+  double bx[8];     /* X-ray fit b_i^(X), m^2 (CX_i > 0 with RAD_TRAJ_MS_EL)                    */
+  double cx;        /* X-ray constant c^(X), electrons at the nucleus (finite)                  */
+  double I_eV;      /* mean ionisation energy of the target, eV (> 0 with RAD_TRAJ_MS_EL)        */
+} rad_planar_potential;
 
 /*
  * rad_channeling_trajectories -- integrates n_particles trajectories in the channel `ch` and
@@ -396,6 +422,21 @@ int rad_channeling_trajectories(const rad_channel *ch, int64_t n_particles, cons
                                 int64_t n_samples_total, const double *energy_eV, const double *x0,
                                 const double *thx0, const double *thy0, const int64_t *particle_ids,
                                 double dt, uint64_t seed, double *out, double *energy_out, void *stream);
+
+/*
+ * rad_crystal_trajectories -- rad_channeling_trajectories in the Doyle-Turner planar potential
+ * `pot` (host struct, read during the call) instead of the harmonic well: F = -q dU/dx with U
+ * above, q = ch->charge_sign (U0_eV is ignored). Every other argument, the records, the random
+ * streams and both precisions are those of rad_channeling_trajectories. Flags may add
+ * RAD_TRAJ_MS_EL (needs RAD_TRAJ_MS). Host checks (null ch or pot, n_terms or n_neighbours out of
+ * range, N <= 0, a non-finite coefficient, C_i <= 0, with RAD_TRAJ_MS_EL CX_i <= 0 or I_eV <= 0,
+ * and the checks of rad_channeling_trajectories) return RAD_EINVAL before anything is enqueued.
+ */
+int rad_crystal_trajectories(const rad_channel *ch, const rad_planar_potential *pot, int64_t n_particles,
+                             const int64_t *offsets, int64_t n_samples_total, const double *energy_eV,
+                             const double *x0, const double *thx0, const double *thy0,
+                             const int64_t *particle_ids, double dt, uint64_t seed, double *out,
+                             double *energy_out, void *stream);
 
 /*
  * rad_device_status -- waits for the current device to finish, returns the first

@@ -29,9 +29,28 @@ continuum potential, whose Doyle-Turner tables the paper does not print):
 Records (the radiation integral's input, Sec. II variables): t = k dt, x, y, dz, v_x, v_y,
 dvz = v_z - beta0, a_x = F/E + kick, a_y = kick, a_z = (dgamma/dt / gamma^3 - v_perp.a_perp)/v_z.
 
+With a Doyle-Turner planar potential (`PlanarPotential`, Sec. III, Eq. plane) the harmonic
+well is replaced by the thermally averaged continuum potential of the planes at x = m d_p,
+  U(x) = 2 sqrt(pi) e^2 a0 N d_p sum_planes sum_i a_i / sqrt(C_i) exp(-r^2 / C_i),
+  C_i = b_i / (4 pi^2) + rho^2, r = distance to the plane,
+for a unit positive charge (a particle of charge sign q feels q U, force -q dU/dx), summed over
+the 2K planes m0-K+1 .. m0+K around the cell m0 = floor(x/d_p) that holds x. The fit
+coefficients are the caller's (the paper prints no tables). With scattering on valence electrons
+(Sec. III, Eq. elscat) each angle's kick variance gains
+  (1/2) dt pi r0^2 / (gamma^2 beta^4) max(ln(2 m_e gamma^2 beta^2 / I) - beta^2, 0) n_el(x),
+  n_el(x) = (N d_p / sqrt(pi)) sum_planes sum_i a_i^X / sqrt(C_i^X) exp(-r^2 / C_i^X)
+            + c^X N n(x)/N,   C_i^X = b_i^X / (4 pi^2) + rho^2
+(the prefactor N d_p / sqrt(pi) is the reading under which a plane holds N d_p (sum a^X + c^X)
+electrons per unit area, as the X-ray factors' normalisation requires; the paper prints d_p/pi).
+
 Pinned in tests/test_traj_oracle.py: Philox published vectors, the closed-form harmonic
 solution and its dz, transverse-energy conservation, the Larmor integral of the energy loss,
-the per-kick scattering loss, kick statistics, and agreement with the input generator.
+the per-kick scattering loss, kick statistics, and agreement with the input generator. The
+planar potential is pinned in tests/test_potential_oracle.py by its Fourier series (Poisson
+summation), the thermal smearing as a Gaussian convolution, mirror symmetry, the electron count
+per plane, transverse-energy conservation and the small-oscillation frequency. The electron-
+scattering rate's prefactor (pi r0^2 and the logarithm) is parity unpinned: no closed form or
+printed value fixes it independently of the formula itself.
 """
 from __future__ import annotations
 
@@ -41,6 +60,10 @@ import numpy as np
 
 ALPHA = 7.2973525693e-3
 HBARC_EV_M = 1.973269804e-7
+E2_EV_M = ALPHA * HBARC_EV_M      # e^2 (Gaussian units) in eV m
+A0_M = 5.29177210903e-11          # Bohr radius, m
+R0_M = 2.8179403262e-15           # classical electron radius, m
+ME_EV = 0.51099895e6              # electron rest energy, eV (target electrons)
 
 _M0, _M1 = np.uint64(0xD2511F53), np.uint64(0xCD9E8D57)
 _W0, _W1 = np.uint32(0x9E3779B9), np.uint32(0xBB67AE85)
@@ -89,6 +112,60 @@ def force(x, U0_eV, d_p, charge):
     return -8.0 * U0_eV * s / (d_p * d_p)
 
 
+class PlanarPotential:
+    """Doyle-Turner fit of one plane (Sec. III): electron-scattering terms a [m], b [m^2] of the
+    potential; X-ray terms ax [electrons], bx [m^2] and cx of the electron density; atom density
+    N [m^-3]; mean ionisation energy I_eV; K neighbouring planes on each side of the cell."""
+
+    def __init__(self, a, b, N, ax=(), bx=(), cx=0.0, I_eV=0.0, K=3):
+        self.a, self.b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+        self.ax, self.bx = np.asarray(ax, np.float64), np.asarray(bx, np.float64)
+        self.N, self.cx, self.I_eV, self.K = float(N), float(cx), float(I_eV), int(K)
+
+
+def _plane_distances(x, d_p, K):
+    """r[..., j] = x - (m0 + j) d_p for j = -K+1 .. K, m0 = floor(x / d_p)."""
+    x = np.asarray(x, dtype=np.float64)
+    m0 = np.floor(x / d_p)
+    j = np.arange(-K + 1, K + 1, dtype=np.float64)
+    return x[..., None] - (m0[..., None] + j) * d_p
+
+
+def planar_potential(x, pot, d_p, rho):
+    """U(x) in eV for a unit positive charge: Eq. plane summed over the 2K nearest planes."""
+    C = pot.b / (4.0 * math.pi ** 2) + rho * rho
+    r2 = _plane_distances(x, d_p, pot.K)[..., None] ** 2
+    P = 2.0 * math.sqrt(math.pi) * E2_EV_M * A0_M * pot.N * d_p
+    return P * (pot.a / np.sqrt(C) * np.exp(-r2 / C)).sum((-1, -2))
+
+
+def planar_force(x, pot, d_p, rho, charge):
+    """Transverse force -charge dU/dx (eV/m) of the planar potential."""
+    C = pot.b / (4.0 * math.pi ** 2) + rho * rho
+    r = _plane_distances(x, d_p, pot.K)[..., None]
+    P = 2.0 * math.sqrt(math.pi) * E2_EV_M * A0_M * pot.N * d_p
+    # d/dr of exp(-r^2/C) is -(2 r / C) exp(-r^2/C)
+    return charge * P * (pot.a / np.sqrt(C) * (2.0 * r / C) * np.exp(-r * r / C)).sum((-1, -2))
+
+
+def electron_density(x, pot, d_p, rho):
+    """n_el(x) in m^-3: the X-ray Gaussians of the 2K nearest planes plus c^X times the nuclear
+    density (Sec. III)."""
+    CX = pot.bx / (4.0 * math.pi ** 2) + rho * rho
+    r2 = _plane_distances(x, d_p, pot.K)[..., None] ** 2
+    valence = pot.N * d_p / math.sqrt(math.pi) * (pot.ax / np.sqrt(CX) * np.exp(-r2 / CX)).sum((-1, -2))
+    return valence + pot.cx * pot.N * plane_density(x, d_p, rho)
+
+
+def electron_scattering_rate(gamma, n_el, I_eV):
+    """Mean squared scattering angle per unit length on electrons, Sec. III Eq. elscat (with the
+    paper's factor 2 removed), clamped at 0 where the logarithm's bracket would be negative."""
+    gamma = np.asarray(gamma, dtype=np.float64)
+    b2 = 1.0 - 1.0 / (gamma * gamma)
+    bracket = np.maximum(np.log(2.0 * ME_EV * gamma * gamma * b2 / I_eV) - b2, 0.0)
+    return math.pi * R0_M ** 2 / (gamma * gamma * b2 * b2) * bracket * n_el
+
+
 def plane_density(x, d_p, rho):
     """n(x)/N: Gaussian plane density (thermal amplitude rho) summed over the two nearest planes."""
     m = np.floor(x / d_p)
@@ -98,10 +175,19 @@ def plane_density(x, d_p, rho):
 
 def trajectories(x0, thx0, thy0, E0_eV, n_samples: int, dt: float, seed: int, *, charge=+1,
                  U0_eV=20.0, d_p=1.92e-10, eps_s_eV=10.6e6, X0=0.0937, rho=0.075e-10, ms=True,
-                 ll=False, ms_loss=False, mass_eV=0.51099895e6, particle_ids=None, energies=False):
+                 ll=False, ms_loss=False, mass_eV=0.51099895e6, particle_ids=None, energies=False,
+                 pot=None, ms_el=False):
     """Records [n][n_samples][10] of n particles with entry (x0, thx0, thy0) and energy E0
     (scalar or per particle); particle_ids index the random streams (default 0..n-1).
-    With energies=True also returns the energy at every sample [n][n_samples]."""
+    With energies=True also returns the energy at every sample [n][n_samples]. A PlanarPotential
+    `pot` replaces the harmonic well (U0_eV unused); ms_el adds scattering on valence electrons
+    to the kicks (needs pot and ms)."""
+    if ms_el and (pot is None or not ms):
+        raise ValueError("electron scattering needs a planar potential and ms")
+
+    def field(x):
+        return force(x, U0_eV, d_p, charge) if pot is None else planar_force(x, pot, d_p, rho, charge)
+
     x0 = np.asarray(x0, dtype=np.float64)
     n = x0.shape[0]
     pid = np.arange(n, dtype=np.uint64) if particle_ids is None else np.asarray(particle_ids, dtype=np.uint64)
@@ -125,7 +211,7 @@ def trajectories(x0, thx0, thy0, E0_eV, n_samples: int, dt: float, seed: int, *,
         g = st[:, 5] / mass_eV
         vp2 = st[:, 2] ** 2 + st[:, 3] ** 2
         vz = np.sqrt(1.0 - 1.0 / (g * g) - vp2)
-        F = force(st[:, 0], U0_eV, d_p, charge)
+        F = field(st[:, 0])
         d = np.empty_like(st)
         d[:, 0] = st[:, 2]
         d[:, 1] = st[:, 3]
@@ -142,7 +228,7 @@ def trajectories(x0, thx0, thy0, E0_eV, n_samples: int, dt: float, seed: int, *,
         g = s[:, 5] / mass_eV
         vp2 = s[:, 2] ** 2 + s[:, 3] ** 2
         vz = np.sqrt(1.0 - 1.0 / (g * g) - vp2)
-        F = force(s[:, 0], U0_eV, d_p, charge)
+        F = field(s[:, 0])
         ax = F / s[:, 5] + kick[:, 0]
         ay = kick[:, 1]
         gd = gamma_dot(F, s[:, 5]) if ll else np.zeros(n)
@@ -169,6 +255,9 @@ def trajectories(x0, thx0, thy0, E0_eV, n_samples: int, dt: float, seed: int, *,
         if ms:
             E = s[:, 5]
             var = 0.5 * (eps_s_eV / E) ** 2 * (dt / X0) * plane_density(s[:, 0], d_p, rho)
+            if ms_el:
+                var = var + 0.5 * dt * electron_scattering_rate(
+                    E / mass_eV, electron_density(s[:, 0], pot, d_p, rho), pot.I_eV)
             z0, z1 = kick_normals(seed, pid, k)
             dthx, dthy = np.sqrt(var) * z0, np.sqrt(var) * z1
             kick[:, 0], kick[:, 1] = dthx / dt, dthy / dt

@@ -21,7 +21,7 @@ RAD_OK, RAD_EINVAL, RAD_ENOMEM, RAD_ECUDA, RAD_ETIMEOUT, RAD_EUNSUPPORTED, RAD_E
 RAD_CLASSICAL, RAD_SPIN0, RAD_SPIN_HALF = 0, 1, 2
 RAD_FP64, RAD_MIXED, RAD_FP64_DF = 0, 1, 2
 RAD_NREC = 10
-RAD_TRAJ_MS, RAD_TRAJ_LL, RAD_TRAJ_MS_LOSS, RAD_TRAJ_FP32 = 1, 2, 4, 8
+RAD_TRAJ_MS, RAD_TRAJ_LL, RAD_TRAJ_MS_LOSS, RAD_TRAJ_FP32, RAD_TRAJ_MS_EL = 1, 2, 4, 8, 16
 
 
 class RadChannel(ctypes.Structure):
@@ -29,6 +29,20 @@ class RadChannel(ctypes.Structure):
     _fields_ = [("U0_eV", ctypes.c_double), ("d_p", ctypes.c_double), ("eps_s_eV", ctypes.c_double),
                 ("X0", ctypes.c_double), ("rho", ctypes.c_double), ("mass_eV", ctypes.c_double),
                 ("charge_sign", ctypes.c_int), ("flags", ctypes.c_int)]
+
+
+class RadPlanarPotential(ctypes.Structure):
+    """rad_planar_potential: Doyle-Turner planar fit (potential and X-ray terms) of the crystal."""
+    _fields_ = [("n_terms", ctypes.c_int), ("n_neighbours", ctypes.c_int), ("N", ctypes.c_double),
+                ("a", ctypes.c_double * 8), ("b", ctypes.c_double * 8), ("ax", ctypes.c_double * 8),
+                ("bx", ctypes.c_double * 8), ("cx", ctypes.c_double), ("I_eV", ctypes.c_double)]
+
+    @classmethod
+    def make(cls, a, b, N, ax=(), bx=(), cx=0.0, I_eV=0.0, n_neighbours=3):
+        if len(a) != len(b) or (len(ax) and len(ax) != len(a)) or len(ax) != len(bx) or not 1 <= len(a) <= 8:
+            raise ValueError("a, b (and ax, bx) must have the same length, 1..8")
+        pad = lambda v: (ctypes.c_double * 8)(*(list(map(float, v)) + [0.0] * (8 - len(v))))
+        return cls(len(a), int(n_neighbours), float(N), pad(a), pad(b), pad(ax), pad(bx), float(cx), float(I_eV))
 MODES = {"classical": RAD_CLASSICAL, "spin0": RAD_SPIN0, "spin_half": RAD_SPIN_HALF}
 PRECISIONS = {"fp64": RAD_FP64, "mixed": RAD_MIXED, "fp64_df": RAD_FP64_DF}
 
@@ -82,6 +96,9 @@ def load(build_if_missing: bool = True):
         lib.rad_channeling_trajectories.argtypes = [ctypes.POINTER(RadChannel), i64, P, i64, P, P, P, P, P,
                                                     ctypes.c_double, u64, P, P, P]
         lib.rad_channeling_trajectories.restype = c_int
+        lib.rad_crystal_trajectories.argtypes = [ctypes.POINTER(RadChannel), ctypes.POINTER(RadPlanarPotential), i64,
+                                                 P, i64, P, P, P, P, P, ctypes.c_double, u64, P, P, P]
+        lib.rad_crystal_trajectories.restype = c_int
         lib.rad_mlp_create.argtypes = [c_int, c_int, c_int, c_int, i64, u64, ctypes.POINTER(P)]
         lib.rad_mlp_create.restype = c_int
         lib.rad_mlp_destroy.argtypes = [P]
@@ -277,6 +294,20 @@ def rad_channeling_trajectories(channel, offsets, energy_eV, x0, thx0, out, dt, 
         _dev_ptr(energy_eV, f64, "energy_eV"), _dev_ptr(x0, f64, "x0"), _dev_ptr(thx0, f64, "thx0"),
         _dev_ptr(thy0, f64, "thy0"), _dev_ptr(particle_ids, torch.int64, "particle_ids"), float(dt), int(seed),
         _dev_ptr(out, f64, "out"), _dev_ptr(energy_out, f64, "energy_out"), _stream(stream))
+
+
+def rad_crystal_trajectories(channel, potential, offsets, energy_eV, x0, thx0, out, dt, seed, thy0=None,
+                             particle_ids=None, energy_out=None, stream=None) -> int:
+    """rad_channeling_trajectories in the Doyle-Turner planar potential `potential`
+    (RadPlanarPotential, or None to see the library reject it)."""
+    import torch
+    f64 = torch.float64
+    return load().rad_crystal_trajectories(
+        ctypes.byref(channel), ctypes.byref(potential) if potential is not None else None, _numel(offsets) - 1,
+        _dev_ptr(offsets, torch.int64, "offsets"), _numel(out) // RAD_NREC, _dev_ptr(energy_eV, f64, "energy_eV"),
+        _dev_ptr(x0, f64, "x0"), _dev_ptr(thx0, f64, "thx0"), _dev_ptr(thy0, f64, "thy0"),
+        _dev_ptr(particle_ids, torch.int64, "particle_ids"), float(dt), int(seed), _dev_ptr(out, f64, "out"),
+        _dev_ptr(energy_out, f64, "energy_out"), _stream(stream))
 
 
 class MLP:

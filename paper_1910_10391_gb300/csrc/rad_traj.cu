@@ -13,6 +13,13 @@
 //   with variance (1/2)(eps_s/E)^2 (dt/X0) n(x)/N, n(x)/N the Gaussian plane density of the
 //   two nearest planes; the next sample's acceleration carries the kick as delta_v/dt; with
 //   scattering loss each kick costs m alpha/(2 pi) gamma^3 theta^2.
+// Doyle-Turner form (rad_crystal_trajectories): the harmonic well is replaced by the thermally
+// averaged continuum potential of the planes at x = m d_p (Sec. III, Eq. plane), summed over the
+// 2K planes around the particle's cell: F = sum_planes sum_i fk_i r exp(-r^2 / C_i) with
+// fk_i = 2 q (2 sqrt(pi) e^2 a0 N d_p) a_i / C_i^(3/2), C_i = b_i/(4 pi^2) + rho^2; with electron
+// scattering the kick variance gains (1/2) dt pi r0^2 / (gamma^2 beta^4) [ln(2 m_e gamma^2
+// beta^2 / I) - beta^2]_+ n_el(x) (Sec. III), n_el from the X-ray Gaussians of the same planes
+// plus c^X times the nuclear density.
 // Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) with counter
 // (particle low, step, 1, particle high) and key (seed low, seed high); two 53-bit uniforms
 // per block and Box-Muller normals.
@@ -28,6 +35,19 @@ namespace {
 struct Chan {
   double U0, d_p, eps_s, X0, rho, mass, centre, inv_d, force_k, dens_pref, inv_rho2, var_k, loss_k, ll_k;
   int ms, ll, ms_loss;
+};
+
+constexpr int kMaxTerms = 8;
+constexpr double kR0 = 2.8179403262e-15;  // classical electron radius, m (CODATA 2018)
+constexpr double kMe = 0.51099895e6;      // electron rest energy, eV (target electrons)
+constexpr double kA0 = 5.29177210903e-11; // Bohr radius, m (CODATA 2018)
+
+// Doyle-Turner planar potential, FP64 form. Force terms fk[i] r exp(-r^2 ck[i]); electron-
+// density terms ek[i] exp(-r^2 eck[i]) and ecx n(x)/N, all pre-multiplied by (1/2) dt pi r0^2.
+struct Planar {
+  int nt, K, el;
+  double fk[kMaxTerms], ck[kMaxTerms], ek[kMaxTerms], eck[kMaxTerms];
+  double ecx, lk;  // lk = 2 m_e / I
 };
 
 // ---------------- Philox4x32-10 ----------------
@@ -75,6 +95,36 @@ __device__ __forceinline__ double plane_density(const Chan &C, double x) {
   return C.dens_pref * (exp(-(r1 * r1) * C.inv_rho2) + exp(-(r2 * r2) * C.inv_rho2));
 }
 
+// position within its cell, xi = x - floor(x/d_p) d_p; plane j of the 2K is at distance xi - j d_p
+__device__ __forceinline__ double planar_force(const Chan &C, const Planar &P, double x) {
+  const double xi = x - floor(x * C.inv_d) * C.d_p;
+  double F = 0.0;
+  for (int j = 1 - P.K; j <= P.K; ++j) {
+    const double r = xi - j * C.d_p, r2 = r * r;
+    double g = 0.0;
+    for (int i = 0; i < P.nt; ++i) g += P.fk[i] * exp(-r2 * P.ck[i]);
+    F += r * g;
+  }
+  return F;
+}
+
+// (1/2) dt pi r0^2 n_el(x): the X-ray Gaussians of the 2K planes plus c^X N n(x)/N
+__device__ __forceinline__ double electron_density_scaled(const Chan &C, const Planar &P, double x, double n_nuc) {
+  const double xi = x - floor(x * C.inv_d) * C.d_p;
+  double n = P.ecx * n_nuc;
+  for (int j = 1 - P.K; j <= P.K; ++j) {
+    const double r = xi - j * C.d_p, r2 = r * r;
+    for (int i = 0; i < P.nt; ++i) n += P.ek[i] * exp(-r2 * P.eck[i]);
+  }
+  return n;
+}
+
+template <bool DT>
+__device__ __forceinline__ double field(const Chan &C, const Planar &P, double x) {
+  if constexpr (DT) return planar_force(C, P, x);
+  else return force(C, x);
+}
+
 // v_z - beta0 without cancellation: ((1/g0^2 - 1/g^2) - vp2 - 1/(4 g0^4)) / (v_z + beta0)
 __device__ __forceinline__ double dvz_of(double g, double g0, double q0, double beta0, double vp2, double &vz) {
   vz = sqrt(1.0 - 1.0 / (g * g) - vp2);
@@ -86,12 +136,14 @@ struct State {
   double x, y, vx, vy, dz, E;
 };
 
-__device__ __forceinline__ State deriv(const Chan &C, double g0, double q0, double beta0, const State &s) {
+template <bool DT>
+__device__ __forceinline__ State deriv(const Chan &C, const Planar &P, double g0, double q0, double beta0,
+                                       const State &s) {
   const double g = s.E / C.mass;
   const double vp2 = s.vx * s.vx + s.vy * s.vy;
   double vz;
   const double dvz = dvz_of(g, g0, q0, beta0, vp2, vz);
-  const double F = force(C, s.x);
+  const double F = field<DT>(C, P, s.x);
   State d;
   d.x = s.vx;
   d.y = s.vy;
@@ -106,7 +158,8 @@ __device__ __forceinline__ State axpy(const State &s, double h, const State &d) 
   return State{s.x + h * d.x, s.y + h * d.y, s.vx + h * d.vx, s.vy + h * d.vy, s.dz + h * d.dz, s.E + h * d.E};
 }
 
-__global__ void k_channel(const Chan C, int64_t n_particles, const int64_t *__restrict__ offsets,
+template <bool DT>
+__global__ void k_channel(const Chan C, const Planar P, int64_t n_particles, const int64_t *__restrict__ offsets,
                           int64_t n_total, const double *__restrict__ energy, const double *__restrict__ x0,
                           const double *__restrict__ thx0, const double *__restrict__ thy0,
                           const int64_t *__restrict__ ids, double dt, uint64_t seed, double *__restrict__ out,
@@ -133,7 +186,7 @@ __global__ void k_channel(const Chan C, int64_t n_particles, const int64_t *__re
       const double vp2 = s.vx * s.vx + s.vy * s.vy;
       double vz;
       const double dvz = dvz_of(g, g0, q0, beta0, vp2, vz);
-      const double F = force(C, s.x);
+      const double F = field<DT>(C, P, s.x);
       const double ax = F / s.E + kx, ay = ky;
       const double gdot = C.ll ? C.ll_k * (g * g) * (F * F) / C.mass : 0.0;
       rec[F_T] = static_cast<double>(k) * dt;
@@ -150,10 +203,10 @@ __global__ void k_channel(const Chan C, int64_t n_particles, const int64_t *__re
       kx = ky = 0.0;
       if (k == L - 1) break;
       // RK4 step
-      const State k1 = deriv(C, g0, q0, beta0, s);
-      const State k2 = deriv(C, g0, q0, beta0, axpy(s, 0.5 * dt, k1));
-      const State k3 = deriv(C, g0, q0, beta0, axpy(s, 0.5 * dt, k2));
-      const State k4 = deriv(C, g0, q0, beta0, axpy(s, dt, k3));
+      const State k1 = deriv<DT>(C, P, g0, q0, beta0, s);
+      const State k2 = deriv<DT>(C, P, g0, q0, beta0, axpy(s, 0.5 * dt, k1));
+      const State k3 = deriv<DT>(C, P, g0, q0, beta0, axpy(s, 0.5 * dt, k2));
+      const State k4 = deriv<DT>(C, P, g0, q0, beta0, axpy(s, dt, k3));
       const double h6 = dt / 6.0;
       s.x += h6 * (k1.x + 2.0 * k2.x + 2.0 * k3.x + k4.x);
       s.y += h6 * (k1.y + 2.0 * k2.y + 2.0 * k3.y + k4.y);
@@ -163,7 +216,13 @@ __global__ void k_channel(const Chan C, int64_t n_particles, const int64_t *__re
       s.E += h6 * (k1.E + 2.0 * k2.E + 2.0 * k3.E + k4.E);
       if (C.ms) {
         const double E = s.E;
-        const double var = C.var_k / (E * E) * plane_density(C, s.x);
+        const double n_nuc = plane_density(C, s.x);
+        double var = C.var_k / (E * E) * n_nuc;
+        if (DT && P.el) {
+          const double g = E / C.mass, b2 = 1.0 - 1.0 / (g * g);
+          const double br = fmax(log(P.lk * (g * g) * b2) - b2, 0.0);
+          var += electron_density_scaled(C, P, s.x, n_nuc) * (br / ((g * g) * (b2 * b2)));
+        }
         double z0, z1;
         kick_normals(seed, pid, static_cast<uint64_t>(k), z0, z1);
         const double sd = sqrt(var);
@@ -196,6 +255,13 @@ struct Chan32 {
       var_k, inv_mass;
   double d_p, centre, dt, mass;
   int ms, ll, ms_loss;
+};
+
+// Doyle-Turner planar potential, FP32 form: the exponentials as exp2f with -1/(C ln 2) factors.
+struct Planar32 {
+  int nt, K, el;
+  float fk[kMaxTerms], ck2[kMaxTerms], ek[kMaxTerms], eck2[kMaxTerms];
+  float ecx, lk;
 };
 
 struct DF {
@@ -233,16 +299,62 @@ struct D32 {
   float vx, vy, a, dvz, dE;
 };
 
+// Planes relative to the channel centre, from the offset sw in [-d/2, d/2): the 2K planes of the
+// cell that holds the particle, as in the FP64 form (positron channels are cells, with planes at
+// (j - 1/2) d; an electron channel centre is a plane, and the cell is the one on sw's side).
+// The nearest plane's distance sw - p is exact (Sterbenz), so the core of the plane is resolved
+// to FP32 precision of the distance itself.
+__device__ __forceinline__ void plane_frame(const Chan32 &C, const Planar32 &P, float sw, int &jlo, float &jofs) {
+  if (C.centre != 0.0) {
+    jlo = 1 - P.K;
+    jofs = -0.5f;
+  } else {
+    jlo = sw >= 0.f ? 1 - P.K : -P.K;
+    jofs = 0.f;
+  }
+}
+
+__device__ __forceinline__ float planar_force32(const Chan32 &C, const Planar32 &P, float sw) {
+  int jlo;
+  float jofs;
+  plane_frame(C, P, sw, jlo, jofs);
+  float F = 0.f;
+  for (int j = jlo; j < jlo + 2 * P.K; ++j) {
+    const float r = sw - (static_cast<float>(j) + jofs) * C.d_f, r2 = r * r;
+    float g = 0.f;
+    for (int i = 0; i < P.nt; ++i) g = __fmaf_rn(P.fk[i], exp2f(r2 * P.ck2[i]), g);
+    F = __fmaf_rn(r, g, F);
+  }
+  return F;
+}
+
+// (1/2) dt pi r0^2 n_el at offset sw, with n_nuc = n(x)/N
+__device__ __forceinline__ float electron_density32(const Chan32 &C, const Planar32 &P, float sw, float n_nuc) {
+  int jlo;
+  float jofs;
+  plane_frame(C, P, sw, jlo, jofs);
+  float n = P.ecx * n_nuc;
+  for (int j = jlo; j < jlo + 2 * P.K; ++j) {
+    const float r = sw - (static_cast<float>(j) + jofs) * C.d_f, r2 = r * r;
+    for (int i = 0; i < P.nt; ++i) n = __fmaf_rn(P.ek[i], exp2f(r2 * P.eck2[i]), n);
+  }
+  return n;
+}
+
 // stage derivative at offset s (any value; wrapped into the channel), velocity (vx, vy), energy
 // offset dEoff from the entry energy E0 (for 1/gamma0^2 - 1/gamma^2), reciprocal of the step's
 // energy (iE_hi, iE_lo) and the stage's energy change within the step dEs (radiation reaction:
 // 1/(E + dEs) = (1/E)(1 - dEs/E) to first order, dEs/E ~ 1e-7)
-__device__ __forceinline__ D32 deriv32(const Chan32 &C, float s, float vx, float vy, float dEoff, float dEs,
-                                       float g, float g0, float q0, float iE_hi, float iE_lo) {
+template <bool DT>
+__device__ __forceinline__ D32 deriv32(const Chan32 &C, const Planar32 &P, float s, float vx, float vy,
+                                       float dEoff, float dEs, float g, float g0, float q0, float iE_hi,
+                                       float iE_lo) {
   float sw = s;
   if (sw >= C.half_d) sw -= C.d_f;
   else if (sw < -C.half_d) sw += C.d_f;
-  const float F = -__fmaf_rn(C.kf_hi, sw, C.kf_lo * sw);  // -8 U0 s / d_p^2, eV/m
+  float F;
+  if constexpr (DT) F = planar_force32(C, P, sw);
+  else F = -__fmaf_rn(C.kf_hi, sw, C.kf_lo * sw);  // -8 U0 s / d_p^2, eV/m
   D32 d;
   d.vx = vx;
   d.vy = vy;
@@ -258,7 +370,8 @@ __device__ __forceinline__ D32 deriv32(const Chan32 &C, float s, float vx, float
   return d;
 }
 
-__global__ void k_channel_mixed(const Chan32 C, int64_t n_particles, const int64_t *__restrict__ offsets,
+template <bool DT>
+__global__ void k_channel_mixed(const Chan32 C, const Planar32 P, int64_t n_particles, const int64_t *__restrict__ offsets,
                                 int64_t n_total, const double *__restrict__ energy, const double *__restrict__ x0,
                                 const double *__restrict__ thx0, const double *__restrict__ thy0,
                                 const int64_t *__restrict__ ids, uint64_t seed, double *__restrict__ out,
@@ -294,7 +407,7 @@ __global__ void k_channel_mixed(const Chan32 C, int64_t n_particles, const int64
       const float res = __fmaf_rn(-E.lo, r, __fmaf_rn(-E.hi, r, 1.0f));
       const float iE_hi = r, iE_lo = res * r;
       // record k
-      const D32 d0 = deriv32(C, s.hi + s.lo, vx.hi, vy.hi, dEoff, 0.f, g, g0, q0, iE_hi, iE_lo);
+      const D32 d0 = deriv32<DT>(C, P, s.hi + s.lo, vx.hi, vy.hi, dEoff, 0.f, g, g0, q0, iE_hi, iE_lo);
       const float ax = d0.a + kx, ay = ky;
       const float gdot = C.ll ? d0.dE * C.inv_mass : 0.f;
       rec[F_T] = static_cast<double>(k) * C.dt;
@@ -314,11 +427,11 @@ __global__ void k_channel_mixed(const Chan32 C, int64_t n_particles, const int64
       // RK4 stages in FP32 around the double-float state
       const float h2 = C.h_half, h = C.dt_hi;
       const D32 k1 = d0;
-      const D32 k2 = deriv32(C, s.hi + (s.lo + h2 * k1.vx), vx.hi + (vx.lo + h2 * k1.a), vy.hi + vy.lo,
+      const D32 k2 = deriv32<DT>(C, P, s.hi + (s.lo + h2 * k1.vx), vx.hi + (vx.lo + h2 * k1.a), vy.hi + vy.lo,
                              dEoff + h2 * k1.dE, h2 * k1.dE, g, g0, q0, iE_hi, iE_lo);
-      const D32 k3 = deriv32(C, s.hi + (s.lo + h2 * k2.vx), vx.hi + (vx.lo + h2 * k2.a), vy.hi + vy.lo,
+      const D32 k3 = deriv32<DT>(C, P, s.hi + (s.lo + h2 * k2.vx), vx.hi + (vx.lo + h2 * k2.a), vy.hi + vy.lo,
                              dEoff + h2 * k2.dE, h2 * k2.dE, g, g0, q0, iE_hi, iE_lo);
-      const D32 k4 = deriv32(C, s.hi + (s.lo + h * k3.vx), vx.hi + (vx.lo + h * k3.a), vy.hi + vy.lo,
+      const D32 k4 = deriv32<DT>(C, P, s.hi + (s.lo + h * k3.vx), vx.hi + (vx.lo + h * k3.a), vy.hi + vy.lo,
                              dEoff + h * k3.dE, h * k3.dE, g, g0, q0, iE_hi, iE_lo);
       // x' = v is linear in the stages: sum/6 = v + h (a1 + a2 + a3)/6. Every factor that
       // multiplies all steps alike (dt, dt/6) is a double-float pair: an FP32-rounded constant
@@ -358,7 +471,12 @@ __global__ void k_channel_mixed(const Chan32 C, int64_t n_particles, const int64
           r2 = C.d_f - r1;
         }
         const float n = C.dens_pref * (exp2f(C.nexp2_rho * r1 * r1) + exp2f(C.nexp2_rho * r2 * r2));
-        const float var = (C.var_k * n) / (E.hi * E.hi);
+        float var = (C.var_k * n) / (E.hi * E.hi);
+        if (DT && P.el) {
+          const float gk = E.hi * C.inv_mass, b2 = 1.f - 1.f / (gk * gk);
+          const float br = fmaxf(logf(P.lk * (gk * gk) * b2) - b2, 0.f);
+          var = __fmaf_rn(electron_density32(C, P, sc, n), br / ((gk * gk) * (b2 * b2)), var);
+        }
         if (var > 0.f) {
           uint32_t c[4] = {static_cast<uint32_t>(pid), static_cast<uint32_t>(k), 1u, static_cast<uint32_t>(pid >> 32)};
           philox(c, static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32));
@@ -389,19 +507,66 @@ __global__ void k_channel_mixed(const Chan32 C, int64_t n_particles, const int64
 }  // namespace
 }  // namespace rad
 
-extern "C" int rad_channeling_trajectories(const rad_channel *ch, int64_t n_particles, const int64_t *offsets,
-                                           int64_t n_samples_total, const double *energy_eV, const double *x0,
-                                           const double *thx0, const double *thy0, const int64_t *particle_ids,
-                                           double dt, uint64_t seed, double *out, double *energy_out,
-                                           void *stream) {
-  using namespace rad;
+namespace rad {
+namespace {
+
+// Host checks of the planar potential; fills the FP64 and FP32 coefficient sets.
+int make_planar(const rad_channel *ch, const rad_planar_potential *pot, double dt, Planar &P, Planar32 &P32) {
+  P = Planar{};
+  P32 = Planar32{};
+  if (!pot) return RAD_OK;
+  const bool el = (ch->flags & RAD_TRAJ_MS_EL) != 0;
+  if (pot->n_terms < 1 || pot->n_terms > kMaxTerms || pot->n_neighbours < 1 || pot->n_neighbours > 8 ||
+      !(pot->N > 0.0) || !isfinite(pot->N) || !isfinite(pot->cx) || !(ch->rho >= 0.0) || !isfinite(ch->rho))
+    return RAD_EINVAL;
+  if (el && !(pot->I_eV > 0.0 && isfinite(pot->I_eV))) return RAD_EINVAL;
+  const double rho2 = ch->rho * ch->rho;
+  // one plane: U = pref sum_i a_i / sqrt(C_i) exp(-r^2/C_i); -dU/dr = pref sum_i 2 a_i r / C_i^1.5 exp(..)
+  const double pref = 2.0 * sqrt(kPi) * (kAlpha * kHbarC) * kA0 * pot->N * ch->d_p;
+  const double el_pref = 0.5 * dt * kPi * kR0 * kR0;
+  P.nt = P32.nt = pot->n_terms;
+  P.K = P32.K = pot->n_neighbours;
+  P.el = P32.el = el ? 1 : 0;
+  for (int i = 0; i < pot->n_terms; ++i) {
+    const double C = pot->b[i] / (4.0 * kPi * kPi) + rho2;
+    if (!isfinite(pot->a[i]) || !isfinite(C) || !(C > 0.0)) return RAD_EINVAL;
+    P.fk[i] = 2.0 * ch->charge_sign * pref * pot->a[i] / (C * sqrt(C));
+    P.ck[i] = 1.0 / C;
+    if (el) {
+      const double CX = pot->bx[i] / (4.0 * kPi * kPi) + rho2;
+      if (!isfinite(pot->ax[i]) || !isfinite(CX) || !(CX > 0.0)) return RAD_EINVAL;
+      P.ek[i] = el_pref * pot->N * ch->d_p / sqrt(kPi) * pot->ax[i] / sqrt(CX);
+      P.eck[i] = 1.0 / CX;
+    }
+    P32.fk[i] = static_cast<float>(P.fk[i]);
+    P32.ck2[i] = static_cast<float>(-P.ck[i] / log(2.0));
+    P32.ek[i] = static_cast<float>(P.ek[i]);
+    P32.eck2[i] = static_cast<float>(-P.eck[i] / log(2.0));
+  }
+  P.ecx = el ? el_pref * pot->cx * pot->N : 0.0;
+  P.lk = el ? 2.0 * kMe / pot->I_eV : 0.0;
+  P32.ecx = static_cast<float>(P.ecx);
+  P32.lk = static_cast<float>(P.lk);
+  return RAD_OK;
+}
+
+int launch_trajectories(const rad_channel *ch, const rad_planar_potential *pot, int64_t n_particles,
+                        const int64_t *offsets, int64_t n_samples_total, const double *energy_eV,
+                        const double *x0, const double *thx0, const double *thy0, const int64_t *particle_ids,
+                        double dt, uint64_t seed, double *out, double *energy_out, void *stream) {
   if (!ch || n_particles < 0 || n_samples_total < 0) return RAD_EINVAL;
-  if (n_particles == 0) return RAD_OK;
-  if (!offsets || !energy_eV || !x0 || !thx0 || !out) return RAD_EINVAL;
-  if (!(dt > 0.0) || !isfinite(dt) || !(ch->d_p > 0.0) || !(ch->mass_eV > 0.0) || !(ch->U0_eV >= 0.0) ||
-      (ch->charge_sign != 1 && ch->charge_sign != -1) || (ch->flags & ~15))
+  const int known = pot ? 31 : 15;
+  if (!(dt > 0.0) || !isfinite(dt) || !(ch->d_p > 0.0) || !(ch->mass_eV > 0.0) ||
+      (!pot && !(ch->U0_eV >= 0.0)) || (ch->charge_sign != 1 && ch->charge_sign != -1) || (ch->flags & ~known))
     return RAD_EINVAL;
   if ((ch->flags & RAD_TRAJ_MS) && !(ch->X0 > 0.0 && ch->rho > 0.0 && ch->eps_s_eV >= 0.0)) return RAD_EINVAL;
+  if ((ch->flags & RAD_TRAJ_MS_EL) && !(ch->flags & RAD_TRAJ_MS)) return RAD_EINVAL;
+  Planar P;
+  Planar32 P32;
+  const int pc = make_planar(ch, pot, dt, P, P32);
+  if (pc != RAD_OK) return pc;
+  if (n_particles == 0) return RAD_OK;
+  if (!offsets || !energy_eV || !x0 || !thx0 || !out) return RAD_EINVAL;
   cudaError_t e;
   int *ds = device_status_word(&e);
   if (!ds) return cuda_status(e);
@@ -428,6 +593,7 @@ extern "C" int rad_channeling_trajectories(const rad_channel *ch, int64_t n_part
   const int block = n_particles < 152 * 4 * 32 ? 32 : 128;
   int64_t grid = (n_particles + block - 1) / block;
   if (grid > 1 << 20) grid = 1 << 20;
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (ch->flags & RAD_TRAJ_FP32) {
     Chan32 M;
     M.d_p = ch->d_p;
@@ -454,13 +620,45 @@ extern "C" int rad_channeling_trajectories(const rad_channel *ch, int64_t n_part
     M.ms = C.ms;
     M.ll = C.ll;
     M.ms_loss = C.ms_loss;
-    k_channel_mixed<<<static_cast<unsigned>(grid), block, 0, static_cast<cudaStream_t>(stream)>>>(
-        M, n_particles, offsets, n_samples_total, energy_eV, x0, thx0, thy0, particle_ids, seed, out, energy_out, ds);
+    if (pot)
+      k_channel_mixed<true><<<static_cast<unsigned>(grid), block, 0, st>>>(
+          M, P32, n_particles, offsets, n_samples_total, energy_eV, x0, thx0, thy0, particle_ids, seed, out,
+          energy_out, ds);
+    else
+      k_channel_mixed<false><<<static_cast<unsigned>(grid), block, 0, st>>>(
+          M, P32, n_particles, offsets, n_samples_total, energy_eV, x0, thx0, thy0, particle_ids, seed, out,
+          energy_out, ds);
+  } else if (pot) {
+    k_channel<true><<<static_cast<unsigned>(grid), block, 0, st>>>(C, P, n_particles, offsets, n_samples_total,
+                                                                   energy_eV, x0, thx0, thy0, particle_ids, dt,
+                                                                   seed, out, energy_out, ds);
   } else {
-    k_channel<<<static_cast<unsigned>(grid), block, 0, static_cast<cudaStream_t>(stream)>>>(
-        C, n_particles, offsets, n_samples_total, energy_eV, x0, thx0, thy0, particle_ids, dt, seed, out,
-        energy_out, ds);
+    k_channel<false><<<static_cast<unsigned>(grid), block, 0, st>>>(C, P, n_particles, offsets, n_samples_total,
+                                                                    energy_eV, x0, thx0, thy0, particle_ids, dt,
+                                                                    seed, out, energy_out, ds);
   }
   e = cudaGetLastError();
   return e == cudaSuccess ? RAD_OK : cuda_status(e);
+}
+
+}  // namespace
+}  // namespace rad
+
+extern "C" int rad_channeling_trajectories(const rad_channel *ch, int64_t n_particles, const int64_t *offsets,
+                                           int64_t n_samples_total, const double *energy_eV, const double *x0,
+                                           const double *thx0, const double *thy0, const int64_t *particle_ids,
+                                           double dt, uint64_t seed, double *out, double *energy_out,
+                                           void *stream) {
+  return rad::launch_trajectories(ch, nullptr, n_particles, offsets, n_samples_total, energy_eV, x0, thx0, thy0,
+                                  particle_ids, dt, seed, out, energy_out, stream);
+}
+
+extern "C" int rad_crystal_trajectories(const rad_channel *ch, const rad_planar_potential *pot, int64_t n_particles,
+                                        const int64_t *offsets, int64_t n_samples_total, const double *energy_eV,
+                                        const double *x0, const double *thx0, const double *thy0,
+                                        const int64_t *particle_ids, double dt, uint64_t seed, double *out,
+                                        double *energy_out, void *stream) {
+  if (!pot) return RAD_EINVAL;
+  return rad::launch_trajectories(ch, pot, n_particles, offsets, n_samples_total, energy_eV, x0, thx0, thy0,
+                                  particle_ids, dt, seed, out, energy_out, stream);
 }

@@ -272,6 +272,18 @@ SI110_DP = 1.92e-10        # Si (110) interplanar distance, m
 SI_X0 = 0.0937             # Si radiation length, m
 EPS_S_EV = 10.6e6          # MS energy constant of Sec. III
 RHO_THERMAL = 0.075e-10    # thermal vibration amplitude used for n(r), m (not given in the paper)
+SI_N = 4.994e28            # Si atom density, m^-3 (8 atoms per cubic cell of 5.431 A)
+SI_I_EV = 173.0            # mean ionisation energy of Si, eV
+
+# A synthetic four-Gaussian planar fit with the form and scale of a Doyle-Turner fit (Sec. III):
+# the paper prints no coefficient tables, so these values are made up for tests and benchmarks
+# and are not any crystal's. Potential terms a [m], b [m^2]; X-ray terms ax [electrons],
+# bx [m^2], cx, with sum(ax) + cx = 14 electrons per atom.
+SYNTH_DT_A = (2.0e-10, 2.0e-10, 1.0e-10, 0.3e-10)
+SYNTH_DT_B = (40e-20, 10e-20, 2e-20, 0.4e-20)
+SYNTH_DT_AX = (5.0, 3.0, 2.5, 1.5)
+SYNTH_DT_BX = (30e-20, 8e-20, 1.5e-20, 0.3e-20)
+SYNTH_DT_CX = 2.0
 
 
 def channeling(n_particles: int, E_eV: float, charge: int, lengths, dt: float, seed: int,

@@ -62,3 +62,44 @@ def test_trajectory_argument_checks(lib):
         assert lib.rad_channeling_trajectories(*args(ctypes.byref(c2), 1, 5e-9)) == rad.RAD_EINVAL, bad
     r = lib.rad_channeling_trajectories(ctypes.byref(ch), 1, None, 10, P, P, P, None, None, 5e-9, 1, P, None, None)
     assert r == rad.RAD_EINVAL  # null offsets
+
+
+def test_crystal_trajectory_argument_checks(lib):
+    """rad_crystal_trajectories rejects a missing or malformed planar potential, and electron
+    scattering without nuclear scattering, before any device work."""
+    from paper_1910_10391_gb300 import inputs as I
+    flags = rad.RAD_TRAJ_MS | rad.RAD_TRAJ_MS_EL
+    ch = rad.RadChannel(0.0, I.SI110_DP, I.EPS_S_EV, I.SI_X0, I.RHO_THERMAL, I.ME_EV, 1, flags)
+    good = dict(a=I.SYNTH_DT_A, b=I.SYNTH_DT_B, N=I.SI_N, ax=I.SYNTH_DT_AX, bx=I.SYNTH_DT_BX, cx=I.SYNTH_DT_CX,
+                I_eV=I.SI_I_EV)
+    pot = rad.RadPlanarPotential.make(**good)
+    P = ctypes.c_void_p(16)  # never dereferenced
+    call = lambda c, p, n=1: lib.rad_crystal_trajectories(c, p, n, P, 10, P, P, P, None, None, 5e-9, 1, P, None,
+                                                          None)
+    assert call(ctypes.byref(ch), ctypes.byref(pot), 0) == rad.RAD_OK
+    assert call(ctypes.byref(ch), None) == rad.RAD_EINVAL
+    assert call(None, ctypes.byref(pot)) == rad.RAD_EINVAL
+    for field, v in (("n_terms", 0), ("n_terms", 9), ("n_neighbours", 0), ("n_neighbours", 9), ("N", 0.0),
+                     ("I_eV", 0.0), ("cx", float("nan"))):
+        p2 = rad.RadPlanarPotential.make(**good)
+        setattr(p2, field, v)
+        assert call(ctypes.byref(ch), ctypes.byref(p2), 0) == rad.RAD_EINVAL, field
+    for arr, v in (("a", float("inf")), ("b", -1.0), ("bx", -1.0), ("ax", float("nan"))):
+        p2 = rad.RadPlanarPotential.make(**good)
+        getattr(p2, arr)[1] = v
+        assert call(ctypes.byref(ch), ctypes.byref(p2), 0) == rad.RAD_EINVAL, arr
+    # C_i = b/(4 pi^2) + rho^2 must be positive: b = 0 is fine while rho > 0
+    p2 = rad.RadPlanarPotential.make(**good)
+    p2.b[0] = 0.0
+    assert call(ctypes.byref(ch), ctypes.byref(p2), 0) == rad.RAD_OK
+    # electron scattering needs nuclear scattering; the harmonic entry point does not know the flag
+    c2 = rad.RadChannel(0.0, I.SI110_DP, I.EPS_S_EV, I.SI_X0, I.RHO_THERMAL, I.ME_EV, 1, rad.RAD_TRAJ_MS_EL)
+    assert call(ctypes.byref(c2), ctypes.byref(pot), 0) == rad.RAD_EINVAL
+    assert lib.rad_channeling_trajectories(ctypes.byref(ch), 0, P, 10, P, P, P, None, None, 5e-9, 1, P, None,
+                                           None) == rad.RAD_EINVAL
+    # without electron scattering the X-ray terms and I are not needed
+    c3 = rad.RadChannel(0.0, I.SI110_DP, I.EPS_S_EV, I.SI_X0, I.RHO_THERMAL, I.ME_EV, -1, rad.RAD_TRAJ_MS)
+    p3 = rad.RadPlanarPotential.make(I.SYNTH_DT_A, I.SYNTH_DT_B, I.SI_N)
+    assert call(ctypes.byref(c3), ctypes.byref(p3), 0) == rad.RAD_OK
+    with pytest.raises(ValueError):
+        rad.RadPlanarPotential.make((1.0, 2.0), (1.0,), 1.0)

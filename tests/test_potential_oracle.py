@@ -1,0 +1,167 @@
+"""Pins of the oracle's Doyle-Turner planar potential (Sec. III, Eq. plane) and of the valence-
+electron density of the same planes (Sec. III), each against something other than the real-space
+formula itself:
+  * Poisson summation: the sum of one plane's Gaussians over the lattice equals its Fourier
+    series with coefficients (2 pi e^2 a0 N) a_i exp(-C_i G^2 / 4), G = 2 pi n / d_p;
+  * thermal smearing: the potential at amplitude rho equals the static one (rho = 0) convolved
+    with the thermal density exp(-u^2/rho^2) / (sqrt(pi) rho), by quadrature;
+  * mirror symmetry about a plane and about the mid-plane;
+  * normalisation: one period holds N d_p (sum a^X + c^X) electrons and N d_p nuclei per area;
+  * dynamics: a positron near the channel centre oscillates with Omega^2 = U''(centre)/E (U'' from
+    the Fourier series); the transverse energy E v^2/2 + q U is conserved to RK4 accuracy, whose
+    error falls by about 2^4 when dt halves.
+The electron-scattering rate's prefactor (Eq. elscat) has no independent pin; its plumbing
+(variance per angle, density average) is checked by kick statistics."""
+import math
+
+import numpy as np
+import pytest
+from scipy.integrate import quad
+
+from oracle import traj as T
+from paper_1910_10391_gb300 import inputs as I
+
+D_P, RHO = I.SI110_DP, I.RHO_THERMAL
+
+
+def pot(K=3, **kw):
+    args = dict(a=I.SYNTH_DT_A, b=I.SYNTH_DT_B, N=I.SI_N, ax=I.SYNTH_DT_AX, bx=I.SYNTH_DT_BX, cx=I.SYNTH_DT_CX,
+                I_eV=I.SI_I_EV, K=K)
+    args.update(kw)
+    return T.PlanarPotential(**args)
+
+
+def fourier(x, p, rho, deriv=0, n_max=80):
+    """Lattice sum by its Fourier series: sum over n of c_n cos(G_n x) with c_0 counted once."""
+    C = p.b / (4 * math.pi ** 2) + rho * rho
+    pref = 2 * math.pi * T.E2_EV_M * T.A0_M * p.N
+    x = np.asarray(x, dtype=np.float64)
+    out = np.zeros_like(x) + (pref * p.a.sum() if deriv == 0 else 0.0)
+    for n in range(1, n_max + 1):
+        G = 2 * math.pi * n / D_P
+        c = 2 * pref * (p.a * np.exp(-C * G * G / 4)).sum()
+        if deriv == 0:
+            out += c * np.cos(G * x)
+        elif deriv == 1:
+            out += -c * G * np.sin(G * x)
+        else:
+            out += -c * G * G * np.cos(G * x)
+    return out
+
+
+def test_lattice_sum_equals_fourier_series():
+    p = pot(K=8)
+    x = np.concatenate([np.linspace(-3 * D_P, 4 * D_P, 701), [0.0, D_P, 1e-14, D_P - 1e-14]])
+    U = T.planar_potential(x, p, D_P, RHO)
+    Uf = fourier(x, p, RHO)
+    assert np.abs(U - Uf).max() <= 1e-12 * np.abs(Uf).max()
+    # force = -q dU/dx for both charges
+    for q in (+1, -1):
+        F = T.planar_force(x, p, D_P, RHO, q)
+        Ff = -q * fourier(x, p, RHO, deriv=1)
+        assert np.abs(F - Ff).max() <= 1e-12 * np.abs(Ff).max()
+    # three neighbours on each side already hold the lattice sum to 1e-13 for this fit
+    p3 = pot(K=3)
+    assert np.abs(T.planar_potential(x, p3, D_P, RHO) - Uf).max() <= 1e-13 * np.abs(Uf).max()
+
+
+def test_mean_of_the_potential_over_a_period():
+    """The period average is 2 pi e^2 a0 N sum(a_i), whatever the widths and rho."""
+    for rho in (RHO, 0.2e-10):
+        p = pot(K=8)
+        mean = quad(lambda x: T.planar_potential(np.array([x]), p, D_P, rho)[0], 0, D_P, epsabs=0,
+                    epsrel=1e-13, limit=200)[0] / D_P
+        expect = 2 * math.pi * T.E2_EV_M * T.A0_M * I.SI_N * sum(I.SYNTH_DT_A)
+        assert abs(mean / expect - 1) < 1e-11
+
+
+def test_thermal_smearing_is_a_gaussian_convolution():
+    p = pot(K=8)
+    w = lambda u: math.exp(-u * u / (RHO * RHO)) / (math.sqrt(math.pi) * RHO)
+    for x in (0.0, 0.03e-10, 0.2e-10, 0.5 * D_P, 0.9 * D_P):
+        conv = quad(lambda u: T.planar_potential(np.array([x - u]), p, D_P, 0.0)[0] * w(u), -12 * RHO, 12 * RHO,
+                    epsabs=0, epsrel=1e-12, limit=400, points=[x - D_P, x, x + D_P])[0]
+        direct = T.planar_potential(np.array([x]), p, D_P, RHO)[0]
+        assert abs(conv / direct - 1) < 1e-10, (x, conv, direct)
+
+
+def test_mirror_symmetry():
+    p = pot()
+    x = np.linspace(0.001, 0.999, 97) * D_P
+    U = T.planar_potential(x, p, D_P, RHO)
+    np.testing.assert_allclose(T.planar_potential(D_P - x, p, D_P, RHO), U, rtol=1e-14)
+    np.testing.assert_allclose(T.planar_potential(-x, p, D_P, RHO), U, rtol=1e-14)
+    F = T.planar_force(x, p, D_P, RHO, +1)
+    np.testing.assert_allclose(T.planar_force(D_P - x, p, D_P, RHO, +1), -F, rtol=1e-12, atol=1e-4)
+    assert abs(T.planar_force(np.array([0.5 * D_P]), p, D_P, RHO, +1)[0]) < 1e-3 * np.abs(F).max()
+    # positrons are pushed off the planes (towards the channel centre), electrons pulled on
+    assert np.all(F[x < 0.49 * D_P] > 0) and np.all(T.planar_force(x, p, D_P, RHO, -1)[x < 0.49 * D_P] < 0)
+
+
+def test_electron_and_nucleus_counts_per_plane():
+    p = pot()
+    n_el = quad(lambda x: T.electron_density(np.array([x]), p, D_P, RHO)[0], 0, D_P, epsabs=0, epsrel=1e-12,
+                limit=400, points=[0.05 * D_P, 0.95 * D_P])[0]
+    n_nuc = quad(lambda x: I.SI_N * T.plane_density(np.array([x]), D_P, RHO)[0], 0, D_P, epsabs=0,
+                 epsrel=1e-12, limit=400, points=[0.05 * D_P, 0.95 * D_P])[0]
+    Z = sum(I.SYNTH_DT_AX) + I.SYNTH_DT_CX
+    assert abs(n_el / (I.SI_N * D_P * Z) - 1) < 1e-10
+    assert abs(n_nuc / (I.SI_N * D_P) - 1) < 1e-10
+
+
+def test_small_oscillation_frequency():
+    """A positron entering 1e-3 d_p off the channel centre with zero angle oscillates with
+    Omega = sqrt(U''(d_p/2) / E); anharmonic terms shift it by (A / width)^2 ~ 1e-6."""
+    p = pot()
+    E, dt, L = 10e9, 5e-9, 8001
+    xc = 0.5 * D_P
+    rec = T.trajectories([xc + 1e-3 * D_P], [0.0], 0.0, E, L, dt, seed=0, ms=False, pot=p)[0]
+    s = rec[:, 1] - xc
+    k = np.nonzero((s[:-1] > 0) & (s[1:] <= 0))[0]
+    tz = rec[k, 0] + s[k] / (s[k] - s[k + 1]) * dt
+    period = np.diff(tz).mean()
+    Upp = fourier(np.array([xc]), p, RHO, deriv=2)[0]
+    expect = 2 * math.pi / math.sqrt(Upp / E)
+    assert len(tz) >= 4
+    assert abs(period / expect - 1) < 1e-5, (period, expect)
+
+
+@pytest.mark.parametrize("charge", [+1, -1])
+def test_transverse_energy_is_conserved(charge):
+    p = pot()
+    E = 20e9
+    rng = np.random.default_rng(3)
+    x0 = rng.uniform(0, D_P, 6)
+    th0 = rng.normal(0, 2e-5, 6)
+
+    def drift(dt, L):
+        rec = T.trajectories(x0, th0, 0.0, E, L, dt, seed=0, ms=False, pot=p, charge=charge)
+        Et = E * rec[:, :, 4] ** 2 / 2 + charge * T.planar_potential(rec[:, :, 1], p, D_P, RHO)
+        return np.abs(Et - Et[:, :1]).max()
+
+    d1, d2 = drift(5e-9, 3001), drift(2.5e-9, 6001)
+    assert d1 <= 1e-7 * 28.0
+    # RK4: the energy error per unit length falls as dt^4
+    assert 8.0 < d1 / d2 < 40.0, (d1, d2)
+
+
+def test_electron_scattering_kicks_average_over_the_period():
+    """Zero field (a = 0) and uniform entry over the period: the mean squared kick angle over a
+    short length l is (eps_s/E)^2 l / X0 + rate_el(gamma, N Z) l with the period-averaged
+    electron density N Z (Z = sum a^X + c^X), within the statistical spread."""
+    n, L, dt, E = 4000, 201, 5e-9, 100e9
+    p = pot(a=(0.0, 0.0, 0.0, 0.0))
+    x0 = (np.arange(n) + 0.5) / n * D_P
+    rec = T.trajectories(x0, np.zeros(n), 0.0, E, L, dt, seed=12, pot=p, ms_el=True)
+    l = (L - 1) * dt
+    Z = sum(I.SYNTH_DT_AX) + I.SYNTH_DT_CX
+    nuc = (10.6e6 / E) ** 2 * l / 0.0937
+    el = T.electron_scattering_rate(E / I.ME_EV, I.SI_N * Z, I.SI_I_EV) * l
+    kicks = np.diff(rec[:, :, 4], axis=1) ** 2 + np.diff(rec[:, :, 5], axis=1) ** 2
+    got = kicks.sum(1).mean()
+    # the nuclear part's relative spread (second moment of the plane density 10.2) bounds both
+    assert abs(got / (nuc + el) - 1) < 3 * math.sqrt(10.2 / (200 * n))
+    # the electron term is a visible part of it (about a tenth here)
+    assert el > 0.05 * nuc
+    with pytest.raises(ValueError):
+        T.trajectories(x0[:2], np.zeros(2), 0.0, E, 3, dt, seed=1, ms_el=True)
