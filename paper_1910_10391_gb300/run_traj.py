@@ -1,10 +1,12 @@
-"""Time the GPU trajectory integrator (rad_channeling_trajectories) on a planar-channeling ensemble.
+"""Time the GPU trajectory integrator (rad_channeling_trajectories, or rad_crystal_trajectories
+with --potential doyle-turner) on a planar-channeling ensemble.
 
   python -m paper_1910_10391_gb300.run_traj --particles 1024 --samples 20000 --precision fp32
 
 Entry conditions: x0 uniform over the channel, theta_x0 ~ N(0, (0.3 theta_L)^2) (the ensemble
-workloads' beam), Si(110) harmonic well with U0 = 20 eV. Prints one JSON line with the CUDA-event
-time of the integrator (best of --repeat) and samples/s.
+workloads' beam), Si(110) harmonic well with U0 = 20 eV, or the synthetic four-Gaussian
+Doyle-Turner fit of the input module (3 neighbouring planes on each side). Prints one JSON line
+with the CUDA-event time of the integrator (best of --repeat) and samples/s.
 """
 from __future__ import annotations
 
@@ -26,7 +28,8 @@ def main(argv=None):
     ap.add_argument("--energy", type=float, default=10e9)
     ap.add_argument("--charge", type=int, default=+1, choices=[+1, -1])
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32"])
-    ap.add_argument("--physics", default="ms", choices=["none", "ms", "ms+ll+loss"])
+    ap.add_argument("--physics", default="ms", choices=["none", "ms", "ms+ll+loss", "ms+el+ll+loss"])
+    ap.add_argument("--potential", default="harmonic", choices=["harmonic", "doyle-turner"])
     ap.add_argument("--repeat", type=int, default=3)
     ap.add_argument("--seed", type=int, default=2)
     a = ap.parse_args(argv)
@@ -43,7 +46,14 @@ def main(argv=None):
     doff = torch.from_numpy(off).cuda()
     out = torch.empty((int(off[-1]), rad.RAD_NREC), dtype=torch.float64, device="cuda")
     flags = {"none": 0, "ms": rad.RAD_TRAJ_MS,
-             "ms+ll+loss": rad.RAD_TRAJ_MS | rad.RAD_TRAJ_LL | rad.RAD_TRAJ_MS_LOSS}[a.physics]
+             "ms+ll+loss": rad.RAD_TRAJ_MS | rad.RAD_TRAJ_LL | rad.RAD_TRAJ_MS_LOSS,
+             "ms+el+ll+loss": rad.RAD_TRAJ_MS | rad.RAD_TRAJ_MS_EL | rad.RAD_TRAJ_LL | rad.RAD_TRAJ_MS_LOSS}[a.physics]
+    pot = None
+    if a.potential == "doyle-turner":
+        pot = rad.RadPlanarPotential.make(I.SYNTH_DT_A, I.SYNTH_DT_B, I.SI_N, I.SYNTH_DT_AX, I.SYNTH_DT_BX,
+                                          I.SYNTH_DT_CX, I.SI_I_EV, n_neighbours=3)
+    elif flags & rad.RAD_TRAJ_MS_EL:
+        raise SystemExit("electron scattering needs --potential doyle-turner")
     if a.precision == "fp32":
         flags |= rad.RAD_TRAJ_FP32
     ch = rad.RadChannel(20.0, I.SI110_DP, I.EPS_S_EV, I.SI_X0, I.RHO_THERMAL, I.ME_EV, a.charge, flags)
@@ -53,10 +63,13 @@ def main(argv=None):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record(st)
-        rc = rad.rad_channeling_trajectories(ch, doff, E, x0, th, out, 5e-9, a.seed)
+        if pot is None:
+            rc = rad.rad_channeling_trajectories(ch, doff, E, x0, th, out, 5e-9, a.seed)
+        else:
+            rc = rad.rad_crystal_trajectories(ch, pot, doff, E, x0, th, out, 5e-9, a.seed)
         e1.record(st)
         if rc:
-            raise rad.RadError(rc, "rad_channeling_trajectories")
+            raise rad.RadError(rc, "trajectory integrator")
         torch.cuda.synchronize()
         if r:  # the first call is a warm-up
             ms.append(e0.elapsed_time(e1))
@@ -65,7 +78,8 @@ def main(argv=None):
         raise rad.RadError(status, "device status")
     best = min(ms)
     print(json.dumps({"particles": n, "samples_total": int(off[-1]), "max_length": int(lens.max()),
-                      "precision": a.precision, "physics": a.physics, "charge": a.charge, "ms": ms,
+                      "precision": a.precision, "physics": a.physics, "potential": a.potential,
+                      "charge": a.charge, "ms": ms,
                       "samples_per_s": int(off[-1]) / best * 1e3,
                       "checksum": float(out[:, 1].double().abs().sum().item())}))
 
