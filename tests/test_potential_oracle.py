@@ -11,7 +11,9 @@ formula itself:
     the Fourier series); the transverse energy E v^2/2 + q U is conserved to RK4 accuracy, whose
     error falls by about 2^4 when dt halves.
 The electron-scattering rate's prefactor (Eq. elscat) has no independent pin; its plumbing
-(variance per angle, density average) is checked by kick statistics."""
+(variance per angle, density average) is checked by kick statistics. The physical constants are
+typed here independently of the oracle (CODATA 2018), and test_planted_mistakes_are_caught
+plants single mistakes in the oracle and checks that a pin fails for each."""
 import math
 
 import numpy as np
@@ -22,6 +24,8 @@ from oracle import traj as T
 from paper_1910_10391_gb300 import inputs as I
 
 D_P, RHO = I.SI110_DP, I.RHO_THERMAL
+E2 = 7.2973525693e-3 * 197.3269804e-9   # e^2 = alpha hbar c, eV m
+BOHR = 0.529177210903e-10               # a0, m
 
 
 def pot(K=3, **kw):
@@ -34,7 +38,7 @@ def pot(K=3, **kw):
 def fourier(x, p, rho, deriv=0, n_max=80):
     """Lattice sum by its Fourier series: sum over n of c_n cos(G_n x) with c_0 counted once."""
     C = p.b / (4 * math.pi ** 2) + rho * rho
-    pref = 2 * math.pi * T.E2_EV_M * T.A0_M * p.N
+    pref = 2 * math.pi * E2 * BOHR * p.N
     x = np.asarray(x, dtype=np.float64)
     out = np.zeros_like(x) + (pref * p.a.sum() if deriv == 0 else 0.0)
     for n in range(1, n_max + 1):
@@ -50,6 +54,10 @@ def fourier(x, p, rho, deriv=0, n_max=80):
 
 
 def test_lattice_sum_equals_fourier_series():
+    check_lattice_sum_equals_fourier_series()
+
+
+def check_lattice_sum_equals_fourier_series():
     p = pot(K=8)
     x = np.concatenate([np.linspace(-3 * D_P, 4 * D_P, 701), [0.0, D_P, 1e-14, D_P - 1e-14]])
     U = T.planar_potential(x, p, D_P, RHO)
@@ -66,16 +74,24 @@ def test_lattice_sum_equals_fourier_series():
 
 
 def test_mean_of_the_potential_over_a_period():
+    check_mean_of_the_potential_over_a_period()
+
+
+def check_mean_of_the_potential_over_a_period():
     """The period average is 2 pi e^2 a0 N sum(a_i), whatever the widths and rho."""
     for rho in (RHO, 0.2e-10):
         p = pot(K=8)
         mean = quad(lambda x: T.planar_potential(np.array([x]), p, D_P, rho)[0], 0, D_P, epsabs=0,
                     epsrel=1e-13, limit=200)[0] / D_P
-        expect = 2 * math.pi * T.E2_EV_M * T.A0_M * I.SI_N * sum(I.SYNTH_DT_A)
+        expect = 2 * math.pi * E2 * BOHR * I.SI_N * sum(I.SYNTH_DT_A)
         assert abs(mean / expect - 1) < 1e-11
 
 
 def test_thermal_smearing_is_a_gaussian_convolution():
+    check_thermal_smearing_is_a_gaussian_convolution()
+
+
+def check_thermal_smearing_is_a_gaussian_convolution():
     p = pot(K=8)
     w = lambda u: math.exp(-u * u / (RHO * RHO)) / (math.sqrt(math.pi) * RHO)
     for x in (0.0, 0.03e-10, 0.2e-10, 0.5 * D_P, 0.9 * D_P):
@@ -86,7 +102,16 @@ def test_thermal_smearing_is_a_gaussian_convolution():
 
 
 def test_mirror_symmetry():
-    p = pot()
+    check_mirror_symmetry()
+
+
+def check_mirror_symmetry():
+    for K in (1, 3):
+        check_mirror_symmetry_K(K)
+
+
+def check_mirror_symmetry_K(K):
+    p = pot(K=K)
     x = np.linspace(0.001, 0.999, 97) * D_P
     U = T.planar_potential(x, p, D_P, RHO)
     np.testing.assert_allclose(T.planar_potential(D_P - x, p, D_P, RHO), U, rtol=1e-14)
@@ -99,6 +124,10 @@ def test_mirror_symmetry():
 
 
 def test_electron_and_nucleus_counts_per_plane():
+    check_electron_and_nucleus_counts_per_plane()
+
+
+def check_electron_and_nucleus_counts_per_plane():
     p = pot()
     n_el = quad(lambda x: T.electron_density(np.array([x]), p, D_P, RHO)[0], 0, D_P, epsabs=0, epsrel=1e-12,
                 limit=400, points=[0.05 * D_P, 0.95 * D_P])[0]
@@ -165,3 +194,45 @@ def test_electron_scattering_kicks_average_over_the_period():
     assert el > 0.05 * nuc
     with pytest.raises(ValueError):
         T.trajectories(x0[:2], np.zeros(2), 0.0, E, 3, dt, seed=1, ms_el=True)
+
+
+FAST_CHECKS = (check_lattice_sum_equals_fourier_series, check_mean_of_the_potential_over_a_period,
+               check_thermal_smearing_is_a_gaussian_convolution, check_mirror_symmetry,
+               check_electron_and_nucleus_counts_per_plane)
+
+
+def _plants():
+    U, F, ne, dist = T.planar_potential, T.planar_force, T.electron_density, T._plane_distances
+
+    def widths_4pi(f):  # B_i = b/(4 pi) instead of b/(4 pi^2)
+        return lambda x, p, d, rho, *c: f(x, T.PlanarPotential(p.a, p.b * math.pi, p.N, p.ax, p.bx, p.cx, p.I_eV,
+                                                                p.K), d, rho, *c)
+
+    def printed_density(x, p, d, rho):  # the valence prefactor as printed: d_p / pi
+        nuc = p.cx * p.N * T.plane_density(x, d, rho)
+        return (ne(x, p, d, rho) - nuc) * math.sqrt(math.pi) / (math.pi * p.N) + nuc
+
+    return {
+        "prefactor sqrt(pi) for 2 sqrt(pi)": {"planar_potential": lambda *a: 0.5 * U(*a),
+                                              "planar_force": lambda *a: 0.5 * F(*a)},
+        "no rho^2 in C_i": {"planar_potential": lambda x, p, d, rho: U(x, p, d, 0.0),
+                            "planar_force": lambda x, p, d, rho, c: F(x, p, d, 0.0, c)},
+        "B_i = b/(4 pi)": {"planar_potential": widths_4pi(U), "planar_force": widths_4pi(F)},
+        "force sign": {"planar_force": lambda *a: -F(*a)},
+        "force without its factor 2": {"planar_force": lambda *a: 0.5 * F(*a)},
+        "electron density prefactor as printed": {"electron_density": printed_density},
+        "plane set shifted by one": {"_plane_distances": lambda x, d, K: dist(x, d, K) + d},
+    }
+
+
+@pytest.mark.parametrize("plant", list(_plants()))
+def test_planted_mistakes_are_caught(plant, monkeypatch):
+    for name, fn in _plants()[plant].items():
+        monkeypatch.setattr(T, name, fn)
+    failed = []
+    for check in FAST_CHECKS:
+        try:
+            check()
+        except AssertionError:
+            failed.append(check.__name__)
+    assert failed, f"no pin caught: {plant}"
