@@ -15,7 +15,8 @@
 //   scattering loss each kick costs m alpha/(2 pi) gamma^3 theta^2.
 // Doyle-Turner form (rad_crystal_trajectories): the harmonic well is replaced by the thermally
 // averaged continuum potential of the planes at x = m d_p (Sec. III, Eq. plane), summed over the
-// 2K planes around the particle's cell: F = sum_planes sum_i fk_i r exp(-r^2 / C_i) with
+// 2K planes around the particle's cell: F = sum_planes sum_i fk_i r exp(-r^2 / C_i) (in FP64 by a
+// geometric walk outward from the nearest plane, three exponentials per term) with
 // fk_i = 2 q (2 sqrt(pi) e^2 a0 N d_p) a_i / C_i^(3/2), C_i = b_i/(4 pi^2) + rho^2; with electron
 // scattering the kick variance gains (1/2) dt pi r0^2 / (gamma^2 beta^4) [ln(2 m_e gamma^2
 // beta^2 / I) - beta^2]_+ n_el(x) (Sec. III), n_el from the X-ray Gaussians of the same planes
@@ -46,8 +47,8 @@ constexpr double kA0 = 5.29177210903e-11; // Bohr radius, m (CODATA 2018)
 // density terms ek[i] exp(-r^2 eck[i]) and ecx n(x)/N, all pre-multiplied by (1/2) dt pi r0^2.
 struct Planar {
   int nt, K, el;
-  double fk[kMaxTerms], ck[kMaxTerms], ek[kMaxTerms], eck[kMaxTerms];
-  double ecx, lk;  // lk = 2 m_e / I
+  double fk[kMaxTerms], ck[kMaxTerms], q[kMaxTerms], ek[kMaxTerms], eck[kMaxTerms];
+  double ecx, lk;  // q = exp(-2 ck d_p^2); lk = 2 m_e / I
 };
 
 // ---------------- Philox4x32-10 ----------------
@@ -95,15 +96,42 @@ __device__ __forceinline__ double plane_density(const Chan &C, double x) {
   return C.dens_pref * (exp(-(r1 * r1) * C.inv_rho2) + exp(-(r2 * r2) * C.inv_rho2));
 }
 
-// position within its cell, xi = x - floor(x/d_p) d_p; plane j of the 2K is at distance xi - j d_p
+// The 2K planes of the particle's cell (xi = x - floor(x/d_p) d_p in [0, d_p); plane j at distance
+// xi - j d_p, j = 1-K .. K), walked outward from the nearest one, at distance r (|r| <= d_p/2).
+// Along the planes each Gaussian is geometric in its ratios: with E_m = exp(-k (r - m d)^2),
+// E_{m+1}/E_m = exp(k (2 (r - m d) d - d^2)) and successive ratios differ by the factor
+// q = exp(-2 k d^2). So a term costs three exponentials (the nearest plane and the first ratio
+// each way, all <= 1) and products, instead of one exponential per plane. The ratios' large
+// arguments only touch terms already below exp(-k d^2/4) of the nearest one.
 __device__ __forceinline__ double planar_force(const Chan &C, const Planar &P, double x) {
-  const double xi = x - floor(x * C.inv_d) * C.d_p;
+  const double d = C.d_p;
+  const double xi = x - floor(x * C.inv_d) * d;
+  const bool low = xi < 0.5 * d;
+  const double r = low ? xi : xi - d;
+  const int n_up = low ? P.K : P.K - 1;  // planes at r - m d, m = 1 .. n_up
+  const int n_dn = low ? P.K - 1 : P.K;  // planes at r + m d, m = 1 .. n_dn
   double F = 0.0;
-  for (int j = 1 - P.K; j <= P.K; ++j) {
-    const double r = xi - j * C.d_p, r2 = r * r;
-    double g = 0.0;
-    for (int i = 0; i < P.nt; ++i) g += P.fk[i] * exp(-r2 * P.ck[i]);
-    F += r * g;
+  for (int i = 0; i < P.nt; ++i) {
+    const double k = P.ck[i], q = P.q[i];
+    const double E0 = exp(-(r * r) * k);
+    double s = r * E0;
+    double E = E0, rho = exp(k * (2.0 * r * d - d * d)), rm = r;
+    for (int m = 0; m < n_up; ++m) {
+      E *= rho;
+      rho *= q;
+      rm -= d;
+      s += rm * E;
+    }
+    E = E0;
+    rho = exp(-k * (2.0 * r * d + d * d));
+    rm = r;
+    for (int m = 0; m < n_dn; ++m) {
+      E *= rho;
+      rho *= q;
+      rm += d;
+      s += rm * E;
+    }
+    F += P.fk[i] * s;
   }
   return F;
 }
@@ -532,6 +560,7 @@ int make_planar(const rad_channel *ch, const rad_planar_potential *pot, double d
     if (!isfinite(pot->a[i]) || !isfinite(C) || !(C > 0.0)) return RAD_EINVAL;
     P.fk[i] = 2.0 * ch->charge_sign * pref * pot->a[i] / (C * sqrt(C));
     P.ck[i] = 1.0 / C;
+    P.q[i] = exp(-2.0 * ch->d_p * ch->d_p / C);
     if (el) {
       const double CX = pot->bx[i] / (4.0 * kPi * kPi) + rho2;
       if (!isfinite(pot->ax[i]) || !isfinite(CX) || !(CX > 0.0)) return RAD_EINVAL;
