@@ -348,7 +348,9 @@ int rad_standardize(float *y, int64_t rows, int cols, const float *mean, const f
 /* Planar channel of the trajectory integrator: a harmonic well U(s) = U0 (2 s / d_p)^2 in the
  * distance s to the nearest channel centre (a stand-in for the planar continuum potential of
  * Sec. III, whose Doyle-Turner tables the paper does not print), and the nuclear
- * multiple-scattering model of Sec. III. */
+ * multiple-scattering model of Sec. III. rad_crystal_trajectories replaces the well by the
+ * Doyle-Turner planar potential with the caller's fit (rad_planar_potential, below), and may add
+ * scattering on valence electrons. */
 typedef struct {
   double U0_eV;    /* well depth, eV (>= 0)                                                 */
   double d_p;      /* interplanar distance, m (> 0)                                         */

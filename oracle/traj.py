@@ -16,7 +16,8 @@ continuum potential, whose Doyle-Turner tables the paper does not print):
     transverse field is a drag along the velocity with the relativistic Larmor power):
       dE/dt = -(2/3) alpha hbar c gamma^2 F^2 / (m c^2)^2;
   * one classical Runge-Kutta (RK4) step of dt on (x, y, v_x, v_y, dz, E) between samples;
-  * multiple Coulomb scattering on nuclei (Sec. III, nuclear term only): after each step,
+  * multiple Coulomb scattering on nuclei (Sec. III; the valence-electron term is added with a
+    planar potential, below): after each step,
     independent Gaussian kicks of both transverse angles with variance
       (1/2) (eps_s / E)^2 (dt / X0) n(x)/N,  n(x)/N = d_p/(sqrt(pi) rho) sum over the two
       nearest planes of exp(-r^2/rho^2),
