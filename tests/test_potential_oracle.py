@@ -236,3 +236,26 @@ def test_planted_mistakes_are_caught(plant, monkeypatch):
         except AssertionError:
             failed.append(check.__name__)
     assert failed, f"no pin caught: {plant}"
+
+
+@pytest.mark.parametrize("charge", [+1, -1])
+def test_radiation_reaction_in_the_planar_potential_is_larmor_power(charge):
+    """With the Doyle-Turner force the energy lost to the Landau-Lifshitz drag equals the Larmor
+    integral of the recorded force along the trajectory (electrons radiate mostly at the plane
+    cores, where the force is steepest)."""
+    p = pot()
+    E0, L, dt = 50e9, 3001, 5e-9
+    rng = np.random.default_rng(4)
+    x0, th0 = rng.uniform(0, D_P, 4), rng.normal(0, 1e-5, 4)
+    rec, Es = T.trajectories(x0, th0, 0.0, E0, L, dt, seed=0, ms=False, ll=True, pot=p, charge=charge,
+                             energies=True)
+    F = rec[:, :, 7] * Es
+    np.testing.assert_allclose(F, T.planar_force(rec[:, :, 1], p, D_P, RHO, charge), rtol=1e-12,
+                               atol=1e-12 * np.abs(F).max())
+    alpha, me = 7.2973525693e-3, 0.51099895e6
+    P = (2 / 3) * alpha * 197.3269804e-9 * (Es / me) ** 2 * (F / me) ** 2
+    lost = np.concatenate([np.zeros((4, 1)), np.cumsum(0.5 * (P[:, 1:] + P[:, :-1]) * dt, 1)], 1)
+    assert lost[:, -1].min() > 10.0
+    # trapezoid error of the reference: at most dt^2/12 |P'| at each end (Euler-Maclaurin)
+    dP = np.abs(np.diff(P, axis=1)).max() / dt
+    np.testing.assert_allclose(E0 - Es, lost, rtol=1e-6, atol=dt * dt / 6 * dP)
