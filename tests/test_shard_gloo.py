@@ -1,5 +1,8 @@
 """Multi-rank particle sharding on CPU: 2 gloo ranks, each sums its particle range with the FP64
-oracle, one all-reduce; the result equals the oracle on the whole ensemble."""
+oracle, one all-reduce; the result equals the oracle on the whole ensemble. Trajectories shard the
+same way: with global particle ids each particle keeps its random stream, so the sharded records
+equal the single-process ones bit for bit. A rank that leaves is detected by the next
+collective."""
 import os
 import socket
 
@@ -108,3 +111,58 @@ def test_rank_that_leaves_is_detected_by_the_next_collective():
             p.kill()
     assert kind != "no error", "the all-reduce with a departed rank returned normally"
     assert dt < 60.0
+
+
+def _worker_traj(rank, world, port, out):
+    """Each rank integrates its particle range with the global particle ids (so every particle
+    keeps its own random stream) and one all-reduce of the zero-padded records assembles the
+    ensemble."""
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    from oracle import traj as T
+    from paper_1910_10391_gb300 import inputs as I
+    from paper_1910_10391_gb300 import shard as S
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    n, L = 7, 400
+    rng = np.random.default_rng(5)
+    x0, th = rng.uniform(0, I.SI110_DP, n), rng.normal(0, 2e-5, n)
+    pot = T.PlanarPotential(I.SYNTH_DT_A, I.SYNTH_DT_B, I.SI_N, I.SYNTH_DT_AX, I.SYNTH_DT_BX, I.SYNTH_DT_CX,
+                            I.SI_I_EV)
+    p0, p1 = S.particle_range(n, world, rank)
+    full = np.zeros((n, L, 10))
+    if p1 > p0:
+        full[p0:p1] = T.trajectories(x0[p0:p1], th[p0:p1], 0.0, 20e9, L, 5e-9, 17, charge=-1, pot=pot, ms_el=True,
+                                     ll=True, ms_loss=True, particle_ids=np.arange(p0, p1))
+    t = torch.from_numpy(full)
+    S.allreduce_sum(t)
+    if rank == 0:
+        out.put(t.numpy())
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_sharded_trajectories_keep_their_random_streams():
+    from oracle import traj as T
+    from paper_1910_10391_gb300 import inputs as I
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker_traj, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = q.get(timeout=180)
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    n, L = 7, 400
+    rng = np.random.default_rng(5)
+    x0, th = rng.uniform(0, I.SI110_DP, n), rng.normal(0, 2e-5, n)
+    pot = T.PlanarPotential(I.SYNTH_DT_A, I.SYNTH_DT_B, I.SI_N, I.SYNTH_DT_AX, I.SYNTH_DT_BX, I.SYNTH_DT_CX,
+                            I.SI_I_EV)
+    ref = T.trajectories(x0, th, 0.0, 20e9, L, 5e-9, 17, charge=-1, pot=pot, ms_el=True, ll=True, ms_loss=True)
+    assert np.array_equal(got, ref)
+    # and the streams differ between particles: no two particles received the same kicks
+    kicks = np.diff(ref[:, :, 4], axis=1)
+    assert len({float(k) for k in kicks[:, 10]}) == n
