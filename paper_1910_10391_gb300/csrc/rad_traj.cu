@@ -271,9 +271,9 @@ __global__ void k_channel(const Chan C, const Planar P, int64_t n_particles, con
 // ------------------------------------------------------------------------------------
 // Mixed precision (RAD_TRAJ_FP32): FP32 arithmetic with double-float state
 // ------------------------------------------------------------------------------------
-// GB300 issues FP32 at 72x its FP64 rate, so this form evaluates the RK4 stages in FP32 and
-// keeps every state variable as an unevaluated sum hi + lo of two floats (about 48 bits),
-// updated with error-free transformations (Knuth's two-sum, FMA two-product). The position is
+// GB300 issues FP32 at 64x its FP64 rate (72x measured), so this form evaluates the RK4 stages in
+// FP32 and keeps every state variable as an unevaluated sum hi + lo of two floats (about 48
+// bits), updated with error-free transformations (Knuth's two-sum, FMA two-product). The position is
 // kept as (channel index m, offset s from the channel centre) so that s stays below d_p/2 in
 // magnitude however far the particle drifts. The x and y increments h v use a double-float
 // product of the step h and the double-float velocity; the other increments are FP32.
