@@ -12,6 +12,12 @@ Parity status: every function here is pinned by tests in tests/test_oracle_pins.
 (straight-line zero, weak-undulator dipole closed form and harmonic positions,
 Jackson synchrotron, Larmor energy, integration-by-parts identities for I and J,
 unexpanded Lienard-Wiechert brute force, quadrature order, symmetry, additivity).
+
+Submodules: ``traj`` (trajectories of Sec. III: harmonic well or Doyle-Turner planar
+potential, scattering on nuclei and electrons, radiation reaction; pinned in
+tests/test_traj_oracle.py and tests/test_potential_oracle.py, except the electron-scattering
+rate's prefactor, which is parity unpinned) and ``mlp`` (the surrogate network in FP64 numpy,
+pinned by finite differences in tests/test_mlp_reference.py).
 """
 from __future__ import annotations
 
