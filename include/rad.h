@@ -432,7 +432,9 @@ int rad_channeling_trajectories(const rad_channel *ch, int64_t n_particles, cons
  * streams and both precisions are those of rad_channeling_trajectories. Flags may add
  * RAD_TRAJ_MS_EL (needs RAD_TRAJ_MS). Host checks (null ch or pot, n_terms or n_neighbours out of
  * range, N <= 0, a non-finite coefficient, C_i <= 0, with RAD_TRAJ_MS_EL CX_i <= 0 or I_eV <= 0,
- * and the checks of rad_channeling_trajectories) return RAD_EINVAL before anything is enqueued.
+ * a derived force or density coefficient that is not finite in the precision used (with
+ * RAD_TRAJ_FP32: in FP32), and the checks of rad_channeling_trajectories) return RAD_EINVAL before
+ * anything is enqueued.
  */
 int rad_crystal_trajectories(const rad_channel *ch, const rad_planar_potential *pot, int64_t n_particles,
                              const int64_t *offsets, int64_t n_samples_total, const double *energy_eV,

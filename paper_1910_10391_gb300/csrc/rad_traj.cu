@@ -576,7 +576,17 @@ int make_planar(const rad_channel *ch, const rad_planar_potential *pot, double d
   P.lk = el ? 2.0 * kMe / pot->I_eV : 0.0;
   P32.ecx = static_cast<float>(P.ecx);
   P32.lk = static_cast<float>(P.lk);
-  return RAD_OK;
+  // every coefficient must be finite in the precision that uses it (an extreme fit, e.g. rho = 0
+  // with a tiny b_i, overflows FP32 first)
+  bool ok = isfinite(P.ecx) && isfinite(P.lk);
+  for (int i = 0; i < pot->n_terms; ++i) ok = ok && isfinite(P.fk[i]) && isfinite(P.ck[i]) && isfinite(P.ek[i]) &&
+                                              isfinite(P.eck[i]);
+  if (ch->flags & RAD_TRAJ_FP32) {
+    ok = ok && isfinite(P32.ecx) && isfinite(P32.lk);
+    for (int i = 0; i < pot->n_terms; ++i)
+      ok = ok && isfinite(P32.fk[i]) && isfinite(P32.ck2[i]) && isfinite(P32.ek[i]) && isfinite(P32.eck2[i]);
+  }
+  return ok ? RAD_OK : RAD_EINVAL;
 }
 
 int launch_trajectories(const rad_channel *ch, const rad_planar_potential *pot, int64_t n_particles,

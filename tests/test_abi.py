@@ -88,6 +88,13 @@ def test_crystal_trajectory_argument_checks(lib):
         p2 = rad.RadPlanarPotential.make(**good)
         getattr(p2, arr)[1] = v
         assert call(ctypes.byref(ch), ctypes.byref(p2), 0) == rad.RAD_EINVAL, arr
+    # a fit whose force coefficients overflow FP32 (rho = 0 and a tiny b_i: C_i ~ 1e-40 m^2) is
+    # refused in the FP32 form and accepted in FP64, where they are finite
+    c0 = rad.RadChannel(0.0, I.SI110_DP, I.EPS_S_EV, I.SI_X0, 0.0, I.ME_EV, 1, 0)
+    tiny = rad.RadPlanarPotential.make((1e-10,), (1e-40 * 4 * 3.141592653589793 ** 2,), I.SI_N)
+    assert call(ctypes.byref(c0), ctypes.byref(tiny), 0) == rad.RAD_OK
+    c0.flags = rad.RAD_TRAJ_FP32
+    assert call(ctypes.byref(c0), ctypes.byref(tiny), 0) == rad.RAD_EINVAL
     # C_i = b/(4 pi^2) + rho^2 must be positive: b = 0 is fine while rho > 0
     p2 = rad.RadPlanarPotential.make(**good)
     p2.b[0] = 0.0
