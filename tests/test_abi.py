@@ -110,3 +110,30 @@ def test_crystal_trajectory_argument_checks(lib):
     assert call(ctypes.byref(c3), ctypes.byref(p3), 0) == rad.RAD_OK
     with pytest.raises(ValueError):
         rad.RadPlanarPotential.make((1.0, 2.0), (1.0,), 1.0)
+
+
+def _declared_parameter_counts():
+    """Number of parameters of every function declared in include/rad.h (comments stripped)."""
+    import re
+    with open(rad._binding.HEADER) as f:
+        txt = re.sub(r"/\*.*?\*/", "", f.read(), flags=re.S)
+    txt = re.sub(r"//[^\n]*", "", txt)
+    counts = {}
+    for m in re.finditer(r"\b(rad_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", txt):
+        params = m.group(2).strip()
+        counts[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return counts
+
+
+def test_binding_argument_lists_match_the_header(lib):
+    """Every declared function the binding gives argument types to takes as many arguments in
+    the binding as the header declares (ctypes would otherwise marshal them silently wrong)."""
+    counts = _declared_parameter_counts()
+    assert len(counts) == len(rad.header_symbols())
+    typed = 0
+    for name, n in counts.items():
+        f = getattr(lib, name)
+        if f.argtypes is not None:
+            typed += 1
+            assert len(f.argtypes) == n, (name, len(f.argtypes), n)
+    assert typed >= 30
