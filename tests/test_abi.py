@@ -137,3 +137,17 @@ def test_binding_argument_lists_match_the_header(lib):
             typed += 1
             assert len(f.argtypes) == n, (name, len(f.argtypes), n)
     assert typed >= 30
+
+
+def test_binding_return_types_match_the_header(lib):
+    """int -> c_int, int64_t -> c_int64, const char * -> c_char_p, void -> None."""
+    import re
+    with open(rad._binding.HEADER) as f:
+        txt = re.sub(r"/\*.*?\*/", "", f.read(), flags=re.S)
+    kinds = {"int": ctypes.c_int, "int64_t": ctypes.c_int64, "const char *": ctypes.c_char_p, "void": None}
+    seen = 0
+    for m in re.finditer(r"^\s*(int64_t|int|const char \*|void)\s*(rad_[a-z0-9_]+)\s*\(", txt, flags=re.M):
+        ret, name = m.group(1), m.group(2)
+        assert getattr(lib, name).restype == kinds[ret], (name, ret, getattr(lib, name).restype)
+        seen += 1
+    assert seen == len(rad.header_symbols())
