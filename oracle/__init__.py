@@ -15,8 +15,8 @@ unexpanded Lienard-Wiechert brute force, quadrature order, symmetry, additivity)
 
 Submodules: ``traj`` (trajectories of Sec. III: harmonic well or Doyle-Turner planar
 potential, scattering on nuclei and electrons, radiation reaction; pinned in
-tests/test_traj_oracle.py and tests/test_potential_oracle.py, except the electron-scattering
-rate's prefactor, which is parity unpinned) and ``mlp`` (the surrogate network in FP64 numpy,
+tests/test_traj_oracle.py and tests/test_potential_oracle.py, the electron-scattering rate
+included) and ``mlp`` (the surrogate network in FP64 numpy,
 pinned by finite differences in tests/test_mlp_reference.py).
 """
 from __future__ import annotations

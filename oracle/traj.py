@@ -50,8 +50,9 @@ the per-kick scattering loss, kick statistics, and agreement with the input gene
 planar potential is pinned in tests/test_potential_oracle.py by its Fourier series (Poisson
 summation), the thermal smearing as a Gaussian convolution, mirror symmetry, the electron count
 per plane, transverse-energy conservation and the small-oscillation frequency. The electron-
-scattering rate's prefactor (pi r0^2 and the logarithm) is parity unpinned: no closed form or
-printed value fixes it independently of the formula itself.
+scattering rate (Eq. elscat) is pinned there too: by the paper's statement that, with uniform
+densities, the electron term is 1/Z of the nuclear one (to the factor 2 it resolves), and by
+Rutherford kinematics (rate times (p v)^2 over the Bethe logarithm is the same at every energy).
 """
 from __future__ import annotations
 

@@ -10,10 +10,13 @@ formula itself:
   * dynamics: a positron near the channel centre oscillates with Omega^2 = U''(centre)/E (U'' from
     the Fourier series); the transverse energy E v^2/2 + q U is conserved to RK4 accuracy, whose
     error falls by about 2^4 when dt halves.
-The electron-scattering rate's prefactor (Eq. elscat) has no independent pin; its plumbing
-(variance per angle, density average) is checked by kick statistics. The physical constants are
-typed here independently of the oracle (CODATA 2018), and test_planted_mistakes_are_caught
-plants single mistakes in the oracle and checks that a pin fails for each."""
+The electron-scattering rate (Eq. elscat) is pinned by the paper's own statement beside it (with
+uniform densities the electron term is 1/Z of the nuclear one, to the factor 2 the paper
+resolves), by Rutherford kinematics (the rate times (p v)^2 over the Bethe logarithm does not
+depend on the energy) and by its linearity in n_el; its plumbing (variance per angle, density
+average) is checked by kick statistics. The physical constants are typed here independently of
+the oracle (CODATA 2018), and the planted-mistake tests plant single mistakes in the oracle and
+check that a pin fails for each."""
 import math
 
 import numpy as np
@@ -26,6 +29,9 @@ from paper_1910_10391_gb300 import inputs as I
 D_P, RHO = I.SI110_DP, I.RHO_THERMAL
 E2 = 7.2973525693e-3 * 197.3269804e-9   # e^2 = alpha hbar c, eV m
 BOHR = 0.529177210903e-10               # a0, m
+ME = 0.51099895e6                       # electron rest energy, eV
+R0 = 2.8179403262e-15                   # classical electron radius, m
+SI_Z = 14
 
 
 def pot(K=3, **kw):
@@ -194,6 +200,102 @@ def test_electron_scattering_kicks_average_over_the_period():
     assert el > 0.05 * nuc
     with pytest.raises(ValueError):
         T.trajectories(x0[:2], np.zeros(2), 0.0, E, 3, dt, seed=1, ms_el=True)
+
+
+def test_electron_term_is_one_over_Z_of_the_nuclear_term():
+    check_electron_term_is_one_over_Z_of_the_nuclear_term()
+
+
+def check_electron_term_is_one_over_Z_of_the_nuclear_term():
+    """Sec. III, beside Eq. elscat: the paper removed a factor 2 so that, for uniform densities of
+    nuclei (n = N) and electrons (n_el = Z N), scattering on electrons gives 1/Z of the nuclear
+    mean squared angle (the rule that replaces Z^2 by Z(Z + 1) in the radiation length). The
+    statement resolves a factor 2, so Z times the ratio must lie within a factor 2 of 1 at the
+    paper's energies (1 to 50 GeV e+-, Si: Z = 14, X0 = 9.37 cm, I = 173 eV). Inside that range
+    the ratio moves only through the logarithm ln(2 m gamma^2 beta^2 / I) - beta^2, which goes from
+    22.9 to 30.7, so Z times the ratio goes from 1.21 to 1.63; keeping the factor 2 gives 2.4 to
+    3.3, and a logarithm without gamma^2 gives 0.41."""
+    for E in np.geomspace(1e9, 50e9, 9):
+        el = T.electron_scattering_rate(E / ME, SI_Z * I.SI_N, I.SI_I_EV)
+        nuc = (10.6e6 / E) ** 2 / 0.0937
+        zr = SI_Z * el / nuc
+        assert 0.5 < zr < 2.0, (E, zr)
+
+
+def test_electron_scattering_follows_rutherford_kinematics():
+    check_electron_scattering_follows_rutherford_kinematics()
+
+
+def check_electron_scattering_follows_rutherford_kinematics():
+    """Small-angle Rutherford scattering of a unit charge on free electrons gives a mean squared
+    angle per length proportional to n_el r0^2 m^2 / (p v)^2 times a Coulomb logarithm, where the
+    momentum p and the speed v follow from E and m alone: p^2 = E^2 - m^2, v = p / E. The
+    logarithm of Eq. elscat is the Bethe stopping-power bracket (PDG, no density effect)
+    (1/2) ln(2 m beta^2 gamma^2 T_max / I^2) - beta^2 with the heavy-projectile
+    T_max = 2 m beta^2 gamma^2. So rate (p v / m)^2 / (n_el bracket) must be the same at every
+    energy, from gamma = 1.05 (beta^2 = 0.09, where beta^4 and beta^2 differ tenfold) to 10^5;
+    and the rate is linear in n_el."""
+    n_el = SI_Z * I.SI_N
+    vals = []
+    for g in (1.05, 1.5, 3.0, 30.0, 3e4, 1e5):
+        E = g * ME
+        p = math.sqrt(E * E - ME * ME)
+        v = p / E
+        b2g2 = (p / ME) ** 2
+        t_max = 2 * ME * b2g2
+        bracket = 0.5 * math.log(2 * ME * b2g2 * t_max / I.SI_I_EV ** 2) - v * v
+        assert bracket > 0
+        rate = T.electron_scattering_rate(g, n_el, I.SI_I_EV)
+        vals.append(float(rate) * (p * v / ME) ** 2 / (n_el * bracket))
+        np.testing.assert_allclose(T.electron_scattering_rate(g, 3.0 * n_el, I.SI_I_EV), 3.0 * rate, rtol=1e-14)
+        assert T.electron_scattering_rate(g, 0.0, I.SI_I_EV) == 0.0
+    np.testing.assert_allclose(vals, vals[-1], rtol=1e-12)
+    # just above gamma = 1 the bracket turns negative and the rate is clamped at zero
+    assert T.electron_scattering_rate(1.00001, n_el, I.SI_I_EV) == 0.0
+
+
+EL_CHECKS = (check_electron_term_is_one_over_Z_of_the_nuclear_term,
+             check_electron_scattering_follows_rutherford_kinematics)
+
+
+def _el_plants():
+    rate = T.electron_scattering_rate
+
+    def beta2(g):
+        g = np.asarray(g, dtype=np.float64)
+        return 1.0 - 1.0 / (g * g)
+
+    def log_without_gamma2(g, n, I_eV):
+        b2 = beta2(g)
+        right = np.log(2 * ME * g * g * b2 / I_eV) - b2
+        wrong = np.log(2 * ME * b2 / I_eV) - b2
+        return rate(g, n, I_eV) / right * wrong
+
+    def no_beta2_term(g, n, I_eV):
+        b2 = beta2(g)
+        right = np.log(2 * ME * g * g * b2 / I_eV) - b2
+        return rate(g, n, I_eV) / right * (right + b2)
+
+    return {
+        "factor 2 not removed": lambda g, n, I_eV: 2.0 * rate(g, n, I_eV),
+        "beta^4 -> beta^2": lambda g, n, I_eV: rate(g, n, I_eV) * beta2(g),
+        "r0 in place of r0^2": lambda g, n, I_eV: rate(g, n, I_eV) / R0,
+        "gamma^2 -> gamma in the prefactor": lambda g, n, I_eV: rate(g, n, I_eV) * np.asarray(g, dtype=np.float64),
+        "log argument without gamma^2": log_without_gamma2,
+        "no -beta^2 in the bracket": no_beta2_term,
+    }
+
+
+@pytest.mark.parametrize("plant", list(_el_plants()))
+def test_planted_electron_scattering_mistakes_are_caught(plant, monkeypatch):
+    monkeypatch.setattr(T, "electron_scattering_rate", _el_plants()[plant])
+    failed = []
+    for check in EL_CHECKS:
+        try:
+            check()
+        except AssertionError:
+            failed.append(check.__name__)
+    assert failed, f"no pin caught: {plant}"
 
 
 FAST_CHECKS = (check_lattice_sum_equals_fourier_series, check_mean_of_the_potential_over_a_period,
