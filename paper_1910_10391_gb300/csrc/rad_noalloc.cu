@@ -17,7 +17,7 @@
 namespace {
 
 constexpr size_t kNoallocBytes = size_t(32) << 20;  // 32 MiB
-constexpr size_t kCtrlBytes = 256;                   // work counter, call status, publish word
+constexpr size_t kCtrlBytes = 256;  // work counter, call status, publish word; grid maxima from byte 16
 
 // Device-resident scratch. In host code this name is only a host-side stand-in for the
 // symbol: its device address comes from cudaGetSymbolAddress below.
@@ -57,15 +57,18 @@ extern "C" int rad_spectrum_noalloc(const double *samples, int64_t n_samples_tot
   if (!out_cube || !offsets || !hbar_omega_eV || !theta_x || !theta_y) return RAD_EINVAL;
   if (n_particles > 0 && (!samples || !gamma || !energy_eV)) return RAD_EINVAL;
   if (samples && (reinterpret_cast<uintptr_t>(samples) & 15u)) return RAD_EINVAL;
+  // the bin count is compared without forming a product that could overflow
+  const int64_t max_bins = static_cast<int64_t>((kNoallocBytes - kCtrlBytes) / sizeof(double));
+  if (n_omega > max_bins || n_angles > max_bins / n_omega) return RAD_ETOOBIG;
   const int64_t bins = n_omega * n_angles;
-  if (bins > static_cast<int64_t>((kNoallocBytes - kCtrlBytes) / sizeof(double))) return RAD_ETOOBIG;
 
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return RAD_ECUDA;
   int major = 0, sms = 0;
-  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess) return RAD_ECUDA;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+    return RAD_ECUDA;
   if (major < 10) return RAD_EUNSUPPORTED;
   unsigned char *base = nullptr;
   if (scratch_address(dev, &base) != RAD_OK) return RAD_ECUDA;
@@ -83,7 +86,7 @@ extern "C" int rad_spectrum_noalloc(const double *samples, int64_t n_samples_tot
   int64_t chunks = 1;
   if (tiles < 4 * resident) chunks = (4 * resident + tiles - 1) / tiles;
   if (chunks > n_particles) chunks = n_particles > 0 ? n_particles : 1;
-  const int64_t fit = static_cast<int64_t>((kNoallocBytes - kCtrlBytes) / sizeof(double)) / bins;
+  const int64_t fit = max_bins / bins;
   if (chunks > fit) chunks = fit;
 
   Params P{};
@@ -111,6 +114,9 @@ extern "C" int rad_spectrum_noalloc(const double *samples, int64_t n_samples_tot
   P.status = ctrl + 1;
   P.part = reinterpret_cast<double *>(base + kCtrlBytes);
   P.table = nullptr;  // the mixed kernel has no table
+  // grid maxima of the mixed form's error-budget guard, after the three control ints
+  P.grid_max = reinterpret_cast<unsigned long long *>(base + 16);
+  P.phase_budget = kMixedPhaseBudget;
   sh.grid = static_cast<int>(P.n_items < resident ? P.n_items : resident);
   if (sh.grid < 1) sh.grid = 1;
 
@@ -120,10 +126,10 @@ extern "C" int rad_spectrum_noalloc(const double *samples, int64_t n_samples_tot
   if (e == cudaSuccess) e = launch_mixed(P, &sh, st);
   // combine: the cube is written once (cube_new and the output are the same array)
   if (e == cudaSuccess) e = launch_finalize_status(P, out_cube, out_cube, 0, ctrl + 2, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return RAD_ECUDA;
+  // the status word comes back on the caller's stream: one wait, for this call's work only
   int status = 0;
-  e = cudaMemcpy(&status, ctrl + 1, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&status, ctrl + 1, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return RAD_ECUDA;
   return status;
 }

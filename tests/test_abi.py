@@ -151,3 +151,15 @@ def test_binding_return_types_match_the_header(lib):
         assert getattr(lib, name).restype == kinds[ret], (name, ret, getattr(lib, name).restype)
         seen += 1
     assert seen == len(rad.header_symbols())
+
+
+def test_noalloc_rejects_oversize_shapes_without_overflow(lib):
+    """rad_spectrum_noalloc compares n_omega * n_angles with its fixed scratch without forming a
+    product that could overflow: 2^32 x 2^32 (whose int64 product wraps to 0) and other
+    oversize shapes return RAD_ETOOBIG before any device work."""
+    P = ctypes.c_void_p(256)  # never dereferenced: every call below fails its host checks
+    for n_omega, n_angles in ((1 << 32, 1 << 32), (1 << 62, 4), (3, 1 << 62), (4194273, 1), (2048, 4096)):
+        rc = lib.rad_spectrum_noalloc(P, 4, P, 2, P, P, None, P, n_omega, P, P, n_angles, 0, P, None)
+        assert rc == rad.RAD_ETOOBIG, (n_omega, n_angles, rc)
+    assert lib.rad_spectrum_noalloc(P, 4, P, 2, P, P, None, P, -1, P, P, 4, 0, P, None) == rad.RAD_EINVAL
+    assert lib.rad_spectrum_noalloc(P, 4, P, 2, P, P, None, P, 4, P, P, 4, 7, P, None) == rad.RAD_EINVAL
