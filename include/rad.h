@@ -40,7 +40,9 @@
  *     Checks that need device data (finite values, offsets, gamma > 1, hw > 0,
  *     hw < E in quantum modes) run in a small kernel on the same stream; a failure
  *     skips the computation and is recorded in the per-device status word read by
- *     rad_device_status(). Outputs of a call whose device checks failed are left
+ *     rad_device_status(). RAD_MIXED also bounds its in-tile phase offsets on the device
+ *     and records RAD_EPRECISION when they exceed its error budget (see
+ *     rad_plan_set_phase_budget). Outputs of a call whose device checks failed are left
  *     unchanged.
  *   - Each device-side wait in the kernels has an iteration limit; if it runs out
  *     the kernel records RAD_ETIMEOUT in the status word and returns.
@@ -65,6 +67,8 @@ extern "C" {
 #define RAD_EUNSUPPORTED 5 /* valid request this build cannot serve (e.g. no sm_103a GPU) */
 #define RAD_EDATA 6        /* device-side data check failed (see rad.h conventions)       */
 #define RAD_ETOOBIG 7      /* request exceeds rad_spectrum_noalloc's fixed scratch        */
+#define RAD_EPRECISION 8   /* RAD_MIXED: in-tile phase offsets beyond its error budget;   */
+                           /* the same call in RAD_FP64_DF has no such limit              */
 
 /* ---- enums ---- */
 #define RAD_CLASSICAL 0
@@ -145,13 +149,19 @@ int rad_spectrum_host(const double *samples, int64_t n_samples_total, const int6
  *   Scratch: one fixed device array of 32 MiB inside the library, held by every GPU that
  *   loads the library until the process exits. Requests with n_omega * n_angles above
  *   (32 MiB - 256 B) / 8 = 4,194,272 bins return RAD_ETOOBIG before anything is enqueued.
- *   The first call on a device looks up the array's device address (once per device).
+ *   The first call on a device looks up the array's device address (once per device, with
+ *   that device current) and keeps it for the life of the process; make that first call
+ *   outside any stream capture. cudaDeviceReset unloads the library's device code, so the
+ *   kept address is stale afterwards: a process that resets a device must not call this
+ *   entry point on that device again.
  *   Every call shares the array: calls that overlap on the GPU (other streams, other host
  *   threads) race on it, so the caller must serialize them. Each call clears the control
  *   words it needs and leaves its partial sums in the array.
  *   Synchronous: returns after the cube is complete; device-side data check failures
- *   come back as RAD_EDATA (the cube is then left unchanged), bounded-wait expiry as
- *   RAD_ETIMEOUT. Calls no cudaMalloc, cudaFree or allocating library routine.
+ *   come back as RAD_EDATA and phase offsets beyond the mixed form's default error budget
+ *   (see rad_plan_set_phase_budget) as RAD_EPRECISION (the cube is then left unchanged),
+ *   bounded-wait expiry as RAD_ETIMEOUT. Calls no cudaMalloc, cudaFree or allocating library
+ *   routine.
  */
 int rad_spectrum_noalloc(const double *samples, int64_t n_samples_total, const int64_t *offsets,
                          int64_t n_particles, const double *gamma, const double *energy_eV,
@@ -240,6 +250,20 @@ int rad_plan_set_prepass(rad_plan plan, int enable);
  * FP64 plans or the inline-preparation kernel (plan unchanged). The autotuner also tries these.
  */
 int rad_plan_set_sincos_split(rad_plan plan, int every);
+
+/*
+ * rad_plan_set_phase_budget -- RAD_MIXED plans only: the error-budget guard's limit, in radians
+ * (default 8192). Every RAD_MIXED call bounds its in-tile phase offsets on the device,
+ *   X = max over particles and samples of w*_max (c_max |t_k - t_ref| + |dz_k - dz_ref|
+ *       + max|theta_x| |x_k - x_ref| + max|theta_y| |y_k - y_ref|),
+ * with t_ref etc. the middle sample of the sample's time tile, c_max = 1/(2 gamma^2) + max
+ * theta^2/2 over the grid and w*_max the particle's largest w* (Sec. II phase). The per-term phase
+ * error of the FP32 offsets and the SFU sin/cos grows in proportion to X (about 2.7e-7 X rad); a
+ * call with X above the limit records RAD_EPRECISION in the status word and leaves its outputs
+ * unchanged. Raise the limit only where a larger error is acceptable; RAD_FP64_DF has no such
+ * limit. RAD_EINVAL for a non-positive or non-finite value or a plan of another precision.
+ */
+int rad_plan_set_phase_budget(rad_plan plan, double radians);
 
 /*
  * rad_plan_describe -- writes a short text description of the plan's chosen launch

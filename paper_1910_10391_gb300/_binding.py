@@ -17,10 +17,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "librad.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "rad.h")
 
-RAD_OK, RAD_EINVAL, RAD_ENOMEM, RAD_ECUDA, RAD_ETIMEOUT, RAD_EUNSUPPORTED, RAD_EDATA, RAD_ETOOBIG = range(8)
+RAD_OK, RAD_EINVAL, RAD_ENOMEM, RAD_ECUDA, RAD_ETIMEOUT, RAD_EUNSUPPORTED, RAD_EDATA, RAD_ETOOBIG, RAD_EPRECISION = range(9)
 RAD_CLASSICAL, RAD_SPIN0, RAD_SPIN_HALF = 0, 1, 2
 RAD_FP64, RAD_MIXED, RAD_FP64_DF = 0, 1, 2
 RAD_NREC = 10
+RAD_PER_PARTICLE = 8  # rad_plan_create `want` bit: per-particle spectrum/bins
 RAD_TRAJ_MS, RAD_TRAJ_LL, RAD_TRAJ_MS_LOSS, RAD_TRAJ_FP32, RAD_TRAJ_MS_EL = 1, 2, 4, 8, 16
 
 
@@ -138,6 +139,8 @@ def load(build_if_missing: bool = True):
         lib.rad_plan_set_prepass.restype = c_int
         lib.rad_plan_set_sincos_split.argtypes = [P, c_int]
         lib.rad_plan_set_sincos_split.restype = c_int
+        lib.rad_plan_set_phase_budget.argtypes = [P, ctypes.c_double]
+        lib.rad_plan_set_phase_budget.restype = c_int
         lib.rad_plan_describe.argtypes = [P, ctypes.c_char_p, c_int]
         lib.rad_plan_describe.restype = c_int
         lib.rad_plan_set_timing.argtypes = [P, c_int]
@@ -478,6 +481,9 @@ class Plan:
 
     def set_sincos_split(self, every=4) -> int:
         return load().rad_plan_set_sincos_split(self._h, int(every))
+
+    def set_phase_budget(self, radians) -> int:
+        return load().rad_plan_set_phase_budget(self._h, float(radians))
 
     def describe(self) -> str:
         buf = ctypes.create_string_buffer(512)

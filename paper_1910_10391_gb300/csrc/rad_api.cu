@@ -54,7 +54,8 @@ struct rad_plan_s {
   size_t part_cap = 0;  // doubles
   double *cube_new = nullptr;
   float *prep = nullptr;  // pre-pass records (mixed precision with pp = 1), 12 floats per sample
-  int *ctrl = nullptr;    // [0] work counter, [1] call status
+  int *ctrl = nullptr;    // [0] work counter, [1] call status, then RAD_MIXED's grid maxima
+  double phase_budget = rad::kMixedPhaseBudget;  // RAD_MIXED error-budget guard (radians)
   std::string desc;
   bool timing = false;
   bool timed_once = false;
@@ -72,6 +73,8 @@ std::mutex g_mu;
 using ShapeKey = std::tuple<int, int64_t, int64_t, int64_t, int64_t, int, int, int, int>;
 std::map<ShapeKey, Choice> g_tuned;                                  // autotuned choices
 std::map<std::tuple<ShapeKey, void *>, rad_plan> g_plans;            // rad_spectrum cache
+
+constexpr size_t kCtrlBytes = 16 + sizeof(unsigned long long) * kGridMaxWords;
 
 ShapeKey key_of(int dev, int64_t ns, int64_t np, int64_t no, int64_t na, int mode, int prec, int want,
                 int nb) {
@@ -219,6 +222,11 @@ Params make_params(rad_plan p, const double *samples, const int64_t *offsets, co
   P.counter = p->ctrl;
   P.status = p->ctrl + 1;
   P.table = table;
+  // control block: [0] work counter, [1] status, bytes 16..47 the grid maxima of RAD_MIXED's guard
+  P.phase_budget = p->phase_budget;
+  P.grid_max = p->precision == RAD_MIXED
+                   ? reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(p->ctrl) + 16)
+                   : nullptr;
   return P;
 }
 
@@ -265,7 +273,7 @@ int execute(rad_plan p, const double *samples, const int64_t *offsets, const dou
   const double2 *table = device_table(&e);
   if (!table) return cuda_fail(e);
   Params P = make_params(p, samples, offsets, gamma, energy, weight, hw, tx, ty, table);
-  e = cudaMemsetAsync(p->ctrl, 0, 2 * sizeof(int), st);
+  e = cudaMemsetAsync(p->ctrl, 0, kCtrlBytes, st);
   if (e != cudaSuccess) return cuda_fail(e);
   e = launch_validate(P, d_omega, need_dom, bin_of_angle, st);
   if (e != cudaSuccess) return cuda_fail(e);
@@ -329,7 +337,7 @@ int plan_create(int64_t ns, int64_t np, int64_t no, int64_t na, int mode, int pr
   p->precision = prec;
   p->want = want;
   p->n_bins = (want & 4) ? nb : 0;
-  e = cudaMalloc(&p->ctrl, 2 * sizeof(int));
+  e = cudaMalloc(&p->ctrl, kCtrlBytes);
   if (e != cudaSuccess) {
     delete p;
     return cuda_fail(e);
@@ -406,6 +414,9 @@ const char *rad_status_string(int status) {
     case RAD_EUNSUPPORTED: return "unsupported request (needs an sm_100-class or newer GPU)";
     case RAD_EDATA: return "device-side input check failed (non-finite value, bad offsets, gamma <= 1, hw <= 0 or hw >= E)";
     case RAD_ETOOBIG: return "n_omega * n_angles exceeds the no-allocation entry point's fixed 32 MiB scratch";
+    case RAD_EPRECISION:
+      return "RAD_MIXED: the in-tile phase offsets exceed its error budget (directions far outside the emission "
+             "cone, coarse time steps or hw close to E); use RAD_FP64_DF";
     default: return "unknown status";
   }
 }
@@ -461,6 +472,13 @@ int rad_plan_set_sincos_split(rad_plan plan, int every) {
   int rc = configure(plan, c);
   if (rc) configure(plan, old);
   return rc;
+}
+
+int rad_plan_set_phase_budget(rad_plan plan, double radians) {
+  if (!plan || plan->precision != RAD_MIXED) return RAD_EINVAL;
+  if (!(radians > 0.0) || !(radians < 1e300)) return RAD_EINVAL;
+  plan->phase_budget = radians;
+  return RAD_OK;
 }
 
 int rad_plan_describe(rad_plan plan, char *buf, int len) {

@@ -65,7 +65,21 @@ struct Params {
   int *counter;    // work counter (zeroed before launch)
   int *status;     // per-call status word (zeroed before launch)
   const double2 *table;  // FP64 sincos table in global memory (kTabN entries)
+  // RAD_MIXED only (else null): grid maxima filled by the validation kernel, as the bit patterns
+  // of non-negative doubles (zeroed before launch): [0] max |theta_x|, [1] max |theta_y|,
+  // [2] max (theta_x^2 + theta_y^2)/2, [3] max hw (eV). They bound the in-tile phase offsets.
+  unsigned long long *grid_max;
+  double phase_budget;  // RAD_MIXED: largest accepted in-tile phase-offset bound (radians)
 };
+
+// RAD_MIXED's error budget: the largest in-tile phase-offset bound w*_max B_k (radians) it accepts,
+// B_k = c_max |t_k - t_ref| + |dz_k - dz_ref| + max|theta_x| |x_k - x_ref| + max|theta_y| |y_k - y_ref|
+// with c_max = 1/(2 gamma^2) + max theta^2/2 and w*_max the largest w* of the particle. The sum of
+// magnitudes bounds both the FP32 rounding of the offset (about 2^-23 of it per operand) and the SFU
+// sin/cos error (which grows as 2.5e-7 |x|). Calls above it record RAD_EPRECISION; a plan can
+// set another budget (rad_plan_set_phase_budget).
+constexpr double kMixedPhaseBudget = 8192.0;
+constexpr int kGridMaxWords = 4;
 
 // ------------------------------------------------------------------------------------
 // PTX wrappers (sm_90+ mbarrier / bulk async copy), all CTA-scoped

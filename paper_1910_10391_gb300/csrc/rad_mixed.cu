@@ -31,7 +31,8 @@ struct MixLayout {
   static constexpr int kNkWarp = T * 16 + ((MODE == RAD_SPIN_HALF) ? T * 4 : 0);
   static constexpr int kBar = kNk + NW * kNkWarp;
   static constexpr int kMisc = kBar + 16;
-  static constexpr int kTotal = kMisc + 16;
+  static constexpr int kGuard = kMisc + 16;  // error-budget guard: w*_max, c_max, max|theta_x|, max|theta_y|
+  static constexpr int kTotal = kGuard + 16;
 };
 
 template <int MODE, int R, int NW, int T>
@@ -65,6 +66,11 @@ __global__ void __launch_bounds__(NW * 32) k_mixed(const Params P) {
   uint32_t parity[2] = {0u, 0u};
   const int64_t per_chunk = static_cast<int64_t>(P.n_wt) * P.n_nt;
   int s = 0;
+  // error-budget guard (see kMixedPhaseBudget): the current particle's w*_max and c_max and the
+  // grid's max |theta_x|, |theta_y| (from the validation kernel) in shared memory, in units of
+  // the budget
+  float *s_guard = reinterpret_cast<float *>(sm + L::kGuard);
+  bool over = false;
 
   for (;;) {
     if (tid == 0) s_item[0] = atomicAdd(P.counter, 1);
@@ -128,6 +134,15 @@ __global__ void __launch_bounds__(NW * 32) k_mixed(const Params P) {
           cn = inv2g2 + th2h;
           cn_hi = static_cast<float>(cn);
           cn_lo = static_cast<float>(cn - static_cast<double>(cn_hi));
+          if (tid == 0 && P.grid_max) {
+            const double hmax = __longlong_as_double(static_cast<long long>(P.grid_max[3]));
+            const double wsm = (hmax / kHbarC) / (MODE == RAD_CLASSICAL ? 1.0 : (1.0 - hmax / En));
+            const double scale = wsm / P.phase_budget;
+            s_guard[0] = static_cast<float>(scale * (inv2g2 + __longlong_as_double(static_cast<long long>(P.grid_max[2]))));
+            s_guard[1] = static_cast<float>(scale);
+            s_guard[2] = static_cast<float>(scale * __longlong_as_double(static_cast<long long>(P.grid_max[0])));
+            s_guard[3] = static_cast<float>(scale * __longlong_as_double(static_cast<long long>(P.grid_max[1])));
+          }
 #pragma unroll
           for (int r = 0; r < R; ++r) {
             const double w = hwv[r] / kHbarC;
@@ -174,6 +189,11 @@ __global__ void __launch_bounds__(NW * 32) k_mixed(const Params P) {
           sAy[k] = static_cast<float>(rc[F_AY] * w);
           sAz[k] = static_cast<float>(rc[F_AZ] * w);
           sS0[k] = static_cast<float>(inv2g2 - (rc[F_DVZ] + 0.5 * (vx * vx + vy * vy)));
+          if (P.grid_max) {  // w*_max B_k / budget, B_k as in kMixedPhaseBudget
+            const float X = fmaf(s_guard[3], fabsf(sDy[k]),
+                                 fmaf(s_guard[2], fabsf(sDx[k]), fmaf(s_guard[0], fabsf(sDt[k]), s_guard[1] * fabsf(sDdz[k]))));
+            if (!(X <= 1.0f)) over = true;
+          }
         }
         if (tid < NW) {  // FP64 phase A at the reference sample, one per warp's direction
           const int64_t jd = static_cast<int64_t>(nt) * NW + tid;
@@ -301,6 +321,10 @@ __global__ void __launch_bounds__(NW * 32) k_mixed(const Params P) {
         if (!nxt.valid) break;
         cur = nxt;
       }
+    }
+    if (over) {  // the finalize then leaves the outputs untouched
+      set_status(P.status, RAD_EPRECISION);
+      over = false;
     }
     if (jvalid) {
 #pragma unroll

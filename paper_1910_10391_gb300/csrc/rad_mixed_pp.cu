@@ -32,13 +32,33 @@ __device__ __forceinline__ void tile_of(const Params &P, int64_t L, int64_t k, i
   km = k0 + (n - 1) / 2;
 }
 
-// One particle's records: grid x strides over its samples.
-__device__ __forceinline__ void prep_particle(const Params &P, int T, int64_t p, float *__restrict__ out) {
+// w*_max of particle p and the grid maxima of the error-budget guard (see kMixedPhaseBudget).
+struct PhaseBound {
+  double ws_max, c_max, tx_max, ty_max;
+};
+
+__device__ __forceinline__ PhaseBound phase_bound(const Params &P, double inv2g2, double E) {
+  PhaseBound b;
+  const double hmax = __longlong_as_double(static_cast<long long>(P.grid_max[3]));
+  b.ws_max = (hmax / kHbarC) / (P.mode == RAD_CLASSICAL ? 1.0 : (1.0 - hmax / E));
+  b.c_max = inv2g2 + __longlong_as_double(static_cast<long long>(P.grid_max[2]));
+  b.tx_max = __longlong_as_double(static_cast<long long>(P.grid_max[0]));
+  b.ty_max = __longlong_as_double(static_cast<long long>(P.grid_max[1]));
+  return b;
+}
+
+// One particle's records: grid x strides over its samples. Returns true when a sample's
+// in-tile phase-offset bound exceeds the mixed form's error budget.
+__device__ __forceinline__ bool prep_particle(const Params &P, int T, int64_t p, float *__restrict__ out) {
   const int64_t off = P.offsets[p];
   const int64_t L = P.offsets[p + 1] - off;
   const double g = P.gamma[p];
   const double inv2g2 = 1.0 / (2.0 * g * g);
   const double *S = P.samples + off * kRec;
+  const bool guard = P.grid_max != nullptr;
+  PhaseBound pb{0.0, 0.0, 0.0, 0.0};
+  if (guard) pb = phase_bound(P, inv2g2, P.energy[p]);
+  bool over = false;
   for (int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; k < L;
        k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     int64_t k0, km;
@@ -50,11 +70,17 @@ __device__ __forceinline__ void prep_particle(const Params &P, int T, int64_t p,
     const double w = 0.5 * (tp - tm);
     const double vx = rc[F_VX], vy = rc[F_VY];
     float *o = out + (off + k) * kPP;
+    const double dt = rc[F_T] - r0[F_T], ddz = rc[F_DZ] - r0[F_DZ];
+    const double dx = rc[F_X] - r0[F_X], dy = rc[F_Y] - r0[F_Y];
+    if (guard) {
+      const double B = pb.c_max * fabs(dt) + fabs(ddz) + pb.tx_max * fabs(dx) + pb.ty_max * fabs(dy);
+      if (!(pb.ws_max * B <= P.phase_budget)) over = true;
+    }
     float4 a, b, c;
-    a.x = static_cast<float>(rc[F_T] - r0[F_T]);
-    a.y = static_cast<float>(rc[F_DZ] - r0[F_DZ]);
-    a.z = static_cast<float>(rc[F_X] - r0[F_X]);
-    a.w = static_cast<float>(rc[F_Y] - r0[F_Y]);
+    a.x = static_cast<float>(dt);
+    a.y = static_cast<float>(ddz);
+    a.z = static_cast<float>(dx);
+    a.w = static_cast<float>(dy);
     b.x = static_cast<float>(vx);
     b.y = static_cast<float>(vy);
     b.z = static_cast<float>(rc[F_AX] * w);
@@ -67,11 +93,14 @@ __device__ __forceinline__ void prep_particle(const Params &P, int T, int64_t p,
     reinterpret_cast<float4 *>(o)[1] = b;
     reinterpret_cast<float4 *>(o)[2] = c;
   }
+  return over;
 }
 
 __global__ void k_prep_samples(const Params P, int T, float *__restrict__ out) {
   if (*reinterpret_cast<volatile int *>(P.status) != 0) return;  // device data check failed
-  for (int64_t p = blockIdx.y; p < P.n_particles; p += gridDim.y) prep_particle(P, T, p, out);
+  bool over = false;
+  for (int64_t p = blockIdx.y; p < P.n_particles; p += gridDim.y) over |= prep_particle(P, T, p, out);
+  if (over) set_status(P.status, RAD_EPRECISION);  // the integral kernel and the finalize skip
 }
 
 template <int MODE, int R, int NW, int T>

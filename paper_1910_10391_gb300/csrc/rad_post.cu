@@ -55,6 +55,26 @@ __global__ void k_validate(const Params P, const double *d_omega, int need_domeg
   for (int64_t e = t0; e < nv; e += stride)
     if (!finite_d(P.samples[e])) bad = true;
   if (bad) set_status(P.status, RAD_EDATA);
+  // RAD_MIXED: grid maxima for the error-budget guard (non-negative doubles order as their bits)
+  if (P.grid_max) {
+    double m[kGridMaxWords] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t j = t0; j < P.n_angles; j += stride) {
+      const double ux = P.theta_x[j], uy = P.theta_y[j];
+      m[0] = fmax(m[0], fabs(ux));
+      m[1] = fmax(m[1], fabs(uy));
+      m[2] = fmax(m[2], (ux * ux + uy * uy) * 0.5);
+    }
+    for (int64_t i = t0; i < P.n_omega; i += stride) m[3] = fmax(m[3], fabs(P.hw[i]));
+#pragma unroll
+    for (int w = 0; w < kGridMaxWords; ++w) {
+      double v = m[w];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+      // NaN inputs were flagged above; fmax drops them here
+      if ((threadIdx.x & 31) == 0 && v > 0.0)
+        atomicMax(&P.grid_max[w], static_cast<unsigned long long>(__double_as_longlong(v)));
+    }
+  }
 }
 
 // Combine partials into the cube, tile-transposed: part layout [chunk][..][j][i] (i fastest),
