@@ -73,6 +73,12 @@ static inline double nval(const nsum *a) { return a->s + a->c; }
 /* trapezoid weight of sample k of a trajectory with L samples (Sec. II integral, reading c1) */
 static double trap_weight(const double *smp, int64_t L, int64_t k) {
   if (L < 2) return 0.0;
+  if (g_plant == 5) { /* planted: every step taken equal to the first */
+    const double h = smp[1 * NREC + T_] - smp[0 * NREC + T_];
+    return (k == 0 || k == L - 1) ? 0.5 * h : h;
+  }
+  if (g_plant == 6 && k > 0 && k < L - 1) /* planted: forward difference for interior samples */
+    return smp[(k + 1) * NREC + T_] - smp[k * NREC + T_];
   if (k == 0) return 0.5 * (smp[1 * NREC + T_] - smp[0 * NREC + T_]);
   if (k == L - 1) return 0.5 * (smp[(L - 1) * NREC + T_] - smp[(L - 2) * NREC + T_]);
   return 0.5 * (smp[(k + 1) * NREC + T_] - smp[(k - 1) * NREC + T_]);

@@ -194,15 +194,45 @@ def radial_bins(theta_x: np.ndarray, theta_y: np.ndarray, n_bins: int, theta_max
 # --------------------------------------------------------------------------- #
 # Analytic trajectories
 # --------------------------------------------------------------------------- #
+def sample_times(kind: str, n: int, length: float, seed: int = 0, tile: int = 64) -> np.ndarray:
+    """n increasing sample times from 0 to `length`:
+      uniform     equal steps;
+      jitter      steps of relative size 1 + 0.8 (u - 1/2), u uniform (seeded);
+      geometric   steps growing geometrically, the last 8 times the first;
+      tile_jumps  steps of 1 and 3 alternating every `tile` steps, so that the spacing changes at
+                  every multiple of `tile` (the first sample of each time tile);
+      smooth      t = length (s + 0.6 sin(2 pi s) / (2 pi)) at uniform s (a smooth monotone map)."""
+    if n < 2:
+        raise ValueError("need at least 2 samples")
+    m = n - 1
+    if kind == "uniform":
+        return np.linspace(0.0, length, n)
+    if kind == "smooth":
+        s = np.linspace(0.0, 1.0, n)
+        return length * (s + 0.6 * np.sin(2.0 * math.pi * s) / (2.0 * math.pi))
+    if kind == "jitter":
+        inc = 1.0 + 0.8 * (np.random.default_rng(seed).random(m) - 0.5)
+    elif kind == "geometric":
+        inc = 8.0 ** (np.arange(m) / max(m - 1, 1))
+    elif kind == "tile_jumps":
+        inc = np.where((np.arange(m) // tile) % 2 == 0, 1.0, 3.0)
+    else:
+        raise ValueError(kind)
+    t = np.concatenate([[0.0], np.cumsum(inc)])
+    return t * (length / t[-1])
+
+
 def weak_undulator(gamma=1000.0, a=0.5e-10, lam=10e-6, n_periods=5, n_samples=4096,
-                   mass_eV=ME_EV) -> Trajectories:
-    """Planar harmonic motion x = a sin(k t), uniform samples over n_periods.
+                   mass_eV=ME_EV, times=None) -> Trajectories:
+    """Planar harmonic motion x = a sin(k t), uniform samples over n_periods (or the given
+    increasing `times`, which then set n_samples).
 
     Longitudinal variables to leading order: dvz = -vx^2/2, az = -vx*ax,
     dz = -(a k)^2/4 (t + sin(2kt)/(2k)).
     """
     k = 2.0 * math.pi / lam
-    t = np.linspace(0.0, n_periods * lam, n_samples)
+    t = np.linspace(0.0, n_periods * lam, n_samples) if times is None else np.asarray(times, np.float64)
+    n_samples = t.shape[0]
     s = np.zeros((n_samples, NREC))
     s[:, 0] = t
     s[:, 1] = a * np.sin(k * t)
@@ -430,13 +460,15 @@ def undulator_K(B0_T: float, lam_u: float) -> float:
 
 
 def elliptical_undulator(gamma=2000.0, a=0.4e-10, b=0.25e-10, phase=0.7, lam=10e-6, n_periods=3,
-                         n_samples=3073, mass_eV=ME_EV) -> Trajectories:
-    """x = a sin(kt), y = b sin(kt + phase): motion in both transverse planes.
+                         n_samples=3073, mass_eV=ME_EV, times=None) -> Trajectories:
+    """x = a sin(kt), y = b sin(kt + phase): motion in both transverse planes, uniform samples
+    over n_periods (or the given increasing `times`, which then set n_samples).
 
     dvz = -(vx^2 + vy^2)/2, az = -(vx ax + vy ay), dz the exact integral of dvz from t = 0.
     """
     k = 2.0 * math.pi / lam
-    t = np.linspace(0.0, n_periods * lam, n_samples)
+    t = np.linspace(0.0, n_periods * lam, n_samples) if times is None else np.asarray(times, np.float64)
+    n_samples = t.shape[0]
     s = np.zeros((n_samples, NREC))
     s[:, 0] = t
     s[:, 1] = a * np.sin(k * t)

@@ -256,6 +256,54 @@ def test_trapezoid_is_second_order():
     assert np.all((ratio > 3.5) & (ratio < 4.5))
 
 
+def _nonuniform_errors():
+    """Trapezoid sums on non-uniform sample times (Sec. IV: the solver returns the trajectory at
+    caller-controlled times; quadrature reading: w_k = (t_{k+1} - t_{k-1})/2). Returns, per time
+    grid (a smooth monotone map of uniform times; steps of 1 and 3 alternating over fixed
+    fractions of the trajectory), the Richardson ratios of three refinements and the relative
+    distance of the extrapolated limit from the uniform grid's extrapolated limit: the same
+    integral, so the limits must agree to the O(h^4) remainder. At 4097 samples the trapezoid
+    error itself is 1e-4 (uniform) to 2.4e-4 (steps of 1 and 3); the extrapolated limits agree to
+    1e-7, so the bound 1e-6 sits 100 times below the unextrapolated error."""
+    hw1 = I.undulator_first_harmonic_eV(G1, A1, LAM1)
+    grid = I.Grid(np.array([0.9 * hw1, 2.5 * hw1]), np.array([0.3 / G1, 1.0 / G1]),
+                  np.array([0.1 / G1, 0.4 / G1]), np.ones(2))
+    T = 2 * LAM1
+
+    def limit(kind):
+        vals = []
+        for L in (1025, 2049, 4097):
+            t = I.sample_times(kind, L, T, tile=(L - 1) // 8)
+            vals.append(O.spectrum_cube(I.weak_undulator(G1, A1, LAM1, times=t), grid, O.CLASSICAL).ravel())
+        ratio = (vals[0] - vals[1]) / (vals[1] - vals[2])
+        return ratio, vals[2] + (vals[2] - vals[1]) / 3.0
+
+    _, ref = limit("uniform")
+    out = {}
+    for kind in ("smooth", "tile_jumps"):
+        ratio, lim = limit(kind)
+        out[kind] = (ratio, float(np.abs(lim / ref - 1.0).max()))
+    return out
+
+
+def test_nonuniform_times_converge_to_the_same_integral():
+    for kind, (ratio, dist) in _nonuniform_errors().items():
+        assert np.all((ratio > 3.5) & (ratio < 4.5)), (kind, ratio)
+        assert dist < 1e-6, (kind, dist)
+
+
+@pytest.mark.parametrize("plant", [5, 6])
+def test_planted_quadrature_mistakes_are_caught(plant):
+    """Every step taken equal to the first, or forward differences for the interior weights:
+    both agree with the trapezoid rule on uniform grids and must fail on non-uniform ones."""
+    O.set_plant(plant)
+    try:
+        res = _nonuniform_errors()
+    finally:
+        O.set_plant(0)
+    assert any(not np.all((r > 3.5) & (r < 4.5)) or d > 1e-6 for r, d in res.values())
+
+
 def test_spin0_is_lindhard_substitution():
     """dI_q/dhw(w) = (w/w*) dI_c/dhw(w*), per direction, w* = w/(1 - hw/E)."""
     tr = I.elliptical_undulator(gamma=300.0)
