@@ -534,6 +534,14 @@ def workload_electron_batch(n_particles=4096, seed=4, n_omega=1024, n_side=32, m
     return tr, _ensemble_grid(E, 20.0, n_omega, n_side)
 
 
+def workload_strong_undulator_angular(samples_per_period: int = 2048, n_omega: int = 1000, n_side: int = 32):
+    """The paper's second integral test (Sec. IV): the same 2 GeV undulator, dI/dOmega over the
+    photon energies 0-500 eV in a window of half-width 5/gamma: n_omega linear photon energies
+    (500/n_omega ... 500 eV; the trapezoid over them is the energy integral) and n_side x n_side
+    cell-centred directions within +-5/gamma."""
+    return workload_strong_undulator(samples_per_period, n_omega, n_side, 5.0)
+
+
 def workload_strong_undulator(samples_per_period: int = 2048, n_omega: int = 256, n_side: int = 8,
                               half_angle_gammas: float = 0.5):
     """The paper's integral test (Sec. IV): 2 GeV electron, planar undulator with 53 mm period,

@@ -90,3 +90,67 @@ def strong_undulator_on_axis(n, K, gamma, N):
     xi = n * K * K / (4 * (1 + K * K / 2))
     Fn = n * n * K * K / (1 + K * K / 2) ** 2 * (jv((n - 1) // 2, xi) - jv((n + 1) // 2, xi)) ** 2
     return O.ALPHA * N * N * gamma * gamma * Fn
+
+
+def planar_undulator_exact(hw_eV, theta_x, theta_y, gamma, K, lam_u, N):
+    """|I|^2 (the S of the classical model, before alpha/(4 pi^2)) of the planar undulator
+    trajectory x = K/(gamma k) sin(kt), dz = -(K/gamma)^2/4 (t + sin(2kt)/(2k)) over N whole periods,
+    for any photon energy, as the continuous integral of Sec. II's expanded form evaluated in
+    closed form (independent of the time-domain sum):
+      * by parts, f = d/dt[(n - beta)/(1 - n.beta)] and d(phase)/dt = w (1 - n.beta), so
+        I = [g e^{i phase}]_0^T - i w int (n - beta) e^{i phase} dt with g = (n - beta)/(1 - n.beta);
+        g is periodic and the phase gains w_bar T over whole periods, so the boundary term is
+        g(0) (e^{i w_bar T} - 1);
+      * phase = w_bar t + xi sin(2kt) - eta sin(kt), w_bar = w (1 + K^2/2 + gamma^2 theta^2)/(2 gamma^2),
+        xi = w K^2/(8 gamma^2 k), eta = w theta_x K/(gamma k); by Jacobi-Anger
+        e^{i phase} = sum_j C_j e^{i (w_bar + j k) t}, C_j = sum_m J_m(xi) J_{2m-j}(eta);
+      * the transverse and longitudinal parts of n - beta are trigonometric polynomials
+        (theta_x - (K/gamma) cos kt, theta_y, c0 + (K^2/(4 gamma^2)) cos 2kt with
+        c0 = 1/(2 gamma^2) - theta^2/2 + K^2/(4 gamma^2)), so each integral is a sum of
+        G(W) = int_0^T e^{i W t} dt.
+    At a resonance (w_bar = n k) only the terms with j = -n survive and the result is the
+    textbook generalized-Bessel angular-spectral density of harmonic n.
+    hw_eV [n_omega], theta_x/theta_y [n_angles]; returns [n_omega][n_angles]."""
+    from scipy.special import jv
+    hw = np.asarray(hw_eV, np.float64)[:, None]
+    tx = np.asarray(theta_x, np.float64)[None, :]
+    ty = np.asarray(theta_y, np.float64)[None, :]
+    k = 2.0 * np.pi / lam_u
+    T = N * lam_u
+    w = hw / O.HBARC_EV_M
+    g2 = gamma * gamma
+    th2 = tx * tx + ty * ty
+    wbar = w * (1.0 + 0.5 * K * K + g2 * th2) / (2.0 * g2)
+    xi = w * K * K / (8.0 * g2 * k)
+    eta = w * tx * K / (gamma * k)
+    mmax = int(np.ceil(np.max(xi))) + 20
+    jmax = 2 * mmax + int(np.ceil(np.max(np.abs(eta)))) + 24
+    m = np.arange(-mmax, mmax + 1)
+    Jm = jv(m[:, None, None], xi[None, :, :] * np.ones_like(tx)[None, :, :])  # [m][i][j]
+    pmax = 2 * mmax + jmax
+    Jp = jv(np.arange(-pmax, pmax + 1)[:, None, None], eta[None, :, :] * np.ones_like(hw)[None, :, :])
+
+    def C(j):
+        return np.einsum("mij,mij->ij", Jm, Jp[2 * m - j + pmax])
+
+    def G(W):
+        # int_0^T e^{iWt} dt = T e^{iWT/2} sinc(WT/2), without 0/0
+        return T * np.exp(0.5j * W * T) * np.sinc(W * T / (2.0 * np.pi))
+
+    js = np.arange(-jmax, jmax + 1)
+    Gs = {j: G(wbar + j * k) for j in range(-jmax - 2, jmax + 3)}
+    e0 = np.zeros(wbar.shape, complex)
+    c1 = np.zeros(wbar.shape, complex)
+    c2 = np.zeros(wbar.shape, complex)
+    for j in js:
+        Cj = C(j)
+        e0 += Cj * Gs[j]
+        c1 += 0.5 * Cj * (Gs[j + 1] + Gs[j - 1])
+        c2 += 0.5 * Cj * (Gs[j + 2] + Gs[j - 2])
+    c0 = 1.0 / (2.0 * g2) - 0.5 * th2 + K * K / (4.0 * g2)
+    D0 = 1.0 / (2.0 * g2) + 0.5 * th2 + K * K / (2.0 * g2) - tx * K / gamma
+    ring = np.exp(1j * wbar * T) - 1.0
+    Ix = (tx - K / gamma) / D0 * ring - 1j * w * (tx * e0 - (K / gamma) * c1)
+    Iy = ty / D0 * ring - 1j * w * (ty * e0)
+    Iz = (c0 + K * K / (4.0 * g2)) / D0 * ring - 1j * w * (c0 * e0 + (K * K / (4.0 * g2)) * c2)
+    return np.abs(Ix) ** 2 + np.abs(Iy) ** 2 + np.abs(Iz) ** 2

@@ -17,7 +17,7 @@ from scipy.special import jv, kv
 import oracle as O
 from paper_1910_10391_gb300 import inputs as I
 
-from helpers import strong_undulator_on_axis
+from helpers import planar_undulator_exact, strong_undulator_on_axis
 
 PREF = O.ALPHA / (4.0 * math.pi ** 2)
 
@@ -424,6 +424,55 @@ def test_strong_undulator_golden_peak():
     odd = ns % 2 == 1
     np.testing.assert_allclose(on[odd], ref[odd], rtol=1e-12)
     assert np.all(np.abs(on[~odd]) < 1e-20 * ref.max())
+
+
+def _strong():
+    g = 2.0e9 / I.ME_EV
+    K = I.undulator_K(1.0, 0.053)
+    return g, K, 0.053, 20
+
+
+def test_strong_undulator_off_axis_line_heights():
+    """Sec. IV integral test, off axis: at each harmonic's resonance w_n(theta) = 2 gamma^2 n k /
+    (1 + K^2/2 + gamma^2 theta^2) the sum over whole periods equals the generalized-Bessel line height
+    (helpers.planar_undulator_exact; the periodic integrand makes the trapezoid sum spectrally
+    exact), for directions off axis in x, y and both, harmonics 1 to 9."""
+    g, K, lam, N = _strong()
+    tr = I.planar_undulator(g, K, lam, N, 2048)
+    k = 2 * math.pi / lam
+    for gx, gy in [(0.5, 0.0), (1.5, 0.7), (0.0, 2.0), (3.0, -2.5), (4.5, 1.0)]:
+        ns = np.arange(1, 10)
+        hw = 2 * g * g * ns * k * I.HBARC_EV_M / (1 + K * K / 2 + gx * gx + gy * gy)
+        grid = I.Grid(hw, np.array([gx / g]), np.array([gy / g]), np.ones(1))
+        got = O.spectrum_cube(tr, grid, O.CLASSICAL)[:, 0]
+        ref = PREF * planar_undulator_exact(hw, [gx / g], [gy / g], g, K, lam, N)[:, 0]
+        assert np.abs(got - ref).max() <= 1e-12 * ref.max(), (gx, gy, np.abs(got / ref - 1).max())
+
+
+def test_strong_undulator_angular_distribution():
+    """Sec. IV's second integral test: the angular-spectral density over 0-500 eV at directions
+    up to 5/gamma off axis, and its energy integral dI/dOmega, against the closed form at every
+    photon energy (helpers.planar_undulator_exact, which includes the boundary term off
+    resonance). The trapezoid sum converges to it as h^2 (ratio 4 per halving of the step); the
+    Richardson value of 1024 and 2048 samples per period agrees to 1e-9 of each direction's peak
+    (observed 3e-11)."""
+    g, K, lam, N = _strong()
+    hw = np.linspace(1.25, 500.0, 400)
+    tx = np.array([0.0, 0.7, 2.0, -3.5, 4.6]) / g
+    ty = np.array([0.0, 0.4, -1.5, 2.0, 0.2]) / g
+    grid = I.Grid(hw, tx, ty, np.ones(5))
+    ref = PREF * planar_undulator_exact(hw, tx, ty, g, K, lam, N)
+    r = [O.spectrum_cube(I.planar_undulator(g, K, lam, N, spp), grid, O.CLASSICAL) for spp in (512, 1024, 2048)]
+    pk = ref.max(0)
+    e = [np.abs(x - ref).max(0) / pk for x in r]
+    assert np.all((e[0] / e[1] > 3.5) & (e[0] / e[1] < 4.5) & (e[1] / e[2] > 3.5) & (e[1] / e[2] < 4.5)), e
+    rich = (4 * r[2] - r[1]) / 3
+    assert np.all(np.abs(rich - ref).max(0) <= 1e-9 * pk)
+    dIdO, dIdO_ref = np.trapezoid(rich, hw, axis=0), np.trapezoid(ref, hw, axis=0)
+    assert np.all(np.abs(dIdO / dIdO_ref - 1) < 1e-9), dIdO / dIdO_ref - 1
+    # and at a single resolution the h^2 error of the energy integral stays below 1e-5 at 2048
+    # samples per period (the resolution of the E2 workload)
+    assert np.all(np.abs(np.trapezoid(r[2], hw, axis=0) / dIdO_ref - 1) < 1e-5)
 
 
 def test_reduce_partitions():

@@ -1,4 +1,5 @@
-"""Further workloads through the C ABI against the oracle: the paper's strong undulator, and a
+"""Further workloads through the C ABI against the oracle: the paper's strong undulator (forward
+spectrum, on-axis harmonics and the angular distribution over 0-500 eV within 5/gamma), and a
 batch whose record array exceeds 2^31 doubles (64-bit indexing)."""
 import numpy as np
 import pytest
@@ -7,7 +8,8 @@ import oracle as O
 import paper_1910_10391_gb300 as rad
 from paper_1910_10391_gb300 import inputs as I
 
-from helpers import assert_fp64_close, assert_mixed_close, gpu_cube, strong_undulator_on_axis
+from helpers import (assert_fp64_close, assert_mixed_close, gpu_cube, planar_undulator_exact,
+                     strong_undulator_on_axis)
 
 pytestmark = pytest.mark.gpu
 
@@ -37,6 +39,41 @@ def test_strong_undulator_harmonics_closed_form(precision):
     odd = ns % 2 == 1
     np.testing.assert_allclose(got[odd], ref[odd], rtol=1e-9 if precision == rad.RAD_FP64 else 1e-4)
     assert np.all(np.abs(got[~odd]) <= (1e-15 if precision == rad.RAD_FP64 else 1e-7) * ref.max())
+
+
+@pytest.mark.parametrize("precision", [rad.RAD_FP64, rad.RAD_FP64_DF, rad.RAD_MIXED])
+def test_strong_undulator_angular_distribution(precision):
+    """Sec. IV's second integral test at full size: 40961 samples, 1000 photon energies over
+    0-500 eV, 32 x 32 directions within 5/gamma. The cube against the oracle on 24 seeded
+    directions (all energies), and dI/dOmega (the trapezoid over the energies) of those directions
+    against the oracle's and, within the quadrature's h^2 error (below 1e-5 at 2048 samples per
+    period, pinned on the CPU), against the closed form; the whole map is finite and keeps the
+    theta_y -> -theta_y symmetry of motion in the x-z plane (Sec. II integrand with y = 0)."""
+    tr, grid = I.workload_strong_undulator_angular()
+    g, K = float(tr.gamma[0]), I.undulator_K(1.0, 0.053)
+    cube = gpu_cube(tr, grid, rad.RAD_CLASSICAL, precision)["cube"]
+    rng = np.random.default_rng(21)
+    js = np.sort(rng.choice(grid.n_angles, 24, replace=False))
+    sub = I.Grid(grid.hbar_omega_eV, grid.theta_x[js], grid.theta_y[js], grid.d_omega[js])
+    ref = O.spectrum_cube(tr, sub, O.CLASSICAL)
+    hw = grid.hbar_omega_eV
+    dIdO = np.trapezoid(cube, hw, axis=0)
+    dIdO_ref = np.trapezoid(ref, hw, axis=0)
+    exact = O.ALPHA / (4 * np.pi ** 2) * planar_undulator_exact(hw, sub.theta_x, sub.theta_y, g, K, 0.053, 20)
+    assert np.all(np.abs(dIdO_ref / np.trapezoid(exact, hw, axis=0) - 1) < 1e-5)
+    if precision == rad.RAD_MIXED:
+        for c in range(len(js)):
+            assert_mixed_close(cube[:, js[c]], ref[:, c])
+        np.testing.assert_allclose(dIdO[js], dIdO_ref, rtol=1e-4)
+    else:
+        for c in range(len(js)):
+            assert_fp64_close(cube[:, js[c]], ref[:, c])
+        np.testing.assert_allclose(dIdO[js], dIdO_ref, rtol=1e-9)
+    assert np.all(np.isfinite(dIdO)) and dIdO.min() > 0
+    # the cell-centred grid holds (theta_x, theta_y) and (theta_x, -theta_y) in rows iy and 31 - iy
+    m = dIdO.reshape(32, 32)
+    assert np.allclose(grid.theta_y.reshape(32, 32), -grid.theta_y.reshape(32, 32)[::-1, :], rtol=0, atol=1e-18)
+    np.testing.assert_allclose(m, m[::-1, :], rtol=1e-9 if precision != rad.RAD_MIXED else 1e-4)
 
 
 def test_record_array_beyond_2_pow_31_doubles():
