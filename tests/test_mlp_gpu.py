@@ -54,6 +54,62 @@ def test_forward_and_gradients_match_reference():
     m.close()
 
 
+def test_gradients_elementwise_at_the_product_shape():
+    """The surrogate's own shape (62 features -> 3 x 256 -> 2048 outputs, batch 1024, so the
+    weight-gradient GEMMs take the split-K path): every gradient element against the FP64
+    reference with the GPU's BF16-rounded weights. The GEMM operands of layers >= 1 are BF16
+    (relative rounding <= 2^-9 each) with FP32 accumulation, so each element's error is bounded by
+    a small multiple of 2^-9 times the sum of the magnitudes of the products it adds up
+    (oracle.mlp.grad_magnitudes), the multiple covering the two rounded operands and the rounding
+    carried back through the layers."""
+    import torch
+    rng = np.random.default_rng(5)
+    n_in, width, depth, n_out, B = 62, 256, 3, 2048, 1024
+    m = rad.MLP(n_in, width, depth, n_out, max_batch=B, seed=8)
+    x = rng.uniform(-1, 1, (B, n_in)).astype(np.float32)
+    t = rng.normal(0, 1, (B, n_out)).astype(np.float32)
+    mask = np.where(rng.random((B, n_out)) < 0.8, rng.uniform(0.02, 1.0, (B, n_out)), 0.0).astype(np.float32)
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    m.backward(torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda(), loss, mask=torch.from_numpy(mask).cuda())
+    torch.cuda.synchronize()
+    g = m.get(1).astype(np.float64)
+    p = gpu_params_for_reference(m, n_in, width, depth, n_out)
+    _, g_ref = M.loss_and_grad(p, x, t, n_in, width, depth, n_out, mask=mask)
+    mag = M.grad_magnitudes(p, x, t, n_in, width, depth, n_out, mask=mask)
+    ratio = np.abs(g - g_ref) / (2.0 ** -9 * mag + 1e-30)
+    lay, _ = M.layout(n_in, width, depth, n_out)
+    worst = [float(ratio[wo:bo + fo].max()) for (wo, bo, fo, fi) in lay]
+    print("max |dg| / (2^-9 sum|products|) per layer:", worst, "p99:", float(np.quantile(ratio, 0.99)))
+    assert ratio.max() <= 8.0, worst
+    m.close()
+
+
+def test_adamw_matches_reference():
+    """Two AdamW steps (moments, bias correction, decoupled weight decay) against the FP64
+    reference fed the GPU's own gradients; eps comparable to the gradients so that the update is
+    not just their sign."""
+    import torch
+    rng = np.random.default_rng(6)
+    n_in, width, depth, n_out, B = 3, 64, 2, 32, 64
+    m = rad.MLP(n_in, width, depth, n_out, max_batch=B, seed=2)
+    x = torch.from_numpy(rng.uniform(-1, 1, (B, n_in)).astype(np.float32)).cuda()
+    t = torch.from_numpy(rng.normal(0, 1, (B, n_out)).astype(np.float32)).cuda()
+    lr, b1, b2, wd = 1e-2, 0.8, 0.95, 0.05
+    p = m.get(0).astype(np.float64)
+    mom, vel = np.zeros_like(p), np.zeros_like(p)
+    for step in (1, 2):
+        m.backward(x, t)
+        g = m.get(1).astype(np.float64)
+        eps = float(np.median(np.abs(g)))
+        m.adamw(lr, b1, b2, eps, wd)
+        torch.cuda.synchronize()
+        p, mom, vel = M.adamw_step(p, g, mom, vel, step, lr, b1, b2, eps, wd)
+        np.testing.assert_allclose(m.get(2), mom, rtol=1e-5, atol=1e-7 * np.abs(mom).max())
+        np.testing.assert_allclose(m.get(3), vel, rtol=1e-5, atol=1e-7 * np.abs(vel).max())
+        np.testing.assert_allclose(m.get(0), p, rtol=0, atol=2e-6 * (1 + np.abs(p)).max())
+    m.close()
+
+
 def test_training_reduces_loss():
     import torch
     rng = np.random.default_rng(2)
