@@ -38,6 +38,7 @@ SHAPES = {0: (2, 8, 256), 2: (2, 4, 256)}
 # model, counted by ncu (smsp__inst_executed_pipe_fp64, smsp__inst_executed on 1 particle x 20000
 # samples x 128 hw x 32 x 32 directions)
 DF_FP64_OPS_PER_TERM = {0: 2.12, 2: 2.36}
+FP64_OPS_PER_TERM = {0: 20.0, 2: 22.76}
 DF_INST_PER_32_TERMS = {0: 182.8, 2: 210.0}
 WORKLOAD = ("positron ensemble: 1024 e+ at 10 GeV, harmonic planar well (U0 = 20 eV, d_p = 1.92 A), "
             "RK4 + scattering kicks, 20000 samples over 100 um; 512 log hw in [1e-4 E, 0.5 E] x 64x64 "
@@ -74,7 +75,11 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--batch", type=int, default=32, help="particles per step (mixed form)")
     ap.add_argument("--fp64-batch", type=int, default=1, help="particles per plain-FP64 step")
-    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--df-batch", type=int, default=4, help="particles per double-float step")
+    ap.add_argument("--df-steps", type=int, default=3)
+    ap.add_argument("--batch-slice", type=int, default=512,
+                    help="electrons of the 4096-electron lognormal batch in its graph launch (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune", action="store_true",
@@ -163,6 +168,123 @@ def run_oracle_sample(tr, grid, n_dirs, modes):
     dt = time.perf_counter() - t0
     terms = len(modes) * len(bi) * N_SAMP
     return vals, bi, bj, terms, dt, O.max_threads()
+
+
+# --------------------------------------------------------------------------- other workloads
+def time_launches(torch, stream, fn, reps):
+    """CUDA-event milliseconds of fn() on `stream`, per repetition, after one warm-up call."""
+    fn()
+    stream.synchronize()
+    out = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        stream.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return out
+
+
+def undulator_leg(rad, torch, dev, reps=5):
+    """The analytic single-trajectory workload (e+ at gamma = 1000, x = a sin(2 pi t / lambda),
+    4096 samples over 5 periods; 128 linear hw up to 1.2 x the first harmonic x 16 x 16
+    directions within +-2/gamma), classical, in every precision; one plan call per launch."""
+    from paper_1910_10391_gb300 import inputs as I
+    tr, grid = I.workload_undulator_4096()
+    inp = rad.DeviceInputs(tr, grid, device=dev)
+    terms = tr.n_total * grid.n_omega * grid.n_angles
+    st = torch.cuda.current_stream()
+    res, cubes = {}, {}
+    for prec, name in ((rad.RAD_FP64, "fp64"), (rad.RAD_FP64_DF, "fp64_df"), (rad.RAD_MIXED, "mixed")):
+        p = rad.Plan(inp.n_samples, inp.n_particles, inp.n_omega, inp.n_angles, rad.RAD_CLASSICAL, prec, 1, 0)
+        out = torch.empty(inp.n_omega * inp.n_angles, dtype=torch.float64, device=dev)
+
+        def run():
+            rc = p.execute(*inp.args(), out, None, None, None)
+            if rc:
+                raise rad.RadError(rc, "rad_plan_execute")
+
+        ms = time_launches(torch, st, run, reps)
+        res[name] = {"ms_per_call": statistics.median(ms), "terms_per_s": terms / (statistics.median(ms) * 1e-3),
+                     "shape": p.describe()}
+        cubes[name] = out.view(inp.n_omega, inp.n_angles).cpu().numpy()
+        p.close()
+    return {"workload": "undulator: e+ gamma 1000, a = 0.5 A, lambda = 10 um, 4096 uniform samples over 5 "
+                        "periods; 128 linear hw to 1.2 x the first harmonic x 16x16 directions within +-2/gamma; "
+                        "classical", "terms_per_call": terms, "forms": res,
+            "timing": f"CUDA events around one plan call (checks, kernel, combine), median of {reps}"}, (tr, grid, cubes)
+
+
+def batch_leg(rad, torch, dev, n, tune_particles=8, tune_budget_ms=15000, seed=11):
+    """The lognormal electron batch (20 GeV e-, lengths clip(exp(N(ln 2e4, ln10/3))), 2e3, 2e5),
+    BCK spin-1/2 with recoil, 1024 log hw x 32x32 directions): its first n electrons (the
+    generator's streams are per particle, so they are exactly the full batch's first n) in one
+    autotuned, graph-captured launch."""
+    from paper_1910_10391_gb300 import inputs as I
+    import numpy as np
+    L = I.lognormal_lengths(4096, seed=4)[:n]
+    tr = I.channeling(n, 20e9, -1, L, 5e-9, seed=4)
+    tr.weight[:] = 1.0 / 4096
+    grid = I._ensemble_grid(20e9, 20.0, 1024, 32)
+    inp = rad.DeviceInputs(tr, grid, device=dev)
+    mode = rad.RAD_SPIN_HALF
+    plan = rad.Plan(inp.n_samples, inp.n_particles, inp.n_omega, inp.n_angles, mode, rad.RAD_MIXED, 1, 0)
+    sub = rad.DeviceInputs(tr.subset(range(tune_particles)), grid, device=dev)
+    tp = rad.Plan(sub.n_samples, sub.n_particles, sub.n_omega, sub.n_angles, mode, rad.RAD_MIXED, 1, 0)
+    tmp = torch.empty(sub.n_omega * sub.n_angles, dtype=torch.float64, device=dev)
+    t0 = time.perf_counter()
+    rc = tp.autotune(*sub.args(), tmp, None, None, None, budget_ms=tune_budget_ms)
+    if rc:
+        raise rad.RadError(rc, "rad_plan_autotune")
+    tune_s = time.perf_counter() - t0
+    d = dict(kv.split("=") for kv in tp.describe().split())
+    tp.close()
+    del sub, tmp
+    for rc, what in ((plan.set_prepass(int(d.get("pp", "1"))), "set_prepass"),
+                     (plan.set_shape(int(d["R"]), int(d["NW"]), int(d["T"]), 1), "set_shape"),
+                     (plan.set_sincos_split(int(d.get("pe", "0"))) if d.get("pp", "1") == "1" else 0, "split")):
+        if rc:
+            raise rad.RadError(rc, what)
+    out = torch.empty(inp.n_omega * inp.n_angles, dtype=torch.float64, device=dev)
+    st = torch.cuda.Stream(device=dev)
+    torch.cuda.synchronize()
+    graph = plan.graph(*inp.args(), out, None, None, None, stream=st)
+
+    def run():
+        rc = graph.launch(st)
+        if rc:
+            raise rad.RadError(rc, "rad_graph_launch")
+
+    ms = time_launches(torch, st, run, 1)[0]
+    status = rad.rad_device_status(1)
+    if status != rad.RAD_OK:
+        raise rad.RadError(status, "device status")
+    samples = int(tr.lengths().sum())
+    terms = samples * inp.n_omega * inp.n_angles
+    rng = np.random.default_rng(seed)
+    bi = rng.integers(0, inp.n_omega, 24)
+    bj = rng.integers(0, inp.n_angles, 24)
+    got = out.view(inp.n_omega, inp.n_angles).cpu().numpy()[bi, bj]
+    dm = dict(kv.split("=") for kv in plan.describe().split())
+    cpt, _ = clocks_per_term(2, int(dm["R"]), int(dm.get("pe", "0")))
+    peak = SM_COUNT * SM_MAX_MHZ * 1e6 / cpt
+    graph.close()
+    plan.close()
+    res = {"workload": f"electron batch slice: the first {n} of 4096 e- at 20 GeV, lognormal lengths 2k-200k "
+                       f"(median 20k; here {samples} samples, max {int(L.max())}), harmonic planar well, RK4 + "
+                       "scattering kicks; 1024 log hw in [1e-4 E, 0.5 E] x 32x32 directions; spin-1/2 with recoil",
+           "particles": n, "samples": samples, "terms": terms, "ms": ms, "terms_per_s": terms / (ms * 1e-3),
+           "spectra_per_s": n / (ms * 1e-3), "shape": plan_desc_str(dm), "autotune_s": tune_s,
+           "launch": "one CUDA-graph launch of the whole path (checks, pre-pass, persistent kernel, combine), "
+                     "CUDA events on its stream, after one warm-up launch",
+           "roofline": {"bound": "alu", "pipe": "sfu + issue slots", "achieved": terms / (ms * 1e-3) / 1e12,
+                        "peak": peak / 1e12, "unit": "Tterm/s", "frac": terms / (ms * 1e-3) / peak}}
+    return res, (tr, grid, bi, bj, got)
+
+
+def plan_desc_str(d):
+    return " ".join(f"{k}={v}" for k, v in d.items())
 
 
 # --------------------------------------------------------------------------- reference arm
@@ -269,16 +391,27 @@ def main():
 
     l2_flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
+    pending = set()  # plans whose last launch's kernel time has not been read yet
+
+    def read_kernel_ms(ps, m, kernel_ms):
+        if kernel_ms is not None and (id(ps), m) in pending:
+            kernel_ms.append((m, ps[m].last_kernel_ms()))
+            pending.discard((id(ps), m))
+
     def step(s, ps, nb, kernel_ms=None):
         p0, _ = shard.step_batch(s, rank, world, nb, N_PART)
         a = batch_args(p0 // nb, nb)
         l2_flush.zero_()
         for m in modes:
+            # the plan keeps one pair of events: read the previous step's kernel time of this model
+            # just before relaunching it; the other model's kernel of the previous step is still
+            # queued then, so the device never idles on the read
+            read_kernel_ms(ps, m, kernel_ms)
             rc = ps[m].execute(*a, cube[m], spec[m], None, None, accumulate=0)
             if rc:
                 raise rad.RadError(rc, "rad_plan_execute")
             if kernel_ms is not None:
-                kernel_ms.append((m, ps[m].last_kernel_ms()))
+                pending.add((id(ps), m))
 
     def barrier():
         torch.cuda.synchronize()
@@ -298,6 +431,8 @@ def main():
             step(W + s, ps, nb, collect)
         e1.record()
         barrier()
+        for m in modes:
+            read_kernel_ms(ps, m, collect)
         wall = time.perf_counter() - t0
         ms = e0.elapsed_time(e1)
         t = torch.tensor([ms], dtype=torch.float64, device=dev)
@@ -332,13 +467,14 @@ def main():
     fp64_value = world * f_terms / (fms_step * 1e-3)
 
     # ---- FP64-accurate double-float form on the same inputs (same tolerance as plain FP64) ----
-    dfp = make_plans(rad.RAD_FP64_DF, args.fp64_batch)
+    dfp = make_plans(rad.RAD_FP64_DF, args.df_batch)
     for m in modes:
         dfp[m].set_timing(True)
     dkms = []
-    dms, _ = timed(dfp, args.fp64_batch, args.fp64_steps, 1, dkms)
-    dms_step = dms / args.fp64_steps
-    df_value = world * f_terms / (dms_step * 1e-3)
+    dms, _ = timed(dfp, args.df_batch, args.df_steps, 1, dkms)
+    dms_step = dms / args.df_steps
+    df_terms = len(modes) * terms_of(args.df_batch, grid)
+    df_value = world * df_terms / (dms_step * 1e-3)
 
     # ---- end to end through the host-buffer entry point (pinned memory, copies timed) ----
     nb_e = B
@@ -378,6 +514,10 @@ def main():
     status = rad.rad_device_status(1)
     if status != rad.RAD_OK:
         raise rad.RadError(status, "device status")
+
+    # ---- the other workloads: the analytic undulator in every form, the electron batch slice ----
+    und_line, und_data = undulator_leg(rad, torch, dev)
+    bat_line, bat_data = batch_leg(rad, torch, dev, args.batch_slice) if args.batch_slice > 0 else (None, None)
 
     # ---- roofline of the dominant kernel (mixed integral kernel) ----
     mk = [ms for (_, ms) in kms]
@@ -420,21 +560,22 @@ def main():
     fk = [ms for (_, ms) in fkms]
     f_terms_launch = terms_of(args.fp64_batch, grid)
     fp64_kernel_ms = sum(fk) / len(fk)
-    fp64_roof = {"kernel": "k_fp64", "kernel_ms_avg": fp64_kernel_ms,
+    fp64_ops_s = sum(FP64_OPS_PER_TERM[int(m)] * f_terms_launch for (m, _) in fkms) / (sum(fk) * 1e-3)
+    fp64_roof = {"kernel": "k_fp64", "kernel_ms_avg": fp64_kernel_ms, "launches": len(fk),
                  "terms_per_s": f_terms_launch / (fp64_kernel_ms * 1e-3),
-                 "fp64_ops_per_term": 20,
-                 "frac_fp64_pipe": 20 * f_terms_launch / (fp64_kernel_ms * 1e-3) /
-                 (SM_COUNT * FP64_PER_SM_CLK * SM_MAX_MHZ * 1e6)}
+                 "fp64_ops_per_term": FP64_OPS_PER_TERM,
+                 "frac_fp64_pipe": fp64_ops_s / (SM_COUNT * FP64_PER_SM_CLK * SM_MAX_MHZ * 1e6)}
     dk = [ms for (_, ms) in dkms]
     df_kernel_ms = sum(dk) / len(dk)
-    df_fp64_s = sum(DF_FP64_OPS_PER_TERM[int(m)] * f_terms_launch for (m, _) in dkms) / (sum(dk) * 1e-3)
-    df_inst_s = sum(DF_INST_PER_32_TERMS[int(m)] * f_terms_launch / 32 for (m, _) in dkms) / (sum(dk) * 1e-3)
+    df_terms_launch = terms_of(args.df_batch, grid)
+    df_fp64_s = sum(DF_FP64_OPS_PER_TERM[int(m)] * df_terms_launch for (m, _) in dkms) / (sum(dk) * 1e-3)
+    df_inst_s = sum(DF_INST_PER_32_TERMS[int(m)] * df_terms_launch / 32 for (m, _) in dkms) / (sum(dk) * 1e-3)
     # k_df: one FP64 instruction per term (the phase product; the reduction is integer
     # arithmetic) plus the per-(direction, sample) preparation shared by 64 energies and the
     # conversion of the tile sums into FP64 particle amplitudes; it is bound by the issue slots
     # (4 warp instructions per SM per clock), the FP64 pipe second
-    df_roof = {"kernel": "k_df", "kernel_ms_avg": df_kernel_ms,
-               "terms_per_s": f_terms_launch / (df_kernel_ms * 1e-3),
+    df_roof = {"kernel": "k_df", "kernel_ms_avg": df_kernel_ms, "launches": len(dk),
+               "terms_per_s": df_terms_launch / (df_kernel_ms * 1e-3),
                "fp64_ops_per_term": DF_FP64_OPS_PER_TERM, "warp_inst_per_32_terms": DF_INST_PER_32_TERMS,
                "frac_fp64_pipe": df_fp64_s / (SM_COUNT * FP64_PER_SM_CLK * SM_MAX_MHZ * 1e6),
                "frac_issue": df_inst_s / (SM_COUNT * ISSUE_PER_SM_CLK / 32 * SM_MAX_MHZ * 1e6)}
@@ -449,16 +590,18 @@ def main():
                    "l2": "256 MB buffer written between steps (flush)", "shape": mixed_desc},
         "spectra_per_s": spectra_s,
         "plain_fp64": {"value": fp64_value, "unit": "terms/s", "particles_per_step": args.fp64_batch,
-                       "ms_per_step": fms_step, "spectra_per_s": world * len(modes) * args.fp64_batch /
+                       "steps": args.fp64_steps, "ms_per_step": fms_step, "spectra_per_s": world * len(modes) * args.fp64_batch /
                        (fms_step * 1e-3), "shape": {m: fp[m].describe() for m in modes}, "kernel": fp64_roof},
-        "fp64_df": {"value": df_value, "unit": "terms/s", "particles_per_step": args.fp64_batch,
-                    "ms_per_step": dms_step, "spectra_per_s": world * len(modes) * args.fp64_batch /
+        "fp64_df": {"value": df_value, "unit": "terms/s", "particles_per_step": args.df_batch,
+                    "steps": args.df_steps, "ms_per_step": dms_step, "spectra_per_s": world * len(modes) * args.df_batch /
                     (dms_step * 1e-3), "shape": {m: dfp[m].describe() for m in modes}, "kernel": df_roof,
                     "tolerance": "as plain FP64: 1e-9 of a bin, floor 1e-6 of the peak"},
         "mixed_over_fp64": value / fp64_value,
         "roofline": roofline,
         "e2e": {"value": e2e_value, "unit": "terms/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "entry": "rad_spectrum_host (pinned host buffers, copies inside the timed region)"},
+        "undulator": und_line,
+        "electron_batch": bat_line,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
         "wall_s_timed": wall,
@@ -466,6 +609,7 @@ def main():
 
     # ---- CPU baseline: the oracle on a bounded sample, and the GPU error on that sample ----
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle as O
         n_dirs = 128
         vals, bi, bj, terms, dt, cores = run_oracle_sample(tr, grid, n_dirs, modes)
         one = batch_args(0, 1)
@@ -493,6 +637,24 @@ def main():
                     errs[f"{name}_{'classical' if m == 0 else 'spin_half'}"] = {
                         "max_rel_floor_1e-6_peak": float(rel.max()), "bins": int(r.size)}
                 p1.close()
+        # the other workloads against the oracle: the undulator's full cube, the batch's sampled bins
+        utr, ugrid, ucubes = und_data
+        uref = O.spectrum_cube(utr, ugrid, O.CLASSICAL)
+        upk = np.abs(uref).max()
+        for name, c in ucubes.items():
+            if name == "mixed":
+                sel = uref >= 1e-3 * upk
+                und_line["forms"][name]["max_rel_on_bins_ge_1e-3_peak"] = float(
+                    (np.abs(c[sel] - uref[sel]) / uref[sel]).max())
+            else:
+                und_line["forms"][name]["max_rel_floor_1e-6_peak"] = float(
+                    (np.abs(c - uref) / np.maximum(np.abs(uref), 1e-6 * upk)).max())
+        if bat_data is not None:
+            btr, bgrid, bi2, bj2, bgot = bat_data
+            bref = O.spectrum_bins(btr, bgrid, O.SPIN_HALF, bi2, bj2)
+            bsel = bref >= 1e-3 * np.abs(bref).max()
+            bat_line["err_vs_oracle"] = {"bins": int(bi2.size), "bins_ge_1e-3_peak": int(bsel.sum()),
+                                         "max_rel": float((np.abs(bgot[bsel] - bref[bsel]) / bref[bsel]).max())}
         line["cpu_baseline"] = {
             "value": terms / dt, "unit": "terms/s", "cores": cores, "kind": "oracle",
             "sample": f"particle 0 (20000 samples) x 512 hw x {n_dirs} seeded directions x 2 models "
