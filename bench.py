@@ -34,12 +34,13 @@ TUNE_PARTICLES = 8
 # 32-particle launches of this workload (R=2 or 4, NW=4 or 8, T=128 or 256); --autotune lets the
 # library's autotuner choose instead
 SHAPES = {0: (2, 8, 256), 2: (2, 4, 256)}
-# FP64 instructions per term and warp instructions per 32 terms of the double-float kernel per
-# model, counted by ncu (smsp__inst_executed_pipe_fp64, smsp__inst_executed on 1 particle x 20000
-# samples x 128 hw x 32 x 32 directions)
-DF_FP64_OPS_PER_TERM = {0: 2.12, 2: 2.36}
-FP64_OPS_PER_TERM = {0: 20.0, 2: 22.76}
-DF_INST_PER_32_TERMS = {0: 182.8, 2: 210.0}
+# per model: FP64 instructions per term of k_fp64 and k_df, and warp instructions per 32 terms of
+# k_df, counted by ncu (smsp__inst_executed_pipe_fp64.sum x 32 / terms, smsp__inst_executed.sum)
+# on the launch these legs time: one particle of this workload x 512 hw x 64x64 directions, the
+# default shapes (k_fp64 R=2 NW=8 T=64, k_df R=2 NW=4 T=64)
+FP64_OPS_PER_TERM = {0: 20.70, 2: 22.75}
+DF_FP64_OPS_PER_TERM = {0: 2.10, 2: 2.34}
+DF_INST_PER_32_TERMS = {0: 175.6, 2: 200.6}
 WORKLOAD = ("positron ensemble: 1024 e+ at 10 GeV, harmonic planar well (U0 = 20 eV, d_p = 1.92 A), "
             "RK4 + scattering kicks, 20000 samples over 100 um; 512 log hw in [1e-4 E, 0.5 E] x 64x64 "
             "directions within +-(theta_L + 3/gamma); classical + spin-1/2")
