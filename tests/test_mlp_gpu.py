@@ -58,10 +58,11 @@ def test_gradients_elementwise_at_the_product_shape():
     """The surrogate's own shape (62 features -> 3 x 256 -> 2048 outputs, batch 1024, so the
     weight-gradient GEMMs take the split-K path): every gradient element against the FP64
     reference with the GPU's BF16-rounded weights. The GEMM operands of layers >= 1 are BF16
-    (relative rounding <= 2^-9 each) with FP32 accumulation, so each element's error is bounded by
-    a small multiple of 2^-9 times the sum of the magnitudes of the products it adds up
-    (oracle.mlp.grad_magnitudes), the multiple covering the two rounded operands and the rounding
-    carried back through the layers."""
+    (relative rounding <= 2^-9 each) with FP32 accumulation, so each element's error is at most
+    about 2 x 2^-9 times the sum of the magnitudes of the products it adds up
+    (oracle.mlp.grad_magnitudes): one rounding per operand, the rounding carried back through the
+    layers and the FP32 sums being far smaller (observed at most 0.58 x 2^-9 times that sum, in the
+    last layer's weights)."""
     import torch
     rng = np.random.default_rng(5)
     n_in, width, depth, n_out, B = 62, 256, 3, 2048, 1024
@@ -80,7 +81,7 @@ def test_gradients_elementwise_at_the_product_shape():
     lay, _ = M.layout(n_in, width, depth, n_out)
     worst = [float(ratio[wo:bo + fo].max()) for (wo, bo, fo, fi) in lay]
     print("max |dg| / (2^-9 sum|products|) per layer:", worst, "p99:", float(np.quantile(ratio, 0.99)))
-    assert ratio.max() <= 8.0, worst
+    assert ratio.max() <= 2.0, worst
     m.close()
 
 
