@@ -466,6 +466,101 @@ int rad_crystal_trajectories(const rad_channel *ch, const rad_planar_potential *
                              const int64_t *particle_ids, double dt, uint64_t seed, double *out,
                              double *energy_out, void *stream);
 
+/* ---- crystal geometry (Sec. IV: the placement of strings and planes in FCC and BCC crystals,
+ *      in the (100), (110), (111) planes and <100>, <110>, <111> axes) ---- */
+#define RAD_DIAMOND 0 /* diamond cubic (FCC lattice, two-atom basis): Si, C, Ge */
+#define RAD_BCC 1     /* body-centred cubic: W                                  */
+#define RAD_SI 0
+#define RAD_C 1
+#define RAD_GE 2
+#define RAD_W 3
+
+/* Element presets: structure, cubic lattice constant a (m), atomic number, mean ionisation energy
+ * (eV) and radiation length (m): standard tabulated material constants, not values from the paper
+ * (the Doyle-Turner fit coefficients stay the caller's). */
+typedef struct {
+  int structure; /* RAD_DIAMOND or RAD_BCC */
+  double a;      /* lattice constant, m   */
+  int Z;
+  double I_eV;
+  double X0;
+} rad_element;
+
+/* The strings of an axis seen in the transverse plane: a rectangular cell cell_x x cell_y
+ * repeated over the plane, with n_strings strings at (sx[k], sy[k]) in it; d is the mean distance
+ * between atoms along a string, so the atom density is n_strings / (d cell_x cell_y). */
+typedef struct {
+  int n_strings;          /* 1 .. 8 */
+  double cell_x, cell_y;  /* m      */
+  double sx[8], sy[8];    /* m      */
+  double d;               /* m      */
+} rad_string_lattice;
+
+/* The planes of a family along its normal: n_planes planes at offset[k] in every period, each
+ * holding areal[k] atoms per unit area. Equidistant families have n_planes = 1 (the planar
+ * potential's d_p is then the period and N d_p the areal density). */
+typedef struct {
+  int n_planes;      /* 1 .. 4 */
+  double period;     /* m      */
+  double offset[4];  /* m, in [0, period) */
+  double areal[4];   /* m^-2   */
+} rad_plane_stack;
+
+/* rad_crystal_element -- the preset of element RAD_SI, RAD_C, RAD_GE or RAD_W. RAD_EINVAL for
+ * another value or a NULL out. Host only. */
+int rad_crystal_element(int element, rad_element *out);
+
+/* rad_crystal_string_lattice -- the string lattice of the axis <100>, <110> or <111> (axis =
+ * 100, 110, 111) of a crystal of the given structure and lattice constant a (> 0), in the frame
+ * x along [010], y along [001] (<100>); x along [001], y along [1-10] (<110>); x along [1-10], y
+ * along [11-2] (<111>). RAD_EINVAL for another structure or axis, a <= 0 or a NULL out. Host only. */
+int rad_crystal_string_lattice(int structure, double a, int axis, rad_string_lattice *out);
+
+/* rad_crystal_plane_stack -- the plane family (100), (110) or (111) (plane = 100, 110, 111) of
+ * a crystal of the given structure and lattice constant. Diamond (111) is a stack of pairs of
+ * planes (n_planes = 2); the others are equidistant. RAD_EINVAL as above. Host only. */
+int rad_crystal_plane_stack(int structure, double a, int plane, rad_plane_stack *out);
+
+/* Thermally averaged Doyle-Turner continuum potential of the strings of an axis (Sec. III,
+ * Eq. string) and their electron density (Sec. III). A unit positive charge feels
+ *   U(x, y) = sum_strings (2 e^2 a0 / d) sum_i a[i] / C_i exp(-r^2 / C_i),
+ *   C_i = b[i] / (4 pi^2) + rho^2 (rho of rad_channel), r = distance to the string,
+ * summed over the strings of the (2 n_cells + 1)^2 cells around the cell (floor(x / cell_x),
+ * floor(y / cell_y)) that holds the particle. With RAD_TRAJ_MS the kicks take the strings'
+ * nuclear density, n(x, y)/N = sum_strings exp(-r^2 / rho^2) / (pi rho^2 N d) with N =
+ * n_strings / (d cell_x cell_y); with RAD_TRAJ_MS_EL also the electron density
+ *   n_el = (1 / (pi d)) sum_strings sum_i ax[i] / CX_i exp(-r^2 / CX_i) + cx N n(x, y)/N,
+ * CX_i = bx[i] / (4 pi^2) + rho^2, in the electron term of rad_planar_potential. */
+typedef struct {
+  int n_terms;      /* Gaussian terms of each fit, 1 .. 8 */
+  int n_cells;      /* cells summed on each side of the particle's cell in x and y, 1 .. 4 */
+  double a[8];      /* potential fit a_i, m (finite) */
+  double b[8];      /* potential fit b_i, m^2 (C_i > 0) */
+  double ax[8];     /* X-ray fit a_i^(X), electrons (used with RAD_TRAJ_MS_EL) */
+  double bx[8];     /* X-ray fit b_i^(X), m^2 (CX_i > 0 with RAD_TRAJ_MS_EL) */
+  double cx;        /* X-ray constant c^(X) */
+  double I_eV;      /* mean ionisation energy, eV (> 0 with RAD_TRAJ_MS_EL) */
+  rad_string_lattice lattice;
+} rad_axial_potential;
+
+/*
+ * rad_axial_trajectories -- rad_crystal_trajectories for axial channeling: the force is
+ * -q grad U(x, y) of the string potential `pot` (host struct, read during the call), in both
+ * transverse directions; particle p enters at (x0[p], y0[p]) (device; y0 may be NULL for 0) with
+ * angles (thx0[p], thy0[p]). The records, the random streams, the radiation reaction and the
+ * scattering options are those of rad_channeling_trajectories, with the string densities in place
+ * of the plane densities (U0_eV and d_p of rad_channel are ignored). FP64 only: RAD_TRAJ_FP32
+ * returns RAD_EUNSUPPORTED. Host checks (null ch or pot, n_terms, n_cells or n_strings out of
+ * range, a cell side or d <= 0, a non-finite coefficient or position, C_i <= 0, with
+ * RAD_TRAJ_MS_EL CX_i <= 0 or I_eV <= 0, rho <= 0 with RAD_TRAJ_MS, and the checks of
+ * rad_channeling_trajectories) return RAD_EINVAL before anything is enqueued.
+ */
+int rad_axial_trajectories(const rad_channel *ch, const rad_axial_potential *pot, int64_t n_particles,
+                           const int64_t *offsets, int64_t n_samples_total, const double *energy_eV,
+                           const double *x0, const double *y0, const double *thx0, const double *thy0,
+                           const int64_t *particle_ids, double dt, uint64_t seed, double *out,
+                           double *energy_out, void *stream);
+
 /*
  * rad_device_status -- waits for the current device to finish, returns the first
  * device-side error recorded since the last reset (RAD_OK, RAD_EDATA or RAD_ETIMEOUT)

@@ -269,3 +269,166 @@ def trajectories(x0, thx0, thy0, E0_eV, n_samples: int, dt: float, seed: int, *,
                 gk = E / mass_eV
                 s[:, 5] = E - mass_eV * ALPHA / (2.0 * math.pi) * gk ** 3 * (dthx * dthx + dthy * dthy)
     return (out, Es) if energies else out
+
+
+# --------------------------------------------------------------------------------------------
+# Axial (string) continuum potential, Sec. III Eq. string
+# --------------------------------------------------------------------------------------------
+class StringLattice:
+    """Strings of atoms along the axis, seen in the transverse plane: a rectangular cell
+    (cell_x, cell_y) [m] repeated over the plane, holding strings at (sx[k], sy[k]); d [m] is the
+    mean distance between atoms along a string. The atom density is N = n_strings / (d cell_x cell_y)."""
+
+    def __init__(self, cell_x, cell_y, sx, sy, d):
+        self.cell_x, self.cell_y, self.d = float(cell_x), float(cell_y), float(d)
+        self.sx, self.sy = np.asarray(sx, np.float64), np.asarray(sy, np.float64)
+
+    @property
+    def N(self):
+        return self.sx.size / (self.d * self.cell_x * self.cell_y)
+
+
+class AxialPotential:
+    """Doyle-Turner fit of one atom (Sec. III): potential terms a [m], b [m^2]; X-ray terms
+    ax [electrons], bx [m^2], cx; mean ionisation energy I_eV; the string lattice; K cells summed on
+    each side of the particle's cell in both transverse directions."""
+
+    def __init__(self, a, b, lattice, ax=(), bx=(), cx=0.0, I_eV=0.0, K=2):
+        self.a, self.b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+        self.ax, self.bx = np.asarray(ax, np.float64), np.asarray(bx, np.float64)
+        self.lat, self.cx, self.I_eV, self.K = lattice, float(cx), float(I_eV), int(K)
+
+
+def string_offsets(x, y, lat, K):
+    """(dx, dy) [..., n] from every string of the (2K+1)^2 cells around the particle's cell
+    (cx, cy) = (floor(x / cell_x), floor(y / cell_y)) to the point (x, y)."""
+    x, y = np.asarray(x, np.float64), np.asarray(y, np.float64)
+    cx, cy = np.floor(x / lat.cell_x), np.floor(y / lat.cell_y)
+    i = np.arange(-K, K + 1, dtype=np.float64)
+    ox = ((cx[..., None] + i) * lat.cell_x)[..., :, None, None] + lat.sx[None, None, :]   # [.., i, 1, k]
+    oy = ((cy[..., None] + i) * lat.cell_y)[..., None, :, None] + lat.sy[None, None, :]   # [.., 1, j, k]
+    dx = x[..., None, None, None] - ox
+    dy = y[..., None, None, None] - oy
+    dx, dy = np.broadcast_arrays(dx, dy)
+    return dx.reshape(dx.shape[:-3] + (-1,)), dy.reshape(dy.shape[:-3] + (-1,))
+
+
+def axial_potential(x, y, pot, rho):
+    """U(x, y) in eV for a unit positive charge: Eq. string summed over the strings of the
+    (2K+1)^2 cells around the particle, U_s(r) = (2 e^2 a0 / d) sum_i a_i / C_i exp(-r^2 / C_i),
+    C_i = b_i / (4 pi^2) + rho^2."""
+    C = pot.b / (4.0 * math.pi ** 2) + rho * rho
+    dx, dy = string_offsets(x, y, pot.lat, pot.K)
+    r2 = (dx * dx + dy * dy)[..., None]
+    return (2.0 * E2_EV_M * A0_M / pot.lat.d * (pot.a / C) * np.exp(-r2 / C)).sum((-1, -2))
+
+
+def axial_force(x, y, pot, rho, charge):
+    """(F_x, F_y) = -charge grad U in eV/m; d/dr exp(-r^2/C) = -(2 r / C) exp(-r^2/C)."""
+    C = pot.b / (4.0 * math.pi ** 2) + rho * rho
+    dx, dy = string_offsets(x, y, pot.lat, pot.K)
+    e = (2.0 * E2_EV_M * A0_M / pot.lat.d * (pot.a / C) * (2.0 / C)
+         * np.exp(-((dx * dx + dy * dy)[..., None]) / C)).sum(-1)
+    return charge * (dx * e).sum(-1), charge * (dy * e).sum(-1)
+
+
+def string_density(x, y, lat, rho, K):
+    """n(x, y)/N: the nuclear densities of the strings (Sec. III), each
+    n_s(r) = exp(-r^2 / rho^2) / (pi rho^2 d), summed over the (2K+1)^2 cells, over the mean N."""
+    dx, dy = string_offsets(x, y, lat, K)
+    return np.exp(-(dx * dx + dy * dy) / (rho * rho)).sum(-1) / (math.pi * rho * rho * lat.d * lat.N)
+
+
+def axial_electron_density(x, y, pot, rho):
+    """n_el(x, y) in m^-3 (Sec. III): (1/(pi d)) sum_i a_i^X / C_i^X exp(-r^2 / C_i^X) per string
+    plus c^X times the nuclear density, C_i^X = b_i^X / (4 pi^2) + rho^2."""
+    CX = pot.bx / (4.0 * math.pi ** 2) + rho * rho
+    dx, dy = string_offsets(x, y, pot.lat, pot.K)
+    r2 = (dx * dx + dy * dy)[..., None]
+    val = ((pot.ax / CX) * np.exp(-r2 / CX)).sum((-1, -2)) / (math.pi * pot.lat.d)
+    return val + pot.cx * pot.lat.N * string_density(x, y, pot.lat, rho, pot.K)
+
+
+def axial_trajectories(x0, y0, thx0, thy0, E0_eV, n_samples: int, dt: float, seed: int, pot, *, charge=+1,
+                       eps_s_eV=10.6e6, X0=0.0937, rho=0.075e-10, ms=True, ms_el=False, ll=False,
+                       ms_loss=False, mass_eV=0.51099895e6, particle_ids=None, energies=False):
+    """Records [n][n_samples][10] of n particles entering at (x0, y0) with angles (thx0, thy0) in
+    the axial potential `pot` (AxialPotential): the equations, RK4 steps, kicks and records of
+    `trajectories`, with the two-dimensional force -charge grad U(x, y) and the string densities."""
+    x0 = np.asarray(x0, dtype=np.float64)
+    n = x0.shape[0]
+    pid = np.arange(n, dtype=np.uint64) if particle_ids is None else np.asarray(particle_ids, dtype=np.uint64)
+    E0 = np.broadcast_to(np.asarray(E0_eV, dtype=np.float64), (n,)).copy()
+    g0 = E0 / mass_eV
+    beta0 = 1.0 - 1.0 / (2.0 * g0 * g0)
+    bc = lambda v: np.broadcast_to(np.asarray(v, np.float64), (n,)).copy()
+    s = np.stack([x0, bc(y0), bc(thx0), bc(thy0), np.zeros(n), E0], 1)
+
+    def dvz_of(g, vp2, vz):
+        d_inv = ((g - g0) * (g + g0)) / ((g * g) * (g0 * g0))
+        return (d_inv - vp2 - 1.0 / (4.0 * g0 ** 4)) / (vz + beta0)
+
+    def gamma_dot(F2, E):
+        g = E / mass_eV
+        return -(2.0 / 3.0) * ALPHA * HBARC_EV_M * g * g * F2 / mass_eV ** 3
+
+    def deriv(st):
+        g = st[:, 5] / mass_eV
+        vp2 = st[:, 2] ** 2 + st[:, 3] ** 2
+        vz = np.sqrt(1.0 - 1.0 / (g * g) - vp2)
+        Fx, Fy = axial_force(st[:, 0], st[:, 1], pot, rho, charge)
+        d = np.empty_like(st)
+        d[:, 0] = st[:, 2]
+        d[:, 1] = st[:, 3]
+        d[:, 2] = Fx / st[:, 5]
+        d[:, 3] = Fy / st[:, 5]
+        d[:, 4] = dvz_of(g, vp2, vz)
+        d[:, 5] = gamma_dot(Fx * Fx + Fy * Fy, st[:, 5]) * mass_eV if ll else 0.0
+        return d
+
+    out = np.empty((n, n_samples, 10))
+    Es = np.empty((n, n_samples))
+    kick = np.zeros((n, 2))
+    for k in range(n_samples):
+        g = s[:, 5] / mass_eV
+        vp2 = s[:, 2] ** 2 + s[:, 3] ** 2
+        vz = np.sqrt(1.0 - 1.0 / (g * g) - vp2)
+        Fx, Fy = axial_force(s[:, 0], s[:, 1], pot, rho, charge)
+        ax = Fx / s[:, 5] + kick[:, 0]
+        ay = Fy / s[:, 5] + kick[:, 1]
+        gd = gamma_dot(Fx * Fx + Fy * Fy, s[:, 5]) if ll else np.zeros(n)
+        rec = out[:, k]
+        rec[:, 0] = k * dt
+        rec[:, 1] = s[:, 0]
+        rec[:, 2] = s[:, 1]
+        rec[:, 3] = s[:, 4]
+        rec[:, 4] = s[:, 2]
+        rec[:, 5] = s[:, 3]
+        rec[:, 6] = dvz_of(g, vp2, vz)
+        rec[:, 7] = ax
+        rec[:, 8] = ay
+        rec[:, 9] = (gd / g ** 3 - (s[:, 2] * ax + s[:, 3] * ay)) / vz
+        Es[:, k] = s[:, 5]
+        kick[:] = 0.0
+        if k == n_samples - 1:
+            break
+        k1 = deriv(s)
+        k2 = deriv(s + 0.5 * dt * k1)
+        k3 = deriv(s + 0.5 * dt * k2)
+        k4 = deriv(s + dt * k3)
+        s = s + dt / 6.0 * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
+        if ms:
+            E = s[:, 5]
+            var = 0.5 * (eps_s_eV / E) ** 2 * (dt / X0) * string_density(s[:, 0], s[:, 1], pot.lat, rho, pot.K)
+            if ms_el:
+                var = var + 0.5 * dt * electron_scattering_rate(
+                    E / mass_eV, axial_electron_density(s[:, 0], s[:, 1], pot, rho), pot.I_eV)
+            z0, z1 = kick_normals(seed, pid, k)
+            dthx, dthy = np.sqrt(var) * z0, np.sqrt(var) * z1
+            kick[:, 0], kick[:, 1] = dthx / dt, dthy / dt
+            s[:, 2] += dthx
+            s[:, 3] += dthy
+            if ms_loss:
+                gk = E / mass_eV
+                s[:, 5] = E - mass_eV * ALPHA / (2.0 * math.pi) * gk ** 3 * (dthx * dthx + dthy * dthy)
+    return (out, Es) if energies else out

@@ -44,6 +44,49 @@ class RadPlanarPotential(ctypes.Structure):
             raise ValueError("a, b (and ax, bx) must have the same length, 1..8")
         pad = lambda v: (ctypes.c_double * 8)(*(list(map(float, v)) + [0.0] * (8 - len(v))))
         return cls(len(a), int(n_neighbours), float(N), pad(a), pad(b), pad(ax), pad(bx), float(cx), float(I_eV))
+RAD_DIAMOND, RAD_BCC = 0, 1
+RAD_SI, RAD_C, RAD_GE, RAD_W = 0, 1, 2, 3
+
+
+class RadElement(ctypes.Structure):
+    """rad_element: structure, lattice constant, Z, mean ionisation energy, radiation length."""
+    _fields_ = [("structure", ctypes.c_int), ("a", ctypes.c_double), ("Z", ctypes.c_int), ("I_eV", ctypes.c_double),
+                ("X0", ctypes.c_double)]
+
+
+class RadStringLattice(ctypes.Structure):
+    """rad_string_lattice: rectangular transverse cell, string positions, atom spacing along a string."""
+    _fields_ = [("n_strings", ctypes.c_int), ("cell_x", ctypes.c_double), ("cell_y", ctypes.c_double),
+                ("sx", ctypes.c_double * 8), ("sy", ctypes.c_double * 8), ("d", ctypes.c_double)]
+
+    @classmethod
+    def make(cls, cell_x, cell_y, sx, sy, d):
+        if len(sx) != len(sy) or not 1 <= len(sx) <= 8:
+            raise ValueError("sx, sy must have the same length, 1..8")
+        pad = lambda v: (ctypes.c_double * 8)(*(list(map(float, v)) + [0.0] * (8 - len(v))))
+        return cls(len(sx), float(cell_x), float(cell_y), pad(sx), pad(sy), float(d))
+
+
+class RadPlaneStack(ctypes.Structure):
+    """rad_plane_stack: planes per period along the normal, their offsets and areal densities."""
+    _fields_ = [("n_planes", ctypes.c_int), ("period", ctypes.c_double), ("offset", ctypes.c_double * 4),
+                ("areal", ctypes.c_double * 4)]
+
+
+class RadAxialPotential(ctypes.Structure):
+    """rad_axial_potential: Doyle-Turner fit of the atoms and the string lattice of the axis."""
+    _fields_ = [("n_terms", ctypes.c_int), ("n_cells", ctypes.c_int), ("a", ctypes.c_double * 8),
+                ("b", ctypes.c_double * 8), ("ax", ctypes.c_double * 8), ("bx", ctypes.c_double * 8),
+                ("cx", ctypes.c_double), ("I_eV", ctypes.c_double), ("lattice", RadStringLattice)]
+
+    @classmethod
+    def make(cls, a, b, lattice, ax=(), bx=(), cx=0.0, I_eV=0.0, n_cells=2):
+        if len(a) != len(b) or (len(ax) and len(ax) != len(a)) or len(ax) != len(bx) or not 1 <= len(a) <= 8:
+            raise ValueError("a, b (and ax, bx) must have the same length, 1..8")
+        pad = lambda v: (ctypes.c_double * 8)(*(list(map(float, v)) + [0.0] * (8 - len(v))))
+        return cls(len(a), int(n_cells), pad(a), pad(b), pad(ax), pad(bx), float(cx), float(I_eV), lattice)
+
+
 MODES = {"classical": RAD_CLASSICAL, "spin0": RAD_SPIN0, "spin_half": RAD_SPIN_HALF}
 PRECISIONS = {"fp64": RAD_FP64, "mixed": RAD_MIXED, "fp64_df": RAD_FP64_DF}
 
@@ -100,6 +143,15 @@ def load(build_if_missing: bool = True):
         lib.rad_crystal_trajectories.argtypes = [ctypes.POINTER(RadChannel), ctypes.POINTER(RadPlanarPotential), i64,
                                                  P, i64, P, P, P, P, P, ctypes.c_double, u64, P, P, P]
         lib.rad_crystal_trajectories.restype = c_int
+        lib.rad_axial_trajectories.argtypes = [ctypes.POINTER(RadChannel), ctypes.POINTER(RadAxialPotential), i64,
+                                               P, i64, P, P, P, P, P, P, ctypes.c_double, u64, P, P, P]
+        lib.rad_axial_trajectories.restype = c_int
+        lib.rad_crystal_element.argtypes = [c_int, ctypes.POINTER(RadElement)]
+        lib.rad_crystal_element.restype = c_int
+        lib.rad_crystal_string_lattice.argtypes = [c_int, ctypes.c_double, c_int, ctypes.POINTER(RadStringLattice)]
+        lib.rad_crystal_string_lattice.restype = c_int
+        lib.rad_crystal_plane_stack.argtypes = [c_int, ctypes.c_double, c_int, ctypes.POINTER(RadPlaneStack)]
+        lib.rad_crystal_plane_stack.restype = c_int
         lib.rad_mlp_create.argtypes = [c_int, c_int, c_int, c_int, i64, u64, ctypes.POINTER(P)]
         lib.rad_mlp_create.restype = c_int
         lib.rad_mlp_destroy.argtypes = [P]
@@ -311,6 +363,43 @@ def rad_crystal_trajectories(channel, potential, offsets, energy_eV, x0, thx0, o
         _dev_ptr(x0, f64, "x0"), _dev_ptr(thx0, f64, "thx0"), _dev_ptr(thy0, f64, "thy0"),
         _dev_ptr(particle_ids, torch.int64, "particle_ids"), float(dt), int(seed), _dev_ptr(out, f64, "out"),
         _dev_ptr(energy_out, f64, "energy_out"), _stream(stream))
+
+
+def rad_axial_trajectories(channel, potential, offsets, energy_eV, x0, thx0, out, dt, seed, y0=None, thy0=None,
+                           particle_ids=None, energy_out=None, stream=None) -> int:
+    """Trajectories in the axial (string) potential `potential` (RadAxialPotential)."""
+    import torch
+    f64 = torch.float64
+    return load().rad_axial_trajectories(
+        ctypes.byref(channel), ctypes.byref(potential) if potential is not None else None, _numel(offsets) - 1,
+        _dev_ptr(offsets, torch.int64, "offsets"), _numel(out) // RAD_NREC, _dev_ptr(energy_eV, f64, "energy_eV"),
+        _dev_ptr(x0, f64, "x0"), _dev_ptr(y0, f64, "y0"), _dev_ptr(thx0, f64, "thx0"), _dev_ptr(thy0, f64, "thy0"),
+        _dev_ptr(particle_ids, torch.int64, "particle_ids"), float(dt), int(seed), _dev_ptr(out, f64, "out"),
+        _dev_ptr(energy_out, f64, "energy_out"), _stream(stream))
+
+
+def crystal_element(element) -> RadElement:
+    out = RadElement()
+    rc = load().rad_crystal_element(int(element), ctypes.byref(out))
+    if rc:
+        raise RadError(rc, "rad_crystal_element")
+    return out
+
+
+def crystal_string_lattice(structure, a, axis) -> RadStringLattice:
+    out = RadStringLattice()
+    rc = load().rad_crystal_string_lattice(int(structure), float(a), int(axis), ctypes.byref(out))
+    if rc:
+        raise RadError(rc, "rad_crystal_string_lattice")
+    return out
+
+
+def crystal_plane_stack(structure, a, plane) -> RadPlaneStack:
+    out = RadPlaneStack()
+    rc = load().rad_crystal_plane_stack(int(structure), float(a), int(plane), ctypes.byref(out))
+    if rc:
+        raise RadError(rc, "rad_crystal_plane_stack")
+    return out
 
 
 class MLP:

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "librad.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 SOURCES = ["rad_fp64.cu", "rad_mixed.cu", "rad_mixed_pp.cu", "rad_post.cu", "rad_api.cu", "rad_mlp.cu",
-           "rad_noalloc.cu", "rad_traj.cu", "rad_df.cu"]
+           "rad_noalloc.cu", "rad_traj.cu", "rad_df.cu", "rad_crystal.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

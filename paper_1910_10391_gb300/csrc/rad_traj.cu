@@ -269,6 +269,177 @@ __global__ void k_channel(const Chan C, const Planar P, int64_t n_particles, con
 }
 
 // ------------------------------------------------------------------------------------
+// Axial channeling (rad_axial_trajectories): strings of atoms along the axis (Sec. III, Eq.
+// string), FP64. The strings of the (2K+1)^2 cells around the particle's cell are summed; each
+// string's Gaussian exp(-(dx^2 + dy^2)/C) separates into exp(-dx^2/C) exp(-dy^2/C), and the
+// cells of one basis string form a product grid, so the double sum over the cells is a product
+// of two sums of 2K+1 terms: 2(2K+1) exponentials per basis string and term instead of (2K+1)^2.
+// ------------------------------------------------------------------------------------
+struct Axial {
+  int nt, nb, K, el;
+  double Lx, Ly;
+  double sx[8], sy[8];
+  double fk[kMaxTerms];  // q (2 e^2 a0 / d) (a_i / C_i) (2 / C_i)
+  double ck[kMaxTerms];  // 1 / C_i
+  double dens_k;         // 1 / (pi rho^2 N d): n(x, y)/N per unit Gaussian
+  double inv_rho2;
+  double ek[kMaxTerms], eck[kMaxTerms];  // (1/2) dt pi r0^2 ax_i / (pi d CX_i), 1 / CX_i
+  double ecx, lk;                        // (1/2) dt pi r0^2 cx N; 2 m_e / I
+};
+
+// sums over the 2K+1 images u0 + i L of one coordinate: s1 = sum u e^{-u^2 k}, s0 = sum e^{-u^2 k}
+__device__ __forceinline__ void axis_sums(double u0, double L, int K, double k, double &s1, double &s0) {
+  s1 = 0.0;
+  s0 = 0.0;
+  for (int i = -K; i <= K; ++i) {
+    const double u = u0 - static_cast<double>(i) * L;
+    const double e = exp(-(u * u) * k);
+    s1 += u * e;
+    s0 += e;
+  }
+}
+
+__device__ __forceinline__ void axial_force(const Axial &A, double x, double y, double &Fx, double &Fy) {
+  const double cx = floor(x / A.Lx), cy = floor(y / A.Ly);
+  Fx = 0.0;
+  Fy = 0.0;
+  for (int b = 0; b < A.nb; ++b) {
+    // offsets from the strings of the particle's own cell; the images follow at -i L
+    const double ux = x - (cx * A.Lx + A.sx[b]);
+    const double uy = y - (cy * A.Ly + A.sy[b]);
+    for (int t = 0; t < A.nt; ++t) {
+      double sx1, sx0, sy1, sy0;
+      axis_sums(ux, A.Lx, A.K, A.ck[t], sx1, sx0);
+      axis_sums(uy, A.Ly, A.K, A.ck[t], sy1, sy0);
+      Fx += A.fk[t] * (sx1 * sy0);
+      Fy += A.fk[t] * (sx0 * sy1);
+    }
+  }
+}
+
+// n(x, y)/N and, with electron scattering, (1/2) dt pi r0^2 n_el(x, y)
+__device__ __forceinline__ void axial_densities(const Axial &A, double x, double y, double &n_nuc, double &n_el) {
+  const double cx = floor(x / A.Lx), cy = floor(y / A.Ly);
+  double nn = 0.0, ne = 0.0;
+  for (int b = 0; b < A.nb; ++b) {
+    const double ux = x - (cx * A.Lx + A.sx[b]);
+    const double uy = y - (cy * A.Ly + A.sy[b]);
+    double s1, sx0, sy0;
+    axis_sums(ux, A.Lx, A.K, A.inv_rho2, s1, sx0);
+    axis_sums(uy, A.Ly, A.K, A.inv_rho2, s1, sy0);
+    nn += sx0 * sy0;
+    if (A.el) {
+      for (int t = 0; t < A.nt; ++t) {
+        axis_sums(ux, A.Lx, A.K, A.eck[t], s1, sx0);
+        axis_sums(uy, A.Ly, A.K, A.eck[t], s1, sy0);
+        ne += A.ek[t] * (sx0 * sy0);
+      }
+    }
+  }
+  n_nuc = A.dens_k * nn;
+  n_el = ne + A.ecx * n_nuc;
+}
+
+__device__ __forceinline__ State deriv_axial(const Chan &C, const Axial &A, double g0, double q0, double beta0,
+                                             const State &s) {
+  const double g = s.E / C.mass;
+  const double vp2 = s.vx * s.vx + s.vy * s.vy;
+  double vz;
+  const double dvz = dvz_of(g, g0, q0, beta0, vp2, vz);
+  double Fx, Fy;
+  axial_force(A, s.x, s.y, Fx, Fy);
+  State d;
+  d.x = s.vx;
+  d.y = s.vy;
+  d.vx = Fx / s.E;
+  d.vy = Fy / s.E;
+  d.dz = dvz;
+  d.E = C.ll ? C.ll_k * (g * g) * (Fx * Fx + Fy * Fy) : 0.0;
+  return d;
+}
+
+__global__ void k_axial(const Chan C, const Axial A, int64_t n_particles, const int64_t *__restrict__ offsets,
+                        int64_t n_total, const double *__restrict__ energy, const double *__restrict__ x0,
+                        const double *__restrict__ y0, const double *__restrict__ thx0,
+                        const double *__restrict__ thy0, const int64_t *__restrict__ ids, double dt, uint64_t seed,
+                        double *__restrict__ out, double *__restrict__ e_out, int *dev_status) {
+  for (int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; p < n_particles;
+       p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t off = offsets[p], L = offsets[p + 1] - off;
+    const double E0 = energy[p];
+    if (off < 0 || L < 1 || off + L > n_total || !(E0 > C.mass) || !isfinite(E0) || !isfinite(x0[p]) ||
+        (y0 && !isfinite(y0[p])) || !isfinite(thx0[p]) || (thy0 && !isfinite(thy0[p]))) {
+      atomicCAS(dev_status, 0, RAD_EDATA);
+      continue;
+    }
+    const uint64_t pid = ids ? static_cast<uint64_t>(ids[p]) : static_cast<uint64_t>(p);
+    const double g0 = E0 / C.mass;
+    const double beta0 = 1.0 - 1.0 / (2.0 * g0 * g0);
+    const double q0 = 1.0 / (4.0 * (g0 * g0) * (g0 * g0));
+    State s{x0[p], y0 ? y0[p] : 0.0, thx0[p], thy0 ? thy0[p] : 0.0, 0.0, E0};
+    double kx = 0.0, ky = 0.0;
+    double *rec = out + off * kRec;
+    for (int64_t k = 0; k < L; ++k, rec += kRec) {
+      const double g = s.E / C.mass;
+      const double vp2 = s.vx * s.vx + s.vy * s.vy;
+      double vz;
+      const double dvz = dvz_of(g, g0, q0, beta0, vp2, vz);
+      double Fx, Fy;
+      axial_force(A, s.x, s.y, Fx, Fy);
+      const double ax = Fx / s.E + kx, ay = Fy / s.E + ky;
+      const double gdot = C.ll ? C.ll_k * (g * g) * (Fx * Fx + Fy * Fy) / C.mass : 0.0;
+      rec[F_T] = static_cast<double>(k) * dt;
+      rec[F_X] = s.x;
+      rec[F_Y] = s.y;
+      rec[F_DZ] = s.dz;
+      rec[F_VX] = s.vx;
+      rec[F_VY] = s.vy;
+      rec[F_DVZ] = dvz;
+      rec[F_AX] = ax;
+      rec[F_AY] = ay;
+      rec[F_AZ] = (gdot / (g * g * g) - (s.vx * ax + s.vy * ay)) / vz;
+      if (e_out) e_out[off + k] = s.E;
+      kx = ky = 0.0;
+      if (k == L - 1) break;
+      const State k1 = deriv_axial(C, A, g0, q0, beta0, s);
+      const State k2 = deriv_axial(C, A, g0, q0, beta0, axpy(s, 0.5 * dt, k1));
+      const State k3 = deriv_axial(C, A, g0, q0, beta0, axpy(s, 0.5 * dt, k2));
+      const State k4 = deriv_axial(C, A, g0, q0, beta0, axpy(s, dt, k3));
+      const double h6 = dt / 6.0;
+      s.x += h6 * (k1.x + 2.0 * k2.x + 2.0 * k3.x + k4.x);
+      s.y += h6 * (k1.y + 2.0 * k2.y + 2.0 * k3.y + k4.y);
+      s.vx += h6 * (k1.vx + 2.0 * k2.vx + 2.0 * k3.vx + k4.vx);
+      s.vy += h6 * (k1.vy + 2.0 * k2.vy + 2.0 * k3.vy + k4.vy);
+      s.dz += h6 * (k1.dz + 2.0 * k2.dz + 2.0 * k3.dz + k4.dz);
+      s.E += h6 * (k1.E + 2.0 * k2.E + 2.0 * k3.E + k4.E);
+      if (C.ms) {
+        const double E = s.E;
+        double n_nuc, n_el;
+        axial_densities(A, s.x, s.y, n_nuc, n_el);
+        double var = C.var_k / (E * E) * n_nuc;
+        if (A.el) {
+          const double ge = E / C.mass, b2 = 1.0 - 1.0 / (ge * ge);
+          const double br = fmax(log(A.lk * (ge * ge) * b2) - b2, 0.0);
+          var += n_el * (br / ((ge * ge) * (b2 * b2)));
+        }
+        double z0, z1;
+        kick_normals(seed, pid, static_cast<uint64_t>(k), z0, z1);
+        const double sd = sqrt(var);
+        const double dthx = sd * z0, dthy = sd * z1;
+        kx = dthx / dt;
+        ky = dthy / dt;
+        s.vx += dthx;
+        s.vy += dthy;
+        if (C.ms_loss) {
+          const double gk = E / C.mass;
+          s.E = E - C.loss_k * (gk * gk * gk) * (dthx * dthx + dthy * dthy);
+        }
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------
 // Mixed precision (RAD_TRAJ_FP32): FP32 arithmetic with double-float state
 // ------------------------------------------------------------------------------------
 // GB300 issues FP32 at 64x its FP64 rate (72x measured), so this form evaluates the RK4 stages in
@@ -680,8 +851,94 @@ int launch_trajectories(const rad_channel *ch, const rad_planar_potential *pot, 
   return e == cudaSuccess ? RAD_OK : cuda_status(e);
 }
 
+int launch_axial(const rad_channel *ch, const rad_axial_potential *pot, int64_t n_particles, const int64_t *offsets,
+                 int64_t n_samples_total, const double *energy_eV, const double *x0, const double *y0,
+                 const double *thx0, const double *thy0, const int64_t *particle_ids, double dt, uint64_t seed,
+                 double *out, double *energy_out, void *stream) {
+  if (!ch || !pot || n_particles < 0 || n_samples_total < 0) return RAD_EINVAL;
+  if (!(dt > 0.0) || !isfinite(dt) || !(ch->mass_eV > 0.0) || (ch->charge_sign != 1 && ch->charge_sign != -1) ||
+      (ch->flags & ~31))
+    return RAD_EINVAL;
+  if (ch->flags & RAD_TRAJ_FP32) return RAD_EUNSUPPORTED;
+  const bool ms = (ch->flags & RAD_TRAJ_MS) != 0, el = (ch->flags & RAD_TRAJ_MS_EL) != 0;
+  if (ms && !(ch->X0 > 0.0 && ch->rho > 0.0 && ch->eps_s_eV >= 0.0)) return RAD_EINVAL;
+  if (el && !ms) return RAD_EINVAL;
+  if (!(ch->rho >= 0.0) || !isfinite(ch->rho)) return RAD_EINVAL;
+  const rad_string_lattice &Lt = pot->lattice;
+  if (pot->n_terms < 1 || pot->n_terms > kMaxTerms || pot->n_cells < 1 || pot->n_cells > 4 || Lt.n_strings < 1 ||
+      Lt.n_strings > 8 || !(Lt.cell_x > 0.0) || !(Lt.cell_y > 0.0) || !(Lt.d > 0.0) || !isfinite(Lt.cell_x) ||
+      !isfinite(Lt.cell_y) || !isfinite(Lt.d))
+    return RAD_EINVAL;
+  if (el && !(pot->I_eV > 0.0 && isfinite(pot->cx))) return RAD_EINVAL;
+  Axial A{};
+  A.nt = pot->n_terms;
+  A.nb = Lt.n_strings;
+  A.K = pot->n_cells;
+  A.el = el ? 1 : 0;
+  A.Lx = Lt.cell_x;
+  A.Ly = Lt.cell_y;
+  for (int b = 0; b < A.nb; ++b) {
+    if (!isfinite(Lt.sx[b]) || !isfinite(Lt.sy[b])) return RAD_EINVAL;
+    A.sx[b] = Lt.sx[b];
+    A.sy[b] = Lt.sy[b];
+  }
+  const double rho2 = ch->rho * ch->rho;
+  const double N = A.nb / (Lt.d * Lt.cell_x * Lt.cell_y);
+  const double e2 = kAlpha * kHbarC;
+  const double el_pref = 0.5 * dt * kPi * kR0 * kR0;
+  for (int i = 0; i < A.nt; ++i) {
+    const double C = pot->b[i] / (4.0 * kPi * kPi) + rho2;
+    if (!isfinite(pot->a[i]) || !isfinite(C) || !(C > 0.0)) return RAD_EINVAL;
+    A.fk[i] = ch->charge_sign * (2.0 * e2 * kA0 / Lt.d) * (pot->a[i] / C) * (2.0 / C);
+    A.ck[i] = 1.0 / C;
+    if (el) {
+      const double CX = pot->bx[i] / (4.0 * kPi * kPi) + rho2;
+      if (!isfinite(pot->ax[i]) || !isfinite(CX) || !(CX > 0.0)) return RAD_EINVAL;
+      A.ek[i] = el_pref * pot->ax[i] / (kPi * Lt.d * CX);
+      A.eck[i] = 1.0 / CX;
+    }
+  }
+  A.dens_k = ms ? 1.0 / (kPi * rho2 * N * Lt.d) : 0.0;
+  A.inv_rho2 = ms ? 1.0 / rho2 : 0.0;
+  A.ecx = el ? el_pref * pot->cx * N : 0.0;
+  A.lk = el ? 2.0 * kMe / pot->I_eV : 0.0;
+  bool ok = isfinite(A.dens_k) && isfinite(A.inv_rho2) && isfinite(A.ecx) && isfinite(A.lk);
+  for (int i = 0; i < A.nt; ++i) ok = ok && isfinite(A.fk[i]) && isfinite(A.ck[i]) && isfinite(A.ek[i]) && isfinite(A.eck[i]);
+  if (!ok) return RAD_EINVAL;
+  if (n_particles == 0) return RAD_OK;
+  if (!offsets || !energy_eV || !x0 || !thx0 || !out) return RAD_EINVAL;
+  cudaError_t e;
+  int *ds = device_status_word(&e);
+  if (!ds) return cuda_status(e);
+  Chan C{};
+  C.mass = ch->mass_eV;
+  C.var_k = ms ? 0.5 * ch->eps_s_eV * ch->eps_s_eV * (dt / ch->X0) : 0.0;
+  C.loss_k = ch->mass_eV * kAlpha / (2.0 * kPi);
+  C.ll_k = -(2.0 / 3.0) * kAlpha * kHbarC * ch->mass_eV / (ch->mass_eV * ch->mass_eV * ch->mass_eV);
+  C.ms = ms;
+  C.ll = (ch->flags & RAD_TRAJ_LL) != 0;
+  C.ms_loss = (ch->flags & RAD_TRAJ_MS_LOSS) != 0;
+  const int block = n_particles < 152 * 4 * 32 ? 32 : 128;
+  int64_t grid = (n_particles + block - 1) / block;
+  if (grid > 1 << 20) grid = 1 << 20;
+  k_axial<<<static_cast<unsigned>(grid), block, 0, static_cast<cudaStream_t>(stream)>>>(
+      C, A, n_particles, offsets, n_samples_total, energy_eV, x0, y0, thx0, thy0, particle_ids, dt, seed, out,
+      energy_out, ds);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? RAD_OK : cuda_status(e);
+}
+
 }  // namespace
 }  // namespace rad
+
+extern "C" int rad_axial_trajectories(const rad_channel *ch, const rad_axial_potential *pot, int64_t n_particles,
+                                      const int64_t *offsets, int64_t n_samples_total, const double *energy_eV,
+                                      const double *x0, const double *y0, const double *thx0, const double *thy0,
+                                      const int64_t *particle_ids, double dt, uint64_t seed, double *out,
+                                      double *energy_out, void *stream) {
+  return rad::launch_axial(ch, pot, n_particles, offsets, n_samples_total, energy_eV, x0, y0, thx0, thy0,
+                           particle_ids, dt, seed, out, energy_out, stream);
+}
 
 extern "C" int rad_channeling_trajectories(const rad_channel *ch, int64_t n_particles, const int64_t *offsets,
                                            int64_t n_samples_total, const double *energy_eV, const double *x0,

@@ -1,11 +1,15 @@
-"""Time the GPU trajectory integrator (rad_channeling_trajectories, or rad_crystal_trajectories
-with --potential doyle-turner) on a planar-channeling ensemble.
+"""Time the GPU trajectory integrator (rad_channeling_trajectories, rad_crystal_trajectories
+with --potential doyle-turner, or rad_axial_trajectories with --potential axial) on a channeling
+ensemble.
 
   python -m paper_1910_10391_gb300.run_traj --particles 1024 --samples 20000 --precision fp32
 
 Entry conditions: x0 uniform over the channel, theta_x0 ~ N(0, (0.3 theta_L)^2) (the ensemble
 workloads' beam), Si(110) harmonic well with U0 = 20 eV, or the synthetic four-Gaussian
-Doyle-Turner fit of the input module (3 neighbouring planes on each side). Prints one JSON line
+Doyle-Turner fit of the input module (3 neighbouring planes on each side), or that fit on the
+strings of the Si <110> axis (the crystal library's lattice, 2 cells on each side; entry uniform
+over the transverse cell, both angles ~ N(0, (0.3 psi)^2) with psi = sqrt(2 x 35 eV / E), FP64
+only). Prints one JSON line
 with the CUDA-event time of the integrator (best of --repeat) and samples/s.
 """
 from __future__ import annotations
@@ -29,7 +33,7 @@ def main(argv=None):
     ap.add_argument("--charge", type=int, default=+1, choices=[+1, -1])
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32"])
     ap.add_argument("--physics", default="ms", choices=["none", "ms", "ms+ll+loss", "ms+el+ll+loss"])
-    ap.add_argument("--potential", default="harmonic", choices=["harmonic", "doyle-turner"])
+    ap.add_argument("--potential", default="harmonic", choices=["harmonic", "doyle-turner", "axial"])
     ap.add_argument("--repeat", type=int, default=3)
     ap.add_argument("--seed", type=int, default=2)
     a = ap.parse_args(argv)
@@ -49,7 +53,17 @@ def main(argv=None):
              "ms+ll+loss": rad.RAD_TRAJ_MS | rad.RAD_TRAJ_LL | rad.RAD_TRAJ_MS_LOSS,
              "ms+el+ll+loss": rad.RAD_TRAJ_MS | rad.RAD_TRAJ_MS_EL | rad.RAD_TRAJ_LL | rad.RAD_TRAJ_MS_LOSS}[a.physics]
     pot = None
-    if a.potential == "doyle-turner":
+    y0 = thy = None
+    if a.potential == "axial":
+        lat = rad.crystal_string_lattice(rad.RAD_DIAMOND, 5.431e-10, 110)
+        pot = rad.RadAxialPotential.make(I.SYNTH_DT_A, I.SYNTH_DT_B, lat, I.SYNTH_DT_AX, I.SYNTH_DT_BX, I.SYNTH_DT_CX,
+                                         I.SI_I_EV, n_cells=2)
+        psi = math.sqrt(2.0 * 35.0 / a.energy)
+        x0, y0 = d(rng.uniform(0.0, lat.cell_x, n)), d(rng.uniform(0.0, lat.cell_y, n))
+        th, thy = d(rng.normal(0.0, 0.3 * psi, n)), d(rng.normal(0.0, 0.3 * psi, n))
+        if a.precision == "fp32":
+            raise SystemExit("the axial integrator is FP64 only")
+    elif a.potential == "doyle-turner":
         pot = rad.RadPlanarPotential.make(I.SYNTH_DT_A, I.SYNTH_DT_B, I.SI_N, I.SYNTH_DT_AX, I.SYNTH_DT_BX,
                                           I.SYNTH_DT_CX, I.SI_I_EV, n_neighbours=3)
     elif flags & rad.RAD_TRAJ_MS_EL:
@@ -65,6 +79,8 @@ def main(argv=None):
         e0.record(st)
         if pot is None:
             rc = rad.rad_channeling_trajectories(ch, doff, E, x0, th, out, 5e-9, a.seed)
+        elif a.potential == "axial":
+            rc = rad.rad_axial_trajectories(ch, pot, doff, E, x0, th, out, 5e-9, a.seed, y0=y0, thy0=thy)
         else:
             rc = rad.rad_crystal_trajectories(ch, pot, doff, E, x0, th, out, 5e-9, a.seed)
         e1.record(st)
