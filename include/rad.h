@@ -561,6 +561,45 @@ int rad_axial_trajectories(const rad_channel *ch, const rad_axial_potential *pot
                            const int64_t *particle_ids, double dt, uint64_t seed, double *out,
                            double *energy_out, void *stream);
 
+/* Step control of rad_trajectories_adaptive. */
+typedef struct {
+  double rtol;          /* relative tolerance of the embedded error estimate (> 0)                 */
+  double atol_x;        /* absolute tolerance of x, y and dz, m (> 0)                              */
+  double atol_v;        /* absolute tolerance of the angles v_x, v_y (> 0)                          */
+  int max_level;        /* 0 .. 16: the smallest sub-step is an output interval / 2^max_level      */
+  int64_t max_substeps; /* per particle, >= 1: a particle that needs more stops, RAD_EDATA          */
+} rad_step_control;
+
+/*
+ * rad_trajectories_adaptive -- the trajectory integrators with adaptive steps between output
+ * times the caller sets (Sec. IV: an RK45 solver with step-size control and a lower bound on the
+ * step, returning the trajectory at the times the caller asks for). The field is the harmonic
+ * well of `ch` (pot and axial NULL), the planar potential `pot`, or the axial potential `axial`
+ * (at most one of them). Each output interval H = t_{k+1} - t_k is integrated with Dormand-Prince
+ * 5(4) sub-steps H / 2^m (Dormand and Prince, J. Comput. Appl. Math. 6 (1980) 19): a sub-step
+ * whose error estimate, the RMS over (x, y, v_x, v_y, dz, E) of (y5 - y4) / (atol_i + rtol
+ * max(|y_i|, |y5_i|)) with atol = (atol_x, atol_x, atol_v, atol_v, atol_x, 0), exceeds 1 is
+ * repeated at half the size unless m = max_level (the lower bound), where it is kept; after an
+ * accepted sub-step with error below 2^-6 the size doubles when the interval position allows it.
+ * The level starts at 0 and carries over between intervals; each interval ends exactly at its
+ * output time. Kicks (RAD_TRAJ_MS) follow each interval with variances for its length H; the next
+ * record's acceleration carries the kick as delta_v / w, w = (t_{k+2} - t_k)/2, or H for the last
+ * record (delta_v / dt for uniform times, as in rad_channeling_trajectories). times: device,
+ * [n_samples_total], the output times of every record of every particle (increasing within a
+ * particle), or NULL for t_k = k dt. substeps_out: device int64 [n_particles] (may be NULL), the
+ * accepted sub-steps of each particle. Records, entry values (y0, thy0 may be NULL), streams and
+ * flags as in rad_channeling_trajectories / rad_axial_trajectories; FP64 only (RAD_TRAJ_FP32:
+ * RAD_EUNSUPPORTED). Host checks return RAD_EINVAL before anything is enqueued; a particle with
+ * non-increasing or non-finite times, or that exceeds max_substeps, records RAD_EDATA (its
+ * records after that point are not written).
+ */
+int rad_trajectories_adaptive(const rad_channel *ch, const rad_planar_potential *pot,
+                              const rad_axial_potential *axial, const rad_step_control *sc, int64_t n_particles,
+                              const int64_t *offsets, int64_t n_samples_total, const double *energy_eV,
+                              const double *x0, const double *y0, const double *thx0, const double *thy0,
+                              const int64_t *particle_ids, const double *times, double dt, uint64_t seed,
+                              double *out, double *energy_out, int64_t *substeps_out, void *stream);
+
 /*
  * rad_device_status -- waits for the current device to finish, returns the first
  * device-side error recorded since the last reset (RAD_OK, RAD_EDATA or RAD_ETIMEOUT)

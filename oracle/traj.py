@@ -432,3 +432,157 @@ def axial_trajectories(x0, y0, thx0, thy0, E0_eV, n_samples: int, dt: float, see
                 gk = E / mass_eV
                 s[:, 5] = E - mass_eV * ALPHA / (2.0 * math.pi) * gk ** 3 * (dthx * dthx + dthy * dthy)
     return (out, Es) if energies else out
+
+
+# --------------------------------------------------------------------------------------------
+# Adaptive steps between caller-set output times (Sec. IV: an RK45 solver with step-size control
+# and a lower bound on the step, which returns the trajectory at the times the caller asks for)
+# --------------------------------------------------------------------------------------------
+# Dormand-Prince 5(4) pair (J. R. Dormand, P. J. Prince, J. Comput. Appl. Math. 6 (1980) 19): nodes,
+# stage coefficients, the fifth-order weights (the solution) and the embedded fourth-order weights.
+DP_C = (0.0, 1.0 / 5.0, 3.0 / 10.0, 4.0 / 5.0, 8.0 / 9.0, 1.0, 1.0)
+DP_A = ((),
+        (1.0 / 5.0,),
+        (3.0 / 40.0, 9.0 / 40.0),
+        (44.0 / 45.0, -56.0 / 15.0, 32.0 / 9.0),
+        (19372.0 / 6561.0, -25360.0 / 2187.0, 64448.0 / 6561.0, -212.0 / 729.0),
+        (9017.0 / 3168.0, -355.0 / 33.0, 46732.0 / 5247.0, 49.0 / 176.0, -5103.0 / 18656.0),
+        (35.0 / 384.0, 0.0, 500.0 / 1113.0, 125.0 / 192.0, -2187.0 / 6784.0, 11.0 / 84.0))
+DP_B5 = (35.0 / 384.0, 0.0, 500.0 / 1113.0, 125.0 / 192.0, -2187.0 / 6784.0, 11.0 / 84.0, 0.0)
+DP_B4 = (5179.0 / 57600.0, 0.0, 7571.0 / 16695.0, 393.0 / 640.0, -92097.0 / 339200.0, 187.0 / 2100.0, 1.0 / 40.0)
+
+
+def dp5_step(f, y, h):
+    """One Dormand-Prince step of the autonomous system y' = f(y): (fifth-order, fourth-order)."""
+    k = []
+    for i in range(7):
+        yi = y.copy()
+        for j, a in enumerate(DP_A[i]):
+            yi = yi + h * a * k[j]
+        k.append(f(yi))
+    y5, y4 = y.copy(), y.copy()
+    for i in range(7):
+        y5 = y5 + h * DP_B5[i] * k[i]
+        y4 = y4 + h * DP_B4[i] * k[i]
+    return y5, y4
+
+
+def step_error(y, y5, y4, scale_abs, rtol):
+    """RMS over the state's components of (y5 - y4) / (atol_i + rtol max(|y_i|, |y5_i|))."""
+    sc = scale_abs + rtol * np.maximum(np.abs(y), np.abs(y5))
+    return float(np.sqrt(np.mean(((y5 - y4) / sc) ** 2)))
+
+
+def adaptive_interval(f, y, H, level, max_level, scale_abs, rtol, grow_below=2.0 ** -6):
+    """Integrate over one output interval H with sub-steps H / 2^m: a step whose error exceeds 1 is
+    repeated at half the size (m + 1) unless m is the lower bound max_level, where it is kept; after
+    an accepted step with error below grow_below the size doubles (m - 1) when the position is a
+    multiple of the doubled step. The position is an integer count of H / 2^max_level, so the
+    interval ends exactly at H. Returns (y, level, accepted sub-steps)."""
+    unit = 2 ** max_level
+    pos, m, n = 0, level, 0
+    while pos < unit:
+        h = H / (2 ** m)
+        y5, y4 = dp5_step(f, y, h)
+        err = step_error(y, y5, y4, scale_abs, rtol)
+        if err > 1.0 and m < max_level:
+            m += 1
+            continue
+        y = y5
+        pos += 2 ** (max_level - m)
+        n += 1
+        if err < grow_below and m > 0 and pos % (2 ** (max_level - m + 1)) == 0:
+            m -= 1
+    return y, m, n
+
+
+def trajectories_adaptive(x0, thx0, thy0, E0_eV, times, seed: int, *, rtol, atol_x, atol_v, max_level, y0=0.0,
+                          charge=+1, U0_eV=20.0, d_p=1.92e-10, eps_s_eV=10.6e6, X0=0.0937, rho=0.075e-10, ms=True,
+                          ll=False, ms_loss=False, mass_eV=0.51099895e6, particle_ids=None, energies=False, pot=None,
+                          axial=None, ms_el=False, counts=False):
+    """Records [n][len(times)][10] as `trajectories` (harmonic well, planar potential `pot` or axial
+    potential `axial`), with the RK4 step replaced by adaptive Dormand-Prince steps over each output
+    interval (adaptive_interval; the level carries over from one interval to the next, starting at
+    0) and records at the caller's `times` (increasing, one array for all particles). The kick after
+    interval k enters the next record's acceleration as delta_v / w, w = (t_{k+2} - t_k)/2, or the
+    last interval's length for the last record (dt for uniform times). With counts=True also
+    returns the accepted sub-steps per particle."""
+    times = np.asarray(times, dtype=np.float64)
+    L = times.shape[0]
+    x0 = np.atleast_1d(np.asarray(x0, dtype=np.float64))
+    n = x0.shape[0]
+    bc = lambda v: np.broadcast_to(np.asarray(v, np.float64), (n,)).copy()
+    pid = np.arange(n, dtype=np.uint64) if particle_ids is None else np.asarray(particle_ids, dtype=np.uint64)
+    E0 = bc(E0_eV)
+
+    def field(x, y):
+        if axial is not None:
+            return axial_force(x, y, axial, rho, charge)
+        if pot is not None:
+            return planar_force(x, pot, d_p, rho, charge), np.zeros_like(x)
+        return force(x, U0_eV, d_p, charge), np.zeros_like(x)
+
+    def nuclear(x, y):
+        return string_density(x, y, axial.lat, rho, axial.K) if axial is not None else plane_density(x, d_p, rho)
+
+    def electrons(x, y):
+        return axial_electron_density(x, y, axial, rho) if axial is not None else electron_density(x, pot, d_p, rho)
+
+    out = np.empty((n, L, 10))
+    Es = np.empty((n, L))
+    steps = np.zeros(n, dtype=np.int64)
+    scale_abs = np.array([atol_x, atol_x, atol_v, atol_v, atol_x, 0.0])
+    for p in range(n):
+        g0 = E0[p] / mass_eV
+        beta0 = 1.0 - 1.0 / (2.0 * g0 * g0)
+
+        def dvz_of(g, vp2, vz):
+            d_inv = ((g - g0) * (g + g0)) / ((g * g) * (g0 * g0))
+            return (d_inv - vp2 - 1.0 / (4.0 * g0 ** 4)) / (vz + beta0)
+
+        def f(st):
+            g = st[5] / mass_eV
+            vp2 = st[2] ** 2 + st[3] ** 2
+            vz = math.sqrt(1.0 - 1.0 / (g * g) - vp2)
+            Fx, Fy = field(np.array([st[0]]), np.array([st[1]]))
+            Fx, Fy = float(Fx[0]), float(Fy[0])
+            gd = -(2.0 / 3.0) * ALPHA * HBARC_EV_M * g * g * (Fx * Fx + Fy * Fy) / mass_eV ** 3 if ll else 0.0
+            return np.array([st[2], st[3], Fx / st[5], Fy / st[5], dvz_of(g, vp2, vz), gd * mass_eV])
+
+        s = np.array([x0[p], bc(y0)[p], bc(thx0)[p], bc(thy0)[p], 0.0, E0[p]])
+        kick = np.zeros(2)
+        level = 0
+        for k in range(L):
+            g = s[5] / mass_eV
+            vp2 = s[2] ** 2 + s[3] ** 2
+            vz = math.sqrt(1.0 - 1.0 / (g * g) - vp2)
+            Fx, Fy = field(np.array([s[0]]), np.array([s[1]]))
+            Fx, Fy = float(Fx[0]), float(Fy[0])
+            ax, ay = Fx / s[5] + kick[0], Fy / s[5] + kick[1]
+            gd = -(2.0 / 3.0) * ALPHA * HBARC_EV_M * g * g * (Fx * Fx + Fy * Fy) / mass_eV ** 3 if ll else 0.0
+            out[p, k] = (times[k], s[0], s[1], s[4], s[2], s[3], dvz_of(g, vp2, vz), ax, ay,
+                         (gd / g ** 3 - (s[2] * ax + s[3] * ay)) / vz)
+            Es[p, k] = s[5]
+            kick[:] = 0.0
+            if k == L - 1:
+                break
+            s, level, nst = adaptive_interval(f, s, times[k + 1] - times[k], level, max_level, scale_abs, rtol)
+            steps[p] += nst
+            if ms:
+                E = s[5]
+                var = 0.5 * (eps_s_eV / E) ** 2 * ((times[k + 1] - times[k]) / X0) * float(
+                    nuclear(np.array([s[0]]), np.array([s[1]]))[0])
+                if ms_el:
+                    var += 0.5 * (times[k + 1] - times[k]) * float(electron_scattering_rate(
+                        E / mass_eV, electrons(np.array([s[0]]), np.array([s[1]])), (axial or pot).I_eV)[0])
+                z0, z1 = kick_normals(seed, pid[p:p + 1], k)
+                dthx, dthy = math.sqrt(var) * float(z0[0]), math.sqrt(var) * float(z1[0])
+                w = 0.5 * (times[k + 2] - times[k]) if k + 2 < L else times[k + 1] - times[k]
+                kick[0], kick[1] = dthx / w, dthy / w
+                s[2] += dthx
+                s[3] += dthy
+                if ms_loss:
+                    gk = E / mass_eV
+                    s[5] = E - mass_eV * ALPHA / (2.0 * math.pi) * gk ** 3 * (dthx * dthx + dthy * dthy)
+    res = (out, Es) if energies else out
+    return (res, steps) if counts else res

@@ -87,6 +87,12 @@ class RadAxialPotential(ctypes.Structure):
         return cls(len(a), int(n_cells), pad(a), pad(b), pad(ax), pad(bx), float(cx), float(I_eV), lattice)
 
 
+class RadStepControl(ctypes.Structure):
+    """rad_step_control: tolerances, lower bound (max_level) and sub-step budget of the adaptive integrator."""
+    _fields_ = [("rtol", ctypes.c_double), ("atol_x", ctypes.c_double), ("atol_v", ctypes.c_double),
+                ("max_level", ctypes.c_int), ("max_substeps", ctypes.c_int64)]
+
+
 MODES = {"classical": RAD_CLASSICAL, "spin0": RAD_SPIN0, "spin_half": RAD_SPIN_HALF}
 PRECISIONS = {"fp64": RAD_FP64, "mixed": RAD_MIXED, "fp64_df": RAD_FP64_DF}
 
@@ -146,6 +152,10 @@ def load(build_if_missing: bool = True):
         lib.rad_axial_trajectories.argtypes = [ctypes.POINTER(RadChannel), ctypes.POINTER(RadAxialPotential), i64,
                                                P, i64, P, P, P, P, P, P, ctypes.c_double, u64, P, P, P]
         lib.rad_axial_trajectories.restype = c_int
+        lib.rad_trajectories_adaptive.argtypes = [ctypes.POINTER(RadChannel), ctypes.POINTER(RadPlanarPotential),
+                                                  ctypes.POINTER(RadAxialPotential), ctypes.POINTER(RadStepControl),
+                                                  i64, P, i64, P, P, P, P, P, P, P, ctypes.c_double, u64, P, P, P, P]
+        lib.rad_trajectories_adaptive.restype = c_int
         lib.rad_crystal_element.argtypes = [c_int, ctypes.POINTER(RadElement)]
         lib.rad_crystal_element.restype = c_int
         lib.rad_crystal_string_lattice.argtypes = [c_int, ctypes.c_double, c_int, ctypes.POINTER(RadStringLattice)]
@@ -376,6 +386,24 @@ def rad_axial_trajectories(channel, potential, offsets, energy_eV, x0, thx0, out
         _dev_ptr(x0, f64, "x0"), _dev_ptr(y0, f64, "y0"), _dev_ptr(thx0, f64, "thx0"), _dev_ptr(thy0, f64, "thy0"),
         _dev_ptr(particle_ids, torch.int64, "particle_ids"), float(dt), int(seed), _dev_ptr(out, f64, "out"),
         _dev_ptr(energy_out, f64, "energy_out"), _stream(stream))
+
+
+def rad_trajectories_adaptive(channel, step_control, offsets, energy_eV, x0, thx0, out, seed, times=None, dt=0.0,
+                              planar=None, axial=None, y0=None, thy0=None, particle_ids=None, energy_out=None,
+                              substeps_out=None, stream=None) -> int:
+    """Trajectories with adaptive Dormand-Prince steps between output times (`times`, device, per
+    record; or uniform k dt) in the harmonic well, the planar potential `planar` or the axial
+    potential `axial`."""
+    import torch
+    f64 = torch.float64
+    return load().rad_trajectories_adaptive(
+        ctypes.byref(channel), ctypes.byref(planar) if planar is not None else None,
+        ctypes.byref(axial) if axial is not None else None, ctypes.byref(step_control) if step_control else None,
+        _numel(offsets) - 1, _dev_ptr(offsets, torch.int64, "offsets"), _numel(out) // RAD_NREC,
+        _dev_ptr(energy_eV, f64, "energy_eV"), _dev_ptr(x0, f64, "x0"), _dev_ptr(y0, f64, "y0"),
+        _dev_ptr(thx0, f64, "thx0"), _dev_ptr(thy0, f64, "thy0"), _dev_ptr(particle_ids, torch.int64, "particle_ids"),
+        _dev_ptr(times, f64, "times"), float(dt), int(seed), _dev_ptr(out, f64, "out"),
+        _dev_ptr(energy_out, f64, "energy_out"), _dev_ptr(substeps_out, torch.int64, "substeps_out"), _stream(stream))
 
 
 def crystal_element(element) -> RadElement:

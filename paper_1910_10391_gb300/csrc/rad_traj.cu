@@ -440,6 +440,251 @@ __global__ void k_axial(const Chan C, const Axial A, int64_t n_particles, const 
 }
 
 // ------------------------------------------------------------------------------------
+// Adaptive steps between caller-set output times (rad_trajectories_adaptive; Sec. IV: an RK45
+// solver with step-size control and a lower bound on the step). Each output interval H is
+// integrated with Dormand-Prince 5(4) sub-steps H / 2^m (J. R. Dormand, P. J. Prince, J. Comput.
+// Appl. Math. 6 (1980) 19): a sub-step whose embedded error estimate exceeds 1 is repeated at half
+// the size unless m is the lower bound max_level, where it is kept; after an accepted sub-step with
+// error below 2^-6 the size doubles when the position is a multiple of the doubled size. The
+// position is an integer count of H / 2^max_level, so each interval ends exactly at its output
+// time, and the level carries over to the next interval. Error: RMS over (x, y, v_x, v_y, dz, E)
+// of (y5 - y4) / (atol_i + rtol max(|y_i|, |y5_i|)), atol = (atol_x, atol_x, atol_v, atol_v,
+// atol_x, 0). Field kinds: 0 harmonic well, 1 Doyle-Turner planes, 2 axial strings.
+// ------------------------------------------------------------------------------------
+struct StepCtl {
+  double rtol, atol_x, atol_v;
+  int max_level;
+  int64_t max_substeps;
+};
+
+template <int KIND>
+__device__ __forceinline__ void field2(const Chan &C, const Planar &P, const Axial &A, double x, double y, double &Fx,
+                                       double &Fy) {
+  if constexpr (KIND == 2) {
+    axial_force(A, x, y, Fx, Fy);
+  } else {
+    Fx = field<KIND == 1>(C, P, x);
+    Fy = 0.0;
+  }
+}
+
+template <int KIND>
+__device__ __forceinline__ State deriv2(const Chan &C, const Planar &P, const Axial &A, double g0, double q0,
+                                        double beta0, const State &s) {
+  const double g = s.E / C.mass;
+  const double vp2 = s.vx * s.vx + s.vy * s.vy;
+  double vz;
+  const double dvz = dvz_of(g, g0, q0, beta0, vp2, vz);
+  double Fx, Fy;
+  field2<KIND>(C, P, A, s.x, s.y, Fx, Fy);
+  State d;
+  d.x = s.vx;
+  d.y = s.vy;
+  d.vx = Fx / s.E;
+  d.vy = Fy / s.E;
+  d.dz = dvz;
+  d.E = C.ll ? C.ll_k * (g * g) * (Fx * Fx + Fy * Fy) : 0.0;
+  return d;
+}
+
+__device__ __forceinline__ void acc(State &y, double c, const State &k) {
+  y.x += c * k.x;
+  y.y += c * k.y;
+  y.vx += c * k.vx;
+  y.vy += c * k.vy;
+  y.dz += c * k.dz;
+  y.E += c * k.E;
+}
+
+__device__ __forceinline__ double err_term(double e, double y, double y5, double atol, double rtol) {
+  const double sc = atol + rtol * fmax(fabs(y), fabs(y5));
+  const double r = e / sc;
+  return r * r;
+}
+
+// one Dormand-Prince step: y5 (the solution) and the error estimate's RMS
+template <int KIND>
+__device__ __forceinline__ double dp5(const Chan &C, const Planar &P, const Axial &A, double g0, double q0,
+                                      double beta0, const StepCtl &S, const State &y, double h, State &y5) {
+  constexpr double a21 = 1.0 / 5.0;
+  constexpr double a31 = 3.0 / 40.0, a32 = 9.0 / 40.0;
+  constexpr double a41 = 44.0 / 45.0, a42 = -56.0 / 15.0, a43 = 32.0 / 9.0;
+  constexpr double a51 = 19372.0 / 6561.0, a52 = -25360.0 / 2187.0, a53 = 64448.0 / 6561.0, a54 = -212.0 / 729.0;
+  constexpr double a61 = 9017.0 / 3168.0, a62 = -355.0 / 33.0, a63 = 46732.0 / 5247.0, a64 = 49.0 / 176.0,
+                   a65 = -5103.0 / 18656.0;
+  constexpr double b1 = 35.0 / 384.0, b3 = 500.0 / 1113.0, b4 = 125.0 / 192.0, b5 = -2187.0 / 6784.0,
+                   b6 = 11.0 / 84.0;
+  // embedded (fourth-order) weights
+  constexpr double e1 = 5179.0 / 57600.0, e3 = 7571.0 / 16695.0, e4 = 393.0 / 640.0, e5 = -92097.0 / 339200.0,
+                   e6 = 187.0 / 2100.0, e7 = 1.0 / 40.0;
+  const State k1 = deriv2<KIND>(C, P, A, g0, q0, beta0, y);
+  State t = y;
+  acc(t, h * a21, k1);
+  const State k2 = deriv2<KIND>(C, P, A, g0, q0, beta0, t);
+  t = y;
+  acc(t, h * a31, k1);
+  acc(t, h * a32, k2);
+  const State k3 = deriv2<KIND>(C, P, A, g0, q0, beta0, t);
+  t = y;
+  acc(t, h * a41, k1);
+  acc(t, h * a42, k2);
+  acc(t, h * a43, k3);
+  const State k4 = deriv2<KIND>(C, P, A, g0, q0, beta0, t);
+  t = y;
+  acc(t, h * a51, k1);
+  acc(t, h * a52, k2);
+  acc(t, h * a53, k3);
+  acc(t, h * a54, k4);
+  const State k5 = deriv2<KIND>(C, P, A, g0, q0, beta0, t);
+  t = y;
+  acc(t, h * a61, k1);
+  acc(t, h * a62, k2);
+  acc(t, h * a63, k3);
+  acc(t, h * a64, k4);
+  acc(t, h * a65, k5);
+  const State k6 = deriv2<KIND>(C, P, A, g0, q0, beta0, t);
+  y5 = y;
+  acc(y5, h * b1, k1);
+  acc(y5, h * b3, k3);
+  acc(y5, h * b4, k4);
+  acc(y5, h * b5, k5);
+  acc(y5, h * b6, k6);
+  const State k7 = deriv2<KIND>(C, P, A, g0, q0, beta0, y5);
+  State y4 = y;
+  acc(y4, h * e1, k1);
+  acc(y4, h * e3, k3);
+  acc(y4, h * e4, k4);
+  acc(y4, h * e5, k5);
+  acc(y4, h * e6, k6);
+  acc(y4, h * e7, k7);
+  double s2 = err_term(y5.x - y4.x, y.x, y5.x, S.atol_x, S.rtol);
+  s2 += err_term(y5.y - y4.y, y.y, y5.y, S.atol_x, S.rtol);
+  s2 += err_term(y5.vx - y4.vx, y.vx, y5.vx, S.atol_v, S.rtol);
+  s2 += err_term(y5.vy - y4.vy, y.vy, y5.vy, S.atol_v, S.rtol);
+  s2 += err_term(y5.dz - y4.dz, y.dz, y5.dz, S.atol_x, S.rtol);
+  s2 += err_term(y5.E - y4.E, y.E, y5.E, 0.0, S.rtol);
+  return sqrt(s2 / 6.0);
+}
+
+template <int KIND>
+__global__ void k_adaptive(const Chan C, const Planar P, const Axial A, const StepCtl S, int64_t n_particles,
+                           const int64_t *__restrict__ offsets, int64_t n_total, const double *__restrict__ energy,
+                           const double *__restrict__ x0, const double *__restrict__ y0,
+                           const double *__restrict__ thx0, const double *__restrict__ thy0,
+                           const int64_t *__restrict__ ids, const double *__restrict__ times, double dt, uint64_t seed,
+                           double *__restrict__ out, double *__restrict__ e_out, int64_t *__restrict__ counts,
+                           int *dev_status) {
+  for (int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; p < n_particles;
+       p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t off = offsets[p], L = offsets[p + 1] - off;
+    const double E0 = energy[p];
+    if (off < 0 || L < 1 || off + L > n_total || !(E0 > C.mass) || !isfinite(E0) || !isfinite(x0[p]) ||
+        (y0 && !isfinite(y0[p])) || !isfinite(thx0[p]) || (thy0 && !isfinite(thy0[p]))) {
+      atomicCAS(dev_status, 0, RAD_EDATA);
+      continue;
+    }
+    const double *tp = times ? times + off : nullptr;
+    auto t_of = [&](int64_t k) { return tp ? tp[k] : static_cast<double>(k) * dt; };
+    bool bad_t = false;
+    for (int64_t k = 0; k < L && tp; ++k)
+      if (!isfinite(tp[k]) || (k > 0 && !(tp[k] > tp[k - 1]))) bad_t = true;
+    if (bad_t) {
+      atomicCAS(dev_status, 0, RAD_EDATA);
+      continue;
+    }
+    const uint64_t pid = ids ? static_cast<uint64_t>(ids[p]) : static_cast<uint64_t>(p);
+    const double g0 = E0 / C.mass;
+    const double beta0 = 1.0 - 1.0 / (2.0 * g0 * g0);
+    const double q0 = 1.0 / (4.0 * (g0 * g0) * (g0 * g0));
+    State s{x0[p], y0 ? y0[p] : 0.0, thx0[p], thy0 ? thy0[p] : 0.0, 0.0, E0};
+    double kx = 0.0, ky = 0.0;
+    int level = 0;
+    int64_t n_steps = 0, n_tries = 0;  // accepted sub-steps; all sub-steps (accepted or repeated)
+    const int64_t unit = int64_t(1) << S.max_level;
+    double *rec = out + off * kRec;
+    bool stopped = false;
+    for (int64_t k = 0; k < L && !stopped; ++k, rec += kRec) {
+      const double g = s.E / C.mass;
+      const double vp2 = s.vx * s.vx + s.vy * s.vy;
+      double vz;
+      const double dvz = dvz_of(g, g0, q0, beta0, vp2, vz);
+      double Fx, Fy;
+      field2<KIND>(C, P, A, s.x, s.y, Fx, Fy);
+      const double ax = Fx / s.E + kx, ay = Fy / s.E + ky;
+      const double gdot = C.ll ? C.ll_k * (g * g) * (Fx * Fx + Fy * Fy) / C.mass : 0.0;
+      rec[F_T] = t_of(k);
+      rec[F_X] = s.x;
+      rec[F_Y] = s.y;
+      rec[F_DZ] = s.dz;
+      rec[F_VX] = s.vx;
+      rec[F_VY] = s.vy;
+      rec[F_DVZ] = dvz;
+      rec[F_AX] = ax;
+      rec[F_AY] = ay;
+      rec[F_AZ] = (gdot / (g * g * g) - (s.vx * ax + s.vy * ay)) / vz;
+      if (e_out) e_out[off + k] = s.E;
+      kx = ky = 0.0;
+      if (k == L - 1) break;
+      const double H = t_of(k + 1) - t_of(k);
+      int64_t pos = 0;
+      while (pos < unit) {
+        if (n_tries >= S.max_substeps) {  // the particle needs more sub-steps than allowed
+          atomicCAS(dev_status, 0, RAD_EDATA);
+          stopped = true;
+          break;
+        }
+        const double h = H / static_cast<double>(int64_t(1) << level);
+        State y5;
+        const double err = dp5<KIND>(C, P, A, g0, q0, beta0, S, s, h, y5);
+        ++n_tries;
+        if (err > 1.0 && level < S.max_level) {
+          ++level;
+          continue;
+        }
+        s = y5;
+        pos += int64_t(1) << (S.max_level - level);
+        ++n_steps;
+        if (err < 0.015625 && level > 0 && (pos % (int64_t(1) << (S.max_level - level + 1))) == 0) --level;
+      }
+      if (stopped) break;
+      if (C.ms) {
+        const double E = s.E;
+        double n_nuc, n_el;
+        if constexpr (KIND == 2) {
+          axial_densities(A, s.x, s.y, n_nuc, n_el);
+        } else {
+          n_nuc = plane_density(C, s.x);
+          n_el = (KIND == 1 && P.el) ? electron_density_scaled(C, P, s.x, n_nuc) : 0.0;
+        }
+        // variances per unit length (the coefficients are built for a unit step), times H
+        double var = C.var_k / (E * E) * n_nuc * H;
+        const bool el = (KIND == 2) ? (A.el != 0) : (KIND == 1 && P.el);
+        if (el) {
+          const double lk = (KIND == 2) ? A.lk : P.lk;
+          const double ge = E / C.mass, b2 = 1.0 - 1.0 / (ge * ge);
+          const double br = fmax(log(lk * (ge * ge) * b2) - b2, 0.0);
+          var += n_el * (br / ((ge * ge) * (b2 * b2))) * H;
+        }
+        double z0, z1;
+        kick_normals(seed, pid, static_cast<uint64_t>(k), z0, z1);
+        const double sd = sqrt(var);
+        const double dthx = sd * z0, dthy = sd * z1;
+        const double w = (k + 2 < L) ? 0.5 * (t_of(k + 2) - t_of(k)) : H;
+        kx = dthx / w;
+        ky = dthy / w;
+        s.vx += dthx;
+        s.vy += dthy;
+        if (C.ms_loss) {
+          const double gk = E / C.mass;
+          s.E = E - C.loss_k * (gk * gk * gk) * (dthx * dthx + dthy * dthy);
+        }
+      }
+    }
+    if (counts) counts[p] = n_steps;
+  }
+}
+
+// ------------------------------------------------------------------------------------
 // Mixed precision (RAD_TRAJ_FP32): FP32 arithmetic with double-float state
 // ------------------------------------------------------------------------------------
 // GB300 issues FP32 at 64x its FP64 rate (72x measured), so this form evaluates the RK4 stages in
@@ -851,18 +1096,11 @@ int launch_trajectories(const rad_channel *ch, const rad_planar_potential *pot, 
   return e == cudaSuccess ? RAD_OK : cuda_status(e);
 }
 
-int launch_axial(const rad_channel *ch, const rad_axial_potential *pot, int64_t n_particles, const int64_t *offsets,
-                 int64_t n_samples_total, const double *energy_eV, const double *x0, const double *y0,
-                 const double *thx0, const double *thy0, const int64_t *particle_ids, double dt, uint64_t seed,
-                 double *out, double *energy_out, void *stream) {
-  if (!ch || !pot || n_particles < 0 || n_samples_total < 0) return RAD_EINVAL;
-  if (!(dt > 0.0) || !isfinite(dt) || !(ch->mass_eV > 0.0) || (ch->charge_sign != 1 && ch->charge_sign != -1) ||
-      (ch->flags & ~31))
-    return RAD_EINVAL;
-  if (ch->flags & RAD_TRAJ_FP32) return RAD_EUNSUPPORTED;
+// The axial potential's device coefficients; the electron term is scaled by the step length dt
+// (the kick variance per angle over a step of dt).
+int make_axial(const rad_channel *ch, const rad_axial_potential *pot, double dt, Axial &A) {
+  if (!pot) return RAD_EINVAL;
   const bool ms = (ch->flags & RAD_TRAJ_MS) != 0, el = (ch->flags & RAD_TRAJ_MS_EL) != 0;
-  if (ms && !(ch->X0 > 0.0 && ch->rho > 0.0 && ch->eps_s_eV >= 0.0)) return RAD_EINVAL;
-  if (el && !ms) return RAD_EINVAL;
   if (!(ch->rho >= 0.0) || !isfinite(ch->rho)) return RAD_EINVAL;
   const rad_string_lattice &Lt = pot->lattice;
   if (pot->n_terms < 1 || pot->n_terms > kMaxTerms || pot->n_cells < 1 || pot->n_cells > 4 || Lt.n_strings < 1 ||
@@ -870,7 +1108,7 @@ int launch_axial(const rad_channel *ch, const rad_axial_potential *pot, int64_t 
       !isfinite(Lt.cell_y) || !isfinite(Lt.d))
     return RAD_EINVAL;
   if (el && !(pot->I_eV > 0.0 && isfinite(pot->cx))) return RAD_EINVAL;
-  Axial A{};
+  A = Axial{};
   A.nt = pot->n_terms;
   A.nb = Lt.n_strings;
   A.K = pot->n_cells;
@@ -904,7 +1142,24 @@ int launch_axial(const rad_channel *ch, const rad_axial_potential *pot, int64_t 
   A.lk = el ? 2.0 * kMe / pot->I_eV : 0.0;
   bool ok = isfinite(A.dens_k) && isfinite(A.inv_rho2) && isfinite(A.ecx) && isfinite(A.lk);
   for (int i = 0; i < A.nt; ++i) ok = ok && isfinite(A.fk[i]) && isfinite(A.ck[i]) && isfinite(A.ek[i]) && isfinite(A.eck[i]);
-  if (!ok) return RAD_EINVAL;
+  return ok ? RAD_OK : RAD_EINVAL;
+}
+
+int launch_axial(const rad_channel *ch, const rad_axial_potential *pot, int64_t n_particles, const int64_t *offsets,
+                 int64_t n_samples_total, const double *energy_eV, const double *x0, const double *y0,
+                 const double *thx0, const double *thy0, const int64_t *particle_ids, double dt, uint64_t seed,
+                 double *out, double *energy_out, void *stream) {
+  if (!ch || !pot || n_particles < 0 || n_samples_total < 0) return RAD_EINVAL;
+  if (!(dt > 0.0) || !isfinite(dt) || !(ch->mass_eV > 0.0) || (ch->charge_sign != 1 && ch->charge_sign != -1) ||
+      (ch->flags & ~31))
+    return RAD_EINVAL;
+  if (ch->flags & RAD_TRAJ_FP32) return RAD_EUNSUPPORTED;
+  const bool ms = (ch->flags & RAD_TRAJ_MS) != 0, el = (ch->flags & RAD_TRAJ_MS_EL) != 0;
+  if (ms && !(ch->X0 > 0.0 && ch->rho > 0.0 && ch->eps_s_eV >= 0.0)) return RAD_EINVAL;
+  if (el && !ms) return RAD_EINVAL;
+  Axial A;
+  const int ac = make_axial(ch, pot, dt, A);
+  if (ac != RAD_OK) return ac;
   if (n_particles == 0) return RAD_OK;
   if (!offsets || !energy_eV || !x0 || !thx0 || !out) return RAD_EINVAL;
   cudaError_t e;
@@ -928,8 +1183,88 @@ int launch_axial(const rad_channel *ch, const rad_axial_potential *pot, int64_t 
   return e == cudaSuccess ? RAD_OK : cuda_status(e);
 }
 
+int launch_adaptive(const rad_channel *ch, const rad_planar_potential *pot, const rad_axial_potential *axial,
+                    const rad_step_control *sc, int64_t n_particles, const int64_t *offsets, int64_t n_samples_total,
+                    const double *energy_eV, const double *x0, const double *y0, const double *thx0,
+                    const double *thy0, const int64_t *particle_ids, const double *times, double dt, uint64_t seed,
+                    double *out, double *energy_out, int64_t *substeps_out, void *stream) {
+  if (!ch || !sc || n_particles < 0 || n_samples_total < 0 || (pot && axial)) return RAD_EINVAL;
+  const int known = (pot || axial) ? 31 : 15;
+  if (!(ch->mass_eV > 0.0) || (ch->charge_sign != 1 && ch->charge_sign != -1) || (ch->flags & ~known))
+    return RAD_EINVAL;
+  if (!times && !(dt > 0.0 && isfinite(dt))) return RAD_EINVAL;
+  if (ch->flags & RAD_TRAJ_FP32) return RAD_EUNSUPPORTED;
+  if (!axial && !(ch->d_p > 0.0)) return RAD_EINVAL;
+  if (!pot && !axial && !(ch->U0_eV >= 0.0)) return RAD_EINVAL;
+  const bool ms = (ch->flags & RAD_TRAJ_MS) != 0;
+  if (ms && !(ch->X0 > 0.0 && ch->rho > 0.0 && ch->eps_s_eV >= 0.0)) return RAD_EINVAL;
+  if ((ch->flags & RAD_TRAJ_MS_EL) && !ms) return RAD_EINVAL;
+  if (!(sc->rtol > 0.0) || !(sc->atol_x > 0.0) || !(sc->atol_v > 0.0) || !isfinite(sc->rtol) || !isfinite(sc->atol_x) ||
+      !isfinite(sc->atol_v) || sc->max_level < 0 || sc->max_level > 16 || sc->max_substeps < 1)
+    return RAD_EINVAL;
+  // coefficients per unit length: the kernel scales the kick variances by each interval's length
+  Planar P;
+  Planar32 P32;
+  Axial A{};
+  int rc = make_planar(ch, pot, 1.0, P, P32);
+  if (rc != RAD_OK) return rc;
+  if (axial) {
+    rc = make_axial(ch, axial, 1.0, A);
+    if (rc != RAD_OK) return rc;
+  }
+  if (n_particles == 0) return RAD_OK;
+  if (!offsets || !energy_eV || !x0 || !thx0 || !out) return RAD_EINVAL;
+  cudaError_t e;
+  int *ds = device_status_word(&e);
+  if (!ds) return cuda_status(e);
+  Chan C{};
+  C.U0 = ch->U0_eV;
+  C.d_p = axial ? 1.0 : ch->d_p;
+  C.mass = ch->mass_eV;
+  C.rho = ch->rho;
+  C.centre = ch->charge_sign > 0 ? 0.5 * C.d_p : 0.0;
+  C.inv_d = 1.0 / C.d_p;
+  C.force_k = axial ? 0.0 : -8.0 * ch->U0_eV / (ch->d_p * ch->d_p);
+  C.dens_pref = (ms && !axial) ? ch->d_p / (sqrt(kPi) * ch->rho) : 0.0;
+  C.inv_rho2 = ms ? 1.0 / (ch->rho * ch->rho) : 0.0;
+  C.var_k = ms ? 0.5 * ch->eps_s_eV * ch->eps_s_eV / ch->X0 : 0.0;
+  C.loss_k = ch->mass_eV * kAlpha / (2.0 * kPi);
+  C.ll_k = -(2.0 / 3.0) * kAlpha * kHbarC * ch->mass_eV / (ch->mass_eV * ch->mass_eV * ch->mass_eV);
+  C.ms = ms;
+  C.ll = (ch->flags & RAD_TRAJ_LL) != 0;
+  C.ms_loss = (ch->flags & RAD_TRAJ_MS_LOSS) != 0;
+  StepCtl S{sc->rtol, sc->atol_x, sc->atol_v, sc->max_level, sc->max_substeps};
+  const int block = n_particles < 152 * 4 * 32 ? 32 : 128;
+  int64_t grid = (n_particles + block - 1) / block;
+  if (grid > 1 << 20) grid = 1 << 20;
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const unsigned gr = static_cast<unsigned>(grid);
+  if (axial)
+    k_adaptive<2><<<gr, block, 0, st>>>(C, P, A, S, n_particles, offsets, n_samples_total, energy_eV, x0, y0, thx0,
+                                         thy0, particle_ids, times, dt, seed, out, energy_out, substeps_out, ds);
+  else if (pot)
+    k_adaptive<1><<<gr, block, 0, st>>>(C, P, A, S, n_particles, offsets, n_samples_total, energy_eV, x0, y0, thx0,
+                                         thy0, particle_ids, times, dt, seed, out, energy_out, substeps_out, ds);
+  else
+    k_adaptive<0><<<gr, block, 0, st>>>(C, P, A, S, n_particles, offsets, n_samples_total, energy_eV, x0, y0, thx0,
+                                         thy0, particle_ids, times, dt, seed, out, energy_out, substeps_out, ds);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? RAD_OK : cuda_status(e);
+}
+
 }  // namespace
 }  // namespace rad
+
+extern "C" int rad_trajectories_adaptive(const rad_channel *ch, const rad_planar_potential *pot,
+                                         const rad_axial_potential *axial, const rad_step_control *sc,
+                                         int64_t n_particles, const int64_t *offsets, int64_t n_samples_total,
+                                         const double *energy_eV, const double *x0, const double *y0,
+                                         const double *thx0, const double *thy0, const int64_t *particle_ids,
+                                         const double *times, double dt, uint64_t seed, double *out,
+                                         double *energy_out, int64_t *substeps_out, void *stream) {
+  return rad::launch_adaptive(ch, pot, axial, sc, n_particles, offsets, n_samples_total, energy_eV, x0, y0, thx0, thy0,
+                              particle_ids, times, dt, seed, out, energy_out, substeps_out, stream);
+}
 
 extern "C" int rad_axial_trajectories(const rad_channel *ch, const rad_axial_potential *pot, int64_t n_particles,
                                       const int64_t *offsets, int64_t n_samples_total, const double *energy_eV,
