@@ -273,7 +273,8 @@ __global__ void k_channel(const Chan C, const Planar P, int64_t n_particles, con
 // string), FP64. The strings of the (2K+1)^2 cells around the particle's cell are summed; each
 // string's Gaussian exp(-(dx^2 + dy^2)/C) separates into exp(-dx^2/C) exp(-dy^2/C), and the
 // cells of one basis string form a product grid, so the double sum over the cells is a product
-// of two sums of 2K+1 terms: 2(2K+1) exponentials per basis string and term instead of (2K+1)^2.
+// of two sums of 2K+1 terms, each walked outward from the nearest image with three exponentials:
+// 6 per basis string and term instead of (2K+1)^2.
 // ------------------------------------------------------------------------------------
 struct Axial {
   int nt, nb, K, el;
@@ -281,21 +282,43 @@ struct Axial {
   double sx[8], sy[8];
   double fk[kMaxTerms];  // q (2 e^2 a0 / d) (a_i / C_i) (2 / C_i)
   double ck[kMaxTerms];  // 1 / C_i
+  double qx[kMaxTerms], qy[kMaxTerms];    // exp(-2 L^2 / C_i) along x and y
+  double eqx[kMaxTerms], eqy[kMaxTerms];  // the same for the electron terms (1 / CX_i)
+  double rqx, rqy;                         // the same for the nuclear density (1 / rho^2)
   double dens_k;         // 1 / (pi rho^2 N d): n(x, y)/N per unit Gaussian
   double inv_rho2;
   double ek[kMaxTerms], eck[kMaxTerms];  // (1/2) dt pi r0^2 ax_i / (pi d CX_i), 1 / CX_i
   double ecx, lk;                        // (1/2) dt pi r0^2 cx N; 2 m_e / I
 };
 
-// sums over the 2K+1 images u0 + i L of one coordinate: s1 = sum u e^{-u^2 k}, s0 = sum e^{-u^2 k}
-__device__ __forceinline__ void axis_sums(double u0, double L, int K, double k, double &s1, double &s0) {
-  s1 = 0.0;
-  s0 = 0.0;
-  for (int i = -K; i <= K; ++i) {
-    const double u = u0 - static_cast<double>(i) * L;
-    const double e = exp(-(u * u) * k);
-    s1 += u * e;
-    s0 += e;
+// sums over the 2K+1 images u_i = u0 - i L (i = -K .. K) of one coordinate: s1 = sum u e^{-u^2 k},
+// s0 = sum e^{-u^2 k}, with |u0| < L. Walked outward from the nearest image r = u0 - i0 L
+// (|r| <= L/2), as in the planar form: the Gaussian of the next image is the current one times a
+// ratio, and successive ratios differ by the factor q = exp(-2 k L^2), so one axis costs three
+// exponentials (the nearest image and the first ratio each way, all <= 1) instead of 2K+1.
+__device__ __forceinline__ void axis_sums(double u0, double L, int K, double k, double q, double &s1, double &s0) {
+  const int i0 = u0 > 0.5 * L ? 1 : (u0 < -0.5 * L ? -1 : 0);
+  const double r = u0 - static_cast<double>(i0) * L;
+  const double E0 = exp(-(r * r) * k);
+  s1 = r * E0;
+  s0 = E0;
+  double E = E0, rho = exp(k * (2.0 * r * L - L * L)), u = r;
+  for (int m = 0; m < K - i0; ++m) {  // images i0 + 1 .. K at r - m L
+    E *= rho;
+    rho *= q;
+    u -= L;
+    s1 += u * E;
+    s0 += E;
+  }
+  E = E0;
+  rho = exp(-k * (2.0 * r * L + L * L));
+  u = r;
+  for (int m = 0; m < K + i0; ++m) {  // images i0 - 1 .. -K at r + m L
+    E *= rho;
+    rho *= q;
+    u += L;
+    s1 += u * E;
+    s0 += E;
   }
 }
 
@@ -309,8 +332,8 @@ __device__ __forceinline__ void axial_force(const Axial &A, double x, double y, 
     const double uy = y - (cy * A.Ly + A.sy[b]);
     for (int t = 0; t < A.nt; ++t) {
       double sx1, sx0, sy1, sy0;
-      axis_sums(ux, A.Lx, A.K, A.ck[t], sx1, sx0);
-      axis_sums(uy, A.Ly, A.K, A.ck[t], sy1, sy0);
+      axis_sums(ux, A.Lx, A.K, A.ck[t], A.qx[t], sx1, sx0);
+      axis_sums(uy, A.Ly, A.K, A.ck[t], A.qy[t], sy1, sy0);
       Fx += A.fk[t] * (sx1 * sy0);
       Fy += A.fk[t] * (sx0 * sy1);
     }
@@ -325,13 +348,13 @@ __device__ __forceinline__ void axial_densities(const Axial &A, double x, double
     const double ux = x - (cx * A.Lx + A.sx[b]);
     const double uy = y - (cy * A.Ly + A.sy[b]);
     double s1, sx0, sy0;
-    axis_sums(ux, A.Lx, A.K, A.inv_rho2, s1, sx0);
-    axis_sums(uy, A.Ly, A.K, A.inv_rho2, s1, sy0);
+    axis_sums(ux, A.Lx, A.K, A.inv_rho2, A.rqx, s1, sx0);
+    axis_sums(uy, A.Ly, A.K, A.inv_rho2, A.rqy, s1, sy0);
     nn += sx0 * sy0;
     if (A.el) {
       for (int t = 0; t < A.nt; ++t) {
-        axis_sums(ux, A.Lx, A.K, A.eck[t], s1, sx0);
-        axis_sums(uy, A.Ly, A.K, A.eck[t], s1, sy0);
+        axis_sums(ux, A.Lx, A.K, A.eck[t], A.eqx[t], s1, sx0);
+        axis_sums(uy, A.Ly, A.K, A.eck[t], A.eqy[t], s1, sy0);
         ne += A.ek[t] * (sx0 * sy0);
       }
     }
@@ -1138,6 +1161,14 @@ int make_axial(const rad_channel *ch, const rad_axial_potential *pot, double dt,
   }
   A.dens_k = ms ? 1.0 / (kPi * rho2 * N * Lt.d) : 0.0;
   A.inv_rho2 = ms ? 1.0 / rho2 : 0.0;
+  for (int i = 0; i < A.nt; ++i) {
+    A.qx[i] = exp(-2.0 * A.Lx * A.Lx * A.ck[i]);
+    A.qy[i] = exp(-2.0 * A.Ly * A.Ly * A.ck[i]);
+    A.eqx[i] = exp(-2.0 * A.Lx * A.Lx * A.eck[i]);
+    A.eqy[i] = exp(-2.0 * A.Ly * A.Ly * A.eck[i]);
+  }
+  A.rqx = exp(-2.0 * A.Lx * A.Lx * A.inv_rho2);
+  A.rqy = exp(-2.0 * A.Ly * A.Ly * A.inv_rho2);
   A.ecx = el ? el_pref * pot->cx * N : 0.0;
   A.lk = el ? 2.0 * kMe / pot->I_eV : 0.0;
   bool ok = isfinite(A.dens_k) && isfinite(A.inv_rho2) && isfinite(A.ecx) && isfinite(A.lk);

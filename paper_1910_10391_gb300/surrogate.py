@@ -74,7 +74,8 @@ class Config:
     fourier_sigma: float = 1.5
     fourier_seed: int = 11
     n_val: int = 2048
-    calib_quantile: float = 0.95
+    calib_quantile: float = 1.0
+    calib_margin: float = 1.25
     loss_floor_w: float = 0.02
     beams_val: int = 32
     calib_subsets: int = 8
@@ -121,8 +122,9 @@ def sample_entries(cfg: Config, n: int, seed: int, discrete_gamma: bool):
     return x0, th, g
 
 
-def sample_beams(cfg: Config, n_beams: int, per_beam: int, seed: int, divergence=None):
-    """Beams of entries: each beam has one Lorentz factor, log-uniform in [gamma_lo, gamma_hi];
+def sample_beams(cfg: Config, n_beams: int, per_beam: int, seed: int, divergence=None, gammas=None):
+    """Beams of entries: each beam has one Lorentz factor, log-uniform in [gamma_lo, gamma_hi]
+    (or the given `gammas`, one per beam);
     its entries have x0/d_p ~ U[0, 1) and theta0/theta_L ~ N(0, divergence^2) clipped to
     [-theta_frac, theta_frac] (a beam with the ensemble workloads' divergence, 0.3 theta_L), or
     ~ U[-theta_frac, theta_frac] when divergence is None (the training coverage).
@@ -130,6 +132,10 @@ def sample_beams(cfg: Config, n_beams: int, per_beam: int, seed: int, divergence
     rng = np.random.default_rng(seed)
     lo, hi = math.log(cfg.gamma_lo), math.log(cfg.gamma_hi)
     gb = np.exp(rng.uniform(lo, hi, n_beams))
+    if gammas is not None:
+        gb = np.asarray(gammas, dtype=np.float64)
+        if gb.shape != (n_beams,) or np.any(gb < cfg.gamma_lo) or np.any(gb > cfg.gamma_hi):
+            raise ValueError("one Lorentz factor per beam, inside the input domain")
     n = n_beams * per_beam
     x0 = rng.uniform(0.0, 1.0, n)
     if divergence is None:
@@ -419,6 +425,10 @@ class Surrogate:
                                            else np.nan for r in ratios])
                 fill = max(glob, float(np.nanmax(np.r_[self.calib_ens, glob])))
                 self.calib_ens = np.where(np.isnan(self.calib_ens), fill, self.calib_ens)
+            # the validation set is finite: a margin over the largest ratio seen covers beams whose
+            # ratio lies beyond it
+            self.calib = self.calib * cfg.calib_margin
+            self.calib_ens = self.calib_ens * cfg.calib_margin
         return history
 
     def members(self, uvw):
@@ -601,6 +611,8 @@ def main(argv=None):
     ap.add_argument("--models", type=int, default=4)
     ap.add_argument("--n-gamma", type=int, default=64)
     ap.add_argument("--beams", type=int, default=16)
+    ap.add_argument("--edge-beams", type=int, default=4,
+                    help="of the held-out beams, this many at the ends of the Lorentz-factor range")
     ap.add_argument("--save", default="")
     ap.add_argument("--quiet", action="store_true")
     a = ap.parse_args(argv)
@@ -625,7 +637,14 @@ def main(argv=None):
     torch.cuda.synchronize()
     t_fit = time.perf_counter() - t0
     del bins
-    hx0, hth, hg, hbeam = sample_beams(cfg, a.beams, a.heldout // a.beams, seed=6, divergence=cfg.beam_divergence)
+    rng = np.random.default_rng(6)
+    lo, hi = math.log(cfg.gamma_lo), math.log(cfg.gamma_hi)
+    gb = np.exp(rng.uniform(lo, hi, a.beams))
+    edge = [cfg.gamma_lo * 1.02, cfg.gamma_hi / 1.02, cfg.gamma_lo * 1.1, cfg.gamma_hi / 1.1]
+    for k in range(min(a.edge_beams, a.beams)):
+        gb[k] = edge[k % 4] * (1.0 + 0.01 * (k // 4))
+    hx0, hth, hg, hbeam = sample_beams(cfg, a.beams, a.heldout // a.beams, seed=6, divergence=cfg.beam_divergence,
+                                       gammas=gb)
     rep = evaluate(sur, hx0, hth, hg, hbeam)
     # per-entry accuracy over the whole training domain (uniform coverage), no fallback
     ux0, uth, ug, _ = sample_beams(cfg, 64, 16, seed=8)

@@ -59,8 +59,8 @@ def test_harmonic_well_jittered_times(charge):
     t = I.sample_times("jitter", 121, 120 * 200e-9, seed=3)
     st, got, eg, cnt = run_gpu(channel(charge, 0), sc(1e-10), x0, th, t, 0)
     assert st == rad.RAD_OK
-    ref, er, rc = T.trajectories_adaptive(x0, th, 0.0, E, t, 0, rtol=1e-10, atol_x=1e-20, atol_v=1e-16, max_level=10,
-                                          charge=charge, ms=False, energies=True, counts=True)
+    (ref, er), rc = T.trajectories_adaptive(x0, th, 0.0, E, t, 0, rtol=1e-10, atol_x=1e-20, atol_v=1e-16,
+                                            max_level=10, charge=charge, ms=False, energies=True, counts=True)
     close(got, ref)
     np.testing.assert_array_equal(cnt, rc)
     assert cnt.min() > 2 * 120, cnt
@@ -77,9 +77,9 @@ def test_planar_potential_all_flags_tile_jump_times(charge):
     t = I.sample_times("tile_jumps", 301, 300 * 8e-9, tile=32)
     st, got, eg, cnt = run_gpu(channel(charge, ALL, 0.0), sc(1e-9), x0, th, t, 9, planar=pot)
     assert st == rad.RAD_OK
-    ref, er, rc = T.trajectories_adaptive(x0, th, 0.0, E, t, 9, rtol=1e-9, atol_x=1e-20, atol_v=1e-16, max_level=10,
-                                          charge=charge, pot=opot, ms=True, ms_el=True, ll=True, ms_loss=True,
-                                          energies=True, counts=True)
+    (ref, er), rc = T.trajectories_adaptive(x0, th, 0.0, E, t, 9, rtol=1e-9, atol_x=1e-20, atol_v=1e-16,
+                                            max_level=10, charge=charge, pot=opot, ms=True, ms_el=True, ll=True,
+                                            ms_loss=True, energies=True, counts=True)
     close(got, ref)
     np.testing.assert_allclose(eg, er, rtol=1e-12)
     np.testing.assert_array_equal(cnt, rc)
@@ -112,8 +112,9 @@ def test_lower_bound_budget_and_argument_checks():
     # max_level 0: one sub-step per interval whatever the error
     st, got, _, cnt = run_gpu(channel(+1, 0), sc(1e-15, max_level=0), x0, th, t, 0)
     assert st == rad.RAD_OK and np.all(cnt == 100)
-    # a budget below what the tolerance needs: the particle stops and RAD_EDATA is recorded
-    st, _, _, cnt = run_gpu(channel(+1, 0), sc(1e-12, max_level=12, max_substeps=150), x0, th, t, 0)
+    # a budget below what the tolerance needs (400 nm intervals at 1e-12 take over ten sub-steps
+    # each): the particle stops and RAD_EDATA is recorded
+    st, _, _, cnt = run_gpu(channel(+1, 0), sc(1e-12, max_level=12, max_substeps=150), x0, th, 20 * t, 0)
     assert st == rad.RAD_EDATA and np.all(cnt <= 150)
     d = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
     off = torch.tensor([0, 10], dtype=torch.int64, device="cuda")
