@@ -7,8 +7,11 @@ each (100 um); 512 log-spaced photon energies in [1e-4 E, 0.5 E] x 64 x 64 direc
 and Baier-Katkov spin-1/2 models. A step is one pass of the whole path (device checks, the
 integral kernel, the particle/angle combine and the angle integral) over a batch of particles
 in both models. `value` is the chosen form (mixed precision: FP64 phase base and particle sums,
-FP32 sincos and amplitudes) in integrand terms/s; the plain FP64 kernel is timed on the same
-inputs and reported beside it.
+FP32 sincos and amplitudes) in integrand terms/s; the plain FP64 kernel and the FP64-accurate
+double-float kernel are timed on the same inputs and reported beside it. The line also carries
+the other workloads, each with its own timing: the analytic undulator (4096 samples, 128 hw x
+16x16) in every precision, a graph-captured launch over the first 512 electrons of the lognormal
+electron batch, and the learned surrogate trained in the run, at its 1 % contract.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -81,6 +84,8 @@ def parse():
     ap.add_argument("--df-steps", type=int, default=3)
     ap.add_argument("--batch-slice", type=int, default=512,
                     help="electrons of the 4096-electron lognormal batch in its graph launch (0: skip)")
+    ap.add_argument("--surrogate-train", type=int, default=32768,
+                    help="kernel spectra the in-run surrogate trains on (0: skip the surrogate leg)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune", action="store_true",
@@ -282,6 +287,39 @@ def batch_leg(rad, torch, dev, n, tune_particles=8, tune_budget_ms=15000, seed=1
            "roofline": {"bound": "alu", "pipe": "sfu + issue slots", "achieved": terms / (ms * 1e-3) / 1e12,
                         "peak": peak / 1e12, "unit": "Tterm/s", "frac": terms / (ms * 1e-3) / peak}}
     return res, (tr, grid, bi, bj, got)
+
+
+def surrogate_leg(n_train):
+    """The learned surrogate (3 -> 256 x 3 -> 2048 MLPs, BF16 tensor-core GEMMs with FP32
+    accumulation, trained by the library's kernels) at its 1 % contract: a 3-network ensemble
+    trained in the run on n_train kernel spectra (24 Lorentz factors over [2e3, 4e4]), calibrated on
+    16 validation beams, evaluated on 4 held-out beams of 512 entries (two near each end of the
+    Lorentz-factor range) with fallback to the kernel until each beam mean's calibrated estimate is
+    at most 1 %; gain = kernel time / surrogate-with-fallback time for the beam means."""
+    from paper_1910_10391_gb300 import surrogate as S
+    t0 = time.perf_counter()
+    cfg = S.Config(n_gamma_train=24, n_models=3, steps=6000, batch=512, fallback_rel=0.01, calib_gamma_bins=2)
+    x0, th, g = S.sample_entries(cfg, n_train, seed=5, discrete_gamma=True)
+    bins = S.kernel_bins(cfg, x0, th, g)
+    vx0, vth, vg, vb = S.sample_beams(cfg, 16, 48, seed=7, divergence=cfg.beam_divergence)
+    sur = S.Surrogate(cfg)
+    sur.fit(S.raw_inputs(cfg, x0, th, g), bins, S.raw_inputs(cfg, vx0, vth, vg), S.kernel_bins(cfg, vx0, vth, vg), vb)
+    del bins
+    t_train = time.perf_counter() - t0
+    lo, hi = cfg.gamma_lo, cfg.gamma_hi
+    hx0, hth, hg, hb = S.sample_beams(cfg, 4, 512, seed=6, divergence=cfg.beam_divergence,
+                                      gammas=[lo * 1.02, lo * 1.1, hi / 1.1, hi / 1.02])
+    rep = S.evaluate(sur, hx0, hth, hg, hb)
+    sur.close()
+    return {"workload": f"surrogate: 3-network ensemble trained in this run on {n_train} kernel spectra (the full "
+                        "configuration trains on 200 000); 4 held-out beams x 512 entries, 256 hw/E x 8 radial bins, "
+                        "spin-1/2, fallback to the kernel until the beam mean's estimate <= 1 %",
+            "gain": rep["gain"], "spectra_per_s_kernel": rep["spectra_per_s_kernel"],
+            "spectra_per_s_surrogate": rep["spectra_per_s_surrogate"], "fallback_fraction": rep["mean_fallback_fraction"],
+            "beams": [{"gamma": e["gamma"], "error": e["error"], "estimate": e["estimate"],
+                       "n_fallback": e["n_fallback"]} for e in rep["per_beam"]],
+            "error_le_estimate_le_1pct": all(e["error"] <= e["estimate"] <= 0.01 for e in rep["per_beam"]),
+            "train_s": t_train}
 
 
 def plan_desc_str(d):
@@ -519,6 +557,7 @@ def main():
     # ---- the other workloads: the analytic undulator in every form, the electron batch slice ----
     und_line, und_data = undulator_leg(rad, torch, dev)
     bat_line, bat_data = batch_leg(rad, torch, dev, args.batch_slice) if args.batch_slice > 0 else (None, None)
+    sur_line = surrogate_leg(args.surrogate_train) if args.surrogate_train > 0 and rank == 0 else None
 
     # ---- roofline of the dominant kernel (mixed integral kernel) ----
     mk = [ms for (_, ms) in kms]
@@ -603,6 +642,7 @@ def main():
                 "entry": "rad_spectrum_host (pinned host buffers, copies inside the timed region)"},
         "undulator": und_line,
         "electron_batch": bat_line,
+        "surrogate": sur_line,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
         "wall_s_timed": wall,
