@@ -381,6 +381,170 @@ __device__ __forceinline__ State deriv_axial(const Chan &C, const Axial &A, doub
   return d;
 }
 
+// Small ensembles: one particle per group of kGroup lanes. The lanes share the force evaluation
+// (each takes some of the (basis string, term) pairs, the partial forces are summed by a butterfly
+// of shuffles within the group) and keep identical copies of the state, so a step's exponentials
+// run kGroup-wide instead of on one lane; 1024 particles then fill 16384 lanes instead of 1024.
+// The groups of a warp may diverge (different lengths): every shuffle names its own group's lanes.
+constexpr int kGroup = 16;
+// below this many particles the lane-group kernel runs (16 lanes each); above, one lane each
+constexpr int64_t kGroupBelow = 8192;
+
+// the sum over the group, identical in every lane (the butterfly adds in a different order in
+// each lane, so the group's first lane's sum is broadcast: the lanes' states stay bit-identical)
+__device__ __forceinline__ double group_sum(double v, unsigned mask) {
+#pragma unroll
+  for (int o = kGroup / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, kGroup);
+  return __shfl_sync(mask, v, 0, kGroup);
+}
+
+__device__ __forceinline__ void axial_force_group(const Axial &A, double x, double y, int gl, unsigned mask,
+                                                  double &Fx, double &Fy) {
+  const double cx = floor(x / A.Lx), cy = floor(y / A.Ly);
+  double fx = 0.0, fy = 0.0;
+  for (int q = gl; q < A.nb * A.nt; q += kGroup) {
+    const int b = q / A.nt, t = q - b * A.nt;
+    const double ux = x - (cx * A.Lx + A.sx[b]);
+    const double uy = y - (cy * A.Ly + A.sy[b]);
+    double sx1, sx0, sy1, sy0;
+    axis_sums(ux, A.Lx, A.K, A.ck[t], A.qx[t], sx1, sx0);
+    axis_sums(uy, A.Ly, A.K, A.ck[t], A.qy[t], sy1, sy0);
+    fx += A.fk[t] * (sx1 * sy0);
+    fy += A.fk[t] * (sx0 * sy1);
+  }
+  Fx = group_sum(fx, mask);
+  Fy = group_sum(fy, mask);
+}
+
+__device__ __forceinline__ void axial_densities_group(const Axial &A, double x, double y, int gl, unsigned mask,
+                                                      double &n_nuc, double &n_el) {
+  const double cx = floor(x / A.Lx), cy = floor(y / A.Ly);
+  double nn = 0.0, ne = 0.0, s1, sx0, sy0;
+  for (int b = gl; b < A.nb; b += kGroup) {
+    axis_sums(x - (cx * A.Lx + A.sx[b]), A.Lx, A.K, A.inv_rho2, A.rqx, s1, sx0);
+    axis_sums(y - (cy * A.Ly + A.sy[b]), A.Ly, A.K, A.inv_rho2, A.rqy, s1, sy0);
+    nn += sx0 * sy0;
+  }
+  if (A.el) {
+    for (int q = gl; q < A.nb * A.nt; q += kGroup) {
+      const int b = q / A.nt, t = q - b * A.nt;
+      axis_sums(x - (cx * A.Lx + A.sx[b]), A.Lx, A.K, A.eck[t], A.eqx[t], s1, sx0);
+      axis_sums(y - (cy * A.Ly + A.sy[b]), A.Ly, A.K, A.eck[t], A.eqy[t], s1, sy0);
+      ne += A.ek[t] * (sx0 * sy0);
+    }
+  }
+  n_nuc = A.dens_k * group_sum(nn, mask);
+  n_el = (A.el ? group_sum(ne, mask) : 0.0) + A.ecx * n_nuc;
+}
+
+__device__ __forceinline__ State deriv_axial_group(const Chan &C, const Axial &A, double g0, double q0, double beta0,
+                                                   const State &s, int gl, unsigned mask) {
+  const double g = s.E / C.mass;
+  const double vp2 = s.vx * s.vx + s.vy * s.vy;
+  double vz;
+  const double dvz = dvz_of(g, g0, q0, beta0, vp2, vz);
+  double Fx, Fy;
+  axial_force_group(A, s.x, s.y, gl, mask, Fx, Fy);
+  State d;
+  d.x = s.vx;
+  d.y = s.vy;
+  d.vx = Fx / s.E;
+  d.vy = Fy / s.E;
+  d.dz = dvz;
+  d.E = C.ll ? C.ll_k * (g * g) * (Fx * Fx + Fy * Fy) : 0.0;
+  return d;
+}
+
+__global__ void k_axial_group(const Chan C, const Axial A, int64_t n_particles, const int64_t *__restrict__ offsets,
+                              int64_t n_total, const double *__restrict__ energy, const double *__restrict__ x0,
+                              const double *__restrict__ y0, const double *__restrict__ thx0,
+                              const double *__restrict__ thy0, const int64_t *__restrict__ ids, double dt,
+                              uint64_t seed, double *__restrict__ out, double *__restrict__ e_out, int *dev_status) {
+  const int gl = threadIdx.x & (kGroup - 1);
+  const unsigned mask = 0xFFFFu << (threadIdx.x & 16);
+  const int64_t groups = static_cast<int64_t>(gridDim.x) * (blockDim.x / kGroup);
+  for (int64_t p = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) / kGroup; p < n_particles;
+       p += groups) {
+    const int64_t off = offsets[p], L = offsets[p + 1] - off;
+    const double E0 = energy[p];
+    if (off < 0 || L < 1 || off + L > n_total || !(E0 > C.mass) || !isfinite(E0) || !isfinite(x0[p]) ||
+        (y0 && !isfinite(y0[p])) || !isfinite(thx0[p]) || (thy0 && !isfinite(thy0[p]))) {
+      if (gl == 0) atomicCAS(dev_status, 0, RAD_EDATA);
+      continue;
+    }
+    const uint64_t pid = ids ? static_cast<uint64_t>(ids[p]) : static_cast<uint64_t>(p);
+    const double g0 = E0 / C.mass;
+    const double beta0 = 1.0 - 1.0 / (2.0 * g0 * g0);
+    const double q0 = 1.0 / (4.0 * (g0 * g0) * (g0 * g0));
+    State s{x0[p], y0 ? y0[p] : 0.0, thx0[p], thy0 ? thy0[p] : 0.0, 0.0, E0};
+    double kx = 0.0, ky = 0.0;
+    double *rec = out + off * kRec;
+    for (int64_t k = 0; k < L; ++k, rec += kRec) {
+      const double g = s.E / C.mass;
+      const double vp2 = s.vx * s.vx + s.vy * s.vy;
+      double vz;
+      const double dvz = dvz_of(g, g0, q0, beta0, vp2, vz);
+      double Fx, Fy;
+      axial_force_group(A, s.x, s.y, gl, mask, Fx, Fy);
+      const double ax = Fx / s.E + kx, ay = Fy / s.E + ky;
+      const double gdot = C.ll ? C.ll_k * (g * g) * (Fx * Fx + Fy * Fy) / C.mass : 0.0;
+      // every lane holds the record; lane f writes field f
+      double v = 0.0;
+      switch (gl) {
+        case F_T: v = static_cast<double>(k) * dt; break;
+        case F_X: v = s.x; break;
+        case F_Y: v = s.y; break;
+        case F_DZ: v = s.dz; break;
+        case F_VX: v = s.vx; break;
+        case F_VY: v = s.vy; break;
+        case F_DVZ: v = dvz; break;
+        case F_AX: v = ax; break;
+        case F_AY: v = ay; break;
+        case F_AZ: v = (gdot / (g * g * g) - (s.vx * ax + s.vy * ay)) / vz; break;
+        default: break;
+      }
+      if (gl < kRec) rec[gl] = v;
+      if (e_out && gl == 0) e_out[off + k] = s.E;
+      kx = ky = 0.0;
+      if (k == L - 1) break;
+      const State k1 = deriv_axial_group(C, A, g0, q0, beta0, s, gl, mask);
+      const State k2 = deriv_axial_group(C, A, g0, q0, beta0, axpy(s, 0.5 * dt, k1), gl, mask);
+      const State k3 = deriv_axial_group(C, A, g0, q0, beta0, axpy(s, 0.5 * dt, k2), gl, mask);
+      const State k4 = deriv_axial_group(C, A, g0, q0, beta0, axpy(s, dt, k3), gl, mask);
+      const double h6 = dt / 6.0;
+      s.x += h6 * (k1.x + 2.0 * k2.x + 2.0 * k3.x + k4.x);
+      s.y += h6 * (k1.y + 2.0 * k2.y + 2.0 * k3.y + k4.y);
+      s.vx += h6 * (k1.vx + 2.0 * k2.vx + 2.0 * k3.vx + k4.vx);
+      s.vy += h6 * (k1.vy + 2.0 * k2.vy + 2.0 * k3.vy + k4.vy);
+      s.dz += h6 * (k1.dz + 2.0 * k2.dz + 2.0 * k3.dz + k4.dz);
+      s.E += h6 * (k1.E + 2.0 * k2.E + 2.0 * k3.E + k4.E);
+      if (C.ms) {
+        const double E = s.E;
+        double n_nuc, n_el;
+        axial_densities_group(A, s.x, s.y, gl, mask, n_nuc, n_el);
+        double var = C.var_k / (E * E) * n_nuc;
+        if (A.el) {
+          const double ge = E / C.mass, b2 = 1.0 - 1.0 / (ge * ge);
+          const double br = fmax(log(A.lk * (ge * ge) * b2) - b2, 0.0);
+          var += n_el * (br / ((ge * ge) * (b2 * b2)));
+        }
+        double z0, z1;
+        kick_normals(seed, pid, static_cast<uint64_t>(k), z0, z1);
+        const double sd = sqrt(var);
+        const double dthx = sd * z0, dthy = sd * z1;
+        kx = dthx / dt;
+        ky = dthy / dt;
+        s.vx += dthx;
+        s.vy += dthy;
+        if (C.ms_loss) {
+          const double gk = E / C.mass;
+          s.E = E - C.loss_k * (gk * gk * gk) * (dthx * dthx + dthy * dthy);
+        }
+      }
+    }
+  }
+}
+
 __global__ void k_axial(const Chan C, const Axial A, int64_t n_particles, const int64_t *__restrict__ offsets,
                         int64_t n_total, const double *__restrict__ energy, const double *__restrict__ x0,
                         const double *__restrict__ y0, const double *__restrict__ thx0,
@@ -1204,12 +1368,20 @@ int launch_axial(const rad_channel *ch, const rad_axial_potential *pot, int64_t 
   C.ms = ms;
   C.ll = (ch->flags & RAD_TRAJ_LL) != 0;
   C.ms_loss = (ch->flags & RAD_TRAJ_MS_LOSS) != 0;
-  const int block = n_particles < 152 * 4 * 32 ? 32 : 128;
-  int64_t grid = (n_particles + block - 1) / block;
-  if (grid > 1 << 20) grid = 1 << 20;
-  k_axial<<<static_cast<unsigned>(grid), block, 0, static_cast<cudaStream_t>(stream)>>>(
-      C, A, n_particles, offsets, n_samples_total, energy_eV, x0, y0, thx0, thy0, particle_ids, dt, seed, out,
-      energy_out, ds);
+  if (n_particles < kGroupBelow) {  // lane groups share each particle's force evaluation
+    const int block = 128;
+    const int64_t grid = (n_particles * kGroup + block - 1) / block;
+    k_axial_group<<<static_cast<unsigned>(grid), block, 0, static_cast<cudaStream_t>(stream)>>>(
+        C, A, n_particles, offsets, n_samples_total, energy_eV, x0, y0, thx0, thy0, particle_ids, dt, seed, out,
+        energy_out, ds);
+  } else {
+    const int block = n_particles < 152 * 4 * 32 ? 32 : 128;
+    int64_t grid = (n_particles + block - 1) / block;
+    if (grid > 1 << 20) grid = 1 << 20;
+    k_axial<<<static_cast<unsigned>(grid), block, 0, static_cast<cudaStream_t>(stream)>>>(
+        C, A, n_particles, offsets, n_samples_total, energy_eV, x0, y0, thx0, thy0, particle_ids, dt, seed, out,
+        energy_out, ds);
+  }
   e = cudaGetLastError();
   return e == cudaSuccess ? RAD_OK : cuda_status(e);
 }
