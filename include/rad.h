@@ -123,6 +123,20 @@ int rad_spectrum(const double *samples, int64_t n_samples_total, const int64_t *
                  double *out_bins, int accumulate, void *stream);
 
 /*
+ * rad_angular_distribution -- the energy radiated per solid angle over the photon-energy grid,
+ * dI/dOmega (Sec. IV, the second integral test: the angular distribution integrated over a
+ * photon-energy range): out[j] = sum_{i < n_omega - 1} (hw[i+1] - hw[i]) (cube[i][j] +
+ * cube[i+1][j]) / 2, the trapezoid rule in photon energy over the cube rad_spectrum writes.
+ *   cube           device, [n_omega * n_angles] (layout of rad_spectrum's out_cube)
+ *   hbar_omega_eV  device, [n_omega], the cube's photon energies (eV), increasing
+ *   out            device, [n_angles], overwritten (zero when n_omega < 2)
+ * Asynchronous on `stream`; the sum over energies runs in a fixed order (deterministic).
+ * RAD_EINVAL for negative sizes or a NULL pointer that is needed.
+ */
+int rad_angular_distribution(const double *cube, const double *hbar_omega_eV, int64_t n_omega,
+                             int64_t n_angles, double *out, void *stream);
+
+/*
  * rad_spectrum_host -- rad_spectrum on HOST arrays (same arguments, all pointers
  * host memory; pinned memory gives the fastest copies). Copies the inputs to the
  * device, computes, copies the requested outputs back and returns when they are

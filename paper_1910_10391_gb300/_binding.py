@@ -156,6 +156,8 @@ def load(build_if_missing: bool = True):
                                                   ctypes.POINTER(RadAxialPotential), ctypes.POINTER(RadStepControl),
                                                   i64, P, i64, P, P, P, P, P, P, P, ctypes.c_double, u64, P, P, P, P]
         lib.rad_trajectories_adaptive.restype = c_int
+        lib.rad_angular_distribution.argtypes = [P, P, i64, i64, P, P]
+        lib.rad_angular_distribution.restype = c_int
         lib.rad_crystal_element.argtypes = [c_int, ctypes.POINTER(RadElement)]
         lib.rad_crystal_element.restype = c_int
         lib.rad_crystal_string_lattice.argtypes = [c_int, ctypes.c_double, c_int, ctypes.POINTER(RadStringLattice)]
@@ -404,6 +406,15 @@ def rad_trajectories_adaptive(channel, step_control, offsets, energy_eV, x0, thx
         _dev_ptr(thx0, f64, "thx0"), _dev_ptr(thy0, f64, "thy0"), _dev_ptr(particle_ids, torch.int64, "particle_ids"),
         _dev_ptr(times, f64, "times"), float(dt), int(seed), _dev_ptr(out, f64, "out"),
         _dev_ptr(energy_out, f64, "energy_out"), _dev_ptr(substeps_out, torch.int64, "substeps_out"), _stream(stream))
+
+
+def rad_angular_distribution(cube, hbar_omega_eV, out, stream=None) -> int:
+    """dI/dOmega: the trapezoid over the photon energies of a cube [n_omega][n_angles]."""
+    import torch
+    f64 = torch.float64
+    n_omega = _numel(hbar_omega_eV)
+    return load().rad_angular_distribution(_dev_ptr(cube, f64, "cube"), _dev_ptr(hbar_omega_eV, f64, "hbar_omega_eV"),
+                                           n_omega, _numel(out), _dev_ptr(out, f64, "out"), _stream(stream))
 
 
 def crystal_element(element) -> RadElement:

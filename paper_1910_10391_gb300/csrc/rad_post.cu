@@ -395,4 +395,38 @@ cudaError_t launch_zero_outputs(const Params &P, double *out_cube, double *out_s
   return e;
 }
 
+// dI/dOmega over a photon-energy range: out[j] = sum_i w_i cube[i][j], trapezoid weights in hw
+// (Sec. IV, the energy radiated per solid angle). One thread per direction, the energies summed in
+// order (deterministic); lanes along j read the cube rows coalesced.
+__global__ void k_angular(const double *__restrict__ cube, const double *__restrict__ hw, int64_t n_omega,
+                          int64_t n_angles, double *__restrict__ out) {
+  for (int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; j < n_angles;
+       j += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    double acc = 0.0;
+    for (int64_t i = 0; i + 1 < n_omega; ++i) {
+      const double h = hw[i + 1] - hw[i];
+      acc += 0.5 * h * (cube[i * n_angles + j] + cube[(i + 1) * n_angles + j]);
+    }
+    out[j] = acc;
+  }
+}
+
 }  // namespace rad
+
+extern "C" int rad_angular_distribution(const double *cube, const double *hbar_omega_eV, int64_t n_omega,
+                                        int64_t n_angles, double *out, void *stream) {
+  if (n_omega < 0 || n_angles < 0) return RAD_EINVAL;
+  if (n_angles == 0) return RAD_OK;
+  if (!out || (n_omega > 0 && (!cube || !hbar_omega_eV))) return RAD_EINVAL;
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if (n_omega < 2) {
+    e = cudaMemsetAsync(out, 0, sizeof(double) * n_angles, st);
+  } else {
+    int64_t blocks = (n_angles + 255) / 256;
+    if (blocks > 65535) blocks = 65535;
+    rad::k_angular<<<static_cast<unsigned>(blocks), 256, 0, st>>>(cube, hbar_omega_eV, n_omega, n_angles, out);
+    e = cudaGetLastError();
+  }
+  return e == cudaSuccess ? RAD_OK : rad::cuda_status(e);
+}

@@ -387,8 +387,10 @@ __device__ __forceinline__ State deriv_axial(const Chan &C, const Axial &A, doub
 // run kGroup-wide instead of on one lane; 1024 particles then fill 16384 lanes instead of 1024.
 // The groups of a warp may diverge (different lengths): every shuffle names its own group's lanes.
 constexpr int kGroup = 16;
-// below this many particles the lane-group kernel runs (16 lanes each); above, one lane each
-constexpr int64_t kGroupBelow = 8192;
+// below this many particles the lane-group kernel runs (16 lanes each); above, one lane each (the
+// groups' copies of the state cost about a fifth more FP64 work, which pays while one lane per
+// particle leaves the SMs short of warps)
+constexpr int64_t kGroupBelow = 32768;
 
 // the sum over the group, identical in every lane (the butterfly adds in a different order in
 // each lane, so the group's first lane's sum is broadcast: the lanes' states stay bit-identical)

@@ -157,12 +157,12 @@ def test_axial_argument_checks():
 
 
 def test_axial_one_lane_path_for_large_ensembles():
-    """From 8192 particles on, each particle has one lane (below, a group of 16 lanes shares its
-    force evaluation): 8192 positrons over 40 steps with scattering, every record against the
+    """From 32768 particles on, each particle has one lane (below, a group of 16 lanes shares its
+    force evaluation): 32768 positrons over 12 steps with scattering, every record against the
     oracle."""
     lib, orc = potentials(K=1)
     E, dt = 10e9, 5e-9
-    x0, y0, thx, thy = entries(8192, E, orc.lat, seed=21)
-    got, _, _ = run_gpu(channel(+1, MS), lib, x0, y0, thx, thy, E, [40] * 8192, dt, 3)
-    ref = T.axial_trajectories(x0, y0, thx, thy, E, 40, dt, 3, orc, charge=+1, ms=True)
+    x0, y0, thx, thy = entries(32768, E, orc.lat, seed=21)
+    got, _, _ = run_gpu(channel(+1, MS), lib, x0, y0, thx, thy, E, [12] * 32768, dt, 3)
+    ref = T.axial_trajectories(x0, y0, thx, thy, E, 12, dt, 3, orc, charge=+1, ms=True)
     close(got, ref.reshape(-1, 10))

@@ -57,7 +57,14 @@ def test_strong_undulator_angular_distribution(precision):
     sub = I.Grid(grid.hbar_omega_eV, grid.theta_x[js], grid.theta_y[js], grid.d_omega[js])
     ref = O.spectrum_cube(tr, sub, O.CLASSICAL)
     hw = grid.hbar_omega_eV
-    dIdO = np.trapezoid(cube, hw, axis=0)
+    # dI/dOmega by the library's reduction over the energies, against numpy's trapezoid of the cube
+    import torch
+    d_cube = torch.from_numpy(np.ascontiguousarray(cube)).cuda()
+    d_hw = torch.from_numpy(hw).cuda()
+    d_out = torch.full((grid.n_angles,), np.nan, dtype=torch.float64, device="cuda")
+    assert rad.rad_angular_distribution(d_cube, d_hw, d_out) == rad.RAD_OK
+    dIdO = d_out.cpu().numpy()
+    np.testing.assert_allclose(dIdO, np.trapezoid(cube, hw, axis=0), rtol=1e-13)
     dIdO_ref = np.trapezoid(ref, hw, axis=0)
     exact = O.ALPHA / (4 * np.pi ** 2) * planar_undulator_exact(hw, sub.theta_x, sub.theta_y, g, K, 0.053, 20)
     assert np.all(np.abs(dIdO_ref / np.trapezoid(exact, hw, axis=0) - 1) < 1e-5)
@@ -237,3 +244,21 @@ def test_positron_ensemble_full_size_sampled():
     bj2 = np.tile(ref_j, no)
     ref = O.spectrum_bins(one, grid, O.SPIN_HALF, bi2, bj2).reshape(no, 64)
     assert_fp64_close(out[:, ref_j], ref)
+
+
+def test_angular_distribution_edge_cases():
+    """The energy integral of a cube: non-uniform photon energies, a ragged number of directions
+    (more than one block of threads), one energy (zero) and no directions; against numpy."""
+    import torch
+    rng = np.random.default_rng(5)
+    for n_omega, n_angles in ((37, 1000), (2, 3), (1, 5), (300, 257)):
+        hw = np.sort(rng.uniform(1.0, 500.0, n_omega))
+        cube = rng.lognormal(0, 2, (n_omega, n_angles))
+        out = torch.full((n_angles,), np.nan, dtype=torch.float64, device="cuda")
+        rc = rad.rad_angular_distribution(torch.from_numpy(cube).cuda(), torch.from_numpy(hw).cuda(), out)
+        assert rc == rad.RAD_OK
+        ref = np.trapezoid(cube, hw, axis=0) if n_omega > 1 else np.zeros(n_angles)
+        np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=1e-13, atol=0)
+    empty = torch.empty(0, dtype=torch.float64, device="cuda")
+    assert rad.rad_angular_distribution(torch.ones(4, dtype=torch.float64, device="cuda"),
+                                        torch.ones(4, dtype=torch.float64, device="cuda"), empty) == rad.RAD_OK
