@@ -106,10 +106,10 @@ bool same_choice(const Choice &a, const Choice &b) {
 int configure(rad_plan p, const Choice &c) {
   if (!supported(p->precision, c)) return RAD_EINVAL;
   LaunchShape sh{c.R, c.NW, c.T, 0, 0, c.pe};
-  const int occ = p->precision == RAD_FP64      ? occupancy_fp64(sh)
-                  : p->precision == RAD_FP64_DF ? occupancy_df(sh)
-                  : c.pp                        ? occupancy_mixed_pp(sh)
-                                                : occupancy_mixed(sh);
+  const int occ = p->precision == RAD_FP64      ? occupancy_fp64(sh, p->mode)
+                  : p->precision == RAD_FP64_DF ? occupancy_df(sh, p->mode)
+                  : c.pp                        ? occupancy_mixed_pp(sh, p->mode)
+                                                : occupancy_mixed(sh, p->mode);
   if (occ <= 0) return RAD_EUNSUPPORTED;
   const int64_t resident = static_cast<int64_t>(p->sms) * occ;
   p->n_wt = static_cast<int>((p->n_omega + 32 * c.R - 1) / (32 * c.R));

@@ -16,7 +16,10 @@
 //                                        product of Ogita, Rump and Oishi ("Accurate sum and dot
 //                                        product", SIAM J. Sci. Comput. 26 (2005), Dot2): per term
 //                                        and component an error-free product, a TwoSum and the
-//                                        errors summed in FP32
+//                                        errors summed in FP32; f_z is not summed: the expanded f
+//                                        of Sec. II satisfies n_x f_x + n_y f_y + f_z = 0
+//                                        identically, so I_z = -(n_x I_x + n_y I_y) is formed from
+//                                        the particle amplitudes
 // Tile sums are added into FP64 particle amplitudes. The per-term error is about 1e-14 of |f|,
 // far inside the FP64 form's tolerance (1e-9 of a bin, floor 1e-6 of the peak).
 #include <cstdio>
@@ -133,8 +136,16 @@ __device__ __forceinline__ void dot2(float &S, float &C, float fh, float fl, flo
 
 template <int MODE>
 struct DfNcomp {
-  static constexpr int value = (MODE == RAD_SPIN_HALF) ? 8 : 6;
+  static constexpr int value = (MODE == RAD_SPIN_HALF) ? 8 : 6;  // components that leave the kernel
 };
+
+// component c of the NC output components (I_x, I_y, I_z, J as re, im) from the NC - 2 summed ones
+// (I_x, I_y, J): I_z = -(n_x I_x + n_y I_y)
+__device__ __forceinline__ double df_component(const double *a, int c, double nx, double ny) {
+  if (c < 4) return a[c];
+  if (c < 6) return -fma(nx, a[c - 4], ny * a[c - 2]);
+  return a[c - 2];
+}
 
 template <int MODE, int R, int NW, int T>
 struct DfLayout {
@@ -142,7 +153,7 @@ struct DfLayout {
   static constexpr int kTable = 0;                                   // float4 [kDfTabN]
   static constexpr int kStage = kTable + kDfTabN * 16;
   static constexpr int kNk = kStage + 2 * kStageDoubles * 8;         // per warp: A [T] double,
-  static constexpr int kNkWarp = T * 8 + T * 32;                     // Fa, Fb [T] float4
+  static constexpr int kNkWarp = T * 8 + T * 16 + ((MODE == RAD_SPIN_HALF) ? T * 8 : 0);  // Fa [T] float4, Fj [T] float2
   static constexpr int kBar = kNk + NW * kNkWarp;
   static constexpr int kMisc = kBar + 16;
   static constexpr int kTotal = kMisc + 16;
@@ -152,6 +163,7 @@ template <int MODE, int R, int NW, int T>
 __global__ void __launch_bounds__(NW * 32, NW == 4 ? 3 : 1) k_df(const Params P) {
   using L = DfLayout<MODE, R, NW, T>;
   constexpr int NC = DfNcomp<MODE>::value;
+  constexpr int NA = NC - 2;  // summed components
   extern __shared__ __align__(128) unsigned char sm[];
   float4 *tab = reinterpret_cast<float4 *>(sm + L::kTable);
   double *stage_base = reinterpret_cast<double *>(sm + L::kStage);
@@ -181,7 +193,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 4 ? 3 : 1) k_df(const Params P)
   unsigned char *myNk = sm + L::kNk + warp * L::kNkWarp;
   double *myA = reinterpret_cast<double *>(myNk);
   float4 *myFa = reinterpret_cast<float4 *>(myNk + T * 8);   // (fx_hi, fx_lo, fy_hi, fy_lo)
-  float4 *myFb = reinterpret_cast<float4 *>(myNk + T * 24);  // (fz_hi, fz_lo, j_hi, j_lo)
+  float2 *myFj = reinterpret_cast<float2 *>(myNk + T * 24);  // (j_hi, j_lo), spin 1/2 only
 
   const int64_t per_chunk = static_cast<int64_t>(P.n_wt) * P.n_nt;
   int s = 0;
@@ -209,12 +221,12 @@ __global__ void __launch_bounds__(NW * 32, NW == 4 ? 3 : 1) k_df(const Params P)
       hwv[r] = iw[r] < P.n_omega ? P.hw[iw[r]] : 1.0;
     }
     double S_acc[R];
-    double amp[R][NC];
+    double amp[R][NA];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       S_acc[r] = 0.0;
 #pragma unroll
-      for (int c = 0; c < NC; ++c) amp[r][c] = 0.0;
+      for (int c = 0; c < NA; ++c) amp[r][c] = 0.0;
     }
 
     int64_t p0, p1;
@@ -252,7 +264,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 4 ? 3 : 1) k_df(const Params P)
               ws[r] = __ddiv_rn(w, __dsub_rn(1.0, u));
             }
 #pragma unroll
-            for (int c = 0; c < NC; ++c) amp[r][c] = 0.0;
+            for (int c = 0; c < NA; ++c) amp[r][c] = 0.0;
           }
         }
         const bool ok = mbar_wait_bounded(&bar[s], parity[s]);
@@ -285,27 +297,29 @@ __global__ void __launch_bounds__(NW * 32, NW == 4 ? 3 : 1) k_df(const Params P)
           const double gw = w / (D * D);
           const double a = nx - vx, b = ny - vy;
           const double m = az + nx * ax + ny * ay;         // n.beta_dot
-          const double cz = inv2g2 - th2h - dvz;           // n_z - beta_z
-          const double fx = (a * m - ax * D) * gw, fy = (b * m - ay * D) * gw, fz = (cz * m - az * D) * gw;
-          const double fj = (MODE == RAD_SPIN_HALF) ? m * gw : 0.0;
+          const double fx = (a * m - ax * D) * gw, fy = (b * m - ay * D) * gw;
           const float fxh = __double2float_rn(fx), fyh = __double2float_rn(fy);
-          const float fzh = __double2float_rn(fz), fjh = __double2float_rn(fj);
           myA[k] = A;
           myFa[k] = make_float4(fxh, __double2float_rn(fx - fxh), fyh, __double2float_rn(fy - fyh));
-          myFb[k] = make_float4(fzh, __double2float_rn(fz - fzh), fjh, __double2float_rn(fj - fjh));
+          if (MODE == RAD_SPIN_HALF) {
+            const double fj = m * gw;
+            const float fjh = __double2float_rn(fj);
+            myFj[k] = make_float2(fjh, __double2float_rn(fj - fjh));
+          }
         }
         __syncwarp();
 
         // tile sums (S + C per component), compensated
-        float tS[R][NC], tC[R][NC];
+        float tS[R][NA], tC[R][NA];
 #pragma unroll
         for (int r = 0; r < R; ++r)
 #pragma unroll
-          for (int c = 0; c < NC; ++c) tS[r][c] = tC[r][c] = 0.f;
+          for (int c = 0; c < NA; ++c) tS[r][c] = tC[r][c] = 0.f;
 #pragma unroll 2
         for (int k = 0; k < n; ++k) {
           const double A = myA[k];
-          const float4 Fa = myFa[k], Fb = myFb[k];
+          const float4 Fa = myFa[k];
+          const float2 Fj = (MODE == RAD_SPIN_HALF) ? myFj[k] : make_float2(0.f, 0.f);
 #pragma unroll
           for (int r = 0; r < R; ++r) {
             const double phi = __dmul_rn(ws[r], A);
@@ -339,18 +353,16 @@ __global__ void __launch_bounds__(NW * 32, NW == 4 ? 3 : 1) k_df(const Params P)
             dot2(tS[r][1], tC[r][1], Fa.x, Fa.y, sh, sl);
             dot2(tS[r][2], tC[r][2], Fa.z, Fa.w, ch, cl);
             dot2(tS[r][3], tC[r][3], Fa.z, Fa.w, sh, sl);
-            dot2(tS[r][4], tC[r][4], Fb.x, Fb.y, ch, cl);
-            dot2(tS[r][5], tC[r][5], Fb.x, Fb.y, sh, sl);
             if (MODE == RAD_SPIN_HALF) {
-              dot2(tS[r][6], tC[r][6], Fb.z, Fb.w, ch, cl);
-              dot2(tS[r][7], tC[r][7], Fb.z, Fb.w, sh, sl);
+              dot2(tS[r][4], tC[r][4], Fj.x, Fj.y, ch, cl);
+              dot2(tS[r][5], tC[r][5], Fj.x, Fj.y, sh, sl);
             }
           }
         }
 #pragma unroll
         for (int r = 0; r < R; ++r)
 #pragma unroll
-          for (int c = 0; c < NC; ++c)
+          for (int c = 0; c < NA; ++c)
             amp[r][c] += static_cast<double>(tS[r][c]) + static_cast<double>(tC[r][c]);
 
         const bool last_of_particle = !nxt.valid || nxt.p != cur.p;
@@ -359,7 +371,10 @@ __global__ void __launch_bounds__(NW * 32, NW == 4 ? 3 : 1) k_df(const Params P)
           for (int r = 0; r < R; ++r) {
             double I2 = 0.0;
 #pragma unroll
-            for (int c = 0; c < 6; ++c) I2 = fma(amp[r][c], amp[r][c], I2);
+            for (int c = 0; c < 6; ++c) {
+              const double v = df_component(amp[r], c, nx, ny);
+              I2 = fma(v, v, I2);
+            }
             double Sv;
             if (MODE == RAD_CLASSICAL) {
               Sv = I2;
@@ -368,7 +383,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 4 ? 3 : 1) k_df(const Params P)
               if (MODE == RAD_SPIN0) {
                 Sv = (1.0 - u) * I2;
               } else {
-                const double J2 = amp[r][6] * amp[r][6] + amp[r][7] * amp[r][7];
+                const double J2 = amp[r][4] * amp[r][4] + amp[r][5] * amp[r][5];
                 Sv = 0.5 * (1.0 + (1.0 - u) * (1.0 - u)) * I2 + (u * u) / (2.0 * gam * gam) * J2;
               }
             }
@@ -390,7 +405,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 4 ? 3 : 1) k_df(const Params P)
         } else {
 #pragma unroll
           for (int c = 0; c < NC; ++c)
-            P.part[((chunk * NC + c) * P.n_angles + jdir) * P.n_omega + iw[r]] = amp[r][c];
+            P.part[((chunk * NC + c) * P.n_angles + jdir) * P.n_omega + iw[r]] = df_component(amp[r], c, nx, ny);
         }
       }
     }
@@ -444,9 +459,9 @@ cudaError_t launch_df(const Params &P, LaunchShape *shape, cudaStream_t st) {
   return dispatch(P, shape, st, nullptr);
 }
 
-int occupancy_df(const LaunchShape &s) {
+int occupancy_df(const LaunchShape &s, int mode) {
   Params P{};
-  P.mode = RAD_SPIN_HALF;
+  P.mode = mode;
   LaunchShape sh = s;
   int occ = 0;
   if (dispatch(P, &sh, nullptr, &occ) != cudaSuccess) return 0;

@@ -10,7 +10,10 @@
 // with a two-part Cody-Waite reduction (W. J. Cody, W. Waite, "Software Manual for the
 // Elementary Functions", 1980), (cos, sin)(2 pi j/4096) is read from a shared-memory table
 // and sin r, cos r - 1 come from their Taylor series (|r| <= pi/4096: truncation below
-// 3e-18). About 14 FP64 operations per sin/cos pair, 20 per term with the accumulation.
+// 3e-18). About 14 FP64 operations per sin/cos pair, 18 (classical) or 20 (spin 1/2) per term
+// with the accumulation: the expanded f of Sec. II satisfies n_x f_x + n_y f_y + f_z = 0
+// identically, so I_z = -(n_x I_x + n_y I_y) is formed from the particle amplitudes instead of
+// being summed.
 #include <cstdio>
 
 #include "rad_internal.cuh"
@@ -44,12 +47,21 @@ __device__ __forceinline__ void sincos_table(double phi, const double2 *__restri
 
 template <int MODE>
 struct Ncomp {
-  static constexpr int value = (MODE == RAD_SPIN_HALF) ? 8 : 6;
+  static constexpr int value = (MODE == RAD_SPIN_HALF) ? 8 : 6;  // components that leave the kernel
 };
+
+// component c of the NC output components (I_x, I_y, I_z, J as re, im) from the NC - 2 summed ones
+// (I_x, I_y, J): I_z = -(n_x I_x + n_y I_y)
+template <typename V>
+__device__ __forceinline__ double out_component(const V &a, int c, double nx, double ny) {
+  if (c < 4) return a[c];
+  if (c < 6) return -fma(nx, a[c - 4], ny * a[c - 2]);
+  return a[c - 2];
+}
 
 template <int MODE, int R, int NW, int T>
 struct Fp64Layout {
-  static constexpr int NARR = (MODE == RAD_SPIN_HALF) ? 5 : 4;  // A, fx, fy, fz (, j)
+  static constexpr int NARR = (MODE == RAD_SPIN_HALF) ? 4 : 3;  // A, fx, fy (, j)
   static constexpr int kStageDoubles = (T + 2) * kRec;
   static constexpr int kTable = 0;
   static constexpr int kStage = kTable + kTabN * 16;
@@ -63,6 +75,7 @@ template <int MODE, int R, int NW, int T>
 __global__ void __launch_bounds__(NW * 32) k_fp64(const Params P) {
   using L = Fp64Layout<MODE, R, NW, T>;
   constexpr int NC = Ncomp<MODE>::value;
+  constexpr int NA = NC - 2;  // summed components
   constexpr int NARR = L::NARR;
   extern __shared__ __align__(128) unsigned char sm[];
   double2 *tab = reinterpret_cast<double2 *>(sm + L::kTable);
@@ -86,8 +99,8 @@ __global__ void __launch_bounds__(NW * 32) k_fp64(const Params P) {
   __syncthreads();
   uint32_t parity[2] = {0u, 0u};
   double *myA = nk + warp * NARR * T;
-  double *myFx = myA + T, *myFy = myA + 2 * T, *myFz = myA + 3 * T;
-  double *myJ = myA + 4 * T;  // spin-1/2 only
+  double *myFx = myA + T, *myFy = myA + 2 * T;
+  double *myJ = myA + 3 * T;  // spin-1/2 only
 
   const int64_t per_chunk = static_cast<int64_t>(P.n_wt) * P.n_nt;
   int s = 0;  // stage of the next tile to consume
@@ -115,12 +128,12 @@ __global__ void __launch_bounds__(NW * 32) k_fp64(const Params P) {
       hwv[r] = iw[r] < P.n_omega ? P.hw[iw[r]] : 1.0;
     }
     double S_acc[R];
-    double amp[R][NC];
+    double amp[R][NA];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       S_acc[r] = 0.0;
 #pragma unroll
-      for (int c = 0; c < NC; ++c) amp[r][c] = 0.0;
+      for (int c = 0; c < NA; ++c) amp[r][c] = 0.0;
     }
 
     int64_t p0, p1;
@@ -158,7 +171,7 @@ __global__ void __launch_bounds__(NW * 32) k_fp64(const Params P) {
               ws[r] = __ddiv_rn(w, __dsub_rn(1.0, u));
             }
 #pragma unroll
-            for (int c = 0; c < NC; ++c) amp[r][c] = 0.0;
+            for (int c = 0; c < NA; ++c) amp[r][c] = 0.0;
           }
         }
         const bool ok = mbar_wait_bounded(&bar[s], parity[s]);
@@ -192,22 +205,20 @@ __global__ void __launch_bounds__(NW * 32) k_fp64(const Params P) {
           const double gw = w / (D * D);
           const double a = nx - vx, b = ny - vy;
           const double m = az + nx * ax + ny * ay;                 // n.beta_dot
-          const double cz = inv2g2 - th2h - dvz;                   // n_z - beta_z
           myA[k] = A;
           myFx[k] = (a * m - ax * D) * gw;
           myFy[k] = (b * m - ay * D) * gw;
-          myFz[k] = (cz * m - az * D) * gw;
           if (MODE == RAD_SPIN_HALF) myJ[k] = m * gw;
         }
         __syncwarp();
 
-        double tpart[R][NC];
+        double tpart[R][NA];
 #pragma unroll
         for (int r = 0; r < R; ++r)
 #pragma unroll
-          for (int c = 0; c < NC; ++c) tpart[r][c] = 0.0;
+          for (int c = 0; c < NA; ++c) tpart[r][c] = 0.0;
         for (int k = 0; k < n; ++k) {
-          const double A = myA[k], fx = myFx[k], fy = myFy[k], fz = myFz[k];
+          const double A = myA[k], fx = myFx[k], fy = myFy[k];
           double jj = 0.0;
           if (MODE == RAD_SPIN_HALF) jj = myJ[k];
 #pragma unroll
@@ -219,18 +230,16 @@ __global__ void __launch_bounds__(NW * 32) k_fp64(const Params P) {
             tpart[r][1] = fma(fx, sn, tpart[r][1]);
             tpart[r][2] = fma(fy, cs, tpart[r][2]);
             tpart[r][3] = fma(fy, sn, tpart[r][3]);
-            tpart[r][4] = fma(fz, cs, tpart[r][4]);
-            tpart[r][5] = fma(fz, sn, tpart[r][5]);
             if (MODE == RAD_SPIN_HALF) {
-              tpart[r][6] = fma(jj, cs, tpart[r][6]);
-              tpart[r][7] = fma(jj, sn, tpart[r][7]);
+              tpart[r][4] = fma(jj, cs, tpart[r][4]);
+              tpart[r][5] = fma(jj, sn, tpart[r][5]);
             }
           }
         }
 #pragma unroll
         for (int r = 0; r < R; ++r)
 #pragma unroll
-          for (int c = 0; c < NC; ++c) amp[r][c] += tpart[r][c];
+          for (int c = 0; c < NA; ++c) amp[r][c] += tpart[r][c];
 
         const bool last_of_particle = !nxt.valid || nxt.p != cur.p;
         if (last_of_particle && !P.amp_mode) {
@@ -238,7 +247,10 @@ __global__ void __launch_bounds__(NW * 32) k_fp64(const Params P) {
           for (int r = 0; r < R; ++r) {
             double I2 = 0.0;
 #pragma unroll
-            for (int c = 0; c < 6; ++c) I2 = fma(amp[r][c], amp[r][c], I2);
+            for (int c = 0; c < 6; ++c) {
+              const double v = out_component(amp[r], c, nx, ny);
+              I2 = fma(v, v, I2);
+            }
             double Sv;
             if (MODE == RAD_CLASSICAL) {
               Sv = I2;
@@ -247,7 +259,7 @@ __global__ void __launch_bounds__(NW * 32) k_fp64(const Params P) {
               if (MODE == RAD_SPIN0) {
                 Sv = (1.0 - u) * I2;
               } else {
-                const double J2 = amp[r][6] * amp[r][6] + amp[r][7] * amp[r][7];
+                const double J2 = amp[r][4] * amp[r][4] + amp[r][5] * amp[r][5];
                 Sv = 0.5 * (1.0 + (1.0 - u) * (1.0 - u)) * I2 + (u * u) / (2.0 * gam * gam) * J2;
               }
             }
@@ -270,7 +282,7 @@ __global__ void __launch_bounds__(NW * 32) k_fp64(const Params P) {
         } else {
 #pragma unroll
           for (int c = 0; c < NC; ++c)
-            P.part[((chunk * NC + c) * P.n_angles + jdir) * P.n_omega + iw[r]] = amp[r][c];
+            P.part[((chunk * NC + c) * P.n_angles + jdir) * P.n_omega + iw[r]] = out_component(amp[r], c, nx, ny);
         }
       }
     }
@@ -342,9 +354,9 @@ cudaError_t launch_fp64(const Params &P, LaunchShape *shape, cudaStream_t st) {
   return dispatch(P, shape, st, nullptr);
 }
 
-int occupancy_fp64(const LaunchShape &s) {
+int occupancy_fp64(const LaunchShape &s, int mode) {
   Params P{};
-  P.mode = RAD_SPIN_HALF;  // largest footprint of the three modes
+  P.mode = mode;
   LaunchShape sh = s;
   int occ = 0;
   if (dispatch(P, &sh, nullptr, &occ) != cudaSuccess) return 0;

@@ -239,20 +239,21 @@ struct LaunchShape {
 // Returns cudaSuccess or the launch error. Fills shape->smem.
 cudaError_t launch_fp64(const Params &P, LaunchShape *shape, cudaStream_t st);
 cudaError_t launch_mixed(const Params &P, LaunchShape *shape, cudaStream_t st);
-// Occupancy (resident blocks per SM) of a shape; 0 if unsupported.
-int occupancy_fp64(const LaunchShape &s);
-int occupancy_mixed(const LaunchShape &s);
+// Occupancy (resident blocks per SM) of a shape for a mode (default: spin 1/2, the largest
+// footprint); 0 if unsupported.
+int occupancy_fp64(const LaunchShape &s, int mode = RAD_SPIN_HALF);
+int occupancy_mixed(const LaunchShape &s, int mode = RAD_SPIN_HALF);
 bool shape_supported_fp64(int R, int NW, int T);
 bool shape_supported_mixed(int R, int NW, int T);
 // mixed kernel fed by the per-sample pre-pass (rad_mixed_pp.cu); prep holds 12 floats per sample
 bool shape_supported_mixed_pp(int R, int NW, int T);
-int occupancy_mixed_pp(const LaunchShape &s);
+int occupancy_mixed_pp(const LaunchShape &s, int mode = RAD_SPIN_HALF);
 cudaError_t launch_prep_samples(const Params &P, int T, float *prep, cudaStream_t st);
 cudaError_t launch_mixed_pp(const Params &P, const float *prep, LaunchShape *shape, cudaStream_t st);
 
 // FP64-accurate kernel with double-float FP32 arithmetic after the FP64 phase (rad_df.cu)
 bool shape_supported_df(int R, int NW, int T);
-int occupancy_df(const LaunchShape &s);
+int occupancy_df(const LaunchShape &s, int mode = RAD_SPIN_HALF);
 cudaError_t launch_df(const Params &P, LaunchShape *shape, cudaStream_t st);
 
 // post-processing kernels (rad_post.cu)

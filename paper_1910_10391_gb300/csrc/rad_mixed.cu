@@ -14,7 +14,9 @@
 //     paper's g base and free of cancellation), tile sums of f e^{i phi}.
 //   - Tile sums are rotated by e^{i Phi0} and added to Kahan-compensated FP32 running sums
 //     (W. Kahan, "Further remarks on reducing truncation errors", CACM 8 (1965)).
-// Per term: 2 SFU ops (sin, cos) and 8 (classical/spin-0) or 10 (spin-1/2) FMA-pipe ops.
+// Per term: 2 SFU ops (sin, cos) and 6 (classical/spin-0) or 8 (spin-1/2) FMA-pipe ops. f_z is
+// not summed: the expanded f of Sec. II satisfies n_x f_x + n_y f_y + f_z = 0 identically, so
+// I_z = -(n_x I_x + n_y I_y) is formed from the running sums.
 #include "rad_mixed_common.cuh"
 
 namespace rad {
@@ -27,8 +29,8 @@ struct MixLayout {
   static constexpr int kStage = 0;
   static constexpr int kSamp = kStage + 2 * kStageDoubles * 8;
   static constexpr int kRef = kSamp + NS * T * 4;          // per warp: FP64 phase at the reference sample
-  static constexpr int kNk = kRef + 16 * NW;                // per warp: float4 [T] (+ float j[T])
-  static constexpr int kNkWarp = T * 16 + ((MODE == RAD_SPIN_HALF) ? T * 4 : 0);
+  static constexpr int kNk = kRef + 16 * NW;                // per warp: float4 [T] (dA, fx, fy, j)
+  static constexpr int kNkWarp = T * 16;
   static constexpr int kBar = kNk + NW * kNkWarp;
   static constexpr int kMisc = kBar + 16;
   static constexpr int kGuard = kMisc + 16;  // error-budget guard: w*_max, c_max, max|theta_x|, max|theta_y|
@@ -38,7 +40,8 @@ struct MixLayout {
 template <int MODE, int R, int NW, int T>
 __global__ void __launch_bounds__(NW * 32) k_mixed(const Params P) {
   using L = MixLayout<MODE, R, NW, T>;
-  constexpr int NC = (MODE == RAD_SPIN_HALF) ? 8 : 6;
+  constexpr int NC = (MODE == RAD_SPIN_HALF) ? 8 : 6;  // I_x, I_y, I_z (, J) as re, im
+  constexpr int NA = NC - 2;                             // summed: I_x, I_y (, J)
   extern __shared__ __align__(128) unsigned char sm[];
   double *stage_base = reinterpret_cast<double *>(sm + L::kStage);
   float *samp = reinterpret_cast<float *>(sm + L::kSamp);
@@ -50,8 +53,7 @@ __global__ void __launch_bounds__(NW * 32) k_mixed(const Params P) {
   int *s_item = reinterpret_cast<int *>(sm + L::kMisc);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  float4 *myF = reinterpret_cast<float4 *>(sm + L::kNk + warp * L::kNkWarp);  // dA, fx, fy, fz
-  float *myJ = reinterpret_cast<float *>(sm + L::kNk + warp * L::kNkWarp + T * 16);
+  float4 *myF = reinterpret_cast<float4 *>(sm + L::kNk + warp * L::kNkWarp);  // dA, fx, fy, j
   // a failed device data check skips the computation (one read per block, shared by all threads)
   if (tid == 0) s_item[1] = *reinterpret_cast<volatile int *>(P.status);
   __syncthreads();
@@ -96,13 +98,20 @@ __global__ void __launch_bounds__(NW * 32) k_mixed(const Params P) {
       hwv[r] = iw[r] < P.n_omega ? P.hw[iw[r]] : 1.0;
     }
     double S_acc[R];
-    float ks[R][NC], kc[R][NC];  // Kahan running sums of the current particle
+    float ks[R][NA], kc[R][NA];  // Kahan running sums of the current particle
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       S_acc[r] = 0.0;
 #pragma unroll
-      for (int c = 0; c < NC; ++c) ks[r][c] = kc[r][c] = 0.f;
+      for (int c = 0; c < NA; ++c) ks[r][c] = kc[r][c] = 0.f;
     }
+    // output component c (0..NC-1) of energy r from the compensated sums
+    auto component = [&](int r, int c) -> double {
+      auto v = [&](int i) { return static_cast<double>(ks[r][i]) - static_cast<double>(kc[r][i]); };
+      if (c < 4) return v(c);
+      if (c < 6) return -fma(nx, v(c - 4), ny * v(c - 2));
+      return v(c - 2);
+    };
 
     int64_t p0, p1;
     int q;
@@ -152,7 +161,7 @@ __global__ void __launch_bounds__(NW * 32) k_mixed(const Params P) {
             wt_hi[r] = static_cast<float>(wtd);
             wt_lo[r] = static_cast<float>(wtd - static_cast<double>(wt_hi[r]));
 #pragma unroll
-            for (int c = 0; c < NC; ++c) ks[r][c] = kc[r][c] = 0.f;
+            for (int c = 0; c < NA; ++c) ks[r][c] = kc[r][c] = 0.f;
           }
         }
         const bool ok = mbar_wait_bounded(&bar[s], parity[s]);
@@ -213,14 +222,12 @@ __global__ void __launch_bounds__(NW * 32) k_mixed(const Params P) {
           const float D = fmaf(0.5f, fmaf(a, a, b * b), sS0[k]);          // 1 - n.beta
           const float rD = __frcp_rn(D);
           const float g = rD * rD;
-          const float cz = fmaf(-nyf, b, fmaf(-nxf, a, D));               // n_z - beta_z
           float4 o;
           o.x = fmaf(-nyf, sDy[k], fmaf(-nxf, sDx[k], fmaf(cn_hi, sDt[k], fmaf(cn_lo, sDt[k], -sDdz[k]))));
           o.y = fmaf(a, m, -axw * D) * g;
           o.z = fmaf(b, m, -ayw * D) * g;
-          o.w = fmaf(cz, m, -azw * D) * g;
+          o.w = (MODE == RAD_SPIN_HALF) ? m * g : 0.f;
           myF[k] = o;
-          if (MODE == RAD_SPIN_HALF) myJ[k] = m * g;
         }
         __syncwarp();
 
@@ -247,11 +254,11 @@ __global__ void __launch_bounds__(NW * 32) k_mixed(const Params P) {
           __sincosf(rr * kTwoPiF, &s0[r], &c0[r]);
         }
 
-        float tpart[R][NC];
+        float tpart[R][NA];
 #pragma unroll
         for (int r = 0; r < R; ++r)
 #pragma unroll
-          for (int c = 0; c < NC; ++c) tpart[r][c] = 0.f;
+          for (int c = 0; c < NA; ++c) tpart[r][c] = 0.f;
         // per term: phase offset x = w* (A_k - A_ref) in radians (the reference is the tile's
         // middle sample, so |x| stays below ~1e3 rad), SFU sin/cos with the unit's own
         // periodic argument handling (absolute error ~2e-7 |x|, random per term; bounded by
@@ -259,8 +266,6 @@ __global__ void __launch_bounds__(NW * 32) k_mixed(const Params P) {
 #pragma unroll 4
         for (int k = 0; k < n; ++k) {
           const float4 F = myF[k];
-          float jj = 0.f;
-          if (MODE == RAD_SPIN_HALF) jj = myJ[k];
 #pragma unroll
           for (int r = 0; r < R; ++r) {
             const float x = ws_f[r] * F.x;
@@ -270,11 +275,9 @@ __global__ void __launch_bounds__(NW * 32) k_mixed(const Params P) {
             tpart[r][1] = fmaf(F.y, sn, tpart[r][1]);
             tpart[r][2] = fmaf(F.z, cs, tpart[r][2]);
             tpart[r][3] = fmaf(F.z, sn, tpart[r][3]);
-            tpart[r][4] = fmaf(F.w, cs, tpart[r][4]);
-            tpart[r][5] = fmaf(F.w, sn, tpart[r][5]);
             if (MODE == RAD_SPIN_HALF) {
-              tpart[r][6] = fmaf(jj, cs, tpart[r][6]);
-              tpart[r][7] = fmaf(jj, sn, tpart[r][7]);
+              tpart[r][4] = fmaf(F.w, cs, tpart[r][4]);
+              tpart[r][5] = fmaf(F.w, sn, tpart[r][5]);
             }
           }
         }
@@ -282,7 +285,7 @@ __global__ void __launch_bounds__(NW * 32) k_mixed(const Params P) {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
 #pragma unroll
-          for (int c = 0; c < NC; c += 2) {
+          for (int c = 0; c < NA; c += 2) {
             const float re = fmaf(c0[r], tpart[r][c], -s0[r] * tpart[r][c + 1]);
             const float im = fmaf(s0[r], tpart[r][c], c0[r] * tpart[r][c + 1]);
             kahan_add(ks[r][c], kc[r][c], re);
@@ -297,7 +300,7 @@ __global__ void __launch_bounds__(NW * 32) k_mixed(const Params P) {
             double I2 = 0.0;
 #pragma unroll
             for (int c = 0; c < 6; ++c) {
-              const double v = static_cast<double>(ks[r][c]) - static_cast<double>(kc[r][c]);
+              const double v = component(r, c);
               I2 = fma(v, v, I2);
             }
             double Sv;
@@ -308,8 +311,8 @@ __global__ void __launch_bounds__(NW * 32) k_mixed(const Params P) {
               if (MODE == RAD_SPIN0) {
                 Sv = (1.0 - u) * I2;
               } else {
-                const double jr = static_cast<double>(ks[r][6]) - static_cast<double>(kc[r][6]);
-                const double ji = static_cast<double>(ks[r][7]) - static_cast<double>(kc[r][7]);
+                const double jr = component(r, 6);
+                const double ji = component(r, 7);
                 Sv = 0.5 * (1.0 + (1.0 - u) * (1.0 - u)) * I2 + (u * u) / (2.0 * gam * gam) * (jr * jr + ji * ji);
               }
             }
@@ -335,8 +338,7 @@ __global__ void __launch_bounds__(NW * 32) k_mixed(const Params P) {
         } else {
 #pragma unroll
           for (int c = 0; c < NC; ++c)
-            P.part[((chunk * NC + c) * P.n_angles + jdir) * P.n_omega + iw[r]] =
-                static_cast<double>(ks[r][c]) - static_cast<double>(kc[r][c]);
+            P.part[((chunk * NC + c) * P.n_angles + jdir) * P.n_omega + iw[r]] = component(r, c);
         }
       }
     }
@@ -400,9 +402,9 @@ cudaError_t launch_mixed(const Params &P, LaunchShape *shape, cudaStream_t st) {
   return dispatch(P, shape, st, nullptr);
 }
 
-int occupancy_mixed(const LaunchShape &s) {
+int occupancy_mixed(const LaunchShape &s, int mode) {
   Params P{};
-  P.mode = RAD_SPIN_HALF;
+  P.mode = mode;
   LaunchShape sh = s;
   int occ = 0;
   if (dispatch(P, &sh, nullptr, &occ) != cudaSuccess) return 0;

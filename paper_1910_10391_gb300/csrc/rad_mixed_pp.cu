@@ -108,7 +108,7 @@ struct PPLayout {
   static constexpr int kStageBytes = T * kPP * 4;
   static constexpr int kStage = 0;
   static constexpr int kNk = kStage + 2 * kStageBytes;
-  static constexpr int kNkWarp = T * 16 + ((MODE == RAD_SPIN_HALF) ? T * 4 : 0);
+  static constexpr int kNkWarp = T * 16;  // (phase offset, f_x, f_y, j) per sample
   static constexpr int kBar = kNk + NW * kNkWarp;  // full[2], empty[2]
   static constexpr int kMisc = kBar + 32;
   static constexpr int kTotal = kMisc + 16;
@@ -149,14 +149,17 @@ __device__ __forceinline__ void sincos_fma(float x, float &s, float &c) {
 template <int MODE, int R, int NW, int T, int PE>
 __global__ void __launch_bounds__(NW * 32, NW == 8 ? (R <= 2 ? 2 : 1) : 3) k_mixed_pp(const Params P, const float *__restrict__ prep) {
   using L = PPLayout<MODE, R, NW, T>;
+  // NC components leave the kernel (I_x, I_y, I_z and, for spin 1/2, J, each re and im); NA are
+  // summed: the expanded f of Sec. II satisfies n_x f_x + n_y f_y + f_z = 0 identically, so
+  // I_z = -(n_x I_x + n_y I_y) is formed from the sums at the end instead of being summed.
   constexpr int NC = (MODE == RAD_SPIN_HALF) ? 8 : 6;
+  constexpr int NA = NC - 2;
   extern __shared__ __align__(128) unsigned char sm[];
   uint64_t *full = reinterpret_cast<uint64_t *>(sm + L::kBar);
   uint64_t *empty = full + 2;
   int *s_item = reinterpret_cast<int *>(sm + L::kMisc);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float4 *myF = reinterpret_cast<float4 *>(sm + L::kNk + warp * L::kNkWarp);
-  float *myJ = reinterpret_cast<float *>(sm + L::kNk + warp * L::kNkWarp + T * 16);
 
   if (tid == 0) s_item[1] = *reinterpret_cast<volatile int *>(P.status);
   __syncthreads();
@@ -211,13 +214,20 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? (R <= 2 ? 2 : 1) : 3) k_mix
       hwv[r] = iw[r] < P.n_omega ? P.hw[iw[r]] : 1.0;
     }
     double S_acc[R];
-    float ks[R][NC], kc[R][NC];
+    float ks[R][NA], kc[R][NA];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       S_acc[r] = 0.0;
 #pragma unroll
-      for (int c = 0; c < NC; ++c) ks[r][c] = kc[r][c] = 0.f;
+      for (int c = 0; c < NA; ++c) ks[r][c] = kc[r][c] = 0.f;
     }
+    // output component c (0..NC-1) of energy r from the compensated sums
+    auto component = [&](int r, int c) -> double {
+      auto v = [&](int i) { return static_cast<double>(ks[r][i]) - static_cast<double>(kc[r][i]); };
+      if (c < 4) return v(c);
+      if (c < 6) return -fma(nx, v(c - 4), ny * v(c - 2));
+      return v(c - 2);
+    };
     int64_t p0, p1;
     int q;
     chunk_range(P, chunk, p0, p1, q);
@@ -255,7 +265,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? (R <= 2 ? 2 : 1) : 3) k_mix
             wt_hi[r] = static_cast<float>(wtd);
             wt_lo[r] = static_cast<float>(wtd - static_cast<double>(wt_hi[r]));
 #pragma unroll
-            for (int c = 0; c < NC; ++c) ks[r][c] = kc[r][c] = 0.f;
+            for (int c = 0; c < NA; ++c) ks[r][c] = kc[r][c] = 0.f;
           }
         }
         const bool ok = !failed && mbar_wait_bounded(&full[s], full_par[s]);
@@ -283,7 +293,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? (R <= 2 ? 2 : 1) : 3) k_mix
           a0l = static_cast<float>(A0 - static_cast<double>(a0h));
         }
 
-        // per (n, k): weighted f, j and the FP32 phase offset for this warp's direction
+        // per (n, k): weighted f_x, f_y, j and the FP32 phase offset for this warp's direction
         for (int k = lane; k < n; k += 32) {
           const float4 ra = reinterpret_cast<const float4 *>(st + k * kPP)[0];
           const float4 rb = reinterpret_cast<const float4 *>(st + k * kPP)[1];
@@ -294,24 +304,22 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? (R <= 2 ? 2 : 1) : 3) k_mix
           const float D = fmaf(0.5f, fmaf(a, a, b * b), rcz.y);
           const float rD = __frcp_rn(D);
           const float g = rD * rD;
-          const float cz = fmaf(-nyf, b, fmaf(-nxf, a, D));
           float4 o;
           o.x = fmaf(-nyf, ra.w, fmaf(-nxf, ra.z, fmaf(cn_hi, ra.x, fmaf(cn_lo, ra.x, -ra.y))));
           o.y = fmaf(a, m, -axw * D) * g;
           o.z = fmaf(b, m, -ayw * D) * g;
-          o.w = fmaf(cz, m, -azw * D) * g;
+          o.w = (MODE == RAD_SPIN_HALF) ? m * g : 0.f;
           myF[k] = o;
-          if (MODE == RAD_SPIN_HALF) myJ[k] = m * g;
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);  // this warp is done with the stage
 
-        float tpart[R][NC];
+        float tpart[R][NA];
 #pragma unroll
         for (int r = 0; r < R; ++r)
 #pragma unroll
-          for (int c = 0; c < NC; ++c) tpart[r][c] = 0.f;
-        auto term = [&](const float4 &F, float jj, int r, bool on_fma) {
+          for (int c = 0; c < NA; ++c) tpart[r][c] = 0.f;
+        auto term = [&](const float4 &F, int r, bool on_fma) {
           const float x = ws_f[r] * F.x;
           float sn, cs;
           if (on_fma)
@@ -322,34 +330,24 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? (R <= 2 ? 2 : 1) : 3) k_mix
           tpart[r][1] = fmaf(F.y, sn, tpart[r][1]);
           tpart[r][2] = fmaf(F.z, cs, tpart[r][2]);
           tpart[r][3] = fmaf(F.z, sn, tpart[r][3]);
-          tpart[r][4] = fmaf(F.w, cs, tpart[r][4]);
-          tpart[r][5] = fmaf(F.w, sn, tpart[r][5]);
           if (MODE == RAD_SPIN_HALF) {
-            tpart[r][6] = fmaf(jj, cs, tpart[r][6]);
-            tpart[r][7] = fmaf(jj, sn, tpart[r][7]);
+            tpart[r][4] = fmaf(F.w, cs, tpart[r][4]);
+            tpart[r][5] = fmaf(F.w, sn, tpart[r][5]);
           }
         };
         int k = 0;
         for (; k + 8 <= n; k += 8) {
-          // j of the eight samples in two 16-byte loads (k is a multiple of 8 here)
-          const float4 J4 = (MODE == RAD_SPIN_HALF) ? reinterpret_cast<const float4 *>(myJ)[k >> 2]
-                                                    : make_float4(0.f, 0.f, 0.f, 0.f);
-          const float4 J5 = (MODE == RAD_SPIN_HALF) ? reinterpret_cast<const float4 *>(myJ)[(k >> 2) + 1]
-                                                    : make_float4(0.f, 0.f, 0.f, 0.f);
-          const float jq[8] = {J4.x, J4.y, J4.z, J4.w, J5.x, J5.y, J5.z, J5.w};
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
             const float4 F = myF[k + q];
-            const float jj = jq[q];
 #pragma unroll
-            for (int r = 0; r < R; ++r) term(F, jj, r, PE > 0 && (q * R + r) % (PE > 0 ? PE : 1) == PE - 1);
+            for (int r = 0; r < R; ++r) term(F, r, PE > 0 && (q * R + r) % (PE > 0 ? PE : 1) == PE - 1);
           }
         }
         for (; k < n; ++k) {
           const float4 F = myF[k];
-          const float jj = (MODE == RAD_SPIN_HALF) ? myJ[k] : 0.f;
 #pragma unroll
-          for (int r = 0; r < R; ++r) term(F, jj, r, false);
+          for (int r = 0; r < R; ++r) term(F, r, false);
         }
         a0h = __shfl_sync(0xffffffffu, a0h, 0);
         a0l = __shfl_sync(0xffffffffu, a0l, 0);
@@ -359,7 +357,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? (R <= 2 ? 2 : 1) : 3) k_mix
 #pragma unroll
         for (int r = 0; r < R; ++r) {
 #pragma unroll
-          for (int c = 0; c < NC; c += 2) {
+          for (int c = 0; c < NA; c += 2) {
             const float re = fmaf(c0[r], tpart[r][c], -s0[r] * tpart[r][c + 1]);
             const float im = fmaf(s0[r], tpart[r][c], c0[r] * tpart[r][c + 1]);
             kahan_add(ks[r][c], kc[r][c], re);
@@ -373,7 +371,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? (R <= 2 ? 2 : 1) : 3) k_mix
             double I2 = 0.0;
 #pragma unroll
             for (int c = 0; c < 6; ++c) {
-              const double v = static_cast<double>(ks[r][c]) - static_cast<double>(kc[r][c]);
+              const double v = component(r, c);
               I2 = fma(v, v, I2);
             }
             double Sv;
@@ -384,8 +382,8 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? (R <= 2 ? 2 : 1) : 3) k_mix
               if (MODE == RAD_SPIN0) {
                 Sv = (1.0 - u) * I2;
               } else {
-                const double jr = static_cast<double>(ks[r][6]) - static_cast<double>(kc[r][6]);
-                const double ji = static_cast<double>(ks[r][7]) - static_cast<double>(kc[r][7]);
+                const double jr = component(r, 6);
+                const double ji = component(r, 7);
                 Sv = 0.5 * (1.0 + (1.0 - u) * (1.0 - u)) * I2 + (u * u) / (2.0 * gam * gam) * (jr * jr + ji * ji);
               }
             }
@@ -406,8 +404,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? (R <= 2 ? 2 : 1) : 3) k_mix
         } else {
 #pragma unroll
           for (int c = 0; c < NC; ++c)
-            P.part[((chunk * NC + c) * P.n_angles + jdir) * P.n_omega + iw[r]] =
-                static_cast<double>(ks[r][c]) - static_cast<double>(kc[r][c]);
+            P.part[((chunk * NC + c) * P.n_angles + jdir) * P.n_omega + iw[r]] = component(r, c);
         }
       }
     }
@@ -479,9 +476,9 @@ cudaError_t launch_mixed_pp(const Params &P, const float *prep, LaunchShape *sha
   return dispatch(P, prep, shape, st, nullptr);
 }
 
-int occupancy_mixed_pp(const LaunchShape &s) {
+int occupancy_mixed_pp(const LaunchShape &s, int mode) {
   Params P{};
-  P.mode = RAD_SPIN_HALF;
+  P.mode = mode;
   LaunchShape sh = s;
   int occ = 0;
   if (dispatch(P, nullptr, &sh, nullptr, &occ) != cudaSuccess) return 0;

@@ -387,10 +387,12 @@ __device__ __forceinline__ State deriv_axial(const Chan &C, const Axial &A, doub
 // run kGroup-wide instead of on one lane; 1024 particles then fill 16384 lanes instead of 1024.
 // The groups of a warp may diverge (different lengths): every shuffle names its own group's lanes.
 constexpr int kGroup = 16;
-// below this many particles the lane-group kernel runs (16 lanes each); above, one lane each (the
-// groups' copies of the state cost about a fifth more FP64 work, which pays while one lane per
-// particle leaves the SMs short of warps)
-constexpr int64_t kGroupBelow = 32768;
+// below this many particles the lane-group kernel runs (16 lanes each); above, one lane each. One
+// lane per particle keeps the FP64 pipe busy from about one warp per SM sub-partition on; the
+// groups repeat the state update in every lane, so they pay only while the one-lane kernel has
+// fewer warps than that (measured on 2048-step Si <110> ensembles: 4096 particles 0.55 s against
+// 1.01 s, 8192 0.94 s against 1.02 s, 16384 1.85 s against 1.11 s)
+constexpr int64_t kGroupBelow = 9216;
 
 // the sum over the group, identical in every lane (the butterfly adds in a different order in
 // each lane, so the group's first lane's sum is broadcast: the lanes' states stay bit-identical)
@@ -1377,7 +1379,7 @@ int launch_axial(const rad_channel *ch, const rad_axial_potential *pot, int64_t 
         C, A, n_particles, offsets, n_samples_total, energy_eV, x0, y0, thx0, thy0, particle_ids, dt, seed, out,
         energy_out, ds);
   } else {
-    const int block = n_particles < 152 * 4 * 32 ? 32 : 128;
+    const int block = 32;  // one-warp blocks spread the particles evenly over the SMs
     int64_t grid = (n_particles + block - 1) / block;
     if (grid > 1 << 20) grid = 1 << 20;
     k_axial<<<static_cast<unsigned>(grid), block, 0, static_cast<cudaStream_t>(stream)>>>(

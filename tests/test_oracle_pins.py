@@ -240,6 +240,42 @@ def _bruteforce_errors():
     return worst_comp, worst_sq
 
 
+def _transversality_error():
+    """max over directions of |n_x I_x + n_y I_y + I_z| / int |f| dt, both components, on the
+    elliptical undulator (motion in both transverse planes) at directions up to 3/gamma."""
+    tr = I.elliptical_undulator()
+    g = float(tr.gamma[0])
+    ws = 1.3 * I.undulator_first_harmonic_eV(g, 0.4e-10, 10e-6) / I.HBARC_EV_M
+    worst, fz_rel = 0.0, 0.0
+    rng = np.random.default_rng(11)
+    for nx, ny in rng.uniform(-3.0 / g, 3.0 / g, size=(12, 2)):
+        a = O.amplitudes(tr.samples, g, ws, nx, ny)
+        for c in (0, 1):
+            worst = max(worst, abs(nx * a[c] + ny * a[2 + c] + a[4 + c]) / a[8])
+        fz_rel = max(fz_rel, math.hypot(a[4], a[5]) / a[8])
+    return worst, fz_rel
+
+
+def test_amplitudes_are_transverse():
+    """Eq. 2 makes f = n x (...) perpendicular to n; the expanded f of Sec. II keeps this exactly
+    with n = (n_x, n_y, 1): n_x f_x + n_y f_y + f_z = 0 term by term, so the amplitudes satisfy
+    n_x I_x + n_y I_y + I_z = 0 to rounding (the GPU kernels form I_z this way)."""
+    worst, fz_rel = _transversality_error()
+    assert fz_rel > 1e-6       # I_z is not trivially small on this case (1.2e-5 of int |f| dt)
+    assert worst < 1e-14       # observed 5e-21
+
+
+@pytest.mark.parametrize("plant", [1, 3])
+def test_transversality_catches_planted_mistakes(plant):
+    """A dropped bracket in f_x and a dropped f_z each break n_x I_x + n_y I_y + I_z = 0."""
+    O.set_plant(plant)
+    try:
+        worst, _ = _transversality_error()
+    finally:
+        O.set_plant(0)
+    assert worst > 1e-6        # observed 2e-5 and 1e-5
+
+
 def test_expansion_against_unexpanded_bruteforce():
     comp, sq = _bruteforce_errors()
     assert comp < 1e-5
