@@ -33,17 +33,19 @@ sys.path.insert(0, ROOT)
 METRIC = "integrand terms/s (ω·n·t) & spectra/s: plain FP64 vs chosen form at stated err"
 N_PART, N_SAMP, N_OMEGA, N_SIDE = 1024, 20000, 512, 64
 TUNE_PARTICLES = 8
-# launch shapes (R, NW, T) of the mixed kernel per model: the fastest of the shapes timed on
-# 32-particle launches of this workload (R=2 or 4, NW=4 or 8, T=128 or 256); --autotune lets the
-# library's autotuner choose instead
-SHAPES = {0: (2, 8, 256), 2: (2, 4, 256)}
+# launch shapes (R, NW, T) of the mixed kernel per model and its sin/cos split (1/split of the
+# terms on the FMA pipe, 0: none): the fastest timed on 32-particle launches of this workload
+# (R=2 or 4, NW=4 or 8, T=128 or 256, split 0, 4 or 6); --autotune lets the library's autotuner
+# choose instead
+SHAPES = {0: (2, 8, 256), 2: (2, 8, 256)}
+SPLIT = {0: 6, 2: 0}
 # per model: FP64 instructions per term of k_fp64 and k_df, and warp instructions per 32 terms of
 # k_df, counted by ncu (smsp__inst_executed_pipe_fp64.sum x 32 / terms, smsp__inst_executed.sum)
 # on the launch these legs time: one particle of this workload x 512 hw x 64x64 directions, the
 # default shapes (k_fp64 R=2 NW=8 T=64, k_df R=2 NW=4 T=64)
-FP64_OPS_PER_TERM = {0: 20.70, 2: 22.75}
-DF_FP64_OPS_PER_TERM = {0: 2.10, 2: 2.34}
-DF_INST_PER_32_TERMS = {0: 175.6, 2: 200.6}
+FP64_OPS_PER_TERM = {0: 18.53, 2: 20.58}
+DF_FP64_OPS_PER_TERM = {0: 1.85, 2: 2.05}
+DF_INST_PER_32_TERMS = {0: 149.0, 2: 175.2}
 WORKLOAD = ("positron ensemble: 1024 e+ at 10 GeV, harmonic planar well (U0 = 20 eV, d_p = 1.92 A), "
             "RK4 + scattering kicks, 20000 samples over 100 um; 512 log hw in [1e-4 E, 0.5 E] x 64x64 "
             "directions within +-(theta_L + 3/gamma); classical + spin-1/2")
@@ -58,13 +60,12 @@ SPLIT_EXTRA_SLOTS = 18       # FMA-pipe sin/cos (21 slots) in place of prescale 
 def clocks_per_term(mode, R, pe):
     """Lower bound on SM clocks per term of the mixed integral kernel (k_mixed_pp / k_mixed)
     from its two limits: the SFU (2 MUFU per term it serves, 16 per SM per clock) and the issue
-    slots (per SFU term: the phase FMUL, the prescale FMUL, 2 MUFU, 6 or 8 FFMA and the term's
-    share of the shared-memory loads, one float4 (+ one float for spin-1/2) per sample shared by
-    R energies; an FMA-pipe sin/cos term takes 18 slots more). With a split 1/pe, f is the
-    fraction of the 8R terms of an unrolled group whose index is pe - 1 mod pe."""
-    import math
-    nc = 8 if mode == 2 else 6
-    loads = (2 if mode == 2 else 1) / R
+    slots (per SFU term: the phase FMUL, the prescale FMUL, 2 MUFU, 4 or 6 FFMA (I_x, I_y and for
+    spin-1/2 J, each re and im) and the term's share of the shared-memory loads, one float4 per
+    sample shared by R energies; an FMA-pipe sin/cos term takes 18 slots more). With a split
+    1/pe, f is the fraction of the 8R terms of an unrolled group whose index is pe - 1 mod pe."""
+    nc = 6 if mode == 2 else 4
+    loads = 1.0 / R
     f = (sum(1 for i in range(8 * R) if i % pe == pe - 1) / (8 * R)) if pe else 0.0
     sfu = 2.0 * (1.0 - f) / SFU_PER_SM_CLK
     issue = (4 + nc + loads + SPLIT_EXTRA_SLOTS * f) / ISSUE_PER_SM_CLK
@@ -425,6 +426,10 @@ def main():
             rc = plans[m].set_shape(*SHAPES[m], 1)
             if rc:
                 raise rad.RadError(rc, "rad_plan_set_shape")
+            if SPLIT[m]:
+                rc = plans[m].set_sincos_split(SPLIT[m])
+                if rc:
+                    raise rad.RadError(rc, "rad_plan_set_sincos_split")
     for m in modes:
         plans[m].set_timing(True)
 

@@ -17,13 +17,17 @@ def test_clocks_per_term_from_unit_counts():
     for mode, R in ((0, 2), (2, 2), (0, 1), (2, 1)):
         c, f = bench.clocks_per_term(mode, R, 0)
         assert f == 0.0 and c == pytest.approx(2 / 16)
-    # the issue-slot limits: phase FMUL, prescale FMUL, 2 MUFU, 6 or 8 FFMA, shared loads per R
-    # energies: classical (4 + 6 + 1/2)/128 = 0.082, spin-1/2 (4 + 8 + 2/2)/128 = 0.102
-    assert (4 + 6 + 0.5) / 128 < 2 / 16 and (4 + 8 + 1.0) / 128 < 2 / 16
+    # the issue-slot limits: phase FMUL, prescale FMUL, 2 MUFU, 4 or 6 FFMA (I_z is not summed),
+    # one shared load per R energies: classical (4 + 4 + 1/2)/128 = 0.066, spin-1/2
+    # (4 + 6 + 1/2)/128 = 0.082
+    assert (4 + 4 + 0.5) / 128 < 2 / 16 and (4 + 6 + 0.5) / 128 < 2 / 16
     # a 1/4 split at R = 2 moves 4 of every 16 terms to the FMA pipe (18 extra slots each):
-    # SFU 2 * 3/4 / 16 = 0.094, issue (10.5 + 18/4)/128 = 0.117, so issue binds
+    # SFU 2 * 3/4 / 16 = 0.094, issue (8.5 + 18/4)/128 = 0.102, so issue binds
     c, f = bench.clocks_per_term(0, 2, 4)
-    assert f == pytest.approx(0.25) and c == pytest.approx((4 + 6 + 0.5 + 18 * 0.25) / 128)
+    assert f == pytest.approx(0.25) and c == pytest.approx((4 + 4 + 0.5 + 18 * 0.25) / 128)
+    # a 1/6 split at R = 2 moves 2 of every 16 (indices 5 and 11): SFU 2 * 7/8 / 16 = 0.109 binds
+    c, f = bench.clocks_per_term(0, 2, 6)
+    assert f == pytest.approx(0.125) and c == pytest.approx(2 * 0.875 / 16)
     # the benchmark's peak: 152 SMs x 2070 MHz / 0.125 clocks per term
     assert bench.SM_COUNT * bench.SM_MAX_MHZ * 1e6 / (2 / 16) == pytest.approx(2.517e12, rel=1e-3)
 
