@@ -583,16 +583,16 @@ def main():
     terms_all = terms_launch * len(kms)
     sfu_ops = sfu_ops_total / t_meas
     sfu_peak = SM_COUNT * SFU_PER_SM_CLK * SM_MAX_MHZ * 1e6
-    # DRAM bytes per launch of the integral kernel (k_mixed_pp), scaled from its ncu capture on a
+    # DRAM bytes per launch of the integral kernel (k_mixed_pp), scaled from its ncu captures on a
     # small case of the same workload (128 particles x 20000 samples x 64 hw x 256 directions,
-    # shape R=2 NW=4 T=256, 29 particle chunks: 125.39 MB read = the 48-byte pre-pass records once,
-    # 5.24 MB written):
-    # reads grow with the samples a launch processes, writes with the partial sums it stores.
+    # the benchmark's shapes R=2 NW=8 T=256, 38 particle chunks; the two models' mean: 125.16 MB
+    # read = the 48-byte pre-pass records once, 6.10 MB written, of which 4.98 MB are the partial
+    # sums): reads grow with the samples a launch processes, writes with the partial sums it stores.
     samples_launch = B * N_SAMP
     desc0 = dict(kv.split("=") for kv in mixed_desc[modes[0]].split())
     chunks = int(desc0["chunks"])
-    traffic = (125.39e6 * samples_launch / (128 * N_SAMP)
-               + 5.24e6 * (chunks * no * na) / (29 * 64 * 256)) if desc0.get("pp") == "1" else None
+    traffic = (125.16e6 * samples_launch / (128 * N_SAMP)
+               + 6.10e6 * (chunks * no * na) / (38 * 64 * 256)) if desc0.get("pp") == "1" else None
     roofline = {"bound": "alu", "pipe": "sfu + issue slots",
                 "kernel": "k_mixed_pp" if desc0.get("pp") == "1" else "k_mixed",
                 "achieved": terms_all / t_meas / 1e12, "peak": terms_all / t_ideal / 1e12, "unit": "Tterm/s",

@@ -82,13 +82,14 @@ ShapeKey key_of(int dev, int64_t ns, int64_t np, int64_t no, int64_t na, int mod
 }
 
 // Defaults before any autotuning: the fastest shapes on the 10 GeV positron ensemble (512 hw x
-// 64 x 64 directions, 32 particles per launch). Spin-1/2 (8 accumulators per energy) runs best with
-// 4 warps per block, 3 blocks per SM; the other models with 8 warps, 2 blocks per SM.
+// 64 x 64 directions, 32 particles per launch). The mixed kernel runs 8 warps per block, 2 blocks
+// per SM; spin-1/2 keeps every sin/cos on the SFU, classical and spin-0 (two fewer sums per term)
+// take 1/8 of them on the FMA pipe.
 Choice default_choice(int precision, int mode) {
   if (precision == RAD_FP64) return Choice{2, 8, 64, 1, 0};
   if (precision == RAD_FP64_DF) return Choice{2, 4, 64, 1, 0};
-  if (mode == RAD_SPIN_HALF) return Choice{2, 4, 256, 1, 1};
-  return Choice{2, 8, 256, 1, 1};
+  if (mode == RAD_SPIN_HALF) return Choice{2, 8, 256, 1, 1, 0};
+  return Choice{2, 8, 256, 1, 1, 6};
 }
 
 bool supported(int precision, const Choice &c) {

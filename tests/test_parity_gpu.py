@@ -136,11 +136,12 @@ def test_mixed_prepass_every_shape(ragged_batch, shape, mode):
 
 
 @pytest.mark.parametrize("shape", [(2, 8, 256, 1), (2, 4, 256, 1), (4, 8, 128, 2)])
-@pytest.mark.parametrize("split", [4, 6])
+@pytest.mark.parametrize("split", [0, 4, 6])
 @pytest.mark.parametrize("mode", [rad.RAD_CLASSICAL, rad.RAD_SPIN_HALF])
 def test_mixed_sincos_split(ragged_batch, shape, split, mode):
-    """Part of the terms' sin/cos on the FMA pipe (Cody-Waite reduction, Taylor polynomials):
-    the same tolerance as the SFU path, on uneven lengths, ragged grids and every quadrant."""
+    """Part of the terms' sin/cos on the FMA pipe (Cody-Waite reduction, Taylor polynomials), or
+    none (split 0; the classical default takes 1/8): the same tolerance as the SFU path, on uneven
+    lengths, ragged grids and every quadrant."""
     tr, grid = ragged_batch
     ref = oracle_cube(tr, grid, mode)
     got = gpu_cube(tr, grid, mode, rad.RAD_MIXED, shape=shape, prepass=True, split=split)["cube"]
