@@ -160,7 +160,7 @@ struct DfLayout {
 };
 
 template <int MODE, int R, int NW, int T>
-__global__ void __launch_bounds__(NW * 32, NW == 4 ? 4 : 1) k_df(const Params P) {
+__global__ void __launch_bounds__(NW * 32, NW == 4 ? (MODE == RAD_SPIN_HALF ? 4 : 3) : 1) k_df(const Params P) {
   using L = DfLayout<MODE, R, NW, T>;
   constexpr int NC = DfNcomp<MODE>::value;
   constexpr int NA = NC - 2;  // summed components
@@ -176,7 +176,8 @@ __global__ void __launch_bounds__(NW * 32, NW == 4 ? 4 : 1) k_df(const Params P)
   if (s_item[1] != 0) return;
 
   // (cos, sin)(2 pi j / 2048) as float pairs (c_hi, c_lo, s_hi, s_lo) from every other entry of the
-  // FP64 table (2048 entries, 32 KB: four blocks of 4 warps fit on an SM)
+  // FP64 table (2048 entries, 32 KB: four blocks of 4 warps fit on an SM; spin-1/2 is held to 128
+  // registers for that, classical takes 4 blocks at its natural 120)
   for (int i = tid; i < kDfTabN; i += NW * 32) {
     const double2 t = P.table[2 * i];
     const float ch = __double2float_rn(t.x), sh = __double2float_rn(t.y);

@@ -2,10 +2,11 @@
 //
 // Network: x (n_in, FP32) -> [Linear -> GELU] x depth (width) -> Linear -> y (n_out, FP32).
 // The first layer (the input features, n_in <= 64) runs in FP32 so inputs are not quantized;
-// every other layer is a BF16 x BF16 -> FP32 tensor-core GEMM (mma.sync m16n8k16) with the
-// bias, GELU (exact erf form) and their derivatives fused into the GEMM epilogues. FP32 master
-// weights are updated by AdamW (Loshchilov & Hutter, "Decoupled weight decay
-// regularization", ICLR 2019) and copied to BF16 for the GEMMs. Loss: mean squared error.
+// every other layer is a BF16 x BF16 -> FP32 GEMM on the fifth-generation tensor cores
+// (tcgen05.mma, accumulator in tensor memory) with the bias, GELU (exact erf form) and their
+// derivatives fused into the GEMM epilogues. FP32 master weights are updated by AdamW
+// (Loshchilov & Hutter, "Decoupled weight decay regularization", ICLR 2019) and copied to BF16
+// for the GEMMs. Loss: mean squared error.
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -25,103 +26,199 @@ __device__ __forceinline__ float gelu_grad(float z) {
   return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * __expf(-0.5f * z * z);
 }
 
-__device__ __forceinline__ uint32_t ld_u32(const bf16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
-
-__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                         uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-// C[M x N] = sum_k A(m, k) B(k, n), BF16 inputs, FP32 accumulation, epilogue epi(m, n, value).
+// ---- tcgen05 (fifth-generation tensor core) GEMM ----
+// C[M x N] = sum_k A(m, k) B(k, n), BF16 operands, FP32 accumulation in tensor memory, epilogue
+// epi(m, n, value):
 //   A(m, k) = A_KM ? A[m * lda + k] : A[k * lda + m]
 //   B(k, n) = B_KN ? B[n * ldb + k] : B[k * ldb + n]
-// Block tile 64 x 64 x 32, 4 warps (2 x 2), warp tile 32 x 32 (2 x 4 mma tiles). Block z covers
-// the K range [z k_chunk, min(K, (z + 1) k_chunk)) (split K; k_chunk a multiple of 32).
+// Block tile 128 x 128, K in steps of 64, 128 threads. The threads stage both operand tiles in
+// shared memory in the K-major layout without swizzle that the MMA reads through its matrix
+// descriptors: core matrices of 8 rows x 16 bytes (8 K), the two core matrices of a 16-K slice
+// 128 bytes apart, successive 8-row groups 256 bytes apart, one 4 KB slab per 16 K. One thread
+// issues four tcgen05.mma (M = 128, N = 128, K = 16) per K step and commits them to the stage's
+// mbarrier; with two stages the staging of one K step overlaps the MMAs of the previous one. The
+// 128 x 128 FP32 accumulator occupies 128 tensor-memory columns; each warp reads its 32 lanes
+// (rows) back with tcgen05.ld for the epilogue. Block z covers the K range
+// [z k_chunk, min(K, (z + 1) k_chunk)) (split K; k_chunk a multiple of 64). Every mbarrier wait is
+// bounded: when one runs out the block records RAD_ETIMEOUT, waits (bounded) for the MMAs it
+// issued, frees its tensor memory and skips the epilogue.
+constexpr int kTcM = 128, kTcN = 128, kTcK = 64;
+constexpr int kTcSlab = 4096;               // one 16-K slice of a 128-row operand tile
+constexpr int kTcOperand = 4 * kTcSlab;     // 128 rows x 64 K
+constexpr int kTcStage = 2 * kTcOperand;    // A and B tiles
+constexpr int kTcSmem = 2 * kTcStage + 32;  // two stages, two mbarriers, the tensor-memory address
+constexpr uint32_t kTcCols = 128;           // tensor-memory columns: the FP32 accumulator
+
+// byte offset of (row r, k) in an operand tile
+__device__ __forceinline__ uint32_t tc_off(int r, int k) {
+  return static_cast<uint32_t>((k >> 4) * kTcSlab + (r >> 3) * 256 + ((k >> 3) & 1) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// shared-memory matrix descriptor: start address, leading-dimension byte offset (between the two
+// K core matrices, 128 B) and stride byte offset (between 8-row groups, 256 B), each in 16-byte
+// units; descriptor version 1 (bits 46-47); no swizzle (layout type 0 in bits 61-63)
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+  return static_cast<uint64_t>((saddr >> 4) & 0x3FFFu) | (static_cast<uint64_t>(128 >> 4) << 16) |
+         (static_cast<uint64_t>(256 >> 4) << 32) | (1ull << 46);
+}
+
+// instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16 A and B (bits 7-9,
+// 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 in bits 17-22, M >> 4 in bits 24-28
+constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(kTcN >> 3) << 17) |
+                              (static_cast<uint32_t>(kTcM >> 4) << 24);
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t da, uint64_t db, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+      "l"(da), "l"(db), "r"(kTcIdesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// 16 consecutive FP32 columns of this warp's 32 lanes: lane l gets row (lane base + l)
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// One operand tile: rows [r0, r0 + 128) (below `rows`) x K [k0, k0 + 64) (below k_end), zero
+// outside, as 1024 chunks of 8 K-consecutive elements, 8 per thread. K-major sources are read 16
+// bytes at a time (8 rows x 4 chunks per warp: 64 contiguous bytes of each row); row-major-in-K
+// sources (rows contiguous) one element at a time, 32 consecutive rows per warp.
+template <bool KM>
+__device__ __forceinline__ void tc_stage(unsigned char *dst, const bf16 *__restrict__ P, int ld, int r0, int rows,
+                                         int k0, int k_end, bool vec, int tid) {
+  const unsigned short *Q = reinterpret_cast<const unsigned short *>(P);
+#pragma unroll 2
+  for (int c = tid; c < 1024; c += 128) {
+    int r, g;
+    if (KM) {
+      r = ((c >> 6) << 3) | (c & 7);
+      g = (c >> 3) & 7;
+    } else {
+      r = c & 127;
+      g = c >> 7;
+    }
+    const int row = r0 + r, k = k0 + 8 * g;
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (row < rows && k < k_end) {
+      if (KM && vec && k + 8 <= k_end) {
+        v = *reinterpret_cast<const uint4 *>(Q + static_cast<int64_t>(row) * ld + k);
+      } else {
+        uint32_t e[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int kk = k + j;
+          e[j] = kk < k_end ? (KM ? Q[static_cast<int64_t>(row) * ld + kk] : Q[static_cast<int64_t>(kk) * ld + row])
+                            : 0u;
+        }
+        v = make_uint4(e[0] | (e[1] << 16), e[2] | (e[3] << 16), e[4] | (e[5] << 16), e[6] | (e[7] << 16));
+      }
+    }
+    *reinterpret_cast<uint4 *>(dst + tc_off(r, 8 * g)) = v;
+  }
+}
+
 template <bool A_KM, bool B_KN, class Epi>
-__global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const bf16 *__restrict__ A, int lda,
-                                              const bf16 *__restrict__ B, int ldb, Epi epi, int k_chunk) {
-  __shared__ __align__(16) bf16 As[64][40];
-  __shared__ __align__(16) bf16 Bs[64][40];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
-  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-  float acc[2][4][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) acc[i][j][c] = 0.f;
-  const bf16 zero = __float2bfloat16(0.f);
+__global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, const bf16 *__restrict__ A, int lda,
+                                                 const bf16 *__restrict__ B, int ldb, Epi epi, int k_chunk,
+                                                 int *status) {
+  extern __shared__ __align__(128) unsigned char tc_sm[];
+  uint64_t *bar = reinterpret_cast<uint64_t *>(tc_sm + 2 * kTcStage);
+  uint32_t *s_tmem = reinterpret_cast<uint32_t *>(tc_sm + 2 * kTcStage + 16);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.y * kTcM, n0 = blockIdx.x * kTcN;
   const int k_begin = blockIdx.z * k_chunk;
   const int k_end = min(K, k_begin + k_chunk);
-  for (int k0 = k_begin; k0 < k_end; k0 += 32) {
-    for (int e = tid; e < 64 * 32; e += 128) {
-      int mm, kk;
-      if (A_KM) {
-        mm = e >> 5;
-        kk = e & 31;
-      } else {
-        kk = e >> 6;
-        mm = e & 63;
-      }
-      const int m = m0 + mm, k = k0 + kk;
-      As[mm][kk] = (m < M && k < k_end) ? (A_KM ? A[static_cast<int64_t>(m) * lda + k]
-                                            : A[static_cast<int64_t>(k) * lda + m])
-                                    : zero;
-      int nn, kb;
-      if (B_KN) {
-        nn = e >> 5;
-        kb = e & 31;
-      } else {
-        kb = e >> 6;
-        nn = e & 63;
-      }
-      const int n = n0 + nn, k2 = k0 + kb;
-      Bs[nn][kb] = (n < N && k2 < k_end) ? (B_KN ? B[static_cast<int64_t>(n) * ldb + k2]
-                                             : B[static_cast<int64_t>(k2) * ldb + n])
-                                     : zero;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int ks = 0; ks < 32; ks += 16) {
-      const int c = ks + (lane & 3) * 2;
-      uint32_t a[2][4], b[4][2];
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const int r = wm + i * 16 + (lane >> 2);
-        a[i][0] = ld_u32(&As[r][c]);
-        a[i][1] = ld_u32(&As[r + 8][c]);
-        a[i][2] = ld_u32(&As[r][c + 8]);
-        a[i][3] = ld_u32(&As[r + 8][c + 8]);
-      }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int nn = wn + j * 8 + (lane >> 2);
-        b[j][0] = ld_u32(&Bs[nn][c]);
-        b[j][1] = ld_u32(&Bs[nn][c + 8]);
-      }
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], a[i][0], a[i][1], a[i][2], a[i][3], b[j][0], b[j][1]);
-    }
-    __syncthreads();
+  const int nkt = k_end > k_begin ? (k_end - k_begin + kTcK - 1) / kTcK : 0;
+  if (warp == 0) {  // the whole warp allocates; the address lands in shared memory
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_tmem)),
+                 "r"(kTcCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *s_tmem;
+  const bool a_vec = A_KM && (reinterpret_cast<uintptr_t>(A) & 15) == 0 && (lda & 7) == 0;
+  const bool b_vec = B_KN && (reinterpret_cast<uintptr_t>(B) & 15) == 0 && (ldb & 7) == 0;
+  bool failed = false;
+  int issued = 0;  // K steps whose MMAs were issued and committed
+  for (int kt = 0; kt < nkt; ++kt) {
+    const int st = kt & 1;
+    unsigned char *sa = tc_sm + st * kTcStage;
+    unsigned char *sb = sa + kTcOperand;
+    // the MMAs of K step kt - 2 read this stage: their commit is phase (kt - 2) / 2 of its barrier
+    const bool ok = kt < 2 || mbar_wait_bounded(&bar[st], static_cast<uint32_t>((kt - 2) >> 1) & 1u);
+    const int k0 = k_begin + kt * kTcK;
+    if (ok) {
+      tc_stage<A_KM>(sa, A, lda, m0, M, k0, k_end, a_vec, tid);
+      tc_stage<B_KN>(sb, B, ldb, n0, N, k0, k_end, b_vec, tid);
+    }
+    fence_proxy_async();  // the staged tiles become visible to the tensor core's (async) proxy
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t a0 = smem_u32(sa), b0 = smem_u32(sb);
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
+      for (int ks = 0; ks < 4; ++ks)
+        tc_mma(tmem, tc_desc(a0 + ks * kTcSlab), tc_desc(b0 + ks * kTcSlab), (kt | ks) != 0 ? 1u : 0u);
+      tc_commit(&bar[st]);
+    }
+    issued = kt + 1;
+  }
+  // the last commit completes after every MMA issued before it
+  bool done = true;
+  if (issued > 0) done = mbar_wait_bounded(&bar[(issued - 1) & 1], static_cast<uint32_t>((issued - 1) >> 1) & 1u);
+  if (__syncthreads_or(!done)) failed = true;
+  if (failed) {
+    if (tid == 0) set_status(status, RAD_ETIMEOUT);
+  } else {
+    tc_fence_after();
+    const int row = m0 + warp * 32 + lane;
+#pragma unroll 1
+    for (int c0 = 0; c0 < kTcN; c0 += 16) {
+      uint32_t v[16];
+      if (nkt > 0) {
+        tc_ld16(tmem + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(c0), v);
+      } else {
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int m = m0 + wm + i * 16 + (lane >> 2) + ((c & 2) ? 8 : 0);
-        const int n = n0 + wn + j * 8 + (lane & 3) * 2 + (c & 1);
-        if (m < M && n < N) epi(m, n, acc[i][j][c]);
+        for (int j = 0; j < 16; ++j) v[j] = 0u;
       }
+      if (row < M) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (n0 + c0 + j < N) epi(row, n0 + c0 + j, __uint_as_float(v[j]));
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols) : "memory");
 }
 
 // ---- epilogues ----
@@ -179,29 +276,46 @@ __global__ void k_splitk_reduce(int M, int N, int S, const float *__restrict__ w
   }
 }
 
-// Split-K workspace: a grid of fewer than kSplitTarget blocks is split in K until about that
-// many blocks run; then S x M x N <= 2 kSplitTarget x 64 x 64 floats.
+// Split-K workspace: a grid of fewer than kSplitTarget blocks is split in K (at least two K steps
+// of 64 per split) until about that many blocks run; then S x M x N <= 2 kSplitTarget x 128 x 128
+// floats.
 constexpr int kSplitTarget = 2 * 152;
-constexpr int64_t kSplitWsFloats = 2ll * kSplitTarget * 64 * 64;
+constexpr int64_t kSplitWsFloats = 2ll * kSplitTarget * kTcM * kTcN;
+
+template <bool A_KM, bool B_KN, class Epi>
+cudaError_t launch_gemm_tc(dim3 grid, int M, int N, int K, const bf16 *A, int lda, const bf16 *B, int ldb, Epi epi,
+                           int k_chunk, int *status, cudaStream_t st) {
+  static bool attr = false;  // per instantiation: the dynamic shared memory above 48 KB
+  if (!attr) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(k_gemm_tc<A_KM, B_KN, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_gemm_tc<A_KM, B_KN, Epi><<<grid, 128, kTcSmem, st>>>(M, N, K, A, lda, B, ldb, epi, k_chunk, status);
+  return cudaGetLastError();
+}
 
 template <bool A_KM, bool B_KN, class Epi>
 cudaError_t gemm(int M, int N, int K, const bf16 *A, int lda, const bf16 *B, int ldb, Epi epi, float *ws,
                  cudaStream_t st) {
   if (M <= 0 || N <= 0) return cudaSuccess;
-  const int gx = (N + 63) / 64, gy = (M + 63) / 64;
+  cudaError_t e;
+  int *status = device_status_word(&e);
+  if (!status) return e;
+  const int gx = (N + kTcN - 1) / kTcN, gy = (M + kTcM - 1) / kTcM;
   const int blocks = gx * gy;
-  const int kt = (K + 31) / 32;
+  const int kt = (K + kTcK - 1) / kTcK;
   int S = 1;
-  if (ws && blocks < kSplitTarget && kt > 1) S = std::min(kt, (kSplitTarget + blocks - 1) / blocks);
-  const int k_chunk = ((kt + S - 1) / S) * 32;
-  S = (K + k_chunk - 1) / k_chunk;
-  if (S <= 1) {
-    k_gemm<A_KM, B_KN, Epi><<<dim3(gx, gy, 1), 128, 0, st>>>(M, N, K, A, lda, B, ldb, epi, kt * 32);
-    return cudaGetLastError();
-  }
-  EpiPartial part{ws, static_cast<int64_t>(M) * N, N};
-  k_gemm<A_KM, B_KN, EpiPartial><<<dim3(gx, gy, S), 128, 0, st>>>(M, N, K, A, lda, B, ldb, part, k_chunk);
+  if (ws && blocks < kSplitTarget && kt > 2) S = std::min((kt + 1) / 2, (kSplitTarget + blocks - 1) / blocks);
   const int64_t mn = static_cast<int64_t>(M) * N;
+  while (S > 1 && S * mn > kSplitWsFloats) --S;
+  const int k_chunk = ((kt + S - 1) / S) * kTcK;
+  S = (K + k_chunk - 1) / k_chunk;
+  if (S <= 1) return launch_gemm_tc<A_KM, B_KN, Epi>(dim3(gx, gy, 1), M, N, K, A, lda, B, ldb, epi, kt * kTcK, status, st);
+  EpiPartial part{ws, mn, N};
+  e = launch_gemm_tc<A_KM, B_KN, EpiPartial>(dim3(gx, gy, S), M, N, K, A, lda, B, ldb, part, k_chunk, status, st);
+  if (e != cudaSuccess) return e;
   k_splitk_reduce<Epi><<<static_cast<unsigned>(std::min<int64_t>((mn + 255) / 256, 4096)), 256, 0, st>>>(
       M, N, S, ws, epi);
   return cudaGetLastError();
