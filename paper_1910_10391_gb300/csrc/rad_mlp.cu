@@ -28,17 +28,20 @@ __device__ __forceinline__ float gelu_grad(float z) {
 
 // ---- tcgen05 (fifth-generation tensor core) GEMM ----
 // C[M x N] = sum_k A(m, k) B(k, n), BF16 operands, FP32 accumulation in tensor memory, epilogue
-// epi(m, n, value):
+// epi(m, n, value, epi.aux(m, n)):
 //   A(m, k) = A_KM ? A[m * lda + k] : A[k * lda + m]
 //   B(k, n) = B_KN ? B[n * ldb + k] : B[k * ldb + n]
 // Block tile 128 x 128, K in steps of 64, 128 threads. The threads stage both operand tiles in
-// shared memory in the K-major layout without swizzle that the MMA reads through its matrix
-// descriptors: core matrices of 8 rows x 16 bytes (8 K), the two core matrices of a 16-K slice
-// 128 bytes apart, successive 8-row groups 256 bytes apart, one 4 KB slab per 16 K. One thread
+// shared memory in the layouts without swizzle that the MMA reads through its matrix descriptors:
+// core matrices of 8 x 8 elements in 128 bytes (K-major: 8 rows of 8 K; MN-major: 8 K of 8 rows,
+// whichever way the source is contiguous), the two K groups of a 16-K slice 128 bytes apart,
+// successive 8-row groups 256 bytes apart, one 4 KB slab per 16 K. One thread
 // issues four tcgen05.mma (M = 128, N = 128, K = 16) per K step and commits them to the stage's
 // mbarrier; with two stages the staging of one K step overlaps the MMAs of the previous one. The
 // 128 x 128 FP32 accumulator occupies 128 tensor-memory columns; each warp reads its 32 lanes
-// (rows) back with tcgen05.ld for the epilogue. Block z covers the K range
+// (rows) back with tcgen05.ld into shared memory (the stages are free by then), and the block
+// passes the tile to the epilogue row by row, consecutive threads on consecutive columns, so the
+// epilogue's global stores are coalesced. Block z covers the K range
 // [z k_chunk, min(K, (z + 1) k_chunk)) (split K; k_chunk a multiple of 64). Every mbarrier wait is
 // bounded: when one runs out the block records RAD_ETIMEOUT, waits (bounded) for the MMAs it
 // issued, frees its tensor memory and skips the epilogue.
@@ -46,7 +49,9 @@ constexpr int kTcM = 128, kTcN = 128, kTcK = 64;
 constexpr int kTcSlab = 4096;               // one 16-K slice of a 128-row operand tile
 constexpr int kTcOperand = 4 * kTcSlab;     // 128 rows x 64 K
 constexpr int kTcStage = 2 * kTcOperand;    // A and B tiles
-constexpr int kTcSmem = 2 * kTcStage + 32;  // two stages, two mbarriers, the tensor-memory address
+constexpr int kTcTile = kTcM * (kTcN + 1) * 4;  // the accumulator tile for the epilogue, rows padded
+constexpr int kTcData = 2 * kTcStage > kTcTile ? 2 * kTcStage : kTcTile;
+constexpr int kTcSmem = kTcData + 32;       // stages / tile, two mbarriers, the tensor-memory address
 constexpr uint32_t kTcCols = 128;           // tensor-memory columns: the FP32 accumulator
 
 // byte offset of (row r, k) in an operand tile
@@ -55,27 +60,32 @@ __device__ __forceinline__ uint32_t tc_off(int r, int k) {
 }
 
 // shared-memory matrix descriptor: start address, leading-dimension byte offset (between the two
-// K core matrices, 128 B) and stride byte offset (between 8-row groups, 256 B), each in 16-byte
-// units; descriptor version 1 (bits 46-47); no swizzle (layout type 0 in bits 61-63)
+// K groups of 8, 128 B) and stride byte offset (between groups of 8 rows, 256 B), each in 16-byte
+// units; descriptor version 1 (bits 46-47); no swizzle (layout type 0 in bits 61-63). The same
+// offsets serve the K-major and the MN-major tiles.
 __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
   return static_cast<uint64_t>((saddr >> 4) & 0x3FFFu) | (static_cast<uint64_t>(128 >> 4) << 16) |
          (static_cast<uint64_t>(256 >> 4) << 32) | (1ull << 46);
 }
 
 // instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16 A and B (bits 7-9,
-// 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 in bits 17-22, M >> 4 in bits 24-28
-constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(kTcN >> 3) << 17) |
-                              (static_cast<uint32_t>(kTcM >> 4) << 24);
+// 10-12 = 1), A and B K-major (bit 15, 16 = 0) or MN-major (1), N >> 3 in bits 17-22, M >> 4 in
+// bits 24-28
+template <bool A_KM, bool B_KN>
+__host__ __device__ constexpr uint32_t tc_idesc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((A_KM ? 0u : 1u) << 15) | ((B_KN ? 0u : 1u) << 16) |
+         (static_cast<uint32_t>(kTcN >> 3) << 17) | (static_cast<uint32_t>(kTcM >> 4) << 24);
+}
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t da, uint64_t db, uint32_t accumulate) {
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-      "l"(da), "l"(db), "r"(kTcIdesc), "r"(accumulate)
+      "l"(da), "l"(db), "r"(idesc), "r"(accumulate)
       : "memory");
 }
 
@@ -96,40 +106,72 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&v)[16]) {
 }
 
 // One operand tile: rows [r0, r0 + 128) (below `rows`) x K [k0, k0 + 64) (below k_end), zero
-// outside, as 1024 chunks of 8 K-consecutive elements, 8 per thread. K-major sources are read 16
-// bytes at a time (8 rows x 4 chunks per warp: 64 contiguous bytes of each row); row-major-in-K
-// sources (rows contiguous) one element at a time, 32 consecutive rows per warp.
+// outside, as 1024 chunks of 8 consecutive elements of the source, 8 per thread. tc_load reads a
+// thread's 8 chunks into registers (all loads in flight together), tc_store writes them to the
+// tile. A K-major source (KM: K contiguous) is staged K-major: a chunk is 8 K of one row, and a
+// warp reads 8 rows x 4 chunks (64 contiguous bytes of each row). A source with the rows
+// contiguous is staged MN-major (the descriptor's major bit set): a chunk is 8 rows of one K, a
+// core matrix holds 8 K x 8 rows, each K's 8 rows in 16 bytes, and a warp reads 8 K x 4 chunks
+// (64 contiguous bytes of each K). Either way a quarter warp stores 128 contiguous bytes.
 template <bool KM>
-__device__ __forceinline__ void tc_stage(unsigned char *dst, const bf16 *__restrict__ P, int ld, int r0, int rows,
-                                         int k0, int k_end, bool vec, int tid) {
+__device__ __forceinline__ void tc_chunk(int c, int &r, int &k) {
+  if (KM) {  // r: the row, k: the first of 8 K
+    r = ((c >> 6) << 3) | (c & 7);
+    k = ((c >> 3) & 7) << 3;
+  } else {   // r: the first of 8 rows, k: the K
+    k = ((c >> 7) << 3) | (c & 7);
+    r = ((c >> 3) & 15) << 3;
+  }
+}
+
+// byte offset of a chunk in an MN-major tile: (8 rows from r, K k)
+__device__ __forceinline__ uint32_t tc_off_mn(int r, int k) {
+  return static_cast<uint32_t>((k >> 4) * kTcSlab + ((k >> 3) & 1) * 128 + (r >> 3) * 256 + (k & 7) * 16);
+}
+
+template <bool KM>
+__device__ __forceinline__ void tc_load(uint4 (&v)[8], const bf16 *__restrict__ P, int ld, int r0, int rows, int k0,
+                                        int k_end, bool vec, int tid) {
   const unsigned short *Q = reinterpret_cast<const unsigned short *>(P);
-#pragma unroll 2
-  for (int c = tid; c < 1024; c += 128) {
-    int r, g;
-    if (KM) {
-      r = ((c >> 6) << 3) | (c & 7);
-      g = (c >> 3) & 7;
-    } else {
-      r = c & 127;
-      g = c >> 7;
-    }
-    const int row = r0 + r, k = k0 + 8 * g;
-    uint4 v = make_uint4(0u, 0u, 0u, 0u);
-    if (row < rows && k < k_end) {
-      if (KM && vec && k + 8 <= k_end) {
-        v = *reinterpret_cast<const uint4 *>(Q + static_cast<int64_t>(row) * ld + k);
-      } else {
-        uint32_t e[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int kk = k + j;
-          e[j] = kk < k_end ? (KM ? Q[static_cast<int64_t>(row) * ld + kk] : Q[static_cast<int64_t>(kk) * ld + row])
-                            : 0u;
+  for (int i = 0; i < 8; ++i) {
+    int r, kc;
+    tc_chunk<KM>(tid + 128 * i, r, kc);
+    const int row = r0 + r, k = k0 + kc;
+    v[i] = make_uint4(0u, 0u, 0u, 0u);
+    if (KM) {
+      if (row < rows && k < k_end) {
+        if (vec && k + 8 <= k_end) {
+          v[i] = __ldg(reinterpret_cast<const uint4 *>(Q + static_cast<int64_t>(row) * ld + k));
+        } else {
+          uint32_t e[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) e[j] = k + j < k_end ? Q[static_cast<int64_t>(row) * ld + k + j] : 0u;
+          v[i] = make_uint4(e[0] | (e[1] << 16), e[2] | (e[3] << 16), e[4] | (e[5] << 16), e[6] | (e[7] << 16));
         }
-        v = make_uint4(e[0] | (e[1] << 16), e[2] | (e[3] << 16), e[4] | (e[5] << 16), e[6] | (e[7] << 16));
+      }
+    } else {
+      if (k < k_end && row < rows) {
+        if (vec && row + 8 <= rows) {
+          v[i] = __ldg(reinterpret_cast<const uint4 *>(Q + static_cast<int64_t>(k) * ld + row));
+        } else {
+          uint32_t e[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) e[j] = row + j < rows ? Q[static_cast<int64_t>(k) * ld + row + j] : 0u;
+          v[i] = make_uint4(e[0] | (e[1] << 16), e[2] | (e[3] << 16), e[4] | (e[5] << 16), e[6] | (e[7] << 16));
+        }
       }
     }
-    *reinterpret_cast<uint4 *>(dst + tc_off(r, 8 * g)) = v;
+  }
+}
+
+template <bool KM>
+__device__ __forceinline__ void tc_store(unsigned char *dst, const uint4 (&v)[8], int tid) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    int r, k;
+    tc_chunk<KM>(tid + 128 * i, r, k);
+    *reinterpret_cast<uint4 *>(dst + (KM ? tc_off(r, k) : tc_off_mn(r, k))) = v[i];
   }
 }
 
@@ -138,8 +180,8 @@ __global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, const bf16
                                                  const bf16 *__restrict__ B, int ldb, Epi epi, int k_chunk,
                                                  int *status) {
   extern __shared__ __align__(128) unsigned char tc_sm[];
-  uint64_t *bar = reinterpret_cast<uint64_t *>(tc_sm + 2 * kTcStage);
-  uint32_t *s_tmem = reinterpret_cast<uint32_t *>(tc_sm + 2 * kTcStage + 16);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(tc_sm + kTcData);
+  uint32_t *s_tmem = reinterpret_cast<uint32_t *>(tc_sm + kTcData + 16);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.y * kTcM, n0 = blockIdx.x * kTcN;
   const int k_begin = blockIdx.z * k_chunk;
@@ -160,20 +202,26 @@ __global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, const bf16
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *s_tmem;
-  const bool a_vec = A_KM && (reinterpret_cast<uintptr_t>(A) & 15) == 0 && (lda & 7) == 0;
-  const bool b_vec = B_KN && (reinterpret_cast<uintptr_t>(B) & 15) == 0 && (ldb & 7) == 0;
+  const bool a_vec = (reinterpret_cast<uintptr_t>(A) & 15) == 0 && (lda & 7) == 0;
+  const bool b_vec = (reinterpret_cast<uintptr_t>(B) & 15) == 0 && (ldb & 7) == 0;
   bool failed = false;
   int issued = 0;  // K steps whose MMAs were issued and committed
+  // K step kt's operands are read into registers during step kt - 1 (while its MMAs run) and
+  // stored once the MMAs of step kt - 2 have released the stage
+  uint4 ra[8], rb[8];
+  if (nkt > 0) {
+    tc_load<A_KM>(ra, A, lda, m0, M, k_begin, k_end, a_vec, tid);
+    tc_load<B_KN>(rb, B, ldb, n0, N, k_begin, k_end, b_vec, tid);
+  }
   for (int kt = 0; kt < nkt; ++kt) {
     const int st = kt & 1;
     unsigned char *sa = tc_sm + st * kTcStage;
     unsigned char *sb = sa + kTcOperand;
     // the MMAs of K step kt - 2 read this stage: their commit is phase (kt - 2) / 2 of its barrier
     const bool ok = kt < 2 || mbar_wait_bounded(&bar[st], static_cast<uint32_t>((kt - 2) >> 1) & 1u);
-    const int k0 = k_begin + kt * kTcK;
     if (ok) {
-      tc_stage<A_KM>(sa, A, lda, m0, M, k0, k_end, a_vec, tid);
-      tc_stage<B_KN>(sb, B, ldb, n0, N, k0, k_end, b_vec, tid);
+      tc_store<A_KM>(sa, ra, tid);
+      tc_store<B_KN>(sb, rb, tid);
     }
     fence_proxy_async();  // the staged tiles become visible to the tensor core's (async) proxy
     if (__syncthreads_or(!ok)) {
@@ -185,10 +233,16 @@ __global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, const bf16
       const uint32_t a0 = smem_u32(sa), b0 = smem_u32(sb);
 #pragma unroll
       for (int ks = 0; ks < 4; ++ks)
-        tc_mma(tmem, tc_desc(a0 + ks * kTcSlab), tc_desc(b0 + ks * kTcSlab), (kt | ks) != 0 ? 1u : 0u);
+        tc_mma(tmem, tc_desc(a0 + ks * kTcSlab), tc_desc(b0 + ks * kTcSlab), tc_idesc<A_KM, B_KN>(),
+               (kt | ks) != 0 ? 1u : 0u);
       tc_commit(&bar[st]);
     }
     issued = kt + 1;
+    if (kt + 1 < nkt) {
+      const int k1 = k_begin + (kt + 1) * kTcK;
+      tc_load<A_KM>(ra, A, lda, m0, M, k1, k_end, a_vec, tid);
+      tc_load<B_KN>(rb, B, ldb, n0, N, k1, k_end, b_vec, tid);
+    }
   }
   // the last commit completes after every MMA issued before it
   bool done = true;
@@ -198,7 +252,8 @@ __global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, const bf16
     if (tid == 0) set_status(status, RAD_ETIMEOUT);
   } else {
     tc_fence_after();
-    const int row = m0 + warp * 32 + lane;
+    float *tile = reinterpret_cast<float *>(tc_sm);  // [128][129]: row r at r * 129 (bank r + column)
+    const int r = warp * 32 + lane;
 #pragma unroll 1
     for (int c0 = 0; c0 < kTcN; c0 += 16) {
       uint32_t v[16];
@@ -208,10 +263,22 @@ __global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, const bf16
 #pragma unroll
         for (int j = 0; j < 16; ++j) v[j] = 0u;
       }
-      if (row < M) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j)
-          if (n0 + c0 + j < N) epi(row, n0 + c0 + j, __uint_as_float(v[j]));
+      for (int j = 0; j < 16; ++j) tile[r * (kTcN + 1) + c0 + j] = __uint_as_float(v[j]);
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int e0 = tid; e0 < kTcM * kTcN; e0 += 128 * 16) {
+      float a[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int e = e0 + 128 * u, rr = e >> 7, cc = e & (kTcN - 1);
+        a[u] = (m0 + rr < M && n0 + cc < N) ? epi.aux(m0 + rr, n0 + cc) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int e = e0 + 128 * u, rr = e >> 7, cc = e & (kTcN - 1);
+        if (m0 + rr < M && n0 + cc < N) epi(m0 + rr, n0 + cc, tile[rr * (kTcN + 1) + cc], a[u]);
       }
     }
   }
@@ -222,13 +289,16 @@ __global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, const bf16
 }
 
 // ---- epilogues ----
+// epi.aux(m, n) loads what the epilogue of element (m, n) reads besides the accumulator (a
+// block loads a batch of them before it stores any), epi(m, n, v, aux) stores.
 struct EpiHidden {  // Z = acc + b; H = bf16(gelu(Z)); Z kept for the backward pass (may be null)
   const float *bias;
   float *Z;
   bf16 *H;
   int ld;
-  __device__ void operator()(int m, int n, float v) const {
-    const float z = v + bias[n];
+  __device__ float aux(int, int n) const { return __ldg(bias + n); }
+  __device__ void operator()(int m, int n, float v, float b) const {
+    const float z = v + b;
     const int64_t e = static_cast<int64_t>(m) * ld + n;
     if (Z) Z[e] = z;
     H[e] = __float2bfloat16(gelu(z));
@@ -238,28 +308,31 @@ struct EpiOut {  // Y = acc + b (FP32)
   const float *bias;
   float *Y;
   int ld;
-  __device__ void operator()(int m, int n, float v) const { Y[static_cast<int64_t>(m) * ld + n] = v + bias[n]; }
+  __device__ float aux(int, int n) const { return __ldg(bias + n); }
+  __device__ void operator()(int m, int n, float v, float b) const { Y[static_cast<int64_t>(m) * ld + n] = v + b; }
 };
 struct EpiGradAct {  // dZ = bf16(acc * gelu'(Z))
   const float *Z;
   bf16 *dZ;
   int ld;
-  __device__ void operator()(int m, int n, float v) const {
-    const int64_t e = static_cast<int64_t>(m) * ld + n;
-    dZ[e] = __float2bfloat16(v * gelu_grad(Z[e]));
+  __device__ float aux(int m, int n) const { return __ldg(Z + static_cast<int64_t>(m) * ld + n); }
+  __device__ void operator()(int m, int n, float v, float z) const {
+    dZ[static_cast<int64_t>(m) * ld + n] = __float2bfloat16(v * gelu_grad(z));
   }
 };
 struct EpiStore {  // plain FP32 store
   float *C;
   int ld;
-  __device__ void operator()(int m, int n, float v) const { C[static_cast<int64_t>(m) * ld + n] = v; }
+  __device__ float aux(int, int) const { return 0.f; }
+  __device__ void operator()(int m, int n, float v, float) const { C[static_cast<int64_t>(m) * ld + n] = v; }
 };
 
 struct EpiPartial {  // split K: FP32 partial sums of K range z at ws[z][m][n]
   float *ws;
   int64_t mn;
   int ld;
-  __device__ void operator()(int m, int n, float v) const {
+  __device__ float aux(int, int) const { return 0.f; }
+  __device__ void operator()(int m, int n, float v, float) const {
     ws[blockIdx.z * mn + static_cast<int64_t>(m) * ld + n] = v;
   }
 };
@@ -272,13 +345,14 @@ __global__ void k_splitk_reduce(int M, int N, int S, const float *__restrict__ w
        e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     float v = 0.f;
     for (int z = 0; z < S; ++z) v += ws[z * mn + e];
-    epi(static_cast<int>(e / N), static_cast<int>(e % N), v);
+    const int m = static_cast<int>(e / N), n = static_cast<int>(e % N);
+    epi(m, n, v, epi.aux(m, n));
   }
 }
 
-// Split-K workspace: a grid of fewer than kSplitTarget blocks is split in K (at least two K steps
-// of 64 per split) until about that many blocks run; then S x M x N <= 2 kSplitTarget x 128 x 128
-// floats.
+// Split-K workspace: a grid of fewer than kSplitTarget blocks with K of 512 or more is split in K
+// (at least four K steps of 64 per split) until about that many blocks run; then
+// S x M x N <= 2 kSplitTarget x 128 x 128 floats.
 constexpr int kSplitTarget = 2 * 152;
 constexpr int64_t kSplitWsFloats = 2ll * kSplitTarget * kTcM * kTcN;
 
@@ -307,7 +381,7 @@ cudaError_t gemm(int M, int N, int K, const bf16 *A, int lda, const bf16 *B, int
   const int blocks = gx * gy;
   const int kt = (K + kTcK - 1) / kTcK;
   int S = 1;
-  if (ws && blocks < kSplitTarget && kt > 2) S = std::min((kt + 1) / 2, (kSplitTarget + blocks - 1) / blocks);
+  if (ws && blocks < kSplitTarget && kt >= 8) S = std::min(kt / 4, (kSplitTarget + blocks - 1) / blocks);
   const int64_t mn = static_cast<int64_t>(M) * N;
   while (S > 1 && S * mn > kSplitWsFloats) --S;
   const int k_chunk = ((kt + S - 1) / S) * kTcK;
@@ -334,24 +408,46 @@ __global__ void k_layer1(int64_t B, int n_in, int width, const float *__restrict
   H[e] = __float2bfloat16(gelu(z));
 }
 
-// First-layer weight gradient in FP32: dW1[n][k] = sum_b dZ1[b][n] x[b][k] (one thread per (n, k)).
-__global__ void k_layer1_grad(int64_t B, int n_in, int width, const float *__restrict__ x,
-                              const bf16 *__restrict__ dZ, float *dW) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= width * n_in) return;
-  const int n = e / n_in, k = e % n_in;
-  float s = 0.f;
-  for (int64_t b = 0; b < B; ++b) s = fmaf(__bfloat162float(dZ[b * width + n]), x[b * n_in + k], s);
-  dW[e] = s;
+// First-layer weight gradient in FP32: dW1[n][k] = sum_b dZ1[b][n] x[b][k]. One block per hidden
+// unit n: warp w takes every 16th row from row w, lane l the inputs k = l and l + 32 (n_in <= 64);
+// the 16 warps' partial sums are added in a fixed order.
+__global__ void __launch_bounds__(512) k_layer1_grad(int64_t B, int n_in, int width, const float *__restrict__ x,
+                                                     const bf16 *__restrict__ dZ, float *dW) {
+  __shared__ float red[16][64];
+  const int n = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  float s0 = 0.f, s1 = 0.f;
+  for (int64_t b = w; b < B; b += 16) {
+    const float d = __bfloat162float(dZ[b * width + n]);
+    if (lane < n_in) s0 = fmaf(d, x[b * n_in + lane], s0);
+    if (lane + 32 < n_in) s1 = fmaf(d, x[b * n_in + lane + 32], s1);
+  }
+  red[w][lane] = s0;
+  red[w][lane + 32] = s1;
+  __syncthreads();
+  if (threadIdx.x < n_in) {
+    float s = 0.f;
+    for (int i = 0; i < 16; ++i) s += red[i][threadIdx.x];
+    dW[static_cast<int64_t>(n) * n_in + threadIdx.x] = s;
+  }
 }
 
-// Column sums (bias gradients): db[n] = sum_b dZ[b][n].
-__global__ void k_colsum(int64_t rows, int cols, const bf16 *__restrict__ dZ, float *db) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= cols) return;
+// Column sums (bias gradients): db[n] = sum_b dZ[b][n]. A block of 32 x 32 threads covers 32
+// columns: thread (x, y) sums every 32nd row from row y of column x, then the 32 partial sums of a
+// column are added in a fixed tree order.
+__global__ void __launch_bounds__(1024) k_colsum(int64_t rows, int cols, const bf16 *__restrict__ dZ, float *db) {
+  __shared__ float red[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int n = blockIdx.x * 32 + tx;
   float s = 0.f;
-  for (int64_t b = 0; b < rows; ++b) s += __bfloat162float(dZ[b * cols + n]);
-  db[n] = s;
+  if (n < cols)
+    for (int64_t b = ty; b < rows; b += 32) s += __bfloat162float(dZ[b * cols + n]);
+  red[ty][tx] = s;
+  __syncthreads();
+  for (int k = 16; k > 0; k >>= 1) {
+    if (ty < k) red[ty][tx] += red[ty + k][tx];
+    __syncthreads();
+  }
+  if (ty == 0 && n < cols) db[n] = red[0][tx];
 }
 
 // Loss and output gradient: loss terms m (Y - T)^2 and dY = bf16(2 m (Y - T) / (B O)) with the
@@ -375,12 +471,18 @@ __global__ void k_loss(int64_t n, float scale, const float *__restrict__ Y, cons
   if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
 }
 
-__global__ void k_loss_final(int nblocks, float scale, const float *partial, float *loss) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    float s = 0.f;
-    for (int i = 0; i < nblocks; ++i) s += partial[i];
-    *loss = s * scale;
+// the loss: the per-block partials added by 256 threads, then a fixed tree
+__global__ void __launch_bounds__(256) k_loss_final(int nblocks, float scale, const float *partial, float *loss) {
+  __shared__ float red[256];
+  float s = 0.f;
+  for (int i = threadIdx.x; i < nblocks; i += 256) s += partial[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = 128; k > 0; k >>= 1) {
+    if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+    __syncthreads();
   }
+  if (threadIdx.x == 0) *loss = red[0] * scale;
 }
 
 __global__ void k_adamw(int64_t n, float lr, float b1, float b2, float eps, float wd, float bc1, float bc2,
@@ -538,14 +640,14 @@ cudaError_t backward_impl(rad_mlp h, const float *x, const float *target, const 
   int nb = static_cast<int>(std::min<int64_t>(1024, (n + 255) / 256));
   const float scale = 1.f / static_cast<float>(n);
   k_loss<<<nb, 256, 0, st>>>(n, scale, h->Y, target, mask, h->dY, h->partial);
-  if (loss) k_loss_final<<<1, 32, 0, st>>>(nb, scale, h->partial, loss);
+  if (loss) k_loss_final<<<1, 256, 0, st>>>(nb, scale, h->partial, loss);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // output layer: dW_out = dY^T H_last, db_out = colsum(dY), dH = dY W_out
   const bf16 *Hlast = h->H + static_cast<int64_t>(D - 1) * h->max_batch * W;
   EpiStore gW{h->g + h->w_off[D], W};
   e = gemm<false, false>(O, W, static_cast<int>(B), h->dY, O, Hlast, W, gW, h->splitk, st);
   if (e != cudaSuccess) return e;
-  k_colsum<<<nblk(O), 256, 0, st>>>(B, O, h->dY, h->g + h->b_off[D]);
+  k_colsum<<<nblk(O, 32), 1024, 0, st>>>(B, O, h->dY, h->g + h->b_off[D]);
   int cur = 0;
   {
     EpiGradAct ga{h->Z + static_cast<int64_t>(D - 1) * h->max_batch * W, h->dZ, W};
@@ -558,7 +660,7 @@ cudaError_t backward_impl(rad_mlp h, const float *x, const float *target, const 
     EpiStore gw{h->g + h->w_off[l], W};
     e = gemm<false, false>(W, W, static_cast<int>(B), dZl, W, Hin, W, gw, h->splitk, st);
     if (e != cudaSuccess) return e;
-    k_colsum<<<nblk(W), 256, 0, st>>>(B, W, dZl, h->g + h->b_off[l]);
+    k_colsum<<<nblk(W, 32), 1024, 0, st>>>(B, W, dZl, h->g + h->b_off[l]);
     bf16 *dZn = h->dZ + static_cast<int64_t>(cur ^ 1) * h->max_batch * W;
     EpiGradAct ga{h->Z + static_cast<int64_t>(l - 1) * h->max_batch * W, dZn, W};
     e = gemm<true, false>(static_cast<int>(B), W, W, dZl, W, h->wb + h->w_off[l], W, ga, h->splitk, st);
@@ -566,8 +668,8 @@ cudaError_t backward_impl(rad_mlp h, const float *x, const float *target, const 
     cur ^= 1;
   }
   const bf16 *dZ1 = h->dZ + static_cast<int64_t>(cur) * h->max_batch * W;
-  k_layer1_grad<<<nblk(static_cast<int64_t>(W) * h->n_in), 256, 0, st>>>(B, h->n_in, W, x, dZ1, h->g + h->w_off[0]);
-  k_colsum<<<nblk(W), 256, 0, st>>>(B, W, dZ1, h->g + h->b_off[0]);
+  k_layer1_grad<<<static_cast<unsigned>(W), 512, 0, st>>>(B, h->n_in, W, x, dZ1, h->g + h->w_off[0]);
+  k_colsum<<<nblk(W, 32), 1024, 0, st>>>(B, W, dZ1, h->g + h->b_off[0]);
   return cudaGetLastError();
 }
 
