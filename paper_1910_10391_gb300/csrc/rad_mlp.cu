@@ -350,8 +350,8 @@ __global__ void k_splitk_reduce(int M, int N, int S, const float *__restrict__ w
   }
 }
 
-// Split-K workspace: a grid of fewer than kSplitTarget blocks with K of 512 or more is split in K
-// (at least four K steps of 64 per split) until about that many blocks run; then
+// Split-K workspace: a grid of fewer than kSplitTarget blocks with K of 256 or more is split in K
+// (at least two K steps of 64 per split) until about that many blocks run; then
 // S x M x N <= 2 kSplitTarget x 128 x 128 floats.
 constexpr int kSplitTarget = 2 * 152;
 constexpr int64_t kSplitWsFloats = 2ll * kSplitTarget * kTcM * kTcN;
@@ -381,7 +381,7 @@ cudaError_t gemm(int M, int N, int K, const bf16 *A, int lda, const bf16 *B, int
   const int blocks = gx * gy;
   const int kt = (K + kTcK - 1) / kTcK;
   int S = 1;
-  if (ws && blocks < kSplitTarget && kt >= 8) S = std::min(kt / 4, (kSplitTarget + blocks - 1) / blocks);
+  if (ws && blocks < kSplitTarget && kt >= 4) S = std::min(kt / 2, (kSplitTarget + blocks - 1) / blocks);
   const int64_t mn = static_cast<int64_t>(M) * N;
   while (S > 1 && S * mn > kSplitWsFloats) --S;
   const int k_chunk = ((kt + S - 1) / S) * kTcK;
