@@ -549,6 +549,154 @@ __global__ void k_axial_group(const Chan C, const Axial A, int64_t n_particles, 
   }
 }
 
+// Small ensembles in the Doyle-Turner planar potential: one particle per group of kGroup lanes, as
+// k_axial_group. The force's 2 nt walks (each term's planes above and below the particle, see
+// planar_force) are spread over the lanes, and so are the electron density's (plane, term) pairs.
+__device__ __forceinline__ double planar_force_group(const Chan &C, const Planar &P, double x, int gl,
+                                                     unsigned mask) {
+  const double d = C.d_p;
+  const double xi = x - floor(x * C.inv_d) * d;
+  const bool low = xi < 0.5 * d;
+  const double r = low ? xi : xi - d;
+  double F = 0.0;
+  for (int c = gl; c < 2 * P.nt; c += kGroup) {
+    const int i = c >> 1;
+    const bool up = (c & 1) == 0;  // planes at r - m d (up) or r + m d (down), m = 1 .. n
+    const int n = up ? (low ? P.K : P.K - 1) : (low ? P.K - 1 : P.K);
+    const double k = P.ck[i], q = P.q[i];
+    const double E0 = exp(-(r * r) * k);
+    double s = up ? r * E0 : 0.0;  // the nearest plane counted once, by the upward walk
+    double E = E0, rm = r;
+    double rho = up ? exp(k * (2.0 * r * d - d * d)) : exp(-k * (2.0 * r * d + d * d));
+    const double step = up ? -d : d;
+    for (int m = 0; m < n; ++m) {
+      E *= rho;
+      rho *= q;
+      rm += step;
+      s += rm * E;
+    }
+    F += P.fk[i] * s;
+  }
+  return group_sum(F, mask);
+}
+
+__device__ __forceinline__ double electron_density_group(const Chan &C, const Planar &P, double x, double n_nuc,
+                                                         int gl, unsigned mask) {
+  const double xi = x - floor(x * C.inv_d) * C.d_p;
+  double n = 0.0;
+  for (int q = gl; q < 2 * P.K * P.nt; q += kGroup) {
+    const int jj = q / P.nt, i = q - jj * P.nt;
+    const double r = xi - (jj + 1 - P.K) * C.d_p, r2 = r * r;
+    n += P.ek[i] * exp(-r2 * P.eck[i]);
+  }
+  return P.ecx * n_nuc + group_sum(n, mask);
+}
+
+__device__ __forceinline__ State deriv_planar_group(const Chan &C, const Planar &P, double g0, double q0,
+                                                    double beta0, const State &s, int gl, unsigned mask) {
+  const double g = s.E / C.mass;
+  const double vp2 = s.vx * s.vx + s.vy * s.vy;
+  double vz;
+  const double dvz = dvz_of(g, g0, q0, beta0, vp2, vz);
+  const double F = planar_force_group(C, P, s.x, gl, mask);
+  State d;
+  d.x = s.vx;
+  d.y = s.vy;
+  d.vx = F / s.E;
+  d.vy = 0.0;
+  d.dz = dvz;
+  d.E = C.ll ? C.ll_k * (g * g) * (F * F) : 0.0;
+  return d;
+}
+
+__global__ void k_channel_group(const Chan C, const Planar P, int64_t n_particles, const int64_t *__restrict__ offsets,
+                                int64_t n_total, const double *__restrict__ energy, const double *__restrict__ x0,
+                                const double *__restrict__ thx0, const double *__restrict__ thy0,
+                                const int64_t *__restrict__ ids, double dt, uint64_t seed, double *__restrict__ out,
+                                double *__restrict__ e_out, int *dev_status) {
+  const int gl = threadIdx.x & (kGroup - 1);
+  const unsigned mask = 0xFFFFu << (threadIdx.x & 16);
+  const int64_t groups = static_cast<int64_t>(gridDim.x) * (blockDim.x / kGroup);
+  for (int64_t p = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) / kGroup; p < n_particles;
+       p += groups) {
+    const int64_t off = offsets[p], L = offsets[p + 1] - off;
+    const double E0 = energy[p];
+    if (off < 0 || L < 1 || off + L > n_total || !(E0 > C.mass) || !isfinite(E0) || !isfinite(x0[p]) ||
+        !isfinite(thx0[p]) || (thy0 && !isfinite(thy0[p]))) {
+      if (gl == 0) atomicCAS(dev_status, 0, RAD_EDATA);
+      continue;
+    }
+    const uint64_t pid = ids ? static_cast<uint64_t>(ids[p]) : static_cast<uint64_t>(p);
+    const double g0 = E0 / C.mass;
+    const double beta0 = 1.0 - 1.0 / (2.0 * g0 * g0);
+    const double q0 = 1.0 / (4.0 * (g0 * g0) * (g0 * g0));
+    State s{x0[p], 0.0, thx0[p], thy0 ? thy0[p] : 0.0, 0.0, E0};
+    double kx = 0.0, ky = 0.0;
+    double *rec = out + off * kRec;
+    for (int64_t k = 0; k < L; ++k, rec += kRec) {
+      const double g = s.E / C.mass;
+      const double vp2 = s.vx * s.vx + s.vy * s.vy;
+      double vz;
+      const double dvz = dvz_of(g, g0, q0, beta0, vp2, vz);
+      const double F = planar_force_group(C, P, s.x, gl, mask);
+      const double ax = F / s.E + kx, ay = ky;
+      const double gdot = C.ll ? C.ll_k * (g * g) * (F * F) / C.mass : 0.0;
+      // every lane holds the record; lane f writes field f
+      double v = 0.0;
+      switch (gl) {
+        case F_T: v = static_cast<double>(k) * dt; break;
+        case F_X: v = s.x; break;
+        case F_Y: v = s.y; break;
+        case F_DZ: v = s.dz; break;
+        case F_VX: v = s.vx; break;
+        case F_VY: v = s.vy; break;
+        case F_DVZ: v = dvz; break;
+        case F_AX: v = ax; break;
+        case F_AY: v = ay; break;
+        case F_AZ: v = (gdot / (g * g * g) - (s.vx * ax + s.vy * ay)) / vz; break;
+        default: break;
+      }
+      if (gl < kRec) rec[gl] = v;
+      if (e_out && gl == 0) e_out[off + k] = s.E;
+      kx = ky = 0.0;
+      if (k == L - 1) break;
+      const State k1 = deriv_planar_group(C, P, g0, q0, beta0, s, gl, mask);
+      const State k2 = deriv_planar_group(C, P, g0, q0, beta0, axpy(s, 0.5 * dt, k1), gl, mask);
+      const State k3 = deriv_planar_group(C, P, g0, q0, beta0, axpy(s, 0.5 * dt, k2), gl, mask);
+      const State k4 = deriv_planar_group(C, P, g0, q0, beta0, axpy(s, dt, k3), gl, mask);
+      const double h6 = dt / 6.0;
+      s.x += h6 * (k1.x + 2.0 * k2.x + 2.0 * k3.x + k4.x);
+      s.y += h6 * (k1.y + 2.0 * k2.y + 2.0 * k3.y + k4.y);
+      s.vx += h6 * (k1.vx + 2.0 * k2.vx + 2.0 * k3.vx + k4.vx);
+      s.vy += h6 * (k1.vy + 2.0 * k2.vy + 2.0 * k3.vy + k4.vy);
+      s.dz += h6 * (k1.dz + 2.0 * k2.dz + 2.0 * k3.dz + k4.dz);
+      s.E += h6 * (k1.E + 2.0 * k2.E + 2.0 * k3.E + k4.E);
+      if (C.ms) {
+        const double E = s.E;
+        const double n_nuc = plane_density(C, s.x);
+        double var = C.var_k / (E * E) * n_nuc;
+        if (P.el) {
+          const double ge = E / C.mass, b2 = 1.0 - 1.0 / (ge * ge);
+          const double br = fmax(log(P.lk * (ge * ge) * b2) - b2, 0.0);
+          var += electron_density_group(C, P, s.x, n_nuc, gl, mask) * (br / ((ge * ge) * (b2 * b2)));
+        }
+        double z0, z1;
+        kick_normals(seed, pid, static_cast<uint64_t>(k), z0, z1);
+        const double sd = sqrt(var);
+        const double dthx = sd * z0, dthy = sd * z1;
+        kx = dthx / dt;
+        ky = dthy / dt;
+        s.vx += dthx;
+        s.vy += dthy;
+        if (C.ms_loss) {
+          const double gk = E / C.mass;
+          s.E = E - C.loss_k * (gk * gk * gk) * (dthx * dthx + dthy * dthy);
+        }
+      }
+    }
+  }
+}
+
 __global__ void k_axial(const Chan C, const Axial A, int64_t n_particles, const int64_t *__restrict__ offsets,
                         int64_t n_total, const double *__restrict__ energy, const double *__restrict__ x0,
                         const double *__restrict__ y0, const double *__restrict__ thx0,
@@ -1274,6 +1422,11 @@ int launch_trajectories(const rad_channel *ch, const rad_planar_potential *pot, 
       k_channel_mixed<false><<<static_cast<unsigned>(grid), block, 0, st>>>(
           M, P32, n_particles, offsets, n_samples_total, energy_eV, x0, thx0, thy0, particle_ids, seed, out,
           energy_out, ds);
+  } else if (pot && n_particles < kGroupBelow) {  // lane groups share each particle's force evaluation
+    const int64_t ggrid = (n_particles * kGroup + 127) / 128;
+    k_channel_group<<<static_cast<unsigned>(ggrid), 128, 0, st>>>(C, P, n_particles, offsets, n_samples_total,
+                                                                 energy_eV, x0, thx0, thy0, particle_ids, dt, seed,
+                                                                 out, energy_out, ds);
   } else if (pot) {
     k_channel<true><<<static_cast<unsigned>(grid), block, 0, st>>>(C, P, n_particles, offsets, n_samples_total,
                                                                    energy_eV, x0, thx0, thy0, particle_ids, dt,

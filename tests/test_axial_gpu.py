@@ -157,7 +157,7 @@ def test_axial_argument_checks():
 
 
 def test_axial_one_lane_path_for_large_ensembles():
-    """From 32768 particles on, each particle has one lane (below, a group of 16 lanes shares its
+    """From 9216 particles on, each particle has one lane (below, a group of 16 lanes shares its
     force evaluation): 32768 positrons over 12 steps with scattering, every record against the
     oracle."""
     lib, orc = potentials(K=1)

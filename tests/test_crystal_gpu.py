@@ -123,6 +123,22 @@ def test_fp64_long_positron_records():
     np.testing.assert_allclose(eg.reshape(n, L), er, rtol=1e-12)
 
 
+@pytest.mark.parametrize("charge", [+1, -1])
+def test_fp64_one_lane_path_for_large_ensembles(charge):
+    """From 9216 particles on each particle has one lane (below, a group of 16 lanes shares its
+    force and electron-density sums, which every other test here runs): 9216 particles over 12
+    steps with every physics flag, all records against the oracle."""
+    n, L, dt, E, seed = 9216, 12, 5e-9, 20e9, 31
+    lib, orc = potentials()
+    x0, th = entries(n, E, 6)
+    got, eg, _ = run_gpu(channel(charge, ALL), lib, x0, th, E, np.full(n, L), dt, seed)
+    ref, er = oracle(orc, x0, th, E, L, dt, seed, charge, ALL)
+    worst = field_errors(got.reshape(n, L, 10), ref)
+    print("crystal fp64 one lane:", charge, worst)
+    assert max(worst.values()) <= 1e-9, worst
+    np.testing.assert_allclose(eg.reshape(n, L), er, rtol=1e-12)
+
+
 def test_fp64_ragged_lengths_and_stream_ids():
     lens = np.array([1, 2, 3, 700, 1, 1234, 2, 999])
     n = len(lens)
