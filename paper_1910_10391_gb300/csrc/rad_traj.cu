@@ -549,9 +549,22 @@ __global__ void k_axial_group(const Chan C, const Axial A, int64_t n_particles, 
   }
 }
 
-// Small ensembles in the Doyle-Turner planar potential: one particle per group of kGroup lanes, as
+// Small ensembles in the Doyle-Turner planar potential: one particle per group of kPGroup lanes, as
 // k_axial_group. The force's 2 nt walks (each term's planes above and below the particle, see
-// planar_force) are spread over the lanes, and so are the electron density's (plane, term) pairs.
+// planar_force) are spread over the lanes (one each for the usual 4 terms), and so are the
+// electron density's (plane, term) pairs; the group's first lane draws the scattering kick and
+// broadcasts it.
+constexpr int kPGroup = 8;
+static_assert(kRec == 10 && F_AX == 7 && F_AY == 8 && F_AZ == 9 && kPGroup == 8,
+              "k_channel_group writes record field f from lane f, fields 8 and 9 from lanes 0 and 1");
+// below this many particles the planar lane-group kernel runs
+constexpr int64_t kPGroupBelow = 4096;
+
+__device__ __forceinline__ double pgroup_sum(double v, unsigned mask) {
+#pragma unroll
+  for (int o = kPGroup / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, kPGroup);
+  return __shfl_sync(mask, v, 0, kPGroup);
+}
 __device__ __forceinline__ double planar_force_group(const Chan &C, const Planar &P, double x, int gl,
                                                      unsigned mask) {
   const double d = C.d_p;
@@ -559,7 +572,7 @@ __device__ __forceinline__ double planar_force_group(const Chan &C, const Planar
   const bool low = xi < 0.5 * d;
   const double r = low ? xi : xi - d;
   double F = 0.0;
-  for (int c = gl; c < 2 * P.nt; c += kGroup) {
+  for (int c = gl; c < 2 * P.nt; c += kPGroup) {
     const int i = c >> 1;
     const bool up = (c & 1) == 0;  // planes at r - m d (up) or r + m d (down), m = 1 .. n
     const int n = up ? (low ? P.K : P.K - 1) : (low ? P.K - 1 : P.K);
@@ -577,19 +590,20 @@ __device__ __forceinline__ double planar_force_group(const Chan &C, const Planar
     }
     F += P.fk[i] * s;
   }
-  return group_sum(F, mask);
+  return pgroup_sum(F, mask);
 }
 
-__device__ __forceinline__ double electron_density_group(const Chan &C, const Planar &P, double x, double n_nuc,
-                                                         int gl, unsigned mask) {
+// the X-ray Gaussians' part of electron_density_scaled (without the c^X n(x)/N term)
+__device__ __forceinline__ double electron_density_group(const Chan &C, const Planar &P, double x, int gl,
+                                                         unsigned mask) {
   const double xi = x - floor(x * C.inv_d) * C.d_p;
   double n = 0.0;
-  for (int q = gl; q < 2 * P.K * P.nt; q += kGroup) {
+  for (int q = gl; q < 2 * P.K * P.nt; q += kPGroup) {
     const int jj = q / P.nt, i = q - jj * P.nt;
     const double r = xi - (jj + 1 - P.K) * C.d_p, r2 = r * r;
     n += P.ek[i] * exp(-r2 * P.eck[i]);
   }
-  return P.ecx * n_nuc + group_sum(n, mask);
+  return pgroup_sum(n, mask);
 }
 
 __device__ __forceinline__ State deriv_planar_group(const Chan &C, const Planar &P, double g0, double q0,
@@ -614,10 +628,10 @@ __global__ void k_channel_group(const Chan C, const Planar P, int64_t n_particle
                                 const double *__restrict__ thx0, const double *__restrict__ thy0,
                                 const int64_t *__restrict__ ids, double dt, uint64_t seed, double *__restrict__ out,
                                 double *__restrict__ e_out, int *dev_status) {
-  const int gl = threadIdx.x & (kGroup - 1);
-  const unsigned mask = 0xFFFFu << (threadIdx.x & 16);
-  const int64_t groups = static_cast<int64_t>(gridDim.x) * (blockDim.x / kGroup);
-  for (int64_t p = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) / kGroup; p < n_particles;
+  const int gl = threadIdx.x & (kPGroup - 1);
+  const unsigned mask = 0xFFu << (threadIdx.x & 24);
+  const int64_t groups = static_cast<int64_t>(gridDim.x) * (blockDim.x / kPGroup);
+  for (int64_t p = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) / kPGroup; p < n_particles;
        p += groups) {
     const int64_t off = offsets[p], L = offsets[p + 1] - off;
     const double E0 = energy[p];
@@ -641,7 +655,8 @@ __global__ void k_channel_group(const Chan C, const Planar P, int64_t n_particle
       const double F = planar_force_group(C, P, s.x, gl, mask);
       const double ax = F / s.E + kx, ay = ky;
       const double gdot = C.ll ? C.ll_k * (g * g) * (F * F) / C.mass : 0.0;
-      // every lane holds the record; lane f writes field f
+      // every lane holds the record; lane f writes field f, lanes 0 and 1 also fields 8 and 9
+      const double az = (gdot / (g * g * g) - (s.vx * ax + s.vy * ay)) / vz;
       double v = 0.0;
       switch (gl) {
         case F_T: v = static_cast<double>(k) * dt; break;
@@ -651,12 +666,10 @@ __global__ void k_channel_group(const Chan C, const Planar P, int64_t n_particle
         case F_VX: v = s.vx; break;
         case F_VY: v = s.vy; break;
         case F_DVZ: v = dvz; break;
-        case F_AX: v = ax; break;
-        case F_AY: v = ay; break;
-        case F_AZ: v = (gdot / (g * g * g) - (s.vx * ax + s.vy * ay)) / vz; break;
-        default: break;
+        default: v = ax; break;  // F_AX = 7, the last lane of the group
       }
-      if (gl < kRec) rec[gl] = v;
+      rec[gl] = v;
+      if (gl < kRec - kPGroup) rec[gl + kPGroup] = gl == 0 ? ay : az;  // F_AY = 8, F_AZ = 9
       if (e_out && gl == 0) e_out[off + k] = s.E;
       kx = ky = 0.0;
       if (k == L - 1) break;
@@ -673,17 +686,24 @@ __global__ void k_channel_group(const Chan C, const Planar P, int64_t n_particle
       s.E += h6 * (k1.E + 2.0 * k2.E + 2.0 * k3.E + k4.E);
       if (C.ms) {
         const double E = s.E;
-        const double n_nuc = plane_density(C, s.x);
-        double var = C.var_k / (E * E) * n_nuc;
-        if (P.el) {
-          const double ge = E / C.mass, b2 = 1.0 - 1.0 / (ge * ge);
-          const double br = fmax(log(P.lk * (ge * ge) * b2) - b2, 0.0);
-          var += electron_density_group(C, P, s.x, n_nuc, gl, mask) * (br / ((ge * ge) * (b2 * b2)));
+        const double ne = P.el ? electron_density_group(C, P, s.x, gl, mask) : 0.0;
+        double dthx = 0.0, dthy = 0.0;
+        if (gl == 0) {  // the kick, drawn once per group
+          const double n_nuc = plane_density(C, s.x);
+          double var = C.var_k / (E * E) * n_nuc;
+          if (P.el) {
+            const double ge = E / C.mass, b2 = 1.0 - 1.0 / (ge * ge);
+            const double br = fmax(log(P.lk * (ge * ge) * b2) - b2, 0.0);
+            var += (P.ecx * n_nuc + ne) * (br / ((ge * ge) * (b2 * b2)));
+          }
+          double z0, z1;
+          kick_normals(seed, pid, static_cast<uint64_t>(k), z0, z1);
+          const double sd = sqrt(var);
+          dthx = sd * z0;
+          dthy = sd * z1;
         }
-        double z0, z1;
-        kick_normals(seed, pid, static_cast<uint64_t>(k), z0, z1);
-        const double sd = sqrt(var);
-        const double dthx = sd * z0, dthy = sd * z1;
+        dthx = __shfl_sync(mask, dthx, 0, kPGroup);
+        dthy = __shfl_sync(mask, dthy, 0, kPGroup);
         kx = dthx / dt;
         ky = dthy / dt;
         s.vx += dthx;
@@ -1422,8 +1442,8 @@ int launch_trajectories(const rad_channel *ch, const rad_planar_potential *pot, 
       k_channel_mixed<false><<<static_cast<unsigned>(grid), block, 0, st>>>(
           M, P32, n_particles, offsets, n_samples_total, energy_eV, x0, thx0, thy0, particle_ids, seed, out,
           energy_out, ds);
-  } else if (pot && n_particles < kGroupBelow) {  // lane groups share each particle's force evaluation
-    const int64_t ggrid = (n_particles * kGroup + 127) / 128;
+  } else if (pot && n_particles < kPGroupBelow) {  // lane groups share each particle's force evaluation
+    const int64_t ggrid = (n_particles * kPGroup + 127) / 128;
     k_channel_group<<<static_cast<unsigned>(ggrid), 128, 0, st>>>(C, P, n_particles, offsets, n_samples_total,
                                                                  energy_eV, x0, thx0, thy0, particle_ids, dt, seed,
                                                                  out, energy_out, ds);

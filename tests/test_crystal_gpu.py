@@ -125,10 +125,10 @@ def test_fp64_long_positron_records():
 
 @pytest.mark.parametrize("charge", [+1, -1])
 def test_fp64_one_lane_path_for_large_ensembles(charge):
-    """From 9216 particles on each particle has one lane (below, a group of 16 lanes shares its
-    force and electron-density sums, which every other test here runs): 9216 particles over 12
+    """From 4096 particles on each particle has one lane (below, a group of 8 lanes shares its
+    force and electron-density sums, which every other test here runs): 4096 particles over 12
     steps with every physics flag, all records against the oracle."""
-    n, L, dt, E, seed = 9216, 12, 5e-9, 20e9, 31
+    n, L, dt, E, seed = 4096, 12, 5e-9, 20e9, 31
     lib, orc = potentials()
     x0, th = entries(n, E, 6)
     got, eg, _ = run_gpu(channel(charge, ALL), lib, x0, th, E, np.full(n, L), dt, seed)
