@@ -10,6 +10,7 @@
 #include <cuda_bf16.h>
 #include <math.h>
 
+#include <atomic>
 #include <cstdio>
 #include <random>
 #include <vector>
@@ -359,12 +360,16 @@ constexpr int64_t kSplitWsFloats = 2ll * kSplitTarget * kTcM * kTcN;
 template <bool A_KM, bool B_KN, class Epi>
 cudaError_t launch_gemm_tc(dim3 grid, int M, int N, int K, const bf16 *A, int lda, const bf16 *B, int ldb, Epi epi,
                            int k_chunk, int *status, cudaStream_t st) {
-  static bool attr = false;  // per instantiation: the dynamic shared memory above 48 KB
-  if (!attr) {
-    const cudaError_t e =
-        cudaFuncSetAttribute(k_gemm_tc<A_KM, B_KN, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+  // the dynamic shared memory above 48 KB, allowed once per instantiation and device
+  static std::atomic<unsigned long long> allowed{0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+  if (!(allowed.load() & bit)) {
+    e = cudaFuncSetAttribute(k_gemm_tc<A_KM, B_KN, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
     if (e != cudaSuccess) return e;
-    attr = true;
+    allowed.fetch_or(bit);
   }
   k_gemm_tc<A_KM, B_KN, Epi><<<grid, 128, kTcSmem, st>>>(M, N, K, A, lda, B, ldb, epi, k_chunk, status);
   return cudaGetLastError();
