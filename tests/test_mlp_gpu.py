@@ -85,6 +85,35 @@ def test_gradients_elementwise_at_the_product_shape():
     m.close()
 
 
+@pytest.mark.parametrize("n_in,width,depth,n_out,B", [(5, 130, 2, 206, 300), (64, 8, 3, 2, 129)])
+def test_gradients_elementwise_at_ragged_shapes(n_in, width, depth, n_out, B):
+    """Shapes that are no multiple of the GEMM's 128 x 128 tile or its 64-wide K step, and leading
+    dimensions that are no multiple of 8 (width 130: the operand tiles are staged element by
+    element instead of 16 bytes at a time), a batch of 300 for the split-K weight gradients, a
+    width of 8 and a two-output layer: every gradient element within the bound of the product
+    shape's test."""
+    import torch
+    rng = np.random.default_rng(9)
+    m = rad.MLP(n_in, width, depth, n_out, max_batch=B, seed=4)
+    x = rng.uniform(-1, 1, (B, n_in)).astype(np.float32)
+    t = rng.normal(0, 1, (B, n_out)).astype(np.float32)
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    m.backward(torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda(), loss)
+    torch.cuda.synchronize()
+    g = m.get(1).astype(np.float64)
+    p = gpu_params_for_reference(m, n_in, width, depth, n_out)
+    _, g_ref = M.loss_and_grad(p, x, t, n_in, width, depth, n_out)
+    mag = M.grad_magnitudes(p, x, t, n_in, width, depth, n_out)
+    ratio = np.abs(g - g_ref) / (2.0 ** -9 * mag + 1e-30)
+    print("ragged shape", (n_in, width, depth, n_out, B), "max ratio", float(ratio.max()))
+    assert ratio.max() <= 2.0
+    y = m.forward(torch.from_numpy(x).cuda()).cpu().numpy()
+    y_ref = M.forward(p, x, n_in, width, depth, n_out)
+    assert np.abs(y - y_ref).max() <= 2e-2 * np.abs(y_ref).max()
+    assert rad.rad_device_status(1) == rad.RAD_OK
+    m.close()
+
+
 def test_adamw_matches_reference():
     """Two AdamW steps (moments, bias correction, decoupled weight decay) against the FP64
     reference fed the GPU's own gradients; eps comparable to the gradients so that the update is
