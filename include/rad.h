@@ -257,11 +257,13 @@ int rad_plan_set_shape(rad_plan plan, int R, int NW, int T, int chunk_mult);
 int rad_plan_set_prepass(rad_plan plan, int enable);
 
 /*
- * rad_plan_set_sincos_split -- pre-pass kernel only: every = 4 or 6 evaluates about 1/every
- * of the terms' sin/cos on the FMA pipe (Cody-Waite reduction to |r| <= pi/4, Taylor
- * polynomials; same error bound as the SFU's on the in-tile phases) instead of the SFU, so
- * that both pipes share the work; 0 uses the SFU for every term. RAD_EINVAL for other values,
- * FP64 plans or the inline-preparation kernel (plan unchanged). The autotuner also tries these.
+ * rad_plan_set_sincos_split -- pre-pass kernel only: every = 4 or 6 evaluates the sin/cos of the
+ * terms whose index is every - 1 mod every in each group of 8 samples x R energies (R = 2: 1/4 or
+ * 1/8 of them) on the FMA pipe (Cody-Waite reduction to |r| <= pi/4, Taylor polynomials; same
+ * error bound as the SFU's on the in-tile phases) instead of the SFU, so that both pipes share
+ * the work; 0 uses the SFU for every term. A new plan starts with 6 for the classical and spin-0
+ * models and 0 for spin-1/2. RAD_EINVAL for other values, FP64 plans or the inline-preparation
+ * kernel (plan unchanged). The autotuner also tries these.
  */
 int rad_plan_set_sincos_split(rad_plan plan, int every);
 
