@@ -816,26 +816,31 @@ struct StepCtl {
   int64_t max_substeps;
 };
 
-template <int KIND>
+// KIND 0 harmonic, 1 planar (Doyle-Turner), 2 axial; G: one particle per lane group (kPGroup lanes
+// for the planar field, kGroup for the axial one; gl the lane within the group, mask the group's
+// lanes), as k_channel_group and k_axial_group
+template <int KIND, bool G>
 __device__ __forceinline__ void field2(const Chan &C, const Planar &P, const Axial &A, double x, double y, double &Fx,
-                                       double &Fy) {
+                                       double &Fy, int gl, unsigned mask) {
   if constexpr (KIND == 2) {
-    axial_force(A, x, y, Fx, Fy);
+    if constexpr (G) axial_force_group(A, x, y, gl, mask, Fx, Fy);
+    else axial_force(A, x, y, Fx, Fy);
   } else {
-    Fx = field<KIND == 1>(C, P, x);
+    if constexpr (G && KIND == 1) Fx = planar_force_group(C, P, x, gl, mask);
+    else Fx = field<KIND == 1>(C, P, x);
     Fy = 0.0;
   }
 }
 
-template <int KIND>
+template <int KIND, bool G>
 __device__ __forceinline__ State deriv2(const Chan &C, const Planar &P, const Axial &A, double g0, double q0,
-                                        double beta0, const State &s) {
+                                        double beta0, const State &s, int gl, unsigned mask) {
   const double g = s.E / C.mass;
   const double vp2 = s.vx * s.vx + s.vy * s.vy;
   double vz;
   const double dvz = dvz_of(g, g0, q0, beta0, vp2, vz);
   double Fx, Fy;
-  field2<KIND>(C, P, A, s.x, s.y, Fx, Fy);
+  field2<KIND, G>(C, P, A, s.x, s.y, Fx, Fy, gl, mask);
   State d;
   d.x = s.vx;
   d.y = s.vy;
@@ -862,9 +867,10 @@ __device__ __forceinline__ double err_term(double e, double y, double y5, double
 }
 
 // one Dormand-Prince step: y5 (the solution) and the error estimate's RMS
-template <int KIND>
+template <int KIND, bool G>
 __device__ __forceinline__ double dp5(const Chan &C, const Planar &P, const Axial &A, double g0, double q0,
-                                      double beta0, const StepCtl &S, const State &y, double h, State &y5) {
+                                      double beta0, const StepCtl &S, const State &y, double h, State &y5, int gl,
+                                      unsigned mask) {
   constexpr double a21 = 1.0 / 5.0;
   constexpr double a31 = 3.0 / 40.0, a32 = 9.0 / 40.0;
   constexpr double a41 = 44.0 / 45.0, a42 = -56.0 / 15.0, a43 = 32.0 / 9.0;
@@ -876,39 +882,39 @@ __device__ __forceinline__ double dp5(const Chan &C, const Planar &P, const Axia
   // embedded (fourth-order) weights
   constexpr double e1 = 5179.0 / 57600.0, e3 = 7571.0 / 16695.0, e4 = 393.0 / 640.0, e5 = -92097.0 / 339200.0,
                    e6 = 187.0 / 2100.0, e7 = 1.0 / 40.0;
-  const State k1 = deriv2<KIND>(C, P, A, g0, q0, beta0, y);
+  const State k1 = deriv2<KIND, G>(C, P, A, g0, q0, beta0, y, gl, mask);
   State t = y;
   acc(t, h * a21, k1);
-  const State k2 = deriv2<KIND>(C, P, A, g0, q0, beta0, t);
+  const State k2 = deriv2<KIND, G>(C, P, A, g0, q0, beta0, t, gl, mask);
   t = y;
   acc(t, h * a31, k1);
   acc(t, h * a32, k2);
-  const State k3 = deriv2<KIND>(C, P, A, g0, q0, beta0, t);
+  const State k3 = deriv2<KIND, G>(C, P, A, g0, q0, beta0, t, gl, mask);
   t = y;
   acc(t, h * a41, k1);
   acc(t, h * a42, k2);
   acc(t, h * a43, k3);
-  const State k4 = deriv2<KIND>(C, P, A, g0, q0, beta0, t);
+  const State k4 = deriv2<KIND, G>(C, P, A, g0, q0, beta0, t, gl, mask);
   t = y;
   acc(t, h * a51, k1);
   acc(t, h * a52, k2);
   acc(t, h * a53, k3);
   acc(t, h * a54, k4);
-  const State k5 = deriv2<KIND>(C, P, A, g0, q0, beta0, t);
+  const State k5 = deriv2<KIND, G>(C, P, A, g0, q0, beta0, t, gl, mask);
   t = y;
   acc(t, h * a61, k1);
   acc(t, h * a62, k2);
   acc(t, h * a63, k3);
   acc(t, h * a64, k4);
   acc(t, h * a65, k5);
-  const State k6 = deriv2<KIND>(C, P, A, g0, q0, beta0, t);
+  const State k6 = deriv2<KIND, G>(C, P, A, g0, q0, beta0, t, gl, mask);
   y5 = y;
   acc(y5, h * b1, k1);
   acc(y5, h * b3, k3);
   acc(y5, h * b4, k4);
   acc(y5, h * b5, k5);
   acc(y5, h * b6, k6);
-  const State k7 = deriv2<KIND>(C, P, A, g0, q0, beta0, y5);
+  const State k7 = deriv2<KIND, G>(C, P, A, g0, q0, beta0, y5, gl, mask);
   State y4 = y;
   acc(y4, h * e1, k1);
   acc(y4, h * e3, k3);
@@ -925,7 +931,7 @@ __device__ __forceinline__ double dp5(const Chan &C, const Planar &P, const Axia
   return sqrt(s2 / 6.0);
 }
 
-template <int KIND>
+template <int KIND, bool G>
 __global__ void k_adaptive(const Chan C, const Planar P, const Axial A, const StepCtl S, int64_t n_particles,
                            const int64_t *__restrict__ offsets, int64_t n_total, const double *__restrict__ energy,
                            const double *__restrict__ x0, const double *__restrict__ y0,
@@ -933,13 +939,16 @@ __global__ void k_adaptive(const Chan C, const Planar P, const Axial A, const St
                            const int64_t *__restrict__ ids, const double *__restrict__ times, double dt, uint64_t seed,
                            double *__restrict__ out, double *__restrict__ e_out, int64_t *__restrict__ counts,
                            int *dev_status) {
-  for (int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; p < n_particles;
-       p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+  constexpr int W = !G ? 1 : (KIND == 2 ? kGroup : kPGroup);  // lanes per particle
+  const int gl = static_cast<int>(threadIdx.x) & (W - 1);
+  const unsigned mask = W == 1 ? 0u : (((1u << W) - 1u) << (threadIdx.x & 31 & ~(W - 1)));
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * (blockDim.x / W);
+  for (int64_t p = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) / W; p < n_particles; p += stride) {
     const int64_t off = offsets[p], L = offsets[p + 1] - off;
     const double E0 = energy[p];
     if (off < 0 || L < 1 || off + L > n_total || !(E0 > C.mass) || !isfinite(E0) || !isfinite(x0[p]) ||
         (y0 && !isfinite(y0[p])) || !isfinite(thx0[p]) || (thy0 && !isfinite(thy0[p]))) {
-      atomicCAS(dev_status, 0, RAD_EDATA);
+      if (gl == 0) atomicCAS(dev_status, 0, RAD_EDATA);
       continue;
     }
     const double *tp = times ? times + off : nullptr;
@@ -948,7 +957,7 @@ __global__ void k_adaptive(const Chan C, const Planar P, const Axial A, const St
     for (int64_t k = 0; k < L && tp; ++k)
       if (!isfinite(tp[k]) || (k > 0 && !(tp[k] > tp[k - 1]))) bad_t = true;
     if (bad_t) {
-      atomicCAS(dev_status, 0, RAD_EDATA);
+      if (gl == 0) atomicCAS(dev_status, 0, RAD_EDATA);
       continue;
     }
     const uint64_t pid = ids ? static_cast<uint64_t>(ids[p]) : static_cast<uint64_t>(p);
@@ -968,33 +977,41 @@ __global__ void k_adaptive(const Chan C, const Planar P, const Axial A, const St
       double vz;
       const double dvz = dvz_of(g, g0, q0, beta0, vp2, vz);
       double Fx, Fy;
-      field2<KIND>(C, P, A, s.x, s.y, Fx, Fy);
+      field2<KIND, G>(C, P, A, s.x, s.y, Fx, Fy, gl, mask);
       const double ax = Fx / s.E + kx, ay = Fy / s.E + ky;
       const double gdot = C.ll ? C.ll_k * (g * g) * (Fx * Fx + Fy * Fy) / C.mass : 0.0;
-      rec[F_T] = t_of(k);
-      rec[F_X] = s.x;
-      rec[F_Y] = s.y;
-      rec[F_DZ] = s.dz;
-      rec[F_VX] = s.vx;
-      rec[F_VY] = s.vy;
-      rec[F_DVZ] = dvz;
-      rec[F_AX] = ax;
-      rec[F_AY] = ay;
-      rec[F_AZ] = (gdot / (g * g * g) - (s.vx * ax + s.vy * ay)) / vz;
-      if (e_out) e_out[off + k] = s.E;
+      const double az = (gdot / (g * g * g) - (s.vx * ax + s.vy * ay)) / vz;
+      // every lane of a group holds the record; lane f writes fields f, f + W, ...
+      for (int f = gl; f < kRec; f += W) {
+        double v;
+        switch (f) {
+          case F_T: v = t_of(k); break;
+          case F_X: v = s.x; break;
+          case F_Y: v = s.y; break;
+          case F_DZ: v = s.dz; break;
+          case F_VX: v = s.vx; break;
+          case F_VY: v = s.vy; break;
+          case F_DVZ: v = dvz; break;
+          case F_AX: v = ax; break;
+          case F_AY: v = ay; break;
+          default: v = az; break;
+        }
+        rec[f] = v;
+      }
+      if (e_out && gl == 0) e_out[off + k] = s.E;
       kx = ky = 0.0;
       if (k == L - 1) break;
       const double H = t_of(k + 1) - t_of(k);
       int64_t pos = 0;
       while (pos < unit) {
         if (n_tries >= S.max_substeps) {  // the particle needs more sub-steps than allowed
-          atomicCAS(dev_status, 0, RAD_EDATA);
+          if (gl == 0) atomicCAS(dev_status, 0, RAD_EDATA);
           stopped = true;
           break;
         }
         const double h = H / static_cast<double>(int64_t(1) << level);
         State y5;
-        const double err = dp5<KIND>(C, P, A, g0, q0, beta0, S, s, h, y5);
+        const double err = dp5<KIND, G>(C, P, A, g0, q0, beta0, S, s, h, y5, gl, mask);
         ++n_tries;
         if (err > 1.0 && level < S.max_level) {
           ++level;
@@ -1010,10 +1027,14 @@ __global__ void k_adaptive(const Chan C, const Planar P, const Axial A, const St
         const double E = s.E;
         double n_nuc, n_el;
         if constexpr (KIND == 2) {
-          axial_densities(A, s.x, s.y, n_nuc, n_el);
+          if constexpr (G) axial_densities_group(A, s.x, s.y, gl, mask, n_nuc, n_el);
+          else axial_densities(A, s.x, s.y, n_nuc, n_el);
         } else {
           n_nuc = plane_density(C, s.x);
-          n_el = (KIND == 1 && P.el) ? electron_density_scaled(C, P, s.x, n_nuc) : 0.0;
+          if constexpr (G && KIND == 1)
+            n_el = P.el ? P.ecx * n_nuc + electron_density_group(C, P, s.x, gl, mask) : 0.0;
+          else
+            n_el = (KIND == 1 && P.el) ? electron_density_scaled(C, P, s.x, n_nuc) : 0.0;
         }
         // variances per unit length (the coefficients are built for a unit step), times H
         double var = C.var_k / (E * E) * n_nuc * H;
@@ -1039,7 +1060,7 @@ __global__ void k_adaptive(const Chan C, const Planar P, const Axial A, const St
         }
       }
     }
-    if (counts) counts[p] = n_steps;
+    if (counts && gl == 0) counts[p] = n_steps;
   }
 }
 
@@ -1619,15 +1640,30 @@ int launch_adaptive(const rad_channel *ch, const rad_planar_potential *pot, cons
   if (grid > 1 << 20) grid = 1 << 20;
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   const unsigned gr = static_cast<unsigned>(grid);
-  if (axial)
-    k_adaptive<2><<<gr, block, 0, st>>>(C, P, A, S, n_particles, offsets, n_samples_total, energy_eV, x0, y0, thx0,
-                                         thy0, particle_ids, times, dt, seed, out, energy_out, substeps_out, ds);
+  // small ensembles: lane groups share each particle's field sums (the thresholds of the RK4
+  // integrators); 128-thread blocks of 8 or 16 groups
+  const unsigned ggr8 = static_cast<unsigned>((n_particles * kPGroup + 127) / 128);
+  const unsigned ggr16 = static_cast<unsigned>((n_particles * kGroup + 127) / 128);
+  if (axial && n_particles < kGroupBelow)
+    k_adaptive<2, true><<<ggr16, 128, 0, st>>>(C, P, A, S, n_particles, offsets, n_samples_total, energy_eV, x0, y0,
+                                               thx0, thy0, particle_ids, times, dt, seed, out, energy_out,
+                                               substeps_out, ds);
+  else if (axial)
+    k_adaptive<2, false><<<gr, block, 0, st>>>(C, P, A, S, n_particles, offsets, n_samples_total, energy_eV, x0, y0,
+                                                thx0, thy0, particle_ids, times, dt, seed, out, energy_out,
+                                                substeps_out, ds);
+  else if (pot && n_particles < kPGroupBelow)
+    k_adaptive<1, true><<<ggr8, 128, 0, st>>>(C, P, A, S, n_particles, offsets, n_samples_total, energy_eV, x0, y0,
+                                              thx0, thy0, particle_ids, times, dt, seed, out, energy_out,
+                                              substeps_out, ds);
   else if (pot)
-    k_adaptive<1><<<gr, block, 0, st>>>(C, P, A, S, n_particles, offsets, n_samples_total, energy_eV, x0, y0, thx0,
-                                         thy0, particle_ids, times, dt, seed, out, energy_out, substeps_out, ds);
+    k_adaptive<1, false><<<gr, block, 0, st>>>(C, P, A, S, n_particles, offsets, n_samples_total, energy_eV, x0, y0,
+                                                thx0, thy0, particle_ids, times, dt, seed, out, energy_out,
+                                                substeps_out, ds);
   else
-    k_adaptive<0><<<gr, block, 0, st>>>(C, P, A, S, n_particles, offsets, n_samples_total, energy_eV, x0, y0, thx0,
-                                         thy0, particle_ids, times, dt, seed, out, energy_out, substeps_out, ds);
+    k_adaptive<0, false><<<gr, block, 0, st>>>(C, P, A, S, n_particles, offsets, n_samples_total, energy_eV, x0, y0,
+                                                thx0, thy0, particle_ids, times, dt, seed, out, energy_out,
+                                                substeps_out, ds);
   e = cudaGetLastError();
   return e == cudaSuccess ? RAD_OK : cuda_status(e);
 }

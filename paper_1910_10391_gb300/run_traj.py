@@ -9,7 +9,9 @@ workloads' beam), Si(110) harmonic well with U0 = 20 eV, or the synthetic four-G
 Doyle-Turner fit of the input module (3 neighbouring planes on each side), or that fit on the
 strings of the Si <110> axis (the crystal library's lattice, 2 cells on each side; entry uniform
 over the transverse cell, both angles ~ N(0, (0.3 psi)^2) with psi = sqrt(2 x 35 eV / E), FP64
-only). Prints one JSON line
+only). With --adaptive RTOL the records come from rad_trajectories_adaptive (Dormand-Prince
+5(4) sub-steps between outputs --output-dt apart, relative tolerance RTOL, at most 2^10 sub-steps
+per output; FP64), and the line adds the mean accepted sub-steps per output. Prints one JSON line
 with the CUDA-event time of the integrator (best of --repeat) and samples/s.
 """
 from __future__ import annotations
@@ -36,6 +38,8 @@ def main(argv=None):
     ap.add_argument("--potential", default="harmonic", choices=["harmonic", "doyle-turner", "axial"])
     ap.add_argument("--repeat", type=int, default=3)
     ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--adaptive", type=float, default=0.0, help="relative tolerance of the adaptive integrator")
+    ap.add_argument("--output-dt", type=float, default=5e-9, help="output interval (m/c)")
     a = ap.parse_args(argv)
     import torch
     n = a.particles
@@ -69,20 +73,29 @@ def main(argv=None):
     elif flags & rad.RAD_TRAJ_MS_EL:
         raise SystemExit("electron scattering needs --potential doyle-turner")
     if a.precision == "fp32":
+        if a.adaptive > 0:
+            raise SystemExit("the adaptive integrator is FP64 only")
         flags |= rad.RAD_TRAJ_FP32
     ch = rad.RadChannel(20.0, I.SI110_DP, I.EPS_S_EV, I.SI_X0, I.RHO_THERMAL, I.ME_EV, a.charge, flags)
     st = torch.cuda.current_stream()
+    steps = torch.zeros(n, dtype=torch.int64, device="cuda") if a.adaptive > 0 else None  # per particle
+    ctl = rad.RadStepControl(a.adaptive, 1e-20, 1e-16, 10, 1 << 40) if a.adaptive > 0 else None
     ms = []
     for r in range(a.repeat + 1):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record(st)
-        if pot is None:
-            rc = rad.rad_channeling_trajectories(ch, doff, E, x0, th, out, 5e-9, a.seed)
+        if ctl is not None:
+            rc = rad.rad_trajectories_adaptive(ch, ctl, doff, E, x0, th, out, a.seed, dt=a.output_dt,
+                                               planar=pot if a.potential == "doyle-turner" else None,
+                                               axial=pot if a.potential == "axial" else None, y0=y0, thy0=thy,
+                                               substeps_out=steps)
+        elif pot is None:
+            rc = rad.rad_channeling_trajectories(ch, doff, E, x0, th, out, a.output_dt, a.seed)
         elif a.potential == "axial":
-            rc = rad.rad_axial_trajectories(ch, pot, doff, E, x0, th, out, 5e-9, a.seed, y0=y0, thy0=thy)
+            rc = rad.rad_axial_trajectories(ch, pot, doff, E, x0, th, out, a.output_dt, a.seed, y0=y0, thy0=thy)
         else:
-            rc = rad.rad_crystal_trajectories(ch, pot, doff, E, x0, th, out, 5e-9, a.seed)
+            rc = rad.rad_crystal_trajectories(ch, pot, doff, E, x0, th, out, a.output_dt, a.seed)
         e1.record(st)
         if rc:
             raise rad.RadError(rc, "trajectory integrator")
@@ -93,7 +106,11 @@ def main(argv=None):
     if status:
         raise rad.RadError(status, "device status")
     best = min(ms)
-    print(json.dumps({"particles": n, "samples_total": int(off[-1]), "max_length": int(lens.max()),
+    extra = {}
+    if steps is not None:
+        extra = {"adaptive_rtol": a.adaptive, "output_dt": a.output_dt,
+                 "substeps_per_output": float(steps.double().sum().item()) / max(int(off[-1]) - n, 1)}
+    print(json.dumps({**extra, "particles": n, "samples_total": int(off[-1]), "max_length": int(lens.max()),
                       "precision": a.precision, "physics": a.physics, "potential": a.potential,
                       "charge": a.charge, "ms": ms,
                       "samples_per_s": int(off[-1]) / best * 1e3,

@@ -105,6 +105,45 @@ def test_axial_potential_geometric_times():
     np.testing.assert_array_equal(cnt, rc)
 
 
+def test_one_lane_paths_for_large_ensembles():
+    """From 4096 particles on (planar) and 9216 (axial) each particle has one lane; below, a lane
+    group shares its field sums, which the tests above run. A few output intervals of 20 ns
+    (several sub-steps each) at those sizes, against the oracle, accepted sub-steps included."""
+    rng = np.random.default_rng(12)
+    t = I.sample_times("jitter", 5, 4 * 20e-9, seed=5)
+    n = 4096
+    pot = rad.RadPlanarPotential.make(I.SYNTH_DT_A, I.SYNTH_DT_B, I.SI_N, I.SYNTH_DT_AX, I.SYNTH_DT_BX, I.SYNTH_DT_CX,
+                                      I.SI_I_EV, n_neighbours=3)
+    opot = T.PlanarPotential(I.SYNTH_DT_A, I.SYNTH_DT_B, I.SI_N, I.SYNTH_DT_AX, I.SYNTH_DT_BX, I.SYNTH_DT_CX, I.SI_I_EV,
+                             K=3)
+    x0, th = rng.uniform(0, I.SI110_DP, n), rng.normal(0, 2e-5, n)
+    st, got, eg, cnt = run_gpu(channel(-1, ALL, 0.0), sc(1e-9), x0, th, t, 6, planar=pot)
+    assert st == rad.RAD_OK
+    (ref, er), rc = T.trajectories_adaptive(x0, th, 0.0, E, t, 6, rtol=1e-9, atol_x=1e-20, atol_v=1e-16,
+                                            max_level=10, charge=-1, pot=opot, ms=True, ms_el=True, ll=True,
+                                            ms_loss=True, energies=True, counts=True)
+    close(got, ref)
+    np.testing.assert_allclose(eg, er, rtol=1e-12)
+    np.testing.assert_array_equal(cnt, rc)
+    n = 9216
+    lat = rad.crystal_string_lattice(rad.RAD_DIAMOND, 5.431e-10, 110)
+    apot = rad.RadAxialPotential.make(I.SYNTH_DT_A, I.SYNTH_DT_B, lat, I.SYNTH_DT_AX, I.SYNTH_DT_BX, I.SYNTH_DT_CX,
+                                      I.SI_I_EV, n_cells=1)
+    olat = T.StringLattice(lat.cell_x, lat.cell_y, list(lat.sx[:4]), list(lat.sy[:4]), lat.d)
+    oapot = T.AxialPotential(I.SYNTH_DT_A, I.SYNTH_DT_B, olat, I.SYNTH_DT_AX, I.SYNTH_DT_BX, I.SYNTH_DT_CX, I.SI_I_EV,
+                             K=1)
+    x0, y0 = rng.uniform(0, lat.cell_x, n), rng.uniform(0, lat.cell_y, n)
+    psi = math.sqrt(2 * 35.0 / E)
+    thx, thy = rng.normal(0, 0.3 * psi, n), rng.normal(0, 0.3 * psi, n)
+    ta = t[:3]
+    st, got, _, cnt = run_gpu(channel(+1, MS), sc(1e-9), x0, thx, ta, 7, axial=apot, y0=y0, thy=thy)
+    assert st == rad.RAD_OK
+    ref, rc = T.trajectories_adaptive(x0, thx, thy, E, ta, 7, rtol=1e-9, atol_x=1e-20, atol_v=1e-16, max_level=10,
+                                      y0=y0, axial=oapot, ms=True, counts=True)
+    close(got, ref)
+    np.testing.assert_array_equal(cnt, rc)
+
+
 def test_lower_bound_budget_and_argument_checks():
     import torch
     x0, th = np.array([0.3e-10, 0.9e-10]), np.array([1e-5, -1e-5])
