@@ -44,8 +44,8 @@ SPLIT = {0: 6, 2: 0}
 # on the launch these legs time: one particle of this workload x 512 hw x 64x64 directions, the
 # default shapes (k_fp64 R=2 NW=8 T=64, k_df R=2 NW=4 T=64)
 FP64_OPS_PER_TERM = {0: 18.53, 2: 20.58}
-DF_FP64_OPS_PER_TERM = {0: 1.85, 2: 2.05}
-DF_INST_PER_32_TERMS = {0: 149.0, 2: 176.0}
+DF_FP64_OPS_PER_TERM = {0: 1.276, 2: 1.360}
+DF_INST_PER_32_TERMS = {0: 133.7, 2: 159.2}
 WORKLOAD = ("positron ensemble: 1024 e+ at 10 GeV, harmonic planar well (U0 = 20 eV, d_p = 1.92 A), "
             "RK4 + scattering kicks, 20000 samples over 100 um; 512 log hw in [1e-4 E, 0.5 E] x 64x64 "
             "directions within +-(theta_L + 3/gamma); classical + spin-1/2")
@@ -616,9 +616,9 @@ def main():
     df_fp64_s = sum(DF_FP64_OPS_PER_TERM[int(m)] * df_terms_launch for (m, _) in dkms) / (sum(dk) * 1e-3)
     df_inst_s = sum(DF_INST_PER_32_TERMS[int(m)] * df_terms_launch / 32 for (m, _) in dkms) / (sum(dk) * 1e-3)
     # k_df: one FP64 instruction per term (the phase product; the reduction is integer
-    # arithmetic) plus the per-(direction, sample) preparation shared by 64 energies and the
-    # conversion of the tile sums into FP64 particle amplitudes; it is bound by the issue slots
-    # (4 warp instructions per SM per clock), the FP64 pipe second
+    # arithmetic) plus the per-(direction, sample) preparation shared by a block's 256 energies and
+    # the conversion of the sums of two tiles into FP64 particle amplitudes; it is bound by the
+    # issue slots (4 warp instructions per SM per clock), the FP64 pipe second
     df_roof = {"kernel": "k_df", "kernel_ms_avg": df_kernel_ms, "launches": len(dk),
                "terms_per_s": df_terms_launch / (df_kernel_ms * 1e-3),
                "fp64_ops_per_term": DF_FP64_OPS_PER_TERM, "warp_inst_per_32_terms": DF_INST_PER_32_TERMS,

@@ -238,9 +238,11 @@ int rad_plan_autotune(rad_plan plan, const double *samples, const int64_t *offse
 
 /*
  * rad_plan_set_shape -- selects the plan's launch shape explicitly:
- *   R           photon energies per thread (FP64: 1, 2, 4; mixed: 1, 2, 4)
- *   NW          warps per block = directions per tile (4 or 8)
- *   T           time-tile length (FP64: 64; mixed: 64, 128 or 256)
+ *   R           photon energies per thread (FP64: 1, 2, 4; FP64_DF: 1, 2; mixed: 1, 2, 4)
+ *   NW          warps per block (4 or 8). FP64 and mixed: each warp takes its own direction
+ *               (a work item is NW directions x 32 R energies). FP64_DF: the block takes one
+ *               direction and each warp its own 32 R energies (NW x 32 R energies per item)
+ *   T           time-tile length (FP64, FP64_DF: 64; mixed: 64, 128 or 256)
  *   chunk_mult  >= 1, multiplies the default number of work items (finer split)
  * Returns RAD_EINVAL for a shape this build does not provide (the plan is unchanged).
  * May reallocate scratch (waits for the device); not allowed during stream capture.

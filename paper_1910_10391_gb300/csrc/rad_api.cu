@@ -84,10 +84,11 @@ ShapeKey key_of(int dev, int64_t ns, int64_t np, int64_t no, int64_t na, int mod
 // Defaults before any autotuning: the fastest shapes on the 10 GeV positron ensemble (512 hw x
 // 64 x 64 directions, 32 particles per launch). The mixed kernel runs 8 warps per block, 2 blocks
 // per SM; spin-1/2 keeps every sin/cos on the SFU, classical and spin-0 (two fewer sums per term)
-// take 1/8 of them on the FMA pipe.
-Choice default_choice(int precision, int mode) {
+// take 1/8 of them on the FMA pipe. k_df's blocks of 4 warps take 256 energies of one direction
+// (128 when the grid has no more).
+Choice default_choice(int precision, int mode, int64_t n_omega) {
   if (precision == RAD_FP64) return Choice{2, 8, 64, 1, 0};
-  if (precision == RAD_FP64_DF) return Choice{2, 4, 64, 1, 0};
+  if (precision == RAD_FP64_DF) return Choice{n_omega <= 128 ? 1 : 2, 4, 64, 1, 0};
   if (mode == RAD_SPIN_HALF) return Choice{2, 8, 256, 1, 1, 0};
   return Choice{2, 8, 256, 1, 1, 6};
 }
@@ -113,8 +114,15 @@ int configure(rad_plan p, const Choice &c) {
                                                 : occupancy_mixed(sh, p->mode);
   if (occ <= 0) return RAD_EUNSUPPORTED;
   const int64_t resident = static_cast<int64_t>(p->sms) * occ;
-  p->n_wt = static_cast<int>((p->n_omega + 32 * c.R - 1) / (32 * c.R));
-  p->n_nt = static_cast<int>((p->n_angles + c.NW - 1) / c.NW);
+  if (p->precision == RAD_FP64_DF) {  // k_df: one direction and NW 32 R energies per work item
+    if (p->n_angles > INT32_MAX) return RAD_EINVAL;
+    const int64_t per_block = 32LL * c.R * c.NW;
+    p->n_wt = static_cast<int>((p->n_omega + per_block - 1) / per_block);
+    p->n_nt = static_cast<int>(p->n_angles);
+  } else {  // NW directions and 32 R energies per work item
+    p->n_wt = static_cast<int>((p->n_omega + 32 * c.R - 1) / (32 * c.R));
+    p->n_nt = static_cast<int>((p->n_angles + c.NW - 1) / c.NW);
+  }
   const int64_t tiles = static_cast<int64_t>(p->n_wt) * p->n_nt;
   const int64_t target = resident * 4 * std::max(1, c.chunk_mult);
   p->amp_mode = 0;
@@ -350,7 +358,7 @@ int plan_create(int64_t ns, int64_t np, int64_t no, int64_t na, int mode, int pr
     delete p;
     return cuda_fail(e);
   }
-  Choice c = default_choice(prec, mode);
+  Choice c = default_choice(prec, mode, no);
   {
     std::lock_guard<std::mutex> lk(g_mu);
     auto it = g_tuned.find(key_of(dev, ns, np, no, na, mode, prec, want, p->n_bins));

@@ -20,8 +20,12 @@
 //                                        of Sec. II satisfies n_x f_x + n_y f_y + f_z = 0
 //                                        identically, so I_z = -(n_x I_x + n_y I_y) is formed from
 //                                        the particle amplitudes
-// Tile sums are added into FP64 particle amplitudes. The per-term error is about 1e-14 of |f|,
-// far inside the FP64 form's tolerance (1e-9 of a bin, floor 1e-6 of the peak).
+// The sums of two tiles are added into FP64 particle amplitudes. The per-term error is about 1e-14
+// of |f|, far inside the FP64 form's tolerance (1e-9 of a bin, floor 1e-6 of the peak).
+// Work split: a block takes one direction and NW 32 R energies. The per-(direction, sample)
+// preparation (the FP64 phase A_k(n), 1 - n.beta, f and j) is computed once per block and time
+// tile and shared by all NW 32 R energies, so that the FP64 pipe carries little beyond the phase
+// products.
 #include <cstdio>
 
 #include "rad_internal.cuh"
@@ -75,38 +79,62 @@ constexpr unsigned long long kKL = 17511926765934236664ull;
 constexpr float kChf = 0.003067961661145091f;
 constexpr float kClf = -8.537380524753502e-11f;
 
-// phi = j pi/1024 + r with |r| <= pi/2048; returns j, r as the float pair (xh, xl).
+// 1024/pi 2^64 = kK2 2^64 + kK1 2^32 + kK0 as 32-bit words, and the float-pair constants of pi/1024
+// times 2^-24 and 2^-48 (exact power-of-two scalings, all normal), which take the fraction's two
+// 24-bit parts as plain integers
+constexpr unsigned kK2 = static_cast<unsigned>(kKH);
+constexpr unsigned kK1 = static_cast<unsigned>(kKL >> 32);
+constexpr unsigned kK0 = static_cast<unsigned>(kKL & 0xFFFFFFFFull);
+constexpr float kChf24 = kChf * 5.9604644775390625e-8f;
+constexpr float kClf24 = kClf * 5.9604644775390625e-8f;
+constexpr float kChf48 = kChf * 3.552713678800501e-15f;
+
+// phi = j pi/1024 + r with |r| <= pi/2048; returns j mod 2^16 (the table takes it mod 2048) and r
+// as the float pair (xh, xl).
 // For 2^-10 <= |phi| < 2^22 by a fixed-point (Payne-Hanek) reduction of phi's bits with integer
-// multiplies: |phi| = m 2^(e-1075) with the 53-bit significand m, and phi 1024/pi = m K 2^(e-1139)
-// with K = 1024/pi 2^64 as a 73-bit integer, formed as a 128-bit product; its integer part gives j
-// (rounded to nearest) and the top 48 bits of its fraction F give r = F pi/1024, absolute error
-// below 3e-16 rad. Below 2^-10, r = phi; from 2^22 on, the FP64 Cody-Waite reduction.
+// multiplies: |phi| = m 2^(e-1075) with the 53-bit significand m = m1 2^32 + m0 (m1 of 21 bits), and
+// phi 1024/pi = m K 2^(e-1139) with K = 1024/pi 2^64 as a 73-bit integer. m K is formed from 32-bit
+// products without its lowest word (nothing else lands below bit 32, so every bit from 32 up is
+// exact); X = m K >> (a + 16), a = 1075 - e in [31, 62], taken by funnel shifts, holds the low bits
+// of the integer part from bit 48 (rounded to nearest by the fraction's top bit) and the fraction's
+// top 48 bits F below, so r = F pi/1024 with absolute error below 3e-16 rad. Below 2^-10, r = phi;
+// from 2^22 on, the FP64 Cody-Waite reduction.
 __device__ __forceinline__ int reduce_phase(double phi, float &xh, float &xl) {
-  const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(phi));
-  const int e = static_cast<int>((u >> 52) & 0x7ffull);
-  if (e < 1013) {  // |phi| < 2^-10 < pi/2048
-    split_df(phi, xh, xl);
-    return 0;
-  }
-  if (e > 1044) {  // |phi| >= 2^22
+  const unsigned hi = static_cast<unsigned>(__double2hiint(phi));
+  const unsigned m0 = static_cast<unsigned>(__double2loint(phi));
+  const int e = static_cast<int>((hi >> 20) & 0x7ffu);
+  if (static_cast<unsigned>(e - 1013) > 31u) {
+    if (e < 1013) {  // |phi| < 2^-10 < pi/2048
+      split_df(phi, xh, xl);
+      return 0;
+    }
+    // |phi| >= 2^22
     const double y = fma(phi, kInvStep, kMagic);
     const double jd = y - kMagic;
     split_df(fma(-jd, kC2, fma(-jd, kC1, phi)), xh, xl);
     return __double2loint(y);
   }
-  const unsigned long long m = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-  const int a = 1075 - e;  // 31 .. 62: the integer part starts at bit 64 + a of m K
-  const unsigned long long L = m * kKL;
-  const unsigned long long H = __umul64hi(m, kKL) + m * kKH;  // m K = H 2^64 + L, H < 2^62
-  const unsigned long long I = H >> a;
-  const unsigned long long Ff = (H << (64 - a)) | (L >> a);   // F in units of 2^-64
-  const long long fs = static_cast<long long>(Ff);            // F - 1 when F >= 1/2
-  int j = static_cast<int>(I + (Ff >> 63));
-  const float fa = __int2float_rn(static_cast<int>(fs >> 40)) * 5.9604644775390625e-8f;            // 2^-24
-  const float fb = __int2float_rn(static_cast<int>((fs >> 16) & 0xFFFFFF)) * 3.552713678800501e-15f;  // 2^-48
-  float p = __fmul_rn(fa, kChf);
-  float lo = __fadd_rn(__fmaf_rn(fa, kChf, -p), __fmaf_rn(fa, kClf, __fmul_rn(fb, kChf)));
-  if (u >> 63) {
+  const unsigned m1 = (hi & 0xFFFFFu) | 0x100000u;
+  const unsigned long long a01 = static_cast<unsigned long long>(m0) * kK1;
+  const unsigned long long a10 = static_cast<unsigned long long>(m1) * kK0;
+  const unsigned long long s1 = static_cast<unsigned long long>(__umulhi(m0, kK0)) + static_cast<unsigned>(a01) +
+                                static_cast<unsigned>(a10);  // bits 32.. of m K
+  const unsigned long long h = static_cast<unsigned long long>(m0) * kK2 + static_cast<unsigned long long>(m1) * kK1 +
+                               (a01 >> 32) + (a10 >> 32) + (s1 >> 32) +
+                               (static_cast<unsigned long long>(m1 * kK2) << 32);  // bits 64.. of m K
+  const unsigned w0 = static_cast<unsigned>(s1), w1 = static_cast<unsigned>(h), w2 = static_cast<unsigned>(h >> 32);
+  const int sh = 1059 - e;  // a - 16 in [15, 46]: X = (w2 w1 w0) >> sh
+  const bool big = sh >= 32;
+  const unsigned v0 = big ? w1 : w0, v1 = big ? w2 : w1, v2 = big ? 0u : w2;
+  const unsigned x0 = __funnelshift_r(v0, v1, sh);  // shift taken mod 32
+  const unsigned x1 = __funnelshift_r(v1, v2, sh);
+  const int t24 = static_cast<int>(__funnelshift_r(x0, x1, 24) << 8) >> 8;  // F's signed top 24 bits
+  const int low24 = static_cast<int>(x0 & 0xFFFFFFu);                       // F's next 24 bits
+  int j = static_cast<int>((x1 + 0x8000u) >> 16);
+  const float fa = __int2float_rn(t24), fb = __int2float_rn(low24);
+  float p = __fmul_rn(fa, kChf24);
+  float lo = __fadd_rn(__fmaf_rn(fa, kChf24, -p), __fmaf_rn(fa, kClf24, __fmul_rn(fb, kChf48)));
+  if (hi >> 31) {
     p = -p;
     lo = -lo;
     j = -j;
@@ -121,6 +149,12 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &t) {
   s = __fadd_rn(a, b);
   const float bb = __fsub_rn(s, a);
   t = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// s + t = a + b exactly when |a| >= |b| or a = 0 (Dekker)
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &t) {
+  s = __fadd_rn(a, b);
+  t = __fsub_rn(b, __fsub_rn(s, a));
 }
 
 // one Dot2 step: (S, C) += (fh + fl)(eh + el)
@@ -147,17 +181,27 @@ __device__ __forceinline__ double df_component(const double *a, int c, double nx
   return a[c - 2];
 }
 
+// Shared memory of a block: the float-pair table, the double-buffered stage of trajectory records
+// and the per-sample preparation of the block's direction (A [T] double, Fa [T] float4 and, for
+// spin 1/2, Fj [T] float2), written once per tile by the block and read by all its warps.
 template <int MODE, int R, int NW, int T>
 struct DfLayout {
   static constexpr int kStageDoubles = (T + 2) * kRec;
   static constexpr int kTable = 0;                                   // float4 [kDfTabN]
   static constexpr int kStage = kTable + kDfTabN * 16;
-  static constexpr int kNk = kStage + 2 * kStageDoubles * 8;         // per warp: A [T] double,
-  static constexpr int kNkWarp = T * 8 + T * 16 + ((MODE == RAD_SPIN_HALF) ? T * 8 : 0);  // Fa [T] float4, Fj [T] float2
-  static constexpr int kBar = kNk + NW * kNkWarp;
+  static constexpr int kNk = kStage + 2 * kStageDoubles * 8;
+  static constexpr int kNkBytes = T * 8 + T * 16 + ((MODE == RAD_SPIN_HALF) ? T * 8 : 0);
+  static constexpr int kBar = kNk + kNkBytes;
   static constexpr int kMisc = kBar + 16;
   static constexpr int kTotal = kMisc + 16;
 };
+
+// Tile sums (FP32 Dot2 pairs) are added into the FP64 particle amplitudes every kConvTiles tiles
+// and at the end of a particle. Ogita, Rump and Oishi bound the Dot2 error of n terms by
+// gamma_n^2 times the sum of the products' magnitudes (gamma_n = n u / (1 - n u), u = 2^-24), which
+// for 2 x 64 terms is below 1e-10 of that sum; each conversion costs 4 FP64 instructions per
+// component and energy.
+constexpr int kConvTiles = 2;
 
 template <int MODE, int R, int NW, int T>
 __global__ void __launch_bounds__(NW * 32, NW == 4 ? (MODE == RAD_SPIN_HALF ? 4 : 3) : 1) k_df(const Params P) {
@@ -191,10 +235,9 @@ __global__ void __launch_bounds__(NW * 32, NW == 4 ? (MODE == RAD_SPIN_HALF ? 4 
   }
   __syncthreads();
   uint32_t parity[2] = {0u, 0u};
-  unsigned char *myNk = sm + L::kNk + warp * L::kNkWarp;
-  double *myA = reinterpret_cast<double *>(myNk);
-  float4 *myFa = reinterpret_cast<float4 *>(myNk + T * 8);   // (fx_hi, fx_lo, fy_hi, fy_lo)
-  float2 *myFj = reinterpret_cast<float2 *>(myNk + T * 24);  // (j_hi, j_lo), spin 1/2 only
+  double *sA = reinterpret_cast<double *>(sm + L::kNk);
+  float4 *sFa = reinterpret_cast<float4 *>(sm + L::kNk + T * 8);   // (fx_hi, fx_lo, fy_hi, fy_lo)
+  float2 *sFj = reinterpret_cast<float2 *>(sm + L::kNk + T * 24);  // (j_hi, j_lo), spin 1/2 only
 
   const int64_t per_chunk = static_cast<int64_t>(P.n_wt) * P.n_nt;
   int s = 0;
@@ -207,20 +250,17 @@ __global__ void __launch_bounds__(NW * 32, NW == 4 ? (MODE == RAD_SPIN_HALF ? 4 
     if (item >= P.n_items) break;
     const int64_t chunk = item / per_chunk;
     const int64_t rem = item % per_chunk;
-    const int nt = static_cast<int>(rem / P.n_wt), wt = static_cast<int>(rem % P.n_wt);
-    const int64_t jdir = static_cast<int64_t>(nt) * NW + warp;
-    const bool jvalid = jdir < P.n_angles;
-    const double nx = jvalid ? P.theta_x[jdir] : 0.0;
-    const double ny = jvalid ? P.theta_y[jdir] : 0.0;
+    // one direction per item, shared by the block's warps (the per-sample preparation is done
+    // once for all of them); warp w takes the energies (wt NW + w) 32 R + 32 r + lane
+    const int64_t jdir = rem / P.n_wt;
+    const int wt = static_cast<int>(rem % P.n_wt);
+    const double nx = P.theta_x[jdir];
+    const double ny = P.theta_y[jdir];
     const double th2h = __dmul_rn(__dadd_rn(__dmul_rn(nx, nx), __dmul_rn(ny, ny)), 0.5);
 
-    int64_t iw[R];
-    double hwv[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      iw[r] = static_cast<int64_t>(wt) * 32 * R + r * 32 + lane;
-      hwv[r] = iw[r] < P.n_omega ? P.hw[iw[r]] : 1.0;
-    }
+    // energy indices; the energies themselves are read where they are used
+    const int64_t iw0 = (static_cast<int64_t>(wt) * NW + warp) * 32 * R + lane;
+    auto hw_of = [&](int r) { return iw0 + 32 * r < P.n_omega ? __ldg(P.hw + iw0 + 32 * r) : 1.0; };
     double S_acc[R];
     double amp[R][NA];
 #pragma unroll
@@ -241,6 +281,13 @@ __global__ void __launch_bounds__(NW * 32, NW == 4 ? (MODE == RAD_SPIN_HALF ? 4 
     if (cur.valid) {
       if (tid == 0) issue_tile<T>(P, cur, stage_base + s * L::kStageDoubles, &bar[s]);
       int64_t cur_p = -1;
+      // compensated sums (S + C per component) since the last conversion into amp
+      float tS[R][NA], tC[R][NA];
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int c = 0; c < NA; ++c) tS[r][c] = tC[r][c] = 0.f;
+      int since = 0;
       double ws[R];
       double inv2g2 = 0.0, cn = 0.0, wp = 1.0, gam = 2.0, En = 1.0;
       for (;;) {
@@ -257,11 +304,12 @@ __global__ void __launch_bounds__(NW * 32, NW == 4 ? (MODE == RAD_SPIN_HALF ? 4 
           cn = __dadd_rn(inv2g2, th2h);
 #pragma unroll
           for (int r = 0; r < R; ++r) {
-            const double w = __ddiv_rn(hwv[r], kHbarC);
+            const double hwr = hw_of(r);
+            const double w = __ddiv_rn(hwr, kHbarC);
             if (MODE == RAD_CLASSICAL) {
               ws[r] = w;
             } else {
-              const double u = __ddiv_rn(hwv[r], En);
+              const double u = __ddiv_rn(hwr, En);
               ws[r] = __ddiv_rn(w, __dsub_rn(1.0, u));
             }
 #pragma unroll
@@ -281,8 +329,9 @@ __global__ void __launch_bounds__(NW * 32, NW == 4 ? (MODE == RAD_SPIN_HALF ? 4 
         const double *st = stage_base + s * L::kStageDoubles;
         const int n = static_cast<int>((cur.ke - cur.k0) < T ? (cur.ke - cur.k0) : T);
 
-        // per (n, k): phase A in the oracle's IEEE order (FP64), weighted f and j as float pairs
-        for (int k = lane; k < n; k += 32) {
+        // per (n, k), once per block: phase A in the oracle's IEEE order (FP64), weighted f and j
+        // as float pairs
+        for (int k = tid; k < n; k += NW * 32) {
           const double *rc = st + (k + 1) * kRec;
           const int64_t K = cur.k0 + k;
           const double tm = (K == 0) ? rc[F_T] : st[k * kRec + F_T];
@@ -300,27 +349,22 @@ __global__ void __launch_bounds__(NW * 32, NW == 4 ? (MODE == RAD_SPIN_HALF ? 4 
           const double m = az + nx * ax + ny * ay;         // n.beta_dot
           const double fx = (a * m - ax * D) * gw, fy = (b * m - ay * D) * gw;
           const float fxh = __double2float_rn(fx), fyh = __double2float_rn(fy);
-          myA[k] = A;
-          myFa[k] = make_float4(fxh, __double2float_rn(fx - fxh), fyh, __double2float_rn(fy - fyh));
+          sA[k] = A;
+          sFa[k] = make_float4(fxh, __double2float_rn(fx - fxh), fyh, __double2float_rn(fy - fyh));
           if (MODE == RAD_SPIN_HALF) {
             const double fj = m * gw;
             const float fjh = __double2float_rn(fj);
-            myFj[k] = make_float2(fjh, __double2float_rn(fj - fjh));
+            sFj[k] = make_float2(fjh, __double2float_rn(fj - fjh));
           }
         }
-        __syncwarp();
+        __syncthreads();
 
-        // tile sums (S + C per component), compensated
-        float tS[R][NA], tC[R][NA];
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-#pragma unroll
-          for (int c = 0; c < NA; ++c) tS[r][c] = tC[r][c] = 0.f;
+        // compensated sums over the tile
 #pragma unroll 2
         for (int k = 0; k < n; ++k) {
-          const double A = myA[k];
-          const float4 Fa = myFa[k];
-          const float2 Fj = (MODE == RAD_SPIN_HALF) ? myFj[k] : make_float2(0.f, 0.f);
+          const double A = sA[k];
+          const float4 Fa = sFa[k];
+          const float2 Fj = (MODE == RAD_SPIN_HALF) ? sFj[k] : make_float2(0.f, 0.f);
 #pragma unroll
           for (int r = 0; r < R; ++r) {
             const double phi = __dmul_rn(ws[r], A);
@@ -332,13 +376,15 @@ __global__ void __launch_bounds__(NW * 32, NW == 4 ? (MODE == RAD_SPIN_HALF ? 4 
             // cos x - 1 and the part of sin x below xh
             const float cm = __fmaf_rn(-0.5f, x2e, __fmaf_rn(-xh, xl, __fmul_rn(x2, __fmaf_rn(x2, 1.0f / 24.0f, -0.5f))));
             const float sxl = __fmaf_rn(__fmul_rn(-xh, x2), __fmaf_rn(x2, -1.0f / 120.0f, 1.0f / 6.0f), xl);
-            // sin(phi) = S + S cm + C xh + C sxl
+            // sin(phi) = S + S cm + C xh + C sxl. The table's leading parts are 0 at multiples of pi/2
+            // (filled by exact symmetry) and at least sin(2 pi/2048) = 3.07e-3 in magnitude elsewhere,
+            // twice |C xh| <= pi/2048, so Fast2Sum gives the exact sum of S and C xh
             float sh, sl;
             {
               const float p = __fmul_rn(t.x, xh);
               const float pe = __fmaf_rn(t.x, xh, -p);
               float v;
-              two_sum(t.z, p, sh, v);
+              fast_two_sum(t.z, p, sh, v);
               sl = __fadd_rn(v, __fadd_rn(pe, __fmaf_rn(t.y, xh, __fmaf_rn(t.x, sxl, __fmaf_rn(t.z, cm, t.w)))));
             }
             // cos(phi) = C + C cm - S xh - S sxl
@@ -347,7 +393,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 4 ? (MODE == RAD_SPIN_HALF ? 4 
               const float p = __fmul_rn(-t.z, xh);
               const float pe = __fmaf_rn(-t.z, xh, -p);
               float v;
-              two_sum(t.x, p, ch, v);
+              fast_two_sum(t.x, p, ch, v);
               cl = __fadd_rn(v, __fadd_rn(pe, __fmaf_rn(-t.w, xh, __fmaf_rn(-t.z, sxl, __fmaf_rn(t.x, cm, t.y)))));
             }
             dot2(tS[r][0], tC[r][0], Fa.x, Fa.y, ch, cl);
@@ -360,13 +406,17 @@ __global__ void __launch_bounds__(NW * 32, NW == 4 ? (MODE == RAD_SPIN_HALF ? 4 
             }
           }
         }
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-#pragma unroll
-          for (int c = 0; c < NA; ++c)
-            amp[r][c] += static_cast<double>(tS[r][c]) + static_cast<double>(tC[r][c]);
-
         const bool last_of_particle = !nxt.valid || nxt.p != cur.p;
+        if (last_of_particle || ++since == kConvTiles) {
+#pragma unroll
+          for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int c = 0; c < NA; ++c) {
+              amp[r][c] += static_cast<double>(tS[r][c]) + static_cast<double>(tC[r][c]);
+              tS[r][c] = tC[r][c] = 0.f;
+            }
+          since = 0;
+        }
         if (last_of_particle && !P.amp_mode) {
 #pragma unroll
           for (int r = 0; r < R; ++r) {
@@ -380,7 +430,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 4 ? (MODE == RAD_SPIN_HALF ? 4 
             if (MODE == RAD_CLASSICAL) {
               Sv = I2;
             } else {
-              const double u = hwv[r] / En;
+              const double u = hw_of(r) / En;
               if (MODE == RAD_SPIN0) {
                 Sv = (1.0 - u) * I2;
               } else {
@@ -397,17 +447,16 @@ __global__ void __launch_bounds__(NW * 32, NW == 4 ? (MODE == RAD_SPIN_HALF ? 4 
         cur = nxt;
       }
     }
-    if (jvalid) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        if (iw[r] >= P.n_omega) continue;
-        if (!P.amp_mode) {
-          P.part[(chunk * P.n_angles + jdir) * P.n_omega + iw[r]] = S_acc[r];
-        } else {
+    for (int r = 0; r < R; ++r) {
+      const int64_t iw = iw0 + 32 * r;
+      if (iw >= P.n_omega) continue;
+      if (!P.amp_mode) {
+        P.part[(chunk * P.n_angles + jdir) * P.n_omega + iw] = S_acc[r];
+      } else {
 #pragma unroll
-          for (int c = 0; c < NC; ++c)
-            P.part[((chunk * NC + c) * P.n_angles + jdir) * P.n_omega + iw[r]] = df_component(amp[r], c, nx, ny);
-        }
+        for (int c = 0; c < NC; ++c)
+          P.part[((chunk * NC + c) * P.n_angles + jdir) * P.n_omega + iw] = df_component(amp[r], c, nx, ny);
       }
     }
   }
@@ -435,6 +484,7 @@ cudaError_t launch_t(const Params &P, LaunchShape *shape, cudaStream_t st, int *
 template <int MODE>
 cudaError_t dispatch_mode(const Params &P, LaunchShape *sh, cudaStream_t st, int *occ) {
   if (sh->T != 64) return cudaErrorInvalidValue;
+  if (sh->R == 1 && sh->NW == 4) return launch_t<MODE, 1, 4>(P, sh, st, occ);
   if (sh->R == 1 && sh->NW == 8) return launch_t<MODE, 1, 8>(P, sh, st, occ);
   if (sh->R == 2 && sh->NW == 4) return launch_t<MODE, 2, 4>(P, sh, st, occ);
   if (sh->R == 2 && sh->NW == 8) return launch_t<MODE, 2, 8>(P, sh, st, occ);
@@ -453,7 +503,7 @@ cudaError_t dispatch(const Params &P, LaunchShape *sh, cudaStream_t st, int *occ
 }  // namespace
 
 bool shape_supported_df(int R, int NW, int T) {
-  return T == 64 && ((R == 1 && NW == 8) || (R == 2 && (NW == 4 || NW == 8)));
+  return T == 64 && (R == 1 || R == 2) && (NW == 4 || NW == 8);
 }
 
 cudaError_t launch_df(const Params &P, LaunchShape *shape, cudaStream_t st) {

@@ -58,11 +58,26 @@ def test_df_ensemble(mode):
     print("df ensemble max rel", mode, assert_fp64_close(got, ref))
 
 
-@pytest.mark.parametrize("shape", [(1, 8, 64, 1), (2, 4, 64, 2), (2, 8, 64, 1), (2, 8, 64, 3)])
+@pytest.mark.parametrize("shape", [(1, 4, 64, 1), (1, 8, 64, 1), (2, 4, 64, 2), (2, 8, 64, 1), (2, 8, 64, 3)])
 def test_df_every_shape(ragged_batch, shape):
     tr, grid = ragged_batch
     ref = O.spectrum_cube(tr, grid, O.SPIN_HALF)
     got = gpu_cube(tr, grid, rad.RAD_SPIN_HALF, DF, shape=shape)["cube"]
+    assert_fp64_close(got, ref)
+
+
+@pytest.mark.parametrize("mode", [rad.RAD_CLASSICAL, rad.RAD_SPIN_HALF])
+@pytest.mark.parametrize("shape", [None, (1, 4, 64, 1), (2, 8, 64, 2)])
+def test_df_energy_tiles_with_a_ragged_tail(mode, shape):
+    """A block takes one direction and NW x 32 x R energies: 300 energies make 256 + 44 (R=2, NW=4,
+    the default), 128 + 128 + 44 (R=1, NW=4) or 300 of 512 (R=2, NW=8). Particles of 3, 5, 11 and 16
+    time tiles end the tile-sum runs, which are converted into FP64 every two tiles, after odd and
+    even counts."""
+    L = np.array([130, 257, 700, 1023])
+    tr = I.channeling(4, 10e9, +1, L, 5e-9, seed=7)
+    grid = I._ensemble_grid(10e9, 20.0, 300, 3)
+    ref = O.spectrum_cube(tr, grid, MODE_ORC[mode])
+    got = gpu_cube(tr, grid, mode, DF, shape=shape)["cube"]
     assert_fp64_close(got, ref)
 
 
