@@ -45,7 +45,7 @@ SPLIT = {0: 6, 2: 0}
 # default shapes (k_fp64 R=2 NW=8 T=64, k_df R=2 NW=4 T=64)
 FP64_OPS_PER_TERM = {0: 18.53, 2: 20.58}
 DF_FP64_OPS_PER_TERM = {0: 1.276, 2: 1.360}
-DF_INST_PER_32_TERMS = {0: 133.7, 2: 159.2}
+DF_INST_PER_32_TERMS = {0: 134.5, 2: 159.3}
 WORKLOAD = ("positron ensemble: 1024 e+ at 10 GeV, harmonic planar well (U0 = 20 eV, d_p = 1.92 A), "
             "RK4 + scattering kicks, 20000 samples over 100 um; 512 log hw in [1e-4 E, 0.5 E] x 64x64 "
             "directions within +-(theta_L + 3/gamma); classical + spin-1/2")

@@ -203,8 +203,12 @@ struct DfLayout {
 // component and energy.
 constexpr int kConvTiles = 2;
 
+// Blocks of 4 warps run 5 per SM (46 KB of shared memory each; registers held to 96, for which the
+// compiler spills 12-152 bytes per thread at R = 2): 20 warps per SM hide the float-pair chains'
+// latency better than 16 at 122-128 registers without spills (723 / 839 ms against 754 / 865 ms per
+// 4-particle launch of the positron ensemble, classical / spin-1/2). Blocks of 8 warps run 2 per SM.
 template <int MODE, int R, int NW, int T>
-__global__ void __launch_bounds__(NW * 32, NW == 4 ? (MODE == RAD_SPIN_HALF ? 4 : 3) : 1) k_df(const Params P) {
+__global__ void __launch_bounds__(NW * 32, NW == 4 ? 5 : 2) k_df(const Params P) {
   using L = DfLayout<MODE, R, NW, T>;
   constexpr int NC = DfNcomp<MODE>::value;
   constexpr int NA = NC - 2;  // summed components
@@ -220,8 +224,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 4 ? (MODE == RAD_SPIN_HALF ? 4 
   if (s_item[1] != 0) return;
 
   // (cos, sin)(2 pi j / 2048) as float pairs (c_hi, c_lo, s_hi, s_lo) from every other entry of the
-  // FP64 table (2048 entries, 32 KB: four blocks of 4 warps fit on an SM; spin-1/2 is held to 128
-  // registers for that, classical takes 4 blocks at its natural 120)
+  // FP64 table (2048 entries, 32 KB)
   for (int i = tid; i < kDfTabN; i += NW * 32) {
     const double2 t = P.table[2 * i];
     const float ch = __double2float_rn(t.x), sh = __double2float_rn(t.y);
