@@ -81,6 +81,19 @@ def test_df_energy_tiles_with_a_ragged_tail(mode, shape):
     assert_fp64_close(got, ref)
 
 
+@pytest.mark.parametrize("mode", [rad.RAD_CLASSICAL, rad.RAD_SPIN_HALF])
+def test_df_one_energy_one_direction(mode):
+    """A grid of one photon energy and one direction: one work item per time piece, 255 of the
+    block's 256 energies idle."""
+    tr = I.channeling(3, 10e9, +1, np.array([300, 64, 1000]), 5e-9, seed=9)
+    g = I._ensemble_grid(10e9, 20.0, 8, 4)
+    grid = I.Grid(g.hbar_omega_eV[5:6], g.theta_x[6:7], g.theta_y[6:7], g.d_omega[6:7])
+    ref = O.spectrum_cube(tr, grid, MODE_ORC[mode])
+    assert ref.shape == (1, 1) and ref[0, 0] > 0
+    got = gpu_cube(tr, grid, mode, DF)["cube"]
+    assert_fp64_close(got, ref)
+
+
 def test_df_single_particle_time_split(undulator):
     tr, grid = undulator
     ref = O.spectrum_cube(tr, grid, O.CLASSICAL)

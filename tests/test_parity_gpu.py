@@ -198,17 +198,18 @@ def test_edge_cases():
     tr = I.concat(parts)
     hw1 = I.undulator_first_harmonic_eV(2000.0, 0.4e-10, 10e-6)
     grid = I.make_grid(np.array([0.3, 1.0, 1.7]) * hw1, 3, 3, 1e-3)
-    for prec in (rad.RAD_FP64, rad.RAD_MIXED):
+    for prec in (rad.RAD_FP64, rad.RAD_MIXED, rad.RAD_FP64_DF):
         got = gpu_cube(tr, grid, rad.RAD_CLASSICAL, prec)["cube"]
         ref = oracle_cube(tr, grid, rad.RAD_CLASSICAL)
-        (assert_fp64_close if prec == rad.RAD_FP64 else assert_mixed_close)(got, ref)
-    # no particles: zeros
+        (assert_mixed_close if prec == rad.RAD_MIXED else assert_fp64_close)(got, ref)
     empty = I.Trajectories(np.zeros((0, 10)), np.array([0]), np.zeros(0), np.zeros(0), np.zeros(0))
-    got = gpu_cube(empty, grid, rad.RAD_CLASSICAL, rad.RAD_FP64)["cube"]
-    assert np.all(got == 0.0)
-    # straight line: exactly zero on the GPU too
-    got = gpu_cube(I.straight_line(), grid, rad.RAD_SPIN_HALF, rad.RAD_FP64)["cube"]
-    assert np.all(got == 0.0)
+    for prec in (rad.RAD_FP64, rad.RAD_FP64_DF):
+        # no particles: zeros
+        got = gpu_cube(empty, grid, rad.RAD_CLASSICAL, prec)["cube"]
+        assert np.all(got == 0.0)
+        # straight line: exactly zero on the GPU too
+        got = gpu_cube(I.straight_line(), grid, rad.RAD_SPIN_HALF, prec)["cube"]
+        assert np.all(got == 0.0)
     # no photon energies / no directions: valid, nothing to do
     g0 = I.Grid(np.zeros(0), grid.theta_x, grid.theta_y, grid.d_omega)
     inp = rad.DeviceInputs(tr, g0)
@@ -257,7 +258,7 @@ def test_host_checks():
 
 
 # --------------------------------------------------------------------------- properties
-@pytest.mark.parametrize("precision", [rad.RAD_FP64, rad.RAD_MIXED])
+@pytest.mark.parametrize("precision", [rad.RAD_FP64, rad.RAD_MIXED, rad.RAD_FP64_DF])
 def test_bitwise_deterministic(ragged_batch, precision):
     tr, grid = ragged_batch
     a = gpu_cube(tr, grid, rad.RAD_SPIN_HALF, precision)["cube"]
@@ -291,14 +292,16 @@ def test_graph_replay_and_host_entry(ensemble_small):
     assert np.array_equal(host, direct.cpu().numpy())
 
 
-def test_autotune_keeps_parity(ragged_batch):
+@pytest.mark.parametrize("precision", [rad.RAD_MIXED, rad.RAD_FP64_DF])
+def test_autotune_keeps_parity(ragged_batch, precision):
     import torch
     tr, grid = ragged_batch
     inp = rad.DeviceInputs(tr, grid)
-    plan = rad.Plan(inp.n_samples, inp.n_particles, inp.n_omega, inp.n_angles, 2, 1, 1, 0)
+    plan = rad.Plan(inp.n_samples, inp.n_particles, inp.n_omega, inp.n_angles, 2, precision, 1, 0)
     out = torch.zeros(inp.n_omega * inp.n_angles, dtype=torch.float64, device="cuda")
     assert plan.autotune(*inp.args(), out, None, None, None, budget_ms=3000) == 0
     assert "R=" in plan.describe()
     ref = oracle_cube(tr, grid, rad.RAD_SPIN_HALF)
-    assert_mixed_close(out.view(inp.n_omega, inp.n_angles).cpu().numpy(), ref)
+    check = assert_mixed_close if precision == rad.RAD_MIXED else assert_fp64_close
+    check(out.view(inp.n_omega, inp.n_angles).cpu().numpy(), ref)
     plan.close()
