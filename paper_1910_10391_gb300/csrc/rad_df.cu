@@ -4,14 +4,15 @@
 //   phi = w* A_k(n)                      one FP64 multiply: the same double as the oracle's phase
 //                                        (A_k(n) is formed in the oracle's IEEE order, FP64)
 //   phi = j 2 pi/2048 + r                the table index j and the reduced phase by a fixed-point
-//                                        (Payne-Hanek) reduction of phi's bits with integer multiplies
+//                                        (Payne-Hanek) reduction of phi's bits with 32-bit integer
+//                                        multiplies (rad_df_reduce.cuh)
 // and everything after the reduction runs in double-float FP32 arithmetic (T. J. Dekker, Numer.
-// Math. 18 (1971); error-free products by FMA and sums by Knuth's TwoSum):
+// Math. 18 (1971); error-free products by FMA, sums by Knuth's TwoSum or Dekker's Fast2Sum):
 //   r = (r_hi, r_lo)                     the reduction's fraction times pi/1024 as a float pair
 //   sin r, cos r - 1                     Taylor series on |r| <= pi/2048, FP32 beyond the leading
 //                                        term of sin
 //   sin phi, cos phi                     with a (cos, sin)(2 pi j/2048) table held as float pairs,
-//                                        one error-free product and one TwoSum each
+//                                        one error-free product and one Fast2Sum each
 //   sum_k f_k e^{i phi_k}                 f as float pairs, accumulated with the compensated dot
 //                                        product of Ogita, Rump and Oishi ("Accurate sum and dot
 //                                        product", SIAM J. Sci. Comput. 26 (2005), Dot2): per term
@@ -20,7 +21,7 @@
 //                                        of Sec. II satisfies n_x f_x + n_y f_y + f_z = 0
 //                                        identically, so I_z = -(n_x I_x + n_y I_y) is formed from
 //                                        the particle amplitudes
-// The sums of two tiles are added into FP64 particle amplitudes. The per-term error is about 1e-14
+// The sums over runs of two 64-sample tiles are added into FP64 particle amplitudes. The per-term error is about 1e-14
 // of |f|, far inside the FP64 form's tolerance (1e-9 of a bin, floor 1e-6 of the peak).
 // Work split: a block takes one direction and NW 32 R energies. The per-(direction, sample)
 // preparation (the FP64 phase A_k(n), 1 - n.beta, f and j) is computed once per block and time
