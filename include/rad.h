@@ -110,7 +110,10 @@ extern "C" {
  *   accumulate       0: outputs are overwritten; 1: results are added to them
  *   stream           cudaStream_t as void*
  * Returns RAD_OK when the work was enqueued. n_particles, n_omega or n_angles equal
- * to 0 is valid: outputs are zeroed (accumulate = 0) or left as they are.
+ * to 0 is valid: outputs are zeroed (accumulate = 0) or left as they are. RAD_EINVAL when
+ * n_omega or n_angles exceeds 2^31, or when the call would split into more than about 2^31
+ * work items (RAD_FP64_DF takes one direction per item: at most about 2^31 directions per 256
+ * photon energies).
  * Scratch memory is allocated by the library on first use of a shape and reused
  * (see rad_release). Thread-safe; concurrent calls on different streams are allowed.
  */

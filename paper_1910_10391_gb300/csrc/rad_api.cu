@@ -159,6 +159,9 @@ int configure(rad_plan p, const Choice &c) {
     }
   }
   p->n_items = tiles * p->n_chunks;
+  // the kernels take work items from a 32-bit counter that every resident block advances once
+  // past the last item
+  if (p->n_items > static_cast<int64_t>(INT32_MAX) - resident) return RAD_EINVAL;
   sh.grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(p->n_items, resident)));
   p->shape = sh;
   p->choice = c;
